@@ -1,0 +1,219 @@
+"""CPU oracle for predicted composite distance fields (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package.  The
+product (``paper_2201_05058_gb300``) never imports it and shares no code with
+it; the two meet only through the seeded inputs of ``scenes.py``.
+
+The arithmetic lives in ``oracle.c`` (plain single-threaded C, see its header
+for the definitions it follows); this module compiles it with gcc on first use
+and exposes numpy-friendly wrappers.  A few definitions are also written here
+in numpy where a plain array expression states them directly.
+
+Paper passages followed (Finean et al., arXiv 2201.05058):
+  * Sec. 6: the composite field is a per-voxel ``min`` of the environment field
+    and the field of each dynamic obstacle at its predicted position; the
+    human primitive is a cylinder (read here as a capsule).
+  * Sec. 7, hinge-loss obstacle factor (GPMP2 form): cost ``eps - d`` when the
+    distance ``d`` is within ``eps``, else 0; the sphere radius is added to eps.
+  * Sec. 8: obstacle factor i reads composite field ``min(i, n)``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+INF32 = 2147483647
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_build/liboracle.so (plain -O2, no fast-math,
+    no FMA contraction, so the fp32 float field is IEEE on every host)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            i32, i64, f32, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+            lib.or_capsule_inside.argtypes = [i64, i64, i64, P]
+            lib.or_capsule_inside.restype = ctypes.c_int
+            lib.or_capsule_occupancy.argtypes = [ctypes.c_int] * 4 + [P, P]
+            lib.or_edt_at.argtypes = [ctypes.c_int] * 3 + [P] + [ctypes.c_int] * 3
+            lib.or_edt_at.restype = i32
+            lib.or_edt_brute.argtypes = [ctypes.c_int] * 3 + [P, P]
+            lib.or_edt_separable.argtypes = [ctypes.c_int] * 3 + [P, P]
+            lib.or_composite.argtypes = [sz, P, P, P]
+            lib.or_sdf_from_sq.argtypes = [sz, P, f32, P]
+            lib.or_trilinear.argtypes = [P] + [ctypes.c_int] * 3 + [P, f32, P, P, P]
+            lib.or_trilinear.restype = ctypes.c_double
+            lib.or_hinge_cost.argtypes = [P, ctypes.c_int] + [ctypes.c_int] * 3 + [P, f32, P, P, i64, f32, P, P, P]
+            lib.or_hinge_cost.restype = i64
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# --------------------------------------------------------------------------
+# capsules
+# --------------------------------------------------------------------------
+
+def capsule_inside(p, cap) -> bool:
+    """Exact int64 test: fixed-point point p inside capsule cap (7 int32)."""
+    cap = _c(cap, np.int32)
+    return bool(_load().or_capsule_inside(int(p[0]), int(p[1]), int(p[2]), _ptr(cap)))
+
+
+def capsule_occupancy(shape_zyx, caps) -> np.ndarray:
+    """uint8 [nz,ny,nx] occupancy of the voxels whose centres lie inside any capsule."""
+    nz, ny, nx = shape_zyx
+    caps = _c(np.asarray(caps).reshape(-1, 7), np.int32)
+    occ = np.zeros((nz, ny, nx), np.uint8)
+    _load().or_capsule_occupancy(nx, ny, nz, caps.shape[0], _ptr(caps), _ptr(occ))
+    return occ
+
+
+# --------------------------------------------------------------------------
+# signed squared EDT
+# --------------------------------------------------------------------------
+
+def edt_brute(occ) -> np.ndarray:
+    """Signed squared EDT by its definition (O(V * |opposite set|))."""
+    occ = _c(occ, np.uint8)
+    nz, ny, nx = occ.shape
+    S = np.empty(occ.shape, np.int32)
+    _load().or_edt_brute(nx, ny, nz, _ptr(occ), _ptr(S))
+    return S
+
+
+def edt_at(occ, i, j, k) -> int:
+    """Signed squared EDT at voxel (i, j, k) by its definition (O(V))."""
+    occ = _c(occ, np.uint8)
+    nz, ny, nx = occ.shape
+    return int(_load().or_edt_at(nx, ny, nz, _ptr(occ), int(i), int(j), int(k)))
+
+
+def edt(occ) -> np.ndarray:
+    """Signed squared EDT by the separable lower-envelope algorithm."""
+    occ = _c(occ, np.uint8)
+    nz, ny, nx = occ.shape
+    S = np.empty(occ.shape, np.int32)
+    _load().or_edt_separable(nx, ny, nz, _ptr(occ), _ptr(S))
+    return S
+
+
+def sdf_from_sq(S, vox: float) -> np.ndarray:
+    """float32 field sign(S)*sqrtf(|S|)*vox, +/-INT32_MAX -> +/-inf."""
+    S = _c(S, np.int32)
+    out = np.empty(S.shape, np.float32)
+    _load().or_sdf_from_sq(S.size, _ptr(S), ctypes.c_float(vox), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# composite (Sec. 6) and the per-timestep fields
+# --------------------------------------------------------------------------
+
+def composite(S_static, S_dyn) -> np.ndarray:
+    a = _c(S_static, np.int32)
+    b = _c(S_dyn, np.int32)
+    assert a.shape == b.shape
+    out = np.empty(a.shape, np.int32)
+    _load().or_composite(a.size, _ptr(a), _ptr(b), _ptr(out))
+    return out
+
+
+def dynamic_field(shape_zyx, caps_t) -> np.ndarray:
+    """Signed squared EDT of the capsule-only occupancy at one time."""
+    return edt(capsule_occupancy(shape_zyx, caps_t))
+
+
+def predicted_composite(S_static, caps) -> np.ndarray:
+    """comp[t] = min(S_static, S_dyn[t]) for caps [T][H][7]."""
+    caps = np.asarray(caps, np.int32)
+    T = caps.shape[0]
+    out = np.empty((T,) + S_static.shape, np.int32)
+    for t in range(T):
+        out[t] = composite(S_static, dynamic_field(S_static.shape, caps[t]))
+    return out
+
+
+def from_scratch(occ, caps) -> np.ndarray:
+    """S_t = signed EDT of (occ OR capsules at t), recomputed for every t."""
+    caps = np.asarray(caps, np.int32)
+    T = caps.shape[0]
+    out = np.empty((T,) + occ.shape, np.int32)
+    for t in range(T):
+        u = capsule_occupancy(occ.shape, caps[t]) | (np.asarray(occ) != 0).astype(np.uint8)
+        out[t] = edt(u)
+    return out
+
+
+# --------------------------------------------------------------------------
+# trilinear hinge cost (Sec. 7 / Sec. 8)
+# --------------------------------------------------------------------------
+
+def trilinear(field, origin, vox, p):
+    """(d, oob, grad) at one point of one [nz,ny,nx] float32 field."""
+    field = _c(field, np.float32)
+    nz, ny, nx = field.shape
+    o = _c(origin, np.float32)
+    pp = _c(p, np.float32)
+    oob = ctypes.c_int(0)
+    g = np.zeros(3, np.float64)
+    d = _load().or_trilinear(_ptr(field), nx, ny, nz, _ptr(o), ctypes.c_float(vox), _ptr(pp),
+                             ctypes.byref(oob), _ptr(g))
+    return d, bool(oob.value), g
+
+
+def hinge_cost(sdf, origin, vox, spheres, tidx, eps, need_grad=False):
+    """h[N] (float64), n_oob and optionally (grad_c [N,3], grad_r [N]).
+
+    sdf is float32 [T,nz,ny,nx] (or [nz,ny,nx] for T = 1); spheres float32 [N,4];
+    tidx int32 [N]."""
+    sdf = _c(sdf, np.float32)
+    if sdf.ndim == 3:
+        sdf = sdf[None]
+    T, nz, ny, nx = sdf.shape
+    sph = _c(spheres, np.float32).reshape(-1, 4)
+    N = sph.shape[0]
+    ti = _c(tidx, np.int32).reshape(-1)
+    assert ti.shape[0] == N
+    o = _c(origin, np.float32)
+    h = np.empty(N, np.float64)
+    gc = np.empty((N, 3), np.float64) if need_grad else None
+    gr = np.empty(N, np.float64) if need_grad else None
+    n_oob = _load().or_hinge_cost(_ptr(sdf), T, nx, ny, nz, _ptr(o), ctypes.c_float(vox), _ptr(sph), _ptr(ti),
+                                  N, ctypes.c_float(eps), _ptr(h),
+                                  _ptr(gc) if need_grad else None, _ptr(gr) if need_grad else None)
+    if need_grad:
+        return h, int(n_oob), gc, gr
+    return h, int(n_oob)
