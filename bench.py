@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Throughput of the predicted composite distance field update on GB300.
+
+Workload: a 256^3 grid of 4 cm voxels with a static map of 60 seeded boxes and
+3 humans walking seeded 4-waypoint paths at 1.2 m/s, predicted over T = 20
+steps of 0.1 s as capsules (r = 0.25 m, h = 1.8 m).  One step = the static
+signed EDT of the map plus the T composite fields (int32 squared distances and
+fp32 metres), i.e. the field update of one perception cycle.  The metric is
+T * 256^3 voxels per step / step time, in Gvox/s.
+
+Printed as one JSON line (rank 0).  Beside the main number it carries the
+from-scratch comparator (full EDT per t), the hinge-cost query rate on the
+trajectory-sphere workload, the roofline of the dominant kernel, the
+end-to-end rate through the public API with host buffers, the CPU oracle
+baseline and the SM clocks seen while timing.
+
+``--impl reference`` times the CPU oracle (the plain C implementation under
+oracle/) on the host cores instead, on bounded samples of the same workload.
+
+Multi-GPU (torchrun): every rank updates its own independent environment
+(seed + rank); there is no data-path collective; the timing is the max over
+ranks and the value counts the voxels of all ranks ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "Composite SDF Gvox/s at 256^3 x T=20 (static EDT + T composite fields per step)"
+WORKLOAD = "predicted composite: 256^3 grid, 4 cm voxels, 60 boxes, 3 walking humans, T=20 x 0.1 s"
+N_VOX, T_STEPS, H_HUMANS = 256, 20, 3
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Each rank owns an independent environment (weak scaling, no exchange)."""
+    return seed + 1000 * rank
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel source is unchanged since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2201_05058_gb300", "csrc", d["source"])
+    if not os.path.exists(src) or source_sha(src) != d["source_sha"]:
+        return None
+    return float(d["dram_bytes_per_launch"])
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline of the native arm; the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(sc, n_fields: int, z_depth: int):
+    """Time the oracle on the static field plus n_fields composite fields of the
+    scene cropped to its first z_depth slices.  Returns (seconds_static,
+    seconds_per_field, voxels_per_field)."""
+    import oracle
+    occ = np.ascontiguousarray(sc["occ"][:z_depth])
+    caps = sc["caps"]
+    t0 = time.perf_counter()
+    S_static = oracle.edt(occ)
+    t1 = time.perf_counter()
+    for t in range(n_fields):
+        oracle.composite(S_static, oracle.dynamic_field(occ.shape, caps[t % caps.shape[0]]))
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / max(n_fields, 1), occ.size
+
+
+def cpu_baseline(sc):
+    n_fields = 6
+    ts, tf, vpf = oracle_sample(sc, n_fields, sc["grid"].nz)
+    step_s = ts + T_STEPS * tf  # one update: static + T fields
+    return {"value": T_STEPS * vpf / step_s / 1e9, "unit": "Gvox/s", "cores": 1, "kind": "oracle",
+            "sample": f"single-threaded C oracle (separable EDT): static field + {n_fields} of {T_STEPS} "
+                      f"composite fields of the 256^3 scene, scaled to one static + {T_STEPS}-field update "
+                      f"({ts:.2f} s static, {tf:.2f} s per field)"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    sc = scenes.scene_composite(seed=rank_seed(args.seed, 0), T=T_STEPS, H=H_HUMANS)
+    # size each step so that warmup + steps stay within about three minutes
+    probe_s, probe_f, _ = oracle_sample(sc, 1, 64)
+    per_vox = (probe_s / T_STEPS + probe_f) / (64 * N_VOX * N_VOX)
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    depth = int(max(8, min(N_VOX, budget / (per_vox * N_VOX * N_VOX))))
+    for _ in range(args.warmup):
+        oracle_sample(sc, 1, depth)
+    total, vox = 0.0, 0
+    for k in range(args.steps):
+        ts, tf, v = oracle_sample(sc, 1, depth)
+        total += ts / T_STEPS + tf  # one field plus its share of the static field
+        vox += v
+    value = vox / total / 1e9
+    sample = (f"per step: one composite field + 1/{T_STEPS} of the static field of the 256^3 scene "
+              f"cropped to {depth} z-slices, single-threaded C oracle (separable EDT)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gvox/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [N_VOX] * 3, "T": T_STEPS,
+                                            "H": H_HUMANS, "sample_depth": depth},
+            "cpu_baseline": {"value": value, "unit": "Gvox/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Gvox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+
+def run_native(args):
+    import torch
+
+    import paper_2201_05058_gb300 as pcdf
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    sc = scenes.scene_composite(seed=rank_seed(args.seed, rank), T=T_STEPS, H=H_HUMANS)
+    grid, caps = sc["grid"], sc["caps"]
+    V = grid.nvox
+    T = caps.shape[0]
+    occ = torch.from_numpy(sc["occ"]).to(dev)
+    static_sq = torch.empty(grid.shape, dtype=torch.int32, device=dev)
+    static_sdf = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+    comp_sq = torch.empty((T,) + grid.shape, dtype=torch.int32, device=dev)
+    comp_sdf = torch.empty((T,) + grid.shape, dtype=torch.float32, device=dev)
+    ws = pcdf.composite_workspace(grid, caps, dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(z_events=None):
+        pcdf.build_static_sdf(occ, grid, out_sq=static_sq, out_sdf=static_sdf)
+        pcdf.composite_prepare(grid, caps, ws)
+        if z_events:
+            z_events[0].record(stream)
+        pcdf.composite_finish(static_sq, grid, caps, ws, comp_sq, comp_sdf)
+        if z_events:
+            z_events[1].record(stream)
+
+    def timed(fn, k, extra_events=False):
+        """k steps, L2 flushed before each; per-step CUDA events on the launch stream."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        zev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)] \
+            if extra_events else None
+        for i in range(k):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            fn(zev[i] if zev else None)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        zms = [a.elapsed_time(b) for a, b in zev] if zev else None
+        return ms, zms
+
+    # warm-up
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    gpu_uuid = None
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_uuid = str(local_rank)
+    sampler = ClockSampler(gpu_uuid)
+    sampler.start()
+    time.sleep(0.2)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms, z_ms = timed(step, args.steps, extra_events=True)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps * T * V / (total_ms * 1e-3) / 1e9
+
+    # composite stage alone and the from-scratch comparator (same inputs)
+    def comp_only(_=None):
+        pcdf.composite_prepare(grid, caps, ws)
+        pcdf.composite_finish(static_sq, grid, caps, ws, comp_sq, comp_sdf)
+
+    ws_scr = None
+
+    def scratch(_=None):
+        pcdf.build_from_scratch(occ, grid, caps, out_sq=comp_sq, out_sdf=comp_sdf)
+
+    k_side = max(3, min(args.steps, 10))
+    comp_ms, _ = timed(comp_only, k_side)
+    scratch(None)
+    scr_ms, _ = timed(scratch, k_side)
+    comp_avg = float(np.mean(comp_ms))
+    scr_avg = float(np.mean(scr_ms))
+
+    # roofline of the dominant kernel: the fused z pass (reads static_sq and
+    # the dynamic slab intermediate, writes T int32 + T fp32 fields)
+    S = int(ws.numel() // (T * grid.nx * grid.ny * 6)) if ws.numel() > 256 else 0
+    z_bytes = 4 * V + 4 * T * S * grid.nx * grid.ny + 8 * T * V
+    z_avg_ms = float(np.mean(z_ms))
+    peak, peak_kind = measured_peaks()
+    achieved = z_bytes / (z_avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic("k_composite_z")
+    roofline = {"bound": "hbm", "kernel": "k_composite_z", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+                "algorithmic_bytes": z_bytes, "kernel_ms": z_avg_ms,
+                "kernel_share_of_step": z_avg_ms / ms_per_step}
+
+    # hinge-cost queries: 256 trajectories x 40 states x 30 spheres on T = 20
+    # composite fields of a 64^3 scene
+    qs = scenes.scene_small_walking(seed=rank_seed(args.seed, rank) + 4, T=20, H=1)
+    qgrid = qs["grid"]
+    q_static, _ = pcdf.build_static_sdf(torch.from_numpy(qs["occ"]).to(dev), qgrid)
+    _, q_sdf = pcdf.build_predicted_composite(q_static, qgrid, qs["caps"], want_sq=False)
+    sph, tidx = scenes.spheres_along_paths(qgrid, 256, 40, 30, np.random.default_rng(44), T=20)
+    sph_d = torch.from_numpy(sph).to(dev)
+    tid_d = torch.from_numpy(tidx).to(dev)
+    g_h = torch.ones(tidx.shape, dtype=torch.float32, device=dev)
+    nq = tidx.size
+    for _ in range(3):
+        pcdf.query_cost(q_sdf, qgrid, sph_d, tid_d, 0.2)
+        pcdf.query_cost_backward(q_sdf, qgrid, sph_d, tid_d, 0.2, g_h)
+    fwd_ms, _ = timed(lambda _=None: pcdf.query_cost(q_sdf, qgrid, sph_d, tid_d, 0.2), 20)
+    bwd_ms, _ = timed(lambda _=None: pcdf.query_cost_backward(q_sdf, qgrid, sph_d, tid_d, 0.2, g_h), 20)
+    query = {"workload": "256 trajectories x 40 states x 30 spheres on T=20 composite fields of 64^3 (5 cm)",
+             "spheres": nq, "fwd_queries_per_s": nq / (np.mean(fwd_ms) * 1e-3),
+             "bwd_queries_per_s": nq / (np.mean(bwd_ms) * 1e-3), "fields_l2_resident": True}
+
+    # end to end through the public API with host buffers: pinned occupancy in,
+    # capsules from host memory, composite float fields back to pinned memory
+    occ_h = torch.from_numpy(sc["occ"]).pin_memory()
+    out_h = torch.empty((T,) + grid.shape, dtype=torch.float32).pin_memory()
+    occ_d = torch.empty_like(occ)
+
+    def e2e_step(_=None):
+        occ_d.copy_(occ_h, non_blocking=True)
+        pcdf.build_static_sdf(occ_d, grid, out_sq=static_sq, out_sdf=static_sdf)
+        pcdf.build_predicted_composite(static_sq, grid, caps, out_sq=comp_sq, out_sdf=comp_sdf)
+        out_h.copy_(comp_sdf, non_blocking=True)
+
+    e2e_step()
+    k_e2e = max(3, min(args.steps, 10))
+    e2e_ms, _ = timed(e2e_step, k_e2e)
+    e2e_total = float(sum(e2e_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": world * k_e2e * T * V / (e2e_total * 1e-3) / 1e9, "unit": "Gvox/s",
+           "h2d_bytes_per_step": int(occ_h.numel() + caps.nbytes), "d2h_bytes_per_step": int(out_h.numel() * 4),
+           "ms_per_step": e2e_total / k_e2e,
+           "what": "H2D occupancy (pinned) + capsules, static + composite, D2H of the T float fields (pinned)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc)
+
+    launches_per_step = 6  # static: row, y, z; composite: row, y, fused z
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gvox/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [grid.nx, grid.ny, grid.nz], "vox_m": grid.vox, "T": T,
+                       "H": H_HUMANS, "boxes": 60, "slab_slices": S,
+                       "outputs": "int32 squared + fp32 metres, all T fields",
+                       "l2": "flushed before every timed step (512 MB write)", "parallelism": f"replicas{world}"},
+            "composite_only": {"ms": comp_avg, "gvox_s": T * V / (comp_avg * 1e-3) / 1e9},
+            "from_scratch": {"ms": scr_avg, "gvox_s": T * V / (scr_avg * 1e-3) / 1e9,
+                             "composite_speedup": scr_avg / comp_avg},
+            "query": query, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

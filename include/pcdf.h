@@ -1,0 +1,178 @@
+/*
+ * pcdf.h -- C ABI of the predicted composite distance field library (GB300,
+ * sm_103a).
+ *
+ * The library builds the distance fields of Finean et al., "Motion Planning
+ * in Dynamic Environments Using Context-Aware Human Trajectory Prediction"
+ * (arXiv 2201.05058):
+ *   - Sec. 6: a distance field of the static environment, a field per dynamic
+ *     obstacle (the human primitive, a cylinder in the paper, a capsule here)
+ *     at each predicted position, and the composite field taken as their
+ *     per-voxel minimum;
+ *   - Sec. 8: a sequence of n composite fields, one per predicted timestep,
+ *     where obstacle factor i reads field min(i, n);
+ *   - Sec. 7: the GPMP2 hinge-loss obstacle cost on the distance field,
+ *     evaluated here at robot body-sphere centres by trilinear interpolation,
+ *     and its gradient with respect to the centres.
+ *
+ * Conventions for every call
+ *   Grid: int32 nx, ny, nz in [1, PCDF_MAX_DIM]; voxel edge vox (metres, finite,
+ *   > 0); origin = world position of the grid corner.  Arrays are [nz][ny][nx],
+ *   x fastest.  Voxel (i, j, k) has its centre at
+ *   origin + (i + 1/2, j + 1/2, k + 1/2) * vox.
+ *
+ *   Signed squared EDT S (int32, voxel-index units): for a free voxel, the
+ *   minimum of |v - u|^2 over occupied in-grid voxels u; for an occupied voxel,
+ *   minus the minimum over free in-grid voxels.  An empty opposite set gives
+ *   +PCDF_INF / -PCDF_INF.  S is never 0.  Cells outside the grid are neither
+ *   occupied nor free.
+ *
+ *   Float field (fp32, metres): sign(S) * sqrtf((float)|S|) * vox with an IEEE
+ *   round-to-nearest square root and product; +/-PCDF_INF gives +/-inf.
+ *
+ *   Capsule: 7 int32 (ax, ay, az, bx, by, bz, r) in 1/16-voxel fixed point
+ *   measured from the grid corner, so the centre of voxel (i, j, k) is
+ *   16 * (i, j, k) + 8.  A voxel belongs to the capsule iff its centre lies in
+ *   the closed set of points within r of segment a-b (exact integer test).
+ *   Coordinates must lie in [PCDF_CAP_MIN, PCDF_CAP_MAX] and 0 <= r <=
+ *   PCDF_CAP_MAX_R.
+ *
+ *   Memory: device pointers are owned by the caller; the library keeps none
+ *   past the call and allocates nothing.  Calls that need scratch take a
+ *   caller-owned device workspace and report its size through the matching
+ *   *_workspace_bytes query.  Pointers marked "host" are read during the call
+ *   only.
+ *
+ *   Asynchrony: every device call is enqueued on `stream` (a cudaStream_t; NULL
+ *   is the legacy default stream) and returns without waiting for the GPU.
+ *   Host-side argument checks happen before anything is enqueued.
+ *
+ *   Errors: 0 on success, else a negative PCDF_E* code; pcdf_last_error()
+ *   returns a message for the calling thread's last failure.
+ */
+#ifndef PCDF_H
+#define PCDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PCDF_OK 0
+#define PCDF_EINVAL (-1)   /* bad size, pointer, alignment or capsule range */
+#define PCDF_ENOMEM (-2)   /* workspace smaller than the size query returned */
+#define PCDF_ECUDA (-3)    /* a CUDA launch or runtime call failed */
+
+#define PCDF_INF 2147483647
+#define PCDF_MAX_DIM 512
+#define PCDF_MAX_T 1024
+#define PCDF_MAX_H 64
+#define PCDF_CAP_MIN (-8192)
+#define PCDF_CAP_MAX 16384
+#define PCDF_CAP_MAX_R 8192
+
+typedef struct pcdf_grid {
+    int32_t nx, ny, nz;
+    float vox;
+    float origin[3];
+} pcdf_grid;
+
+/* Message describing the calling thread's most recent failed call ("" if none). */
+const char *pcdf_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int pcdf_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Static environment field (Sec. 6: the environment's distance field, computed
+ * once or maintained).
+ *
+ * occ        device uint8 [nz][ny][nx], nonzero = occupied.
+ * static_sq  device int32 [nz][ny][nx], out: signed squared EDT S.
+ * static_sdf device fp32 [nz][ny][nx] or NULL, out: float field.
+ * workspace  device, >= pcdf_static_workspace_bytes() bytes, 256-byte aligned.
+ * ------------------------------------------------------------------------- */
+int pcdf_static_workspace_bytes(const pcdf_grid *grid, size_t *bytes);
+int pcdf_build_static_sdf(const pcdf_grid *grid, const uint8_t *occ, int32_t *static_sq, float *static_sdf,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Predicted composite fields (Sec. 6 composition; Sec. 8 sequence of n fields).
+ *
+ * For t = 0..T-1:  comp[t] = min(S_static, S_dyn[t])  per voxel, where S_dyn[t]
+ * is the signed squared EDT of the voxels inside any of the H capsules at t.
+ *
+ * static_sq  device int32 [nz][ny][nx] (from pcdf_build_static_sdf).
+ * caps       HOST int32 [T][H][7] capsules (see conventions); may be NULL iff
+ *            H == 0 (then every comp[t] equals the static field).
+ * comp_sq    device int32 [T][nz][ny][nx] or NULL.
+ * comp_sdf   device fp32 [T][nz][ny][nx] or NULL (at least one output non-NULL).
+ * workspace  device, >= pcdf_composite_workspace_bytes(grid, T, H, caps).
+ * 1 <= T <= PCDF_MAX_T, 0 <= H <= PCDF_MAX_H.
+ * ------------------------------------------------------------------------- */
+int pcdf_composite_workspace_bytes(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps,
+                                   size_t *bytes);
+int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_sq, int32_t T, int32_t H,
+                                   const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
+                                   size_t workspace_bytes, void *stream);
+
+/* The two stages of pcdf_build_predicted_composite, for callers that want to
+ * overlap or time them separately (same arguments and workspace; the
+ * workspace carries the dynamic intermediate from the first to the second):
+ *   prepare: the capsule row pass and y pass over the z-slab the capsules touch;
+ *   finish:  the fused z pass, composite min and float epilogue for every t. */
+int pcdf_composite_prepare(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, void *workspace,
+                           size_t workspace_bytes, void *stream);
+int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, int32_t T, int32_t H,
+                          const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * From-scratch comparator (Sec. 6 benchmark: a full exact EDT per subsequent
+ * field instead of the composition).
+ *
+ * For t = 0..T-1: sq[t] = signed squared EDT of (occ OR capsules at t).
+ * Arguments as above; occ is the device occupancy of the static map.
+ * ------------------------------------------------------------------------- */
+int pcdf_scratch_workspace_bytes(const pcdf_grid *grid, int32_t T, int32_t H, size_t *bytes);
+int pcdf_build_from_scratch(const pcdf_grid *grid, const uint8_t *occ, int32_t T, int32_t H, const int32_t *caps,
+                            int32_t *sq, float *sdf, void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Hinge obstacle cost at body spheres (Sec. 7 hinge form, GPMP2 obstacle
+ * factor; Sec. 8 field assignment).
+ *
+ * For sphere q with centre c and radius r (spheres device fp32 [N][4],
+ * 16-byte aligned) and time index s = tidx[q] (device int32 [N]):
+ *   t = clamp(s, 0, T-1);
+ *   per axis u = (c - origin) / vox - 1/2 in fp32, clamped to [0, n-1]
+ *   (NaN -> 0), lower corner i0 = min(floor(u), n-2) (0 if n == 1);
+ *   d = trilinear interpolation of sdf[t] (device fp32 [T][nz][ny][nx]), lerped
+ *   along x, then y, then z; any -inf corner gives d = -inf, else any +inf
+ *   corner gives d = +inf;
+ *   h[q] = max(0, eps + r - d)  (device fp32 [N], out).
+ * n_oob: device int32 or NULL; if given, the number of spheres clamped on some
+ * axis is ADDED to *n_oob (the caller zeroes it).
+ * N may be 0 (nothing is launched).
+ * ------------------------------------------------------------------------- */
+int pcdf_query_cost(const pcdf_grid *grid, const float *sdf, int32_t T, const float *spheres, const int32_t *tidx,
+                    int64_t N, float eps, float *h, int32_t *n_oob, void *stream);
+
+/* Backward of pcdf_query_cost: with the same inputs and upstream gradient
+ * grad_h (device fp32 [N]),
+ *   grad_c[q] = -grad_h[q] * grad_c d(c)   where h > 0 and d is finite, else 0
+ *   (device fp32 [N][3], out; the gradient of d is the analytic derivative of
+ *   the trilinear interpolant divided by vox, zero along clamped or
+ *   single-voxel axes);
+ *   grad_r[q] = grad_h[q] * [h > 0 and d finite]  (device fp32 [N] or NULL). */
+int pcdf_query_cost_backward(const pcdf_grid *grid, const float *sdf, int32_t T, const float *spheres,
+                             const int32_t *tidx, int64_t N, float eps, const float *grad_h, float *grad_c,
+                             float *grad_r, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCDF_H */

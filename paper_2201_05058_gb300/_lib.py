@@ -1,0 +1,80 @@
+"""ctypes loader for libpcdf.so (the C ABI of include/pcdf.h).
+
+The library is built in-tree by ``build.build_library()``.  There is no
+fallback: if the shared library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PcdfGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("vox", ctypes.c_float), ("origin", ctypes.c_float * 3)]
+
+
+EXPORTS = (
+    "pcdf_last_error", "pcdf_version",
+    "pcdf_static_workspace_bytes", "pcdf_build_static_sdf",
+    "pcdf_composite_workspace_bytes", "pcdf_build_predicted_composite",
+    "pcdf_composite_prepare", "pcdf_composite_finish",
+    "pcdf_scratch_workspace_bytes", "pcdf_build_from_scratch",
+    "pcdf_query_cost", "pcdf_query_cost_backward",
+)
+
+
+def _declare(lib):
+    P, I32, I64, F32, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+    G = ctypes.POINTER(PcdfGrid)
+    SZP = ctypes.POINTER(ctypes.c_size_t)
+    lib.pcdf_last_error.restype = ctypes.c_char_p
+    lib.pcdf_last_error.argtypes = []
+    lib.pcdf_version.restype = ctypes.c_int
+    sig = {
+        "pcdf_static_workspace_bytes": [G, SZP],
+        "pcdf_build_static_sdf": [G, P, P, P, P, SZ, P],
+        "pcdf_composite_workspace_bytes": [G, I32, I32, P, SZP],
+        "pcdf_build_predicted_composite": [G, P, I32, I32, P, P, P, P, SZ, P],
+        "pcdf_composite_prepare": [G, I32, I32, P, P, SZ, P],
+        "pcdf_composite_finish": [G, P, I32, I32, P, P, P, P, SZ, P],
+        "pcdf_scratch_workspace_bytes": [G, I32, I32, SZP],
+        "pcdf_build_from_scratch": [G, P, I32, I32, P, P, P, P, SZ, P],
+        "pcdf_query_cost": [G, P, I32, P, P, I64, F32, P, P, P],
+        "pcdf_query_cost_backward": [G, P, I32, P, P, I64, F32, P, P, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpcdf.so (building it first if allowed and needed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing and not _build.up_to_date():
+                _build.build_library()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"libpcdf is not built ({_build.LIB} missing); run build_library()")
+            lib = ctypes.CDLL(_build.LIB)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def check(rc: int, what: str):
+    if rc != 0:
+        msg = load().pcdf_last_error().decode(errors="replace")
+        raise RuntimeError(f"{what} failed ({rc}): {msg}")

@@ -1,0 +1,295 @@
+"""Python binding of the C ABI (argument marshalling only).
+
+Every function here checks tensor placement, dtype and shape, takes the
+workspace from PyTorch's caching allocator, passes raw pointers and the
+current CUDA stream to ``libpcdf.so`` and raises if the library reports an
+error.  No step of the computation runs in Python or PyTorch.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+@dataclass(frozen=True)
+class Grid:
+    """Voxel grid: nx, ny, nz voxels of edge ``vox`` metres, corner at ``origin``."""
+    nx: int
+    ny: int
+    nz: int
+    vox: float
+    origin: tuple = (0.0, 0.0, 0.0)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+def _cgrid(g) -> _lib.PcdfGrid:
+    o = tuple(float(v) for v in getattr(g, "origin", (0.0, 0.0, 0.0)))
+    return _lib.PcdfGrid(int(g.nx), int(g.ny), int(g.nz), float(g.vox), (ctypes.c_float * 3)(*o))
+
+
+def _shape(g):
+    return (int(g.nz), int(g.ny), int(g.nx))
+
+
+def _stream(dev: torch.device) -> int:
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _need(t: torch.Tensor, name: str, dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _caps_host(caps):
+    """int32 [T][H][7] capsules as a contiguous host array (or None for H = 0)."""
+    if isinstance(caps, torch.Tensor):
+        caps = caps.detach().cpu().numpy()
+    caps = np.ascontiguousarray(np.asarray(caps), dtype=np.int32)
+    if caps.ndim != 3 or caps.shape[2] != 7:
+        raise ValueError(f"caps must be [T][H][7], got {caps.shape}")
+    return caps
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _workspace(nbytes: int, dev) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+
+
+def capsule_fixed(a_m, b_m, r_m, grid) -> np.ndarray:
+    """Capsule(s) from metres to the library's 1/16-voxel fixed point.
+
+    a_m, b_m: [..., 3] segment end points (world metres); r_m: [...] radius.
+    Returns int32 [..., 7] (round half to even of (x - origin) / vox * 16)."""
+    o = np.asarray(getattr(grid, "origin", (0.0, 0.0, 0.0)), np.float64)
+    a = np.rint((np.asarray(a_m, np.float64) - o) / grid.vox * 16.0)
+    b = np.rint((np.asarray(b_m, np.float64) - o) / grid.vox * 16.0)
+    r = np.rint(np.asarray(r_m, np.float64) / grid.vox * 16.0)[..., None]
+    return np.concatenate([a, b, r], axis=-1).astype(np.int32)
+
+
+# ---------------------------------------------------------------------------
+# fields
+# ---------------------------------------------------------------------------
+
+def build_static_sdf(occ: torch.Tensor, grid, want_sdf: bool = True, out_sq=None, out_sdf=None):
+    """Signed squared EDT (int32) and float field (fp32, metres) of a static map.
+
+    occ: CUDA uint8 [nz, ny, nx], nonzero = occupied."""
+    shp = _shape(grid)
+    _need(occ, "occ", torch.uint8, shp)
+    dev = occ.device
+    lib = _lib.load()
+    g = _cgrid(grid)
+    nbytes = ctypes.c_size_t(0)
+    _lib.check(lib.pcdf_static_workspace_bytes(ctypes.byref(g), ctypes.byref(nbytes)), "static workspace")
+    sq = out_sq if out_sq is not None else torch.empty(shp, dtype=torch.int32, device=dev)
+    _need(sq, "static_sq", torch.int32, shp)
+    sdf = None
+    if want_sdf:
+        sdf = out_sdf if out_sdf is not None else torch.empty(shp, dtype=torch.float32, device=dev)
+        _need(sdf, "static_sdf", torch.float32, shp)
+    ws = _workspace(nbytes.value, dev)
+    _lib.check(lib.pcdf_build_static_sdf(ctypes.byref(g), _ptr(occ), _ptr(sq), _ptr(sdf), _ptr(ws), ws.numel(),
+                                         ctypes.c_void_p(_stream(dev))), "pcdf_build_static_sdf")
+    return sq, sdf
+
+
+def build_predicted_composite(static_sq: torch.Tensor, grid, caps, want_sq: bool = True, want_sdf: bool = True,
+                              out_sq=None, out_sdf=None):
+    """Composite fields comp[t] = min(static, capsules at t) for t < T (Sec. 6, 8).
+
+    static_sq: CUDA int32 [nz, ny, nx]; caps: host int32 [T][H][7] fixed point.
+    Returns (comp_sq int32 [T, nz, ny, nx] or None, comp_sdf fp32 or None)."""
+    shp = _shape(grid)
+    _need(static_sq, "static_sq", torch.int32, shp)
+    caps = _caps_host(caps)
+    T, H = int(caps.shape[0]), int(caps.shape[1])
+    dev = static_sq.device
+    lib = _lib.load()
+    g = _cgrid(grid)
+    cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+    nbytes = ctypes.c_size_t(0)
+    _lib.check(lib.pcdf_composite_workspace_bytes(ctypes.byref(g), T, H, cp, ctypes.byref(nbytes)),
+               "composite workspace")
+    sq = sdf = None
+    if want_sq:
+        sq = out_sq if out_sq is not None else torch.empty((T,) + shp, dtype=torch.int32, device=dev)
+        _need(sq, "comp_sq", torch.int32, (T,) + shp)
+    if want_sdf:
+        sdf = out_sdf if out_sdf is not None else torch.empty((T,) + shp, dtype=torch.float32, device=dev)
+        _need(sdf, "comp_sdf", torch.float32, (T,) + shp)
+    ws = _workspace(nbytes.value, dev)
+    _lib.check(lib.pcdf_build_predicted_composite(ctypes.byref(g), _ptr(static_sq), T, H, cp, _ptr(sq), _ptr(sdf),
+                                                  _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(dev))),
+               "pcdf_build_predicted_composite")
+    return sq, sdf
+
+
+def composite_workspace(grid, caps, device) -> torch.Tensor:
+    """A device workspace large enough for build_predicted_composite / the stages."""
+    caps = _caps_host(caps)
+    T, H = int(caps.shape[0]), int(caps.shape[1])
+    g = _cgrid(grid)
+    cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+    nbytes = ctypes.c_size_t(0)
+    _lib.check(_lib.load().pcdf_composite_workspace_bytes(ctypes.byref(g), T, H, cp, ctypes.byref(nbytes)),
+               "composite workspace")
+    return _workspace(nbytes.value, device)
+
+
+def composite_prepare(grid, caps, workspace: torch.Tensor):
+    """First stage of the composite: capsule row pass and y pass into workspace."""
+    caps = _caps_host(caps)
+    T, H = int(caps.shape[0]), int(caps.shape[1])
+    _need(workspace, "workspace", torch.uint8)
+    g = _cgrid(grid)
+    cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+    _lib.check(_lib.load().pcdf_composite_prepare(ctypes.byref(g), T, H, cp, _ptr(workspace), workspace.numel(),
+                                                  ctypes.c_void_p(_stream(workspace.device))),
+               "pcdf_composite_prepare")
+
+
+def composite_finish(static_sq, grid, caps, workspace: torch.Tensor, comp_sq=None, comp_sdf=None):
+    """Second stage: fused z pass + composite min + float epilogue into the given outputs."""
+    shp = _shape(grid)
+    caps = _caps_host(caps)
+    T, H = int(caps.shape[0]), int(caps.shape[1])
+    _need(static_sq, "static_sq", torch.int32, shp)
+    _need(workspace, "workspace", torch.uint8)
+    if comp_sq is not None:
+        _need(comp_sq, "comp_sq", torch.int32, (T,) + shp)
+    if comp_sdf is not None:
+        _need(comp_sdf, "comp_sdf", torch.float32, (T,) + shp)
+    g = _cgrid(grid)
+    cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+    _lib.check(_lib.load().pcdf_composite_finish(ctypes.byref(g), _ptr(static_sq), T, H, cp, _ptr(comp_sq),
+                                                 _ptr(comp_sdf), _ptr(workspace), workspace.numel(),
+                                                 ctypes.c_void_p(_stream(static_sq.device))),
+               "pcdf_composite_finish")
+
+
+def build_from_scratch(occ: torch.Tensor, grid, caps, want_sdf: bool = True, out_sq=None, out_sdf=None):
+    """The comparator: full signed EDT of (occ OR capsules at t) for every t."""
+    shp = _shape(grid)
+    _need(occ, "occ", torch.uint8, shp)
+    caps = _caps_host(caps)
+    T, H = int(caps.shape[0]), int(caps.shape[1])
+    dev = occ.device
+    lib = _lib.load()
+    g = _cgrid(grid)
+    cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+    nbytes = ctypes.c_size_t(0)
+    _lib.check(lib.pcdf_scratch_workspace_bytes(ctypes.byref(g), T, H, ctypes.byref(nbytes)), "scratch workspace")
+    sq = out_sq if out_sq is not None else torch.empty((T,) + shp, dtype=torch.int32, device=dev)
+    _need(sq, "sq", torch.int32, (T,) + shp)
+    sdf = None
+    if want_sdf:
+        sdf = out_sdf if out_sdf is not None else torch.empty((T,) + shp, dtype=torch.float32, device=dev)
+        _need(sdf, "sdf", torch.float32, (T,) + shp)
+    ws = _workspace(nbytes.value, dev)
+    _lib.check(lib.pcdf_build_from_scratch(ctypes.byref(g), _ptr(occ), T, H, cp, _ptr(sq), _ptr(sdf), _ptr(ws),
+                                           ws.numel(), ctypes.c_void_p(_stream(dev))), "pcdf_build_from_scratch")
+    return sq, sdf
+
+
+# ---------------------------------------------------------------------------
+# hinge cost (Sec. 7) and its gradient
+# ---------------------------------------------------------------------------
+
+def _query_args(sdf, grid, spheres, tidx):
+    shp = _shape(grid)
+    if sdf.dim() == 3:
+        sdf = sdf.unsqueeze(0)
+    T = int(sdf.shape[0])
+    _need(sdf, "sdf", torch.float32, (T,) + shp)
+    _need(spheres, "spheres", torch.float32)
+    if spheres.shape[-1] != 4:
+        raise ValueError("spheres must be [..., 4] (x, y, z, r)")
+    N = spheres.numel() // 4
+    _need(tidx, "tidx", torch.int32)
+    if tidx.numel() != N:
+        raise ValueError(f"tidx has {tidx.numel()} entries for {N} spheres")
+    return sdf, T, N
+
+
+def query_cost(sdf: torch.Tensor, grid, spheres: torch.Tensor, tidx: torch.Tensor, eps: float,
+               count_oob: bool = False):
+    """h = max(0, eps + r - trilinear(sdf[clamp(tidx)], c)) per sphere.
+
+    sdf: CUDA fp32 [T, nz, ny, nx] (or [nz, ny, nx]); spheres: CUDA fp32
+    [..., 4]; tidx: CUDA int32 [...].  Returns h shaped like tidx (and the
+    number of clamped spheres if count_oob)."""
+    sdf, T, N = _query_args(sdf, grid, spheres, tidx)
+    dev = sdf.device
+    h = torch.empty(tidx.shape, dtype=torch.float32, device=dev)
+    oob = torch.zeros(1, dtype=torch.int32, device=dev) if count_oob else None
+    g = _cgrid(grid)
+    _lib.check(_lib.load().pcdf_query_cost(ctypes.byref(g), _ptr(sdf), T, _ptr(spheres), _ptr(tidx), N,
+                                           float(eps), _ptr(h), _ptr(oob), ctypes.c_void_p(_stream(dev))),
+               "pcdf_query_cost")
+    if count_oob:
+        return h, oob
+    return h
+
+
+def query_cost_backward(sdf: torch.Tensor, grid, spheres: torch.Tensor, tidx: torch.Tensor, eps: float,
+                        grad_h: torch.Tensor, want_grad_r: bool = True):
+    """(grad_c [..., 3], grad_r [...] or None) of sum(grad_h * h)."""
+    sdf, T, N = _query_args(sdf, grid, spheres, tidx)
+    dev = sdf.device
+    _need(grad_h, "grad_h", torch.float32)
+    if grad_h.numel() != N:
+        raise ValueError("grad_h must have one entry per sphere")
+    gc = torch.empty(tuple(spheres.shape[:-1]) + (3,), dtype=torch.float32, device=dev)
+    gr = torch.empty(tidx.shape, dtype=torch.float32, device=dev) if want_grad_r else None
+    g = _cgrid(grid)
+    _lib.check(_lib.load().pcdf_query_cost_backward(ctypes.byref(g), _ptr(sdf), T, _ptr(spheres), _ptr(tidx), N,
+                                                    float(eps), _ptr(grad_h), _ptr(gc), _ptr(gr),
+                                                    ctypes.c_void_p(_stream(dev))),
+               "pcdf_query_cost_backward")
+    return gc, gr
+
+
+class HingeCost(torch.autograd.Function):
+    """Hinge obstacle cost with a hand-written backward to the sphere centres
+    (and radii).  Inputs: centres [..., 3] and radii [...] (fp32, CUDA)."""
+
+    @staticmethod
+    def forward(ctx, centres, radii, sdf, tidx, eps, grid):
+        spheres = torch.cat([centres.detach(), radii.detach().unsqueeze(-1)], dim=-1).contiguous()
+        tidx = tidx.contiguous()
+        h = query_cost(sdf, grid, spheres, tidx, eps)
+        ctx.save_for_backward(spheres, sdf, tidx)
+        ctx.eps = eps
+        ctx.grid = grid
+        return h
+
+    @staticmethod
+    def backward(ctx, grad_h):
+        spheres, sdf, tidx = ctx.saved_tensors
+        gc, gr = query_cost_backward(sdf, ctx.grid, spheres, tidx, ctx.eps, grad_h.contiguous().float(),
+                                     want_grad_r=ctx.needs_input_grad[1])
+        return gc, gr, None, None, None, None
+
+
+def hinge_cost(centres, radii, sdf, tidx, eps, grid):
+    """Differentiable hinge cost h[...] (autograd through HingeCost)."""
+    return HingeCost.apply(centres, radii, sdf, tidx, float(eps), grid)

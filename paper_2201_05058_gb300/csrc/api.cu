@@ -1,0 +1,404 @@
+// Host side of the C ABI declared in include/pcdf.h: argument checks,
+// workspace carving and the launch sequence of each entry point.  Nothing here
+// allocates device memory or synchronises the stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "pcdf_internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(PCDF_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int check_grid(const pcdf_grid *g)
+{
+    if (!g)
+        return fail(PCDF_EINVAL, "grid is NULL");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nx > PCDF_MAX_DIM || g->ny > PCDF_MAX_DIM ||
+        g->nz > PCDF_MAX_DIM)
+        return fail(PCDF_EINVAL, "grid dims %d x %d x %d outside [1, %d]", g->nx, g->ny, g->nz, PCDF_MAX_DIM);
+    if (!std::isfinite(g->vox) || !(g->vox > 0.f))
+        return fail(PCDF_EINVAL, "voxel size must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(g->origin[a]))
+            return fail(PCDF_EINVAL, "origin must be finite");
+    return PCDF_OK;
+}
+
+long long nvox(const pcdf_grid *g) { return (long long)g->nx * g->ny * g->nz; }
+
+// floor(a / b) for b > 0
+long long floordiv(long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Capsule ranges and the voxel-index bounding box of its voxel centres: a
+// centre 16 i + 8 can lie within r of the segment only if it lies within
+// [min(a, b) - r, max(a, b) + r] on every axis.
+int make_capinfo(const pcdf_grid *g, int T, int H, const int32_t *caps, std::vector<pcdf::CapInfo> &out,
+                 int *zlo, int *zhi)
+{
+    const int n[3] = {g->nx, g->ny, g->nz};
+    out.resize((size_t)T * H);
+    *zlo = n[2];
+    *zhi = -1;
+    for (long long q = 0; q < (long long)T * H; ++q) {
+        const int32_t *c = caps + 7 * q;
+        for (int a = 0; a < 6; ++a)
+            if (c[a] < PCDF_CAP_MIN || c[a] > PCDF_CAP_MAX)
+                return fail(PCDF_EINVAL, "capsule %lld coordinate %d = %d outside [%d, %d]", q, a, c[a],
+                            PCDF_CAP_MIN, PCDF_CAP_MAX);
+        if (c[6] < 0 || c[6] > PCDF_CAP_MAX_R)
+            return fail(PCDF_EINVAL, "capsule %lld radius %d outside [0, %d]", q, c[6], PCDF_CAP_MAX_R);
+        pcdf::CapInfo &ci = out[q];
+        std::memset(&ci, 0, sizeof(ci));
+        bool empty = false;
+        for (int a = 0; a < 3; ++a) {
+            ci.a[a] = c[a];
+            ci.b[a] = c[3 + a];
+            const long long mn = std::min(c[a], c[3 + a]) - (long long)c[6];
+            const long long mx = std::max(c[a], c[3 + a]) + (long long)c[6];
+            long long lo = floordiv(mn - 8 + 15, 16);  // ceil((mn - 8) / 16)
+            long long hi = floordiv(mx - 8, 16);
+            lo = std::max(lo, 0LL);
+            hi = std::min(hi, (long long)n[a] - 1);
+            ci.lo[a] = (int32_t)lo;
+            ci.hi[a] = (int32_t)hi;
+            empty |= lo > hi;
+        }
+        ci.r = c[6];
+        if (empty) {
+            for (int a = 0; a < 3; ++a) {
+                ci.lo[a] = 1;
+                ci.hi[a] = 0;
+            }
+            continue;
+        }
+        *zlo = std::min(*zlo, ci.lo[2]);
+        *zhi = std::max(*zhi, ci.hi[2]);
+    }
+    return PCDF_OK;
+}
+
+int check_caps_args(int T, int H, const int32_t *caps)
+{
+    if (T < 1 || T > PCDF_MAX_T)
+        return fail(PCDF_EINVAL, "T = %d outside [1, %d]", T, PCDF_MAX_T);
+    if (H < 0 || H > PCDF_MAX_H)
+        return fail(PCDF_EINVAL, "H = %d outside [0, %d]", H, PCDF_MAX_H);
+    if (H > 0 && !caps)
+        return fail(PCDF_EINVAL, "caps is NULL with H = %d", H);
+    return PCDF_OK;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Static (or union) signed EDT of one grid: row pass (mode 0 or 1 with the
+// capsules of one t), y envelope, z envelope with optional float epilogue.
+int run_full_edt(const pcdf_grid *g, int mode, const uint8_t *occ, const pcdf::CapBatch *caps, int H, int32_t *sq,
+                 float *sdf, void *ws, cudaStream_t st)
+{
+    const long long V = nvox(g);
+    int16_t *g16 = (int16_t *)ws;
+    int32_t *mid = (int32_t *)((char *)ws + align_up((size_t)V * sizeof(int16_t)));
+    cudaError_t e = pcdf::launch_pass_x(mode, occ, caps, H, g->nx, g->ny, 0, g->nz, 1, g16, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "row pass");
+    const long long slice = (long long)g->nx * g->ny;
+    e = pcdf::launch_envelope_i16(g16, mid, g->ny, g->nx, (long long)g->nx * g->nz, slice, g->nx, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "y pass");
+    e = pcdf::launch_envelope_i32(mid, sq, sdf, g->vox, g->nz, g->nx, slice, g->nx, slice, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "z pass");
+    return PCDF_OK;
+}
+
+size_t full_edt_ws(const pcdf_grid *g)
+{
+    const long long V = nvox(g);
+    return align_up((size_t)V * sizeof(int16_t)) + align_up((size_t)V * sizeof(int32_t));
+}
+
+}  // namespace
+
+namespace {
+
+// Slab geometry and capsule table of one composite request.
+struct CompositePlan {
+    std::vector<pcdf::CapInfo> ci;
+    int zlo = 0, zhi = -1, S = 0;
+    long long slab = 0;  // T * S * nx * ny
+    size_t need = 0;     // workspace bytes
+};
+
+int plan_composite(const pcdf_grid *grid, int T, int H, const int32_t *caps, CompositePlan &p)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (int rc = check_caps_args(T, H, caps))
+        return rc;
+    if (H > 0)
+        if (int rc = make_capinfo(grid, T, H, caps, p.ci, &p.zlo, &p.zhi))
+            return rc;
+    p.S = p.zhi >= p.zlo ? p.zhi - p.zlo + 1 : 0;
+    p.slab = (long long)T * p.S * grid->nx * grid->ny;
+    p.need = p.S ? align_up((size_t)p.slab * sizeof(int16_t)) + align_up((size_t)p.slab * sizeof(int32_t)) : 0;
+    return PCDF_OK;
+}
+
+int check_ws(const CompositePlan &p, void *workspace, size_t workspace_bytes)
+{
+    if (p.S == 0)
+        return PCDF_OK;
+    if (!workspace || !aligned(workspace, kAlign))
+        return fail(PCDF_EINVAL, "workspace must be non-NULL and %zu-byte aligned", kAlign);
+    if (workspace_bytes < p.need)
+        return fail(PCDF_ENOMEM, "workspace %zu bytes < %zu needed", workspace_bytes, p.need);
+    return PCDF_OK;
+}
+
+int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &p, void *workspace,
+                      cudaStream_t st)
+{
+    if (p.S == 0)
+        return PCDF_OK;
+    int16_t *g16 = (int16_t *)workspace;
+    int32_t *mid = (int32_t *)((char *)workspace + align_up((size_t)p.slab * sizeof(int16_t)));
+    const long long sliceN = (long long)grid->nx * grid->ny;
+    // row pass over the slab for every t, in chunks whose capsules fit the
+    // kernel-parameter batch
+    const int t_chunk = std::max(1, pcdf::kMaxCapsPerLaunch / std::max(H, 1));
+    static thread_local pcdf::CapBatch batch;
+    for (int t0 = 0; t0 < T; t0 += t_chunk) {
+        const int nt = std::min(t_chunk, T - t0);
+        batch.count = nt * H;
+        std::memcpy(batch.caps, p.ci.data() + (size_t)t0 * H, sizeof(pcdf::CapInfo) * nt * H);
+        cudaError_t e = pcdf::launch_pass_x(2, nullptr, &batch, H, grid->nx, grid->ny, p.zlo, p.S, nt,
+                                            g16 + (long long)t0 * p.S * sliceN, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "dynamic row pass");
+    }
+    // y pass over all T * S slab slices
+    cudaError_t e = pcdf::launch_envelope_i16(g16, mid, grid->ny, grid->nx, (long long)grid->nx * T * p.S, sliceN,
+                                              grid->nx, st);
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "dynamic y pass");
+}
+
+int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, int T, const CompositePlan &p,
+                     int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st)
+{
+    cudaError_t e;
+    if (p.S == 0) {
+        e = pcdf::launch_broadcast_static(static_sq, nvox(grid), T, comp_sq, comp_sdf, grid->vox, st);
+        return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "broadcast");
+    }
+    const int32_t *mid = (const int32_t *)((const char *)workspace + align_up((size_t)p.slab * sizeof(int16_t)));
+    e = pcdf::launch_composite_z(static_sq, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, T, comp_sq, comp_sdf,
+                                 grid->vox, st);
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "composite z pass");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pcdf_last_error(void) { return g_err; }
+
+int pcdf_version(void) { return 100; }
+
+int pcdf_static_workspace_bytes(const pcdf_grid *grid, size_t *bytes)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (!bytes)
+        return fail(PCDF_EINVAL, "bytes is NULL");
+    *bytes = full_edt_ws(grid);
+    return PCDF_OK;
+}
+
+int pcdf_build_static_sdf(const pcdf_grid *grid, const uint8_t *occ, int32_t *static_sq, float *static_sdf,
+                          void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (!occ || !static_sq || !workspace)
+        return fail(PCDF_EINVAL, "occ, static_sq and workspace must be non-NULL");
+    if (!aligned(workspace, kAlign))
+        return fail(PCDF_EINVAL, "workspace must be %zu-byte aligned", kAlign);
+    if (workspace_bytes < full_edt_ws(grid))
+        return fail(PCDF_ENOMEM, "workspace %zu bytes < %zu needed", workspace_bytes, full_edt_ws(grid));
+    static pcdf::CapBatch none;  // unused by the occupancy-only row pass
+    return run_full_edt(grid, 0, occ, &none, 0, static_sq, static_sdf, workspace, (cudaStream_t)stream);
+}
+
+int pcdf_composite_workspace_bytes(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps,
+                                   size_t *bytes)
+{
+    if (!bytes)
+        return fail(PCDF_EINVAL, "bytes is NULL");
+    CompositePlan p;
+    if (int rc = plan_composite(grid, T, H, caps, p))
+        return rc;
+    *bytes = p.need;
+    return PCDF_OK;
+}
+
+int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_sq, int32_t T, int32_t H,
+                                   const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
+                                   size_t workspace_bytes, void *stream)
+{
+    CompositePlan p;
+    if (int rc = plan_composite(grid, T, H, caps, p))
+        return rc;
+    if (!static_sq || (!comp_sq && !comp_sdf))
+        return fail(PCDF_EINVAL, "static_sq and at least one output must be non-NULL");
+    if (int rc = check_ws(p, workspace, workspace_bytes))
+        return rc;
+    if (int rc = composite_prepare(grid, T, H, p, workspace, (cudaStream_t)stream))
+        return rc;
+    return composite_finish(grid, static_sq, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
+}
+
+int pcdf_composite_prepare(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, void *workspace,
+                           size_t workspace_bytes, void *stream)
+{
+    CompositePlan p;
+    if (int rc = plan_composite(grid, T, H, caps, p))
+        return rc;
+    if (int rc = check_ws(p, workspace, workspace_bytes))
+        return rc;
+    return composite_prepare(grid, T, H, p, workspace, (cudaStream_t)stream);
+}
+
+int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, int32_t T, int32_t H,
+                          const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
+                          size_t workspace_bytes, void *stream)
+{
+    CompositePlan p;
+    if (int rc = plan_composite(grid, T, H, caps, p))
+        return rc;
+    if (!static_sq || (!comp_sq && !comp_sdf))
+        return fail(PCDF_EINVAL, "static_sq and at least one output must be non-NULL");
+    if (int rc = check_ws(p, workspace, workspace_bytes))
+        return rc;
+    return composite_finish(grid, static_sq, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
+}
+
+int pcdf_scratch_workspace_bytes(const pcdf_grid *grid, int32_t T, int32_t H, size_t *bytes)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (T < 1 || T > PCDF_MAX_T || H < 0 || H > PCDF_MAX_H)
+        return fail(PCDF_EINVAL, "T or H out of range");
+    if (!bytes)
+        return fail(PCDF_EINVAL, "bytes is NULL");
+    *bytes = full_edt_ws(grid);
+    return PCDF_OK;
+}
+
+int pcdf_build_from_scratch(const pcdf_grid *grid, const uint8_t *occ, int32_t T, int32_t H, const int32_t *caps,
+                            int32_t *sq, float *sdf, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (int rc = check_caps_args(T, H, caps))
+        return rc;
+    if (!occ || !sq || !workspace)
+        return fail(PCDF_EINVAL, "occ, sq and workspace must be non-NULL");
+    if (!aligned(workspace, kAlign))
+        return fail(PCDF_EINVAL, "workspace must be %zu-byte aligned", kAlign);
+    if (workspace_bytes < full_edt_ws(grid))
+        return fail(PCDF_ENOMEM, "workspace %zu bytes < %zu needed", workspace_bytes, full_edt_ws(grid));
+    std::vector<pcdf::CapInfo> ci;
+    int zlo = 0, zhi = -1;
+    if (H > 0)
+        if (int rc = make_capinfo(grid, T, H, caps, ci, &zlo, &zhi))
+            return rc;
+    const long long V = nvox(grid);
+    static thread_local pcdf::CapBatch batch;
+    for (int t = 0; t < T; ++t) {
+        batch.count = H;
+        if (H > 0)
+            std::memcpy(batch.caps, ci.data() + (size_t)t * H, sizeof(pcdf::CapInfo) * H);
+        if (int rc = run_full_edt(grid, H > 0 ? 1 : 0, occ, &batch, H, sq + (long long)t * V,
+                                  sdf ? sdf + (long long)t * V : nullptr, workspace, (cudaStream_t)stream))
+            return rc;
+    }
+    return PCDF_OK;
+}
+
+static int check_query(const pcdf_grid *grid, const float *sdf, int32_t T, const float *spheres,
+                       const int32_t *tidx, int64_t N)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (T < 1 || T > PCDF_MAX_T)
+        return fail(PCDF_EINVAL, "T = %d outside [1, %d]", T, PCDF_MAX_T);
+    if (N < 0)
+        return fail(PCDF_EINVAL, "N < 0");
+    if (N > 0 && (!sdf || !spheres || !tidx))
+        return fail(PCDF_EINVAL, "sdf, spheres and tidx must be non-NULL");
+    if (!aligned(spheres, 16))
+        return fail(PCDF_EINVAL, "spheres must be 16-byte aligned");
+    return PCDF_OK;
+}
+
+static pcdf::QueryGrid qgrid(const pcdf_grid *g)
+{
+    pcdf::QueryGrid q;
+    q.n[0] = g->nx;
+    q.n[1] = g->ny;
+    q.n[2] = g->nz;
+    for (int a = 0; a < 3; ++a)
+        q.origin[a] = g->origin[a];
+    q.vox = g->vox;
+    return q;
+}
+
+int pcdf_query_cost(const pcdf_grid *grid, const float *sdf, int32_t T, const float *spheres, const int32_t *tidx,
+                    int64_t N, float eps, float *h, int32_t *n_oob, void *stream)
+{
+    if (int rc = check_query(grid, sdf, T, spheres, tidx, N))
+        return rc;
+    if (N > 0 && !h)
+        return fail(PCDF_EINVAL, "h must be non-NULL");
+    cudaError_t e = pcdf::launch_query_cost(qgrid(grid), sdf, T, (const float4 *)spheres, tidx, N, eps, h, n_oob,
+                                            (cudaStream_t)stream);
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "query");
+}
+
+int pcdf_query_cost_backward(const pcdf_grid *grid, const float *sdf, int32_t T, const float *spheres,
+                             const int32_t *tidx, int64_t N, float eps, const float *grad_h, float *grad_c,
+                             float *grad_r, void *stream)
+{
+    if (int rc = check_query(grid, sdf, T, spheres, tidx, N))
+        return rc;
+    if (N > 0 && (!grad_h || !grad_c))
+        return fail(PCDF_EINVAL, "grad_h and grad_c must be non-NULL");
+    cudaError_t e = pcdf::launch_query_cost_backward(qgrid(grid), sdf, T, (const float4 *)spheres, tidx, N, eps,
+                                                     grad_h, grad_c, grad_r, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "query backward");
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Internal declarations shared by the CUDA translation units of libpcdf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pcdf.h"
+
+namespace pcdf {
+
+// 1-D distances along x are stored as int16 with the sign of the voxel's own
+// state (+ free, - occupied) and magnitude = distance to the nearest voxel of
+// the other state on the row; kInf16 marks "none on this row".
+constexpr int16_t kInf16 = 0x7FFF;
+constexpr int32_t kInf32 = PCDF_INF;
+
+// One capsule with its voxel-index bounding box, clipped to the grid (lo > hi
+// on some axis when the capsule covers no voxel centre of the grid).
+struct alignas(16) CapInfo {
+    int32_t a[3];
+    int32_t b[3];
+    int32_t r;
+    int32_t lo[3];
+    int32_t hi[3];
+    int32_t pad[3];
+};
+static_assert(sizeof(CapInfo) == 64, "CapInfo layout");
+
+// Capsules handed to one row-pass launch by value (kernel parameters are
+// copied at launch, so the host array may be reused as soon as the call
+// returns and nothing has to be staged in device memory).
+constexpr int kMaxCapsPerLaunch = 384;
+struct CapBatch {
+    int32_t count;
+    int32_t pad[3];
+    CapInfo caps[kMaxCapsPerLaunch];
+};
+
+// Columns handled by one CTA of the lower-envelope pass (the CTA has two
+// threads per column, one per site set).
+constexpr int kEnvCols = 32;
+
+// ---------------------------------------------------------------------------
+// launchers (edt.cu); all return cudaError_t of the launch
+// ---------------------------------------------------------------------------
+
+// Row pass along x.  Rows of slices z = z0 .. z0 + nslices - 1; for every t in
+// [0, n_t) the output block t is g16 + t * nslices * ny * nx and the capsules
+// of that t are caps->caps[t * H .. t * H + H - 1].
+//   mode 0: occupancy only (occ is indexed by absolute z; caps unused)
+//   mode 1: occupancy OR capsules
+//   mode 2: capsules only
+cudaError_t launch_pass_x(int mode, const uint8_t *occ, const CapBatch *caps, int H, int nx, int ny, int z0,
+                          int nslices, int n_t, int16_t *g16, cudaStream_t stream);
+
+// Lower-envelope pass over ncols columns: element e of column c lives at
+// (c / nx) * outer_stride + (c % nx) + e * stride, e in [0, n).
+cudaError_t launch_envelope_i16(const int16_t *in, int32_t *out, int n, int nx, long long ncols,
+                                long long outer_stride, long long stride, cudaStream_t stream);
+cudaError_t launch_envelope_i32(const int32_t *in, int32_t *out, float *sdf, float vox, int n, int nx,
+                                long long ncols, long long outer_stride, long long stride, cudaStream_t stream);
+
+// z-pass of the dynamic field over the slab [zlo, zlo + S) fused with the
+// composite min against static_sq and the float epilogue, for all T.
+cudaError_t launch_composite_z(const int32_t *static_sq, const int32_t *dyn_mid, int nx, int ny, int nz, int zlo,
+                               int S, int T, int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream);
+
+// Copies static_sq into every t of comp (and its float field) when no capsule
+// touches the grid.
+cudaError_t launch_broadcast_static(const int32_t *static_sq, long long V, int T, int32_t *comp_sq,
+                                    float *comp_sdf, float vox, cudaStream_t stream);
+
+// query.cu
+struct QueryGrid {
+    int n[3];
+    float origin[3];
+    float vox;
+};
+cudaError_t launch_query_cost(const QueryGrid &g, const float *sdf, int T, const float4 *spheres,
+                              const int32_t *tidx, long long N, float eps, float *h, int32_t *n_oob,
+                              cudaStream_t stream);
+cudaError_t launch_query_cost_backward(const QueryGrid &g, const float *sdf, int T, const float4 *spheres,
+                                       const int32_t *tidx, long long N, float eps, const float *grad_h,
+                                       float *grad_c, float *grad_r, cudaStream_t stream);
+
+}  // namespace pcdf

@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer fields (signed squared EDT, composite) and the float fields derived
+from them must match bit for bit.  The hinge cost must match the fp64 oracle
+within 1e-5 m and its gradient within 1e-4, away from the hinge kink and the
+cell faces where the derivative jumps.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+pcdf = pytest.importorskip("paper_2201_05058_gb300")
+
+COST_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda", 0)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def gpu_static(occ, grid):
+    sq, sdf = pcdf.build_static_sdf(cuda(occ), grid)
+    return sq.cpu().numpy(), sdf.cpu().numpy()
+
+
+def assert_equal_fields(got, want, what):
+    if not np.array_equal(got, want):
+        bad = np.argwhere(got != want)
+        i = tuple(bad[0])
+        raise AssertionError(f"{what}: {len(bad)} mismatches, first at {i}: got {got[i]} want {want[i]}")
+
+
+def assert_bits_equal(got, want, what):
+    assert_equal_fields(got.view(np.int32), want.view(np.int32), what)
+
+
+# ---------------------------------------------------------------------------
+# static signed EDT
+# ---------------------------------------------------------------------------
+
+SMALL_SHAPES = [(16, 16, 16), (13, 17, 15), (23, 29, 37), (1, 1, 40), (40, 1, 1), (1, 37, 1), (3, 2, 70),
+                (2, 5, 512), (33, 7, 65)]
+
+
+@pytest.mark.parametrize("shape", SMALL_SHAPES)
+@pytest.mark.parametrize("density", [0.0, 0.002, 0.05, 0.3, 0.9, 1.0])
+def test_static_edt_matches_definition(shape, density):
+    rng = np.random.default_rng(hash((shape, density)) % 2 ** 32)
+    occ = scenes.random_occupancy(shape, density, rng)
+    grid = scenes.Grid(shape[2], shape[1], shape[0], 0.05)
+    sq, sdf = gpu_static(occ, grid)
+    want = oracle.edt_brute(occ) if occ.size <= 40000 else oracle.edt(occ)
+    assert_equal_fields(sq, want, "static_sq")
+    assert_bits_equal(sdf, oracle.sdf_from_sq(want, grid.vox), "static_sdf")
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_static_edt_small_scene(seed):
+    sc = scenes.scene_small(seed=seed)
+    grid = sc["grid"]
+    sq, sdf = gpu_static(sc["occ"], grid)
+    want = oracle.edt(sc["occ"])
+    assert_equal_fields(sq, want, "static_sq")
+    assert_bits_equal(sdf, oracle.sdf_from_sq(want, grid.vox), "static_sdf")
+
+
+def test_static_edt_box_and_wall_structures():
+    # walls produce full-depth envelopes; a hollow box produces interior runs
+    shape = (48, 50, 66)
+    occ = np.zeros(shape, np.uint8)
+    occ[:, :, 40] = 1
+    occ[10:30, 5:45, 3:20] = 1
+    occ[12:28, 7:43, 5:18] = 0
+    occ[:, 25, :] |= (np.arange(66) % 3 == 0).astype(np.uint8)
+    grid = scenes.Grid(66, 50, 48, 0.04)
+    sq, _ = gpu_static(occ, grid)
+    assert_equal_fields(sq, oracle.edt(occ), "static_sq")
+
+
+# ---------------------------------------------------------------------------
+# composite fields
+# ---------------------------------------------------------------------------
+
+def check_composite(occ, caps, grid):
+    d = dev()
+    static_sq, _ = pcdf.build_static_sdf(cuda(occ), grid)
+    comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, caps)
+    comp_sq = comp_sq.cpu().numpy()
+    comp_sdf = comp_sdf.cpu().numpy()
+    want = oracle.predicted_composite(oracle.edt(occ), caps)
+    for t in range(caps.shape[0]):
+        assert_equal_fields(comp_sq[t], want[t], f"comp_sq[{t}]")
+        assert_bits_equal(comp_sdf[t], oracle.sdf_from_sq(want[t], grid.vox), f"comp_sdf[{t}]")
+    return comp_sq
+
+
+@pytest.mark.parametrize("seed", [0, 5])
+def test_composite_small_scene_one_human(seed):
+    sc = scenes.scene_small(seed=seed, T=1)
+    check_composite(sc["occ"], sc["caps"], sc["grid"])
+
+
+@pytest.mark.parametrize("H,T", [(1, 5), (2, 7), (4, 3)])
+def test_composite_walking_humans(H, T):
+    sc = scenes.scene_small_walking(seed=10 + H, T=T, H=H)
+    check_composite(sc["occ"], sc["caps"], sc["grid"])
+
+
+def test_composite_ragged_grid_and_edge_capsules():
+    grid = scenes.Grid(45, 70, 37, 0.05)
+    rng = np.random.default_rng(3)
+    occ, _ = scenes.boxes_occupancy(grid, 8, rng)
+    caps = np.array([
+        [[0, 0, 80, 0, 0, 400, 100], [700, 1100, -50, 760, 1150, 300, 60]],      # corner, below floor
+        [[-300, 500, 100, -100, 500, 500, 120], [400, 400, 580, 400, 400, 590, 30]],  # partly outside; near top
+        [[104, 104, 104, 104, 104, 104, 0], [296, 296, 296, 504, 296, 296, 0]],   # r = 0: on-centre points only
+    ], np.int32)
+    check_composite(occ, caps, grid)
+
+
+def test_composite_no_humans_and_humans_outside():
+    sc = scenes.scene_small(seed=1)
+    grid = sc["grid"]
+    static_sq, _ = pcdf.build_static_sdf(cuda(sc["occ"]), grid)
+    want = oracle.edt(sc["occ"])
+    sq, sdf = pcdf.build_predicted_composite(static_sq, grid, np.zeros((3, 0, 7), np.int32))
+    for t in range(3):
+        assert_equal_fields(sq[t].cpu().numpy(), want, "H=0")
+    far = np.array([[[-8000, -8000, -8000, -8000, -8000, -7000, 80]]] * 2, np.int32)
+    sq, sdf = pcdf.build_predicted_composite(static_sq, grid, far)
+    assert_equal_fields(sq[1].cpu().numpy(), want, "outside")
+    assert_bits_equal(sdf[1].cpu().numpy(), oracle.sdf_from_sq(want, grid.vox), "outside sdf")
+
+
+def test_composite_degenerate_maps():
+    grid = scenes.Grid(20, 18, 22, 0.05)
+    caps = np.array([[[160, 144, 80, 160, 144, 200, 48]]], np.int32)
+    # empty static map: composite = dynamic field alone
+    check_composite(np.zeros(grid.shape, np.uint8), caps, grid)
+    # capsule covering the whole grid: no free voxel anywhere at that t
+    big = np.array([[[160, 144, 176, 160, 144, 176, 8000]]], np.int32)
+    comp = check_composite(scenes.random_occupancy(grid.shape, 0.1, np.random.default_rng(0)), big, grid)
+    assert np.all(comp == -oracle.INF32)
+
+
+def test_from_scratch_matches_oracle_and_composite_invariant():
+    sc = scenes.scene_small_walking(seed=21, T=4, H=2)
+    occ, caps, grid = sc["occ"], sc["caps"], sc["grid"]
+    sq, sdf = pcdf.build_from_scratch(cuda(occ), grid, caps)
+    sq = sq.cpu().numpy()
+    want = oracle.from_scratch(occ, caps)
+    for t in range(caps.shape[0]):
+        assert_equal_fields(sq[t], want[t], f"scratch[{t}]")
+        assert_bits_equal(sdf[t].cpu().numpy(), oracle.sdf_from_sq(want[t], grid.vox), f"scratch sdf[{t}]")
+    static_sq, _ = pcdf.build_static_sdf(cuda(occ), grid)
+    comp, _ = pcdf.build_predicted_composite(static_sq, grid, caps)
+    comp = comp.cpu().numpy()
+    for t in range(caps.shape[0]):
+        free = (occ == 0) & (oracle.capsule_occupancy(occ.shape, caps[t]) == 0)
+        assert np.array_equal(comp[t][free], sq[t][free])
+
+
+# ---------------------------------------------------------------------------
+# full-size workload: 256^3, 60 boxes, 3 walking humans, T = 20
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def big_scene():
+    sc = scenes.scene_composite(seed=0)
+    grid = sc["grid"]
+    static_sq, static_sdf = pcdf.build_static_sdf(cuda(sc["occ"]), grid)
+    comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, sc["caps"])
+    torch.cuda.synchronize()
+    return sc, static_sq.cpu().numpy(), static_sdf.cpu().numpy(), comp_sq, comp_sdf
+
+
+def test_full_size_static_matches_oracle(big_scene):
+    sc, static_sq, static_sdf, _, _ = big_scene
+    want = oracle.edt(sc["occ"])
+    assert_equal_fields(static_sq, want, "static_sq 256^3")
+    assert_bits_equal(static_sdf, oracle.sdf_from_sq(want, sc["grid"].vox), "static_sdf 256^3")
+    # and against the definition at sampled voxels
+    rng = np.random.default_rng(0)
+    for _ in range(60):
+        k, j, i = (int(rng.integers(0, 256)) for _ in range(3))
+        assert static_sq[k, j, i] == oracle.edt_at(sc["occ"], i, j, k)
+
+
+@pytest.mark.parametrize("t", [0, 9, 19])
+def test_full_size_composite_matches_oracle(big_scene, t):
+    sc, _, _, comp_sq, comp_sdf = big_scene
+    grid = sc["grid"]
+    S_static = oracle.edt(sc["occ"])
+    dyn_occ = oracle.capsule_occupancy(grid.shape, sc["caps"][t])
+    want = oracle.composite(S_static, oracle.edt(dyn_occ))
+    got = comp_sq[t].cpu().numpy()
+    assert_equal_fields(got, want, f"comp_sq[{t}] 256^3")
+    assert_bits_equal(comp_sdf[t].cpu().numpy(), oracle.sdf_from_sq(want, grid.vox), f"comp_sdf[{t}] 256^3")
+    # sampled against the definition, biased towards the humans
+    rng = np.random.default_rng(t)
+    occ_pts = np.argwhere(dyn_occ)
+    for q in range(30):
+        if q % 2 == 0 and len(occ_pts):
+            k, j, i = occ_pts[rng.integers(0, len(occ_pts))] + rng.integers(-3, 4, 3)
+            k, j, i = (int(np.clip(v, 0, 255)) for v in (k, j, i))
+        else:
+            k, j, i = (int(rng.integers(0, 256)) for _ in range(3))
+        w = min(oracle.edt_at(sc["occ"], i, j, k), oracle.edt_at(dyn_occ, i, j, k))
+        assert got[k, j, i] == w
+
+
+# ---------------------------------------------------------------------------
+# hinge cost and gradient
+# ---------------------------------------------------------------------------
+
+def oracle_distance(sdf, grid, sph, tidx):
+    """The oracle's interpolated distance d (from its hinge with a huge eps)."""
+    big = 1.0e4
+    h, _ = oracle.hinge_cost(sdf, grid.origin, grid.vox, sph, tidx, big)
+    return big + sph[:, 3].astype(np.float64) - h
+
+
+def near_face_or_kink(sph, grid, d_oracle, eps, margin_u=1e-3, margin_h=1e-5):
+    """Samples where fp32 and fp64 may legitimately disagree on the derivative:
+    within margin_u (voxels) of a cell face, or within margin_h (m) of the kink."""
+    u = (sph[:, :3].astype(np.float64) - np.asarray(grid.origin)) / grid.vox - 0.5
+    face = np.any(np.abs(u - np.rint(u)) < margin_u, axis=1)
+    kink = np.abs(eps + sph[:, 3].astype(np.float64) - d_oracle) < margin_h
+    return face | kink
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_query_cost_small_scene(seed):
+    sc = scenes.scene_small(seed=seed, T=1)
+    grid = sc["grid"]
+    static_sq, _ = pcdf.build_static_sdf(cuda(sc["occ"]), grid)
+    _, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, sc["caps"], want_sq=False)
+    sph = sc["spheres"].copy()
+    sph[::7, :3] += np.float32(0.3)   # some centres outside the grid
+    sph[1::7, :3] -= np.float32(0.2)
+    h, oob = pcdf.query_cost(comp_sdf, grid, cuda(sph), cuda(sc["tidx"]), sc["eps"], count_oob=True)
+    want, want_oob = oracle.hinge_cost(comp_sdf.cpu().numpy(), grid.origin, grid.vox, sph, sc["tidx"], sc["eps"])
+    assert np.max(np.abs(h.cpu().numpy() - want)) <= COST_TOL
+    assert int(oob.item()) == want_oob
+    assert want_oob > 0 and (want > 0).sum() > 10
+
+
+def test_query_cost_and_gradient_trajectories():
+    """[256 trajectories, 40 support states, 30 spheres] on T = 20 composite
+    fields of a 64^3 scene; tidx = min(state, 19)."""
+    sc = scenes.scene_small_walking(seed=4, T=20, H=1)
+    grid = sc["grid"]
+    static_sq, _ = pcdf.build_static_sdf(cuda(sc["occ"]), grid)
+    _, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, sc["caps"], want_sq=False)
+    rng = np.random.default_rng(44)
+    sph, tidx = scenes.spheres_along_paths(grid, 256, 40, 30, rng, T=20)
+    sph_f = sph.reshape(-1, 4)
+    tid_f = tidx.reshape(-1)
+    h = pcdf.query_cost(comp_sdf, grid, cuda(sph), cuda(tidx), 0.2).cpu().numpy().reshape(-1)
+    sdf_np = comp_sdf.cpu().numpy()
+    want, _, gc, gr = oracle.hinge_cost(sdf_np, grid.origin, grid.vox, sph_f, tid_f, 0.2, need_grad=True)
+    assert np.max(np.abs(h - want)) <= COST_TOL
+    g_h = rng.normal(size=tid_f.shape).astype(np.float32)
+    got_c, got_r = pcdf.query_cost_backward(comp_sdf, grid, cuda(sph), cuda(tidx), 0.2, cuda(g_h.reshape(tidx.shape)))
+    got_c = got_c.cpu().numpy().reshape(-1, 3)
+    got_r = got_r.cpu().numpy().reshape(-1)
+    skip = near_face_or_kink(sph_f, grid, oracle_distance(sdf_np, grid, sph_f, tid_f), 0.2)
+    keep = ~skip
+    assert keep.mean() > 0.95
+    want_c = gc * g_h[:, None].astype(np.float64)
+    want_r = gr * g_h.astype(np.float64)
+    assert np.max(np.abs(got_c[keep] - want_c[keep])) <= GRAD_TOL
+    assert np.max(np.abs(got_r[keep] - want_r[keep])) <= GRAD_TOL
+    assert (gr > 0).sum() > 1000
+
+
+def test_hinge_autograd_function():
+    sc = scenes.scene_small(seed=6, T=1, n_spheres=2048)
+    grid = sc["grid"]
+    static_sq, _ = pcdf.build_static_sdf(cuda(sc["occ"]), grid)
+    _, sdf = pcdf.build_predicted_composite(static_sq, grid, sc["caps"], want_sq=False)
+    sph = sc["spheres"].copy()
+    sph[:, 3] = 0.5
+    centres = cuda(sph[:, :3]).requires_grad_(True)
+    radii = cuda(sph[:, 3]).requires_grad_(True)
+    tidx = cuda(sc["tidx"])
+    h = pcdf.hinge_cost(centres, radii, sdf, tidx, 0.2, grid)
+    loss = (h * h).sum()
+    loss.backward()
+    want, _, gc, gr = oracle.hinge_cost(sdf.detach().cpu().numpy(), grid.origin, grid.vox, sph, sc["tidx"], 0.2,
+                                        need_grad=True)
+    up = 2.0 * want
+    keep = ~near_face_or_kink(sph, grid, oracle_distance(sdf.detach().cpu().numpy(), grid, sph, sc["tidx"]), 0.2)
+    gcn = centres.grad.cpu().numpy()
+    assert np.max(np.abs(gcn[keep] - (gc * up[:, None])[keep])) <= 10 * GRAD_TOL
+    assert np.max(np.abs(radii.grad.cpu().numpy()[keep] - (gr * up)[keep])) <= 10 * GRAD_TOL
+    # fp32 central differences on the GPU (reported, loosely bounded: error ~ ulp / step)
+    step = 1e-3
+    idx = np.nonzero(keep & (want > 0.05))[0][:64]
+    for a in range(3):
+        cp = centres.detach().clone()
+        cm = centres.detach().clone()
+        cp[idx, a] += step
+        cm[idx, a] -= step
+        hp = pcdf.hinge_cost(cp, radii.detach(), sdf, tidx, 0.2, grid)
+        hm = pcdf.hinge_cost(cm, radii.detach(), sdf, tidx, 0.2, grid)
+        fd = ((hp * hp - hm * hm) / (2 * step)).cpu().numpy()[idx]
+        assert np.max(np.abs(fd - gcn[idx, a])) < 0.05
+
+
+def test_query_edge_cases():
+    grid = scenes.Grid(1, 5, 7, 0.1)  # single-voxel x axis
+    occ = np.zeros(grid.shape, np.uint8)
+    occ[3, 2, 0] = 1
+    sq, sdf = pcdf.build_static_sdf(cuda(occ), grid)
+    sph = np.array([[0.05, 0.25, 0.35, 0.1], [0.3, 0.21, 0.33, 0.05], [np.nan, 0.2, 0.3, 0.1]], np.float32)
+    tid = np.array([0, 3, -1], np.int32)
+    h, oob = pcdf.query_cost(sdf, grid, cuda(sph), cuda(tid), 0.2, count_oob=True)
+    want, want_oob = oracle.hinge_cost(sdf.cpu().numpy(), grid.origin, grid.vox, sph, tid, 0.2)
+    assert np.max(np.abs(h.cpu().numpy() - want)) <= COST_TOL
+    assert int(oob.item()) == want_oob
+    # N = 0
+    h0 = pcdf.query_cost(sdf, grid, cuda(np.zeros((0, 4), np.float32)), cuda(np.zeros(0, np.int32)), 0.2)
+    assert h0.numel() == 0
+    # infinite fields: empty map -> h = 0; full map -> h = inf
+    for fill, expect in ((0, 0.0), (1, np.inf)):
+        s2, f2 = pcdf.build_static_sdf(cuda(np.full(grid.shape, fill, np.uint8)), grid)
+        hh = pcdf.query_cost(f2, grid, cuda(sph[:2]), cuda(tid[:2]), 0.2).cpu().numpy()
+        assert np.all(hh == expect)
