@@ -118,6 +118,12 @@ int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_
                                    const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
                                    size_t workspace_bytes, void *stream);
 
+/* The z-slab [zlo, zlo + S) of voxel slices that some capsule of some t
+ * touches (S = 0: no capsule touches the grid).  The dynamic field's sites all
+ * lie in it; the workspace holds one int32 per slab voxel per t. */
+int pcdf_composite_slab(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, int32_t *zlo,
+                        int32_t *S);
+
 /* The two stages of pcdf_build_predicted_composite, for callers that want to
  * overlap or time them separately (same arguments and workspace; the
  * workspace carries the dynamic intermediate from the first to the second):

@@ -16,6 +16,7 @@ from .api import (  # noqa: F401
     capsule_fixed,
     composite_finish,
     composite_prepare,
+    composite_slab,
     composite_workspace,
     hinge_cost,
     query_cost,

@@ -155,6 +155,18 @@ def composite_workspace(grid, caps, device) -> torch.Tensor:
     return _workspace(nbytes.value, device)
 
 
+def composite_slab(grid, caps):
+    """(zlo, S): the z-slab of voxel slices that the capsules touch."""
+    caps = _caps_host(caps)
+    T, H = int(caps.shape[0]), int(caps.shape[1])
+    g = _cgrid(grid)
+    cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+    zlo, S = ctypes.c_int32(0), ctypes.c_int32(0)
+    _lib.check(_lib.load().pcdf_composite_slab(ctypes.byref(g), T, H, cp, ctypes.byref(zlo), ctypes.byref(S)),
+               "pcdf_composite_slab")
+    return zlo.value, S.value
+
+
 def composite_prepare(grid, caps, workspace: torch.Tensor):
     """First stage of the composite: capsule row pass and y pass into workspace."""
     caps = _caps_host(caps)

@@ -149,6 +149,8 @@ struct CompositePlan {
     std::vector<pcdf::CapInfo> ci;
     int zlo = 0, zhi = -1, S = 0;
     long long slab = 0;  // T * S * nx * ny
+    bool fused = false;  // analytic x+y kernel (else row pass + y envelope)
+    int cap = 0;         // its per-thread stack capacity
     size_t need = 0;     // workspace bytes
 };
 
@@ -163,8 +165,33 @@ int plan_composite(const pcdf_grid *grid, int T, int H, const int32_t *caps, Com
             return rc;
     p.S = p.zhi >= p.zlo ? p.zhi - p.zlo + 1 : 0;
     p.slab = (long long)T * p.S * grid->nx * grid->ny;
-    p.need = p.S ? align_up((size_t)p.slab * sizeof(int16_t)) + align_up((size_t)p.slab * sizeof(int32_t)) : 0;
+    // stack bound of the analytic kernel: rows holding a run (<= sum of the
+    // capsules' y extents) plus two free rows per run (one run per capsule)
+    int ext_max = 0;
+    for (int t = 0; t < T; ++t) {
+        int ext = 0;
+        for (int h = 0; h < H; ++h) {
+            const pcdf::CapInfo &c = p.ci[(size_t)t * H + h];
+            if (c.lo[0] <= c.hi[0])
+                ext += c.hi[1] - c.lo[1] + 1;
+        }
+        ext_max = std::max(ext_max, ext);
+    }
+    p.cap = std::min(ext_max + 2 * H + 2, grid->ny + 2);
+    p.fused = H <= pcdf::kMaxCapsPerLaunch && pcdf::dyn_xy_fits(grid->ny, H, p.cap);
+    if (p.S == 0)
+        p.need = 0;
+    else if (p.fused)
+        p.need = align_up((size_t)p.slab * sizeof(int32_t));
+    else
+        p.need = align_up((size_t)p.slab * sizeof(int16_t)) + align_up((size_t)p.slab * sizeof(int32_t));
     return PCDF_OK;
+}
+
+int32_t *plan_mid(const CompositePlan &p, void *workspace)
+{
+    return p.fused ? (int32_t *)workspace
+                   : (int32_t *)((char *)workspace + align_up((size_t)p.slab * sizeof(int16_t)));
 }
 
 int check_ws(const CompositePlan &p, void *workspace, size_t workspace_bytes)
@@ -183,13 +210,23 @@ int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &
 {
     if (p.S == 0)
         return PCDF_OK;
-    int16_t *g16 = (int16_t *)workspace;
-    int32_t *mid = (int32_t *)((char *)workspace + align_up((size_t)p.slab * sizeof(int16_t)));
+    int32_t *mid = plan_mid(p, workspace);
     const long long sliceN = (long long)grid->nx * grid->ny;
-    // row pass over the slab for every t, in chunks whose capsules fit the
-    // kernel-parameter batch
+    // capsules travel as kernel parameters, in chunks of whole time steps
     const int t_chunk = std::max(1, pcdf::kMaxCapsPerLaunch / std::max(H, 1));
     static thread_local pcdf::CapBatch batch;
+    if (p.fused) {
+        for (int t0 = 0; t0 < T; t0 += t_chunk) {
+            const int nt = std::min(t_chunk, T - t0);
+            batch.count = nt * H;
+            std::memcpy(batch.caps, p.ci.data() + (size_t)t0 * H, sizeof(pcdf::CapInfo) * nt * H);
+            cudaError_t e = pcdf::launch_dyn_xy(&batch, H, grid->nx, grid->ny, p.zlo, p.S, t0, nt, p.cap, mid, st);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "dynamic x+y pass");
+        }
+        return PCDF_OK;
+    }
+    int16_t *g16 = (int16_t *)workspace;
     for (int t0 = 0; t0 < T; t0 += t_chunk) {
         const int nt = std::min(t_chunk, T - t0);
         batch.count = nt * H;
@@ -199,7 +236,6 @@ int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &
         if (e != cudaSuccess)
             return cuda_fail(e, "dynamic row pass");
     }
-    // y pass over all T * S slab slices
     cudaError_t e = pcdf::launch_envelope_i16(g16, mid, grid->ny, grid->nx, (long long)grid->nx * T * p.S, sliceN,
                                               grid->nx, st);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "dynamic y pass");
@@ -213,7 +249,7 @@ int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, int T, con
         e = pcdf::launch_broadcast_static(static_sq, nvox(grid), T, comp_sq, comp_sdf, grid->vox, st);
         return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "broadcast");
     }
-    const int32_t *mid = (const int32_t *)((const char *)workspace + align_up((size_t)p.slab * sizeof(int16_t)));
+    const int32_t *mid = plan_mid(p, workspace);
     e = pcdf::launch_composite_z(static_sq, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, T, comp_sq, comp_sdf,
                                  grid->vox, st);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "composite z pass");
@@ -261,6 +297,19 @@ int pcdf_composite_workspace_bytes(const pcdf_grid *grid, int32_t T, int32_t H, 
     if (int rc = plan_composite(grid, T, H, caps, p))
         return rc;
     *bytes = p.need;
+    return PCDF_OK;
+}
+
+int pcdf_composite_slab(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, int32_t *zlo,
+                        int32_t *S)
+{
+    if (!zlo || !S)
+        return fail(PCDF_EINVAL, "zlo and S must be non-NULL");
+    CompositePlan p;
+    if (int rc = plan_composite(grid, T, H, caps, p))
+        return rc;
+    *zlo = p.S ? p.zlo : 0;
+    *S = p.S;
     return PCDF_OK;
 }
 

@@ -1,0 +1,557 @@
+// Predicted composite fields (Sec. 6 composition, Sec. 8 sequence of fields)
+// on sm_103a.
+//
+// The field of the humans at time t is the exact signed EDT of the voxels
+// inside their capsules; its sites all lie in the z-slab [zlo, zlo + S) that
+// the capsules touch.  Two kernels build the composite of every t:
+//
+//  k_dyn_xy      one CTA per (slab slice, t): the exact x-interval of each
+//                capsule on every row of the slice, then per column x the
+//                y lower envelopes of the row distances to those intervals.
+//                Output: the 2-D partial field of the slice (signed int32),
+//                with no row-pass intermediate in memory.
+//  k_composite_z thread per (column (x, y), t): the z envelope of the slab's
+//                2-D partials, evaluated at every z, min with the static
+//                field, float epilogue; the T CTAs that share a static column
+//                block run together so that block is read from DRAM once.
+#include <cuda_runtime.h>
+
+#include "edt_common.cuh"
+
+namespace pcdf {
+namespace {
+
+// ---------------------------------------------------------------------------
+// k_dyn_xy
+// ---------------------------------------------------------------------------
+// Shared memory: rows[ny][H + 1] = interval count, then the merged maximal
+// occupied runs of the row as (xa << 16 | xb); then a stack of `cap` words per
+// thread, laid out [entry][thread].
+
+__device__ __forceinline__ bool row_inside(const int32_t *r, int x)
+{
+    const int cnt = r[0];
+    for (int i = 1; i <= cnt; ++i)
+        if (x >= (r[i] >> 16) && x <= (r[i] & 0xFFFF))
+            return true;
+    return false;
+}
+
+// squared distance along the row from x to the nearest occupied voxel (-1: none)
+__device__ __forceinline__ int row_g_occ(const int32_t *r, int x)
+{
+    const int cnt = r[0];
+    if (cnt == 0)
+        return -1;
+    int d = 1 << 20;
+    for (int i = 1; i <= cnt; ++i) {
+        const int a = r[i] >> 16, b = r[i] & 0xFFFF;
+        const int di = x < a ? a - x : (x > b ? x - b : 0);
+        d = min(d, di);
+    }
+    return d * d;
+}
+
+// squared distance along the row from an occupied x to the nearest free voxel
+// (-1: the whole row is occupied); runs are maximal, so the neighbours of the
+// run holding x are free
+__device__ __forceinline__ int row_g_free(const int32_t *r, int x, int nx)
+{
+    const int cnt = r[0];
+    for (int i = 1; i <= cnt; ++i) {
+        const int a = r[i] >> 16, b = r[i] & 0xFFFF;
+        if (x >= a && x <= b) {
+            int d = 1 << 20;
+            if (a - 1 >= 0)
+                d = x - a + 1;
+            if (b + 1 <= nx - 1)
+                d = min(d, b - x + 1);
+            return d == (1 << 20) ? -1 : d * d;
+        }
+    }
+    return 0;
+}
+
+__global__ void __launch_bounds__(128)
+    k_dyn_xy(const __grid_constant__ CapBatch caps, int H, int nx, int ny, int zlo, int S, int t0, int cap,
+             int32_t *__restrict__ dyn_mid)
+{
+    extern __shared__ __align__(16) int32_t sm[];
+    __shared__ int s_ylo, s_yhi;
+    const int s = blockIdx.x, tl = blockIdx.y, z = zlo + s;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int rw = H + 1;
+    int32_t *rows = sm;
+    uint32_t *stk = reinterpret_cast<uint32_t *>(sm + ny * rw) + tid;  // entry q at stk[q * nthr]
+    if (tid == 0) {
+        s_ylo = ny;
+        s_yhi = -1;
+    }
+    __syncthreads();
+
+    // rows: merged occupied runs of every capsule crossing this slice
+    for (int y = tid; y < ny; y += nthr) {
+        int32_t *r = rows + y * rw;
+        int cnt = 0;
+        for (int h = 0; h < H; ++h) {
+            const CapInfo &ci = caps.caps[tl * H + h];
+            if (ci.lo[0] > ci.hi[0] || z < ci.lo[2] || z > ci.hi[2] || y < ci.lo[1] || y > ci.hi[1])
+                continue;
+            // the capsule is convex, so its voxels on this row form one run
+            int xa = -1, xb = -2;
+            for (int x = ci.lo[0]; x <= ci.hi[0]; ++x) {
+                if (capsule_contains(ci, x, y, z)) {
+                    if (xa < 0)
+                        xa = x;
+                    xb = x;
+                } else if (xa >= 0) {
+                    break;
+                }
+            }
+            if (xa < 0)
+                continue;
+            int i = cnt;
+            while (i > 0 && (r[i] >> 16) > xa) {
+                r[i + 1] = r[i];
+                --i;
+            }
+            r[i + 1] = (xa << 16) | xb;
+            ++cnt;
+        }
+        int m = 0;  // merge overlapping or touching runs
+        for (int i = 1; i <= cnt; ++i) {
+            const int a = r[i] >> 16, b = r[i] & 0xFFFF;
+            if (m > 0 && a <= (r[m] & 0xFFFF) + 1) {
+                if (b > (r[m] & 0xFFFF))
+                    r[m] = (r[m] & ~0xFFFF) | b;
+            } else {
+                r[++m] = r[i];
+            }
+        }
+        r[0] = m;
+        if (m) {
+            atomicMin(&s_ylo, y);
+            atomicMax(&s_yhi, y);
+        }
+    }
+    __syncthreads();
+    const int ylo = s_ylo, yhi = s_yhi;
+    const int t = t0 + tl;
+    const long long V2 = (long long)nx * ny;
+
+    for (int x = tid; x < nx; x += nthr) {
+        int32_t *oc = dyn_mid + ((long long)t * S + s) * V2 + x;  // element y at oc[y * nx]
+        if (yhi < 0) {
+            for (int y = 0; y < ny; ++y)
+                oc[(long long)y * nx] = kInf32;
+            continue;
+        }
+        int fo = ny, lo_ = -1;  // first / last occupied row of this column
+        for (int y = ylo; y <= yhi; ++y)
+            if (row_inside(rows + y * rw, x)) {
+                if (fo == ny)
+                    fo = y;
+                lo_ = y;
+            }
+
+        // distances to free voxels at the occupied voxels (set F).  Free rows
+        // matter only next to an occupied row: the nearest free voxel of any
+        // occupied voxel is the first free row out of its run.
+        if (lo_ >= 0) {
+            const int y0 = max(fo - 1, 0), y1 = min(lo_ + 1, ny - 1);
+            int top = -1, s0 = 0, g0 = 0, s1 = 0, g1 = 0;
+            bool prev_occ = false;  // y0 - 1 lies before the first occupied row
+            bool cur_occ = y0 >= ylo && y0 <= yhi && row_inside(rows + y0 * rw, x);
+            for (int y = y0; y <= y1; ++y) {
+                const bool next_occ = y + 1 <= y1 && y + 1 >= ylo && y + 1 <= yhi && row_inside(rows + (y + 1) * rw, x);
+                int g;
+                if (cur_occ)
+                    g = row_g_free(rows + y * rw, x, nx);
+                else
+                    g = (prev_occ || next_occ) ? 0 : -1;
+                prev_occ = cur_occ;
+                cur_occ = next_occ;
+                if (g < 0)
+                    continue;
+                while (top >= 1 && dominated(s0, g0, s1, g1, y, g)) {
+                    --top;
+                    s1 = s0;
+                    g1 = g0;
+                    if (top >= 1) {
+                        const uint32_t w = stk[(top - 1) * nthr];
+                        s0 = site_of(w);
+                        g0 = gval_of(w);
+                    }
+                }
+                ++top;
+                stk[top * nthr] = pack_site(y, g);
+                s0 = s1;
+                g0 = g1;
+                s1 = y;
+                g1 = g;
+            }
+            int q = 0, sc = 0, gc = 0;
+            if (top >= 0) {
+                const uint32_t w = stk[0];
+                sc = site_of(w);
+                gc = gval_of(w);
+            }
+            for (int y = fo; y <= lo_; ++y) {
+                if (!row_inside(rows + y * rw, x))
+                    continue;
+                int32_t r = -kInf32;
+                if (top >= 0) {
+                    int fc = parab(y, sc, gc);
+                    while (q < top) {
+                        const uint32_t w = stk[(q + 1) * nthr];
+                        const int fn = parab(y, site_of(w), gval_of(w));
+                        if (fn > fc)
+                            break;
+                        ++q;
+                        sc = site_of(w);
+                        gc = gval_of(w);
+                        fc = fn;
+                    }
+                    r = -fc;
+                }
+                oc[(long long)y * nx] = r;
+            }
+        }
+
+        // distances to occupied voxels at the free voxels (set O): sites are
+        // the rows holding a run (g = 0 where x is inside one)
+        int top = -1, s0 = 0, g0 = 0, s1 = 0, g1 = 0;
+        for (int y = ylo; y <= yhi; ++y) {
+            const int g = row_g_occ(rows + y * rw, x);
+            if (g < 0)
+                continue;
+            while (top >= 1 && dominated(s0, g0, s1, g1, y, g)) {
+                --top;
+                s1 = s0;
+                g1 = g0;
+                if (top >= 1) {
+                    const uint32_t w = stk[(top - 1) * nthr];
+                    s0 = site_of(w);
+                    g0 = gval_of(w);
+                }
+            }
+            ++top;
+            stk[top * nthr] = pack_site(y, g);
+            s0 = s1;
+            g0 = g1;
+            s1 = y;
+            g1 = g;
+        }
+        int q = 0, sc = 0, gc = 0;
+        {
+            const uint32_t w = stk[0];  // top >= 0: some row of [ylo, yhi] holds a run
+            sc = site_of(w);
+            gc = gval_of(w);
+        }
+        for (int y = 0; y < ny; ++y) {
+            if (y >= fo && y <= lo_ && row_inside(rows + y * rw, x))
+                continue;
+            int fc = parab(y, sc, gc);
+            while (q < top) {
+                const uint32_t w = stk[(q + 1) * nthr];
+                const int fn = parab(y, site_of(w), gval_of(w));
+                if (fn > fc)
+                    break;
+                ++q;
+                sc = site_of(w);
+                gc = gval_of(w);
+                fc = fn;
+            }
+            oc[(long long)y * nx] = fc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_composite_z
+// ---------------------------------------------------------------------------
+
+// Forward cursor over an envelope stack in shared memory ([entry][thread]);
+// the current and the next site are kept in registers.
+struct Cursor {
+    const uint32_t *stk;
+    int nthr, top, q;
+    int s, g, sn, gn;
+    __device__ __forceinline__ Cursor(const uint32_t *stk_, int nthr_, int top_) : stk(stk_), nthr(nthr_), top(top_), q(0)
+    {
+        s = g = sn = gn = 0;
+        if (top >= 0) {
+            s = site_of(stk[0]);
+            g = gval_of(stk[0]);
+        }
+        if (top >= 1) {
+            sn = site_of(stk[nthr]);
+            gn = gval_of(stk[nthr]);
+        }
+    }
+    // min over the envelope at z (z non-decreasing between calls); -1 if empty
+    __device__ __forceinline__ int eval(int z)
+    {
+        if (top < 0)
+            return -1;
+        int fc = parab(z, s, g);
+        while (q < top) {
+            const int fn = parab(z, sn, gn);
+            if (fn > fc)
+                break;
+            ++q;
+            s = sn;
+            g = gn;
+            fc = fn;
+            if (q < top) {
+                const uint32_t w = stk[(q + 1) * nthr];
+                sn = site_of(w);
+                gn = gval_of(w);
+            }
+        }
+        return fc;
+    }
+};
+
+// sign(S) sqrt(|S|) vox with the infinities, branch-free apart from the select
+__device__ __forceinline__ float sq_to_sdf_fast(int32_t v, float vox)
+{
+    const int32_t a = v < 0 ? -v : v;
+    float m = __fmul_rn(__fsqrt_rn(__int2float_rn(a)), vox);
+    m = a == kInf32 ? __int_as_float(0x7f800000) : m;
+    return __int_as_float(__float_as_int(m) | (v & (int32_t)0x80000000));
+}
+
+template <bool kCheck>
+__device__ __forceinline__ void emit_one(int z, int32_t sv, Cursor &O, Cursor &F, const uint32_t *mk, int zlo,
+                                         int nthr, int32_t *ocol, float *fcol, long long o, float vox)
+{
+    bool occz = false;
+    if (kCheck) {
+        const int e = z - zlo;
+        occz = (mk[(e >> 5) * nthr] >> (e & 31)) & 1u;
+    }
+    int32_t d;
+    if (occz) {
+        const int f = F.eval(z);
+        d = f < 0 ? -kInf32 : -f;
+    } else {
+        const int f = O.eval(z);
+        d = f < 0 ? kInf32 : f;
+    }
+    const int32_t cv = min(sv, d);
+    if (ocol)
+        __stcs(ocol + o, cv);
+    if (fcol)
+        __stcs(fcol + o, sq_to_sdf_fast(cv, vox));
+}
+
+template <bool kCheck>
+__device__ __forceinline__ void emit_range(int z0, int z1, Cursor &O, Cursor &F, const uint32_t *mk, int zlo,
+                                           int nthr, const int32_t *scol, long long V2, int32_t *ocol, float *fcol,
+                                           float vox)
+{
+    int z = z0;
+    for (; z + 8 <= z1; z += 8) {
+        int32_t sv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            sv[i] = __ldg(scol + (long long)(z + i) * V2);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            emit_one<kCheck>(z + i, sv[i], O, F, mk, zlo, nthr, ocol, fcol, (long long)(z + i) * V2, vox);
+    }
+    for (; z < z1; ++z)
+        emit_one<kCheck>(z, __ldg(scol + (long long)z * V2), O, F, mk, zlo, nthr, ocol, fcol, (long long)z * V2,
+                         vox);
+}
+
+// Shared memory per thread, [entry][thread]: the staged slab column (S words,
+// reused in place as the set-O stack), the set-F stack (S + 2 words) and the
+// occupancy bits of the slab column.
+__global__ void k_composite_z(const int32_t *__restrict__ static_sq, const int32_t *__restrict__ dyn_mid, int nx,
+                              int ny, int nz, int zlo, int S, int T, int32_t *__restrict__ comp_sq,
+                              float *__restrict__ comp_sdf, float vox)
+{
+    extern __shared__ uint32_t smem[];
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const long long V2 = (long long)nx * ny;
+    const int t = blockIdx.x % T;
+    const long long c0 = (long long)(blockIdx.x / T) * nthr;
+    const long long c = c0 + tid;
+    const bool live = c < V2;
+    uint32_t *tile = smem + tid;
+    uint32_t *sF = smem + (size_t)S * nthr + tid;
+    uint32_t *mk = smem + (size_t)(2 * S + 2) * nthr + tid;
+    const int nw = (S + 31) >> 5;
+
+    // stage the slab column: S independent coalesced loads per thread
+    if (live) {
+        const int32_t *dcol = dyn_mid + (long long)t * S * V2 + c;
+#pragma unroll 8
+        for (int e = 0; e < S; ++e)
+            tile[e * nthr] = (uint32_t)__ldcs(dcol + (long long)e * V2);
+    }
+    if (!live)
+        return;
+
+    int firstOcc = S, lastOcc = -1;
+    for (int w = 0; w < nw; ++w) {
+        uint32_t bits = 0;
+        const int e0 = w << 5, cnt = min(32, S - e0);
+        for (int bI = 0; bI < cnt; ++bI)
+            bits |= (uint32_t)((int32_t)tile[(e0 + bI) * nthr] < 0) << bI;
+        mk[w * nthr] = bits;
+        if (bits) {
+            if (firstOcc == S)
+                firstOcc = e0 + __ffs(bits) - 1;
+            lastOcc = e0 + 31 - __clz(bits);
+        }
+    }
+
+    // set F around the occupied run (before the tile is overwritten)
+    int topF = -1;
+    const int zo0 = zlo + firstOcc, zo1 = zlo + lastOcc;  // empty if lastOcc < 0
+    if (lastOcc >= 0) {
+        int a0 = 0, b0 = 0, a1 = 0, b1 = 0;
+        const int zr0 = max(zo0 - 1, 0), zr1 = min(zo1 + 1, nz - 1);
+        for (int z = zr0; z <= zr1; ++z) {
+            int g = 0;
+            const int e = z - zlo;
+            if (e >= 0 && e < S && ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u)) {
+                const int32_t v = (int32_t)tile[e * nthr];
+                g = v == -kInf32 ? -1 : -v;
+            }
+            if (g < 0)
+                continue;
+            while (topF >= 1 && dominated(a0, b0, a1, b1, z, g)) {
+                --topF;
+                a1 = a0;
+                b1 = b0;
+                if (topF >= 1) {
+                    const uint32_t x = sF[(topF - 1) * nthr];
+                    a0 = site_of(x);
+                    b0 = gval_of(x);
+                }
+            }
+            ++topF;
+            sF[topF * nthr] = pack_site(z, g);
+            a0 = a1;
+            b0 = b1;
+            a1 = z;
+            b1 = g;
+        }
+    }
+
+    // set O over the slab, built in place over the staged column: the entry
+    // written at step e lands in a slot <= e that has already been read
+    int topO = -1;
+    {
+        int a0 = 0, b0 = 0, a1 = 0, b1 = 0;
+        for (int e = 0; e < S; ++e) {
+            const int32_t v = (int32_t)tile[e * nthr];
+            const int g = v < 0 ? 0 : (v == kInf32 ? -1 : v);
+            if (g < 0)
+                continue;
+            const int z = zlo + e;
+            while (topO >= 1 && dominated(a0, b0, a1, b1, z, g)) {
+                --topO;
+                a1 = a0;
+                b1 = b0;
+                if (topO >= 1) {
+                    const uint32_t x = tile[(topO - 1) * nthr];
+                    a0 = site_of(x);
+                    b0 = gval_of(x);
+                }
+            }
+            ++topO;
+            tile[topO * nthr] = pack_site(z, g);
+            a0 = a1;
+            b0 = b1;
+            a1 = z;
+            b1 = g;
+        }
+    }
+
+    Cursor O(tile, nthr, topO), F(sF, nthr, topF);
+    const long long V = V2 * nz;
+    const int32_t *scol = static_sq + c;
+    int32_t *ocol = comp_sq ? comp_sq + (long long)t * V + c : nullptr;
+    float *fcol = comp_sdf ? comp_sdf + (long long)t * V + c : nullptr;
+    // z below and above the occupied run need no occupancy test
+    const int za = lastOcc >= 0 ? zo0 : nz, zb = lastOcc >= 0 ? zo1 + 1 : nz;
+    emit_range<false>(0, za, O, F, mk, zlo, nthr, scol, V2, ocol, fcol, vox);
+    emit_range<true>(za, zb, O, F, mk, zlo, nthr, scol, V2, ocol, fcol, vox);
+    emit_range<false>(zb, nz, O, F, mk, zlo, nthr, scol, V2, ocol, fcol, vox);
+}
+
+__global__ void k_broadcast_static(const int32_t *__restrict__ static_sq, long long V, int T,
+                                   int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
+        const int32_t s = __ldg(static_sq + v);
+        const float f = sq_to_sdf(s, vox);
+        for (int t = 0; t < T; ++t) {
+            if (comp_sq)
+                __stcs(comp_sq + (long long)t * V + v, s);
+            if (comp_sdf)
+                __stcs(comp_sdf + (long long)t * V + v, f);
+        }
+    }
+}
+
+constexpr int kDynThreads = 128;
+
+size_t dyn_xy_smem(int ny, int H, int cap) { return ((size_t)ny * (H + 1) + (size_t)cap * kDynThreads) * 4; }
+
+}  // namespace
+
+bool dyn_xy_fits(int ny, int H, int cap) { return dyn_xy_smem(ny, H, cap) <= 200 * 1024; }
+
+cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, int S, int t0, int n_t, int cap,
+                          int32_t *dyn_mid, cudaStream_t stream)
+{
+    if (S <= 0 || n_t <= 0)
+        return cudaSuccess;
+    const size_t smem = dyn_xy_smem(ny, H, cap);
+    cudaError_t e = cudaFuncSetAttribute(k_dyn_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_dyn_xy<<<dim3((unsigned)S, (unsigned)n_t), kDynThreads, smem, stream>>>(*caps, H, nx, ny, zlo, S, t0, cap,
+                                                                               dyn_mid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_z(const int32_t *static_sq, const int32_t *dyn_mid, int nx, int ny, int nz, int zlo,
+                               int S, int T, int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream)
+{
+    const long long V2 = (long long)nx * ny;
+    const int words = 2 * S + 2 + (S + 31) / 32;
+    int nthr = 128;
+    while (nthr > 32 && (size_t)nthr * words * sizeof(uint32_t) > 200 * 1024)
+        nthr >>= 1;
+    const size_t smem = (size_t)nthr * words * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_composite_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    const long long nblk = (V2 + nthr - 1) / nthr * T;
+    k_composite_z<<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, dyn_mid, nx, ny, nz, zlo, S, T, comp_sq,
+                                                          comp_sdf, vox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_broadcast_static(const int32_t *static_sq, long long V, int T, int32_t *comp_sq,
+                                    float *comp_sdf, float vox, cudaStream_t stream)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long nblk = (V + 255) / 256;
+    if (nblk > (long long)sms * 8)
+        nblk = (long long)sms * 8;
+    k_broadcast_static<<<(unsigned)nblk, 256, 0, stream>>>(static_sq, V, T, comp_sq, comp_sdf, vox);
+    return cudaGetLastError();
+}
+
+}  // namespace pcdf

@@ -1,0 +1,67 @@
+// Device helpers shared by the distance-transform kernels.
+//
+// Lower envelopes: the squared distance along one axis to a set of sites i
+// with partial squared distances g(i) is min_i (x - i)^2 + g(i), the lower
+// envelope of equal-curvature parabolas.  Envelopes are kept as stacks of
+// packed words (site << 22 | g): sites are below 512 and g below 2^22 for
+// every grid this library accepts, and all products below stay under 2^31.
+#pragma once
+
+#include "pcdf_internal.cuh"
+
+namespace pcdf {
+
+constexpr uint32_t kG22 = (1u << 22) - 1;
+
+__device__ __forceinline__ uint32_t pack_site(int s, int g) { return ((uint32_t)s << 22) | (uint32_t)g; }
+__device__ __forceinline__ int site_of(uint32_t w) { return (int)(w >> 22); }
+__device__ __forceinline__ int gval_of(uint32_t w) { return (int)(w & kG22); }
+__device__ __forceinline__ int parab(int x, int s, int g) { return (x - s) * (x - s) + g; }
+
+// With sites s0 < s1 < s2, s1 is nowhere strictly below both neighbours iff
+// the parabola of s2 overtakes s1 no later than s1 overtakes s0.  The two
+// abscissae are the fractions (f1 - f0) / 2(s1 - s0) and (f2 - f1) / 2(s2 - s1)
+// with f = s^2 + g; they are compared by cross-multiplication (positive
+// denominators), so the test is exact.
+__device__ __forceinline__ bool dominated(int s0, int g0, int s1, int g1, int s2, int g2)
+{
+    const int f0 = s0 * s0 + g0, f1 = s1 * s1 + g1, f2 = s2 * s2 + g2;
+    return (f2 - f1) * (s1 - s0) <= (f1 - f0) * (s2 - s1);
+}
+
+// Is the centre of voxel (i, j, k), 16 * (i, j, k) + 8 in fixed point, inside
+// the closed capsule?  Squared distance to the segment against r^2 without
+// rounding: with s = (p-a).(b-a) and L = |b-a|^2 the nearest point is a
+// (s <= 0), b (s >= L) or interior, where |p-a|^2 L - s^2 <= r^2 L.
+__device__ __forceinline__ bool capsule_contains(const CapInfo &c, int i, int j, int k)
+{
+    const long long px = 16LL * i + 8, py = 16LL * j + 8, pz = 16LL * k + 8;
+    const long long wx = px - c.a[0], wy = py - c.a[1], wz = pz - c.a[2];
+    const long long dx = (long long)c.b[0] - c.a[0], dy = (long long)c.b[1] - c.a[1],
+                    dz = (long long)c.b[2] - c.a[2];
+    const long long L = dx * dx + dy * dy + dz * dz;
+    const long long s = wx * dx + wy * dy + wz * dz;
+    const long long r2 = (long long)c.r * c.r;
+    if (L == 0 || s <= 0)
+        return wx * wx + wy * wy + wz * wz <= r2;
+    if (s >= L) {
+        const long long ex = px - c.b[0], ey = py - c.b[1], ez = pz - c.b[2];
+        return ex * ex + ey * ey + ez * ez <= r2;
+    }
+    return (wx * wx + wy * wy + wz * wz) * L - s * s <= r2 * L;
+}
+
+// sign(S) * sqrt(|S|) * vox, IEEE round-to-nearest square root and product;
+// +/-kInf32 -> +/-inf.  |S| < 2^24, so the int -> float conversion is exact.
+__device__ __forceinline__ float sq_to_sdf(int32_t s, float vox)
+{
+    if (s == kInf32)
+        return __int_as_float(0x7f800000);
+    if (s == -kInf32)
+        return __int_as_float(0xff800000);
+    const int32_t a = s < 0 ? -s : s;
+    const float m = __fmul_rn(__fsqrt_rn(__int2float_rn(a)), vox);
+    return s < 0 ? -m : m;
+}
+
+}  // namespace pcdf

@@ -60,6 +60,14 @@ cudaError_t launch_envelope_i16(const int16_t *in, int32_t *out, int n, int nx, 
 cudaError_t launch_envelope_i32(const int32_t *in, int32_t *out, float *sdf, float vox, int n, int nx,
                                 long long ncols, long long outer_stride, long long stride, cudaStream_t stream);
 
+// Analytic x+y passes of the capsule field over the slab slices zlo .. zlo+S-1
+// for t = t0 .. t0 + n_t - 1 (capsules of local t at caps->caps[t * H ...]);
+// output dyn_mid[t][s][y][x], signed 2-D partial squared distances.  `cap` is
+// the per-thread stack capacity; dyn_xy_fits tells whether it fits on chip.
+bool dyn_xy_fits(int ny, int H, int cap);
+cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, int S, int t0, int n_t, int cap,
+                          int32_t *dyn_mid, cudaStream_t stream);
+
 // z-pass of the dynamic field over the slab [zlo, zlo + S) fused with the
 // composite min against static_sq and the float epilogue, for all T.
 cudaError_t launch_composite_z(const int32_t *static_sq, const int32_t *dyn_mid, int nx, int ny, int nz, int zlo,
