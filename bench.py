@@ -258,7 +258,7 @@ def run_native(args):
         pcdf.composite_prepare(grid, caps, ws)
         if z_events:
             z_events[0].record(stream)
-        pcdf.composite_finish(static_sq, grid, caps, ws, comp_sq, comp_sdf)
+        pcdf.composite_finish(static_sq, grid, caps, ws, comp_sq, comp_sdf, static_sdf=static_sdf)
         if z_events:
             z_events[1].record(stream)
 
@@ -310,7 +310,7 @@ def run_native(args):
     # composite stage alone and the from-scratch comparator (same inputs)
     def comp_only(_=None):
         pcdf.composite_prepare(grid, caps, ws)
-        pcdf.composite_finish(static_sq, grid, caps, ws, comp_sq, comp_sdf)
+        pcdf.composite_finish(static_sq, grid, caps, ws, comp_sq, comp_sdf, static_sdf=static_sdf)
 
     ws_scr = None
 
@@ -327,7 +327,7 @@ def run_native(args):
     # roofline of the dominant kernel: the fused z pass (reads static_sq and
     # the dynamic slab intermediate, writes T int32 + T fp32 fields)
     _, S = pcdf.composite_slab(grid, caps)
-    z_bytes = 4 * V + 4 * T * S * grid.nx * grid.ny + 8 * T * V
+    z_bytes = 8 * V + 4 * T * S * grid.nx * grid.ny + 8 * T * V  # static int32 + fp32 in, slab in, T fields out
     z_avg_ms = float(np.mean(z_ms))
     peak, peak_kind = measured_peaks()
     achieved = z_bytes / (z_avg_ms * 1e-3) / 1e9
@@ -366,7 +366,8 @@ def run_native(args):
     def e2e_step(_=None):
         occ_d.copy_(occ_h, non_blocking=True)
         pcdf.build_static_sdf(occ_d, grid, out_sq=static_sq, out_sdf=static_sdf)
-        pcdf.build_predicted_composite(static_sq, grid, caps, out_sq=comp_sq, out_sdf=comp_sdf)
+        pcdf.build_predicted_composite(static_sq, grid, caps, out_sq=comp_sq, out_sdf=comp_sdf,
+                                       static_sdf=static_sdf)
         out_h.copy_(comp_sdf, non_blocking=True)
 
     e2e_step()
@@ -423,9 +424,9 @@ def run_profile_case(args):
     occ = torch.from_numpy(sc["occ"]).to(dev)
     for _ in range(2):
         if args.profile_case in ("static", "composite"):
-            static_sq, _ = pcdf.build_static_sdf(occ, grid)
+            static_sq, static_sdf = pcdf.build_static_sdf(occ, grid)
         if args.profile_case == "composite":
-            pcdf.build_predicted_composite(static_sq, grid, caps)
+            pcdf.build_predicted_composite(static_sq, grid, caps, static_sdf=static_sdf)
         if args.profile_case == "scratch":
             pcdf.build_from_scratch(occ, grid, caps)
         if args.profile_case == "query":

@@ -105,6 +105,11 @@ int pcdf_build_static_sdf(const pcdf_grid *grid, const uint8_t *occ, int32_t *st
  * is the signed squared EDT of the voxels inside any of the H capsules at t.
  *
  * static_sq  device int32 [nz][ny][nx] (from pcdf_build_static_sdf).
+ * static_sdf device fp32 [nz][ny][nx] or NULL: the float field that
+ *            pcdf_build_static_sdf produced with static_sq.  When given, the
+ *            float output copies it wherever the static field wins the min
+ *            instead of recomputing the square root (same bits either way; a
+ *            float field that does not belong to static_sq gives wrong output).
  * caps       HOST int32 [T][H][7] capsules (see conventions); may be NULL iff
  *            H == 0 (then every comp[t] equals the static field).
  * comp_sq    device int32 [T][nz][ny][nx] or NULL.
@@ -114,9 +119,9 @@ int pcdf_build_static_sdf(const pcdf_grid *grid, const uint8_t *occ, int32_t *st
  * ------------------------------------------------------------------------- */
 int pcdf_composite_workspace_bytes(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps,
                                    size_t *bytes);
-int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_sq, int32_t T, int32_t H,
-                                   const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
-                                   size_t workspace_bytes, void *stream);
+int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
+                                   int32_t T, int32_t H, const int32_t *caps, int32_t *comp_sq, float *comp_sdf,
+                                   void *workspace, size_t workspace_bytes, void *stream);
 
 /* The z-slab [zlo, zlo + S) of voxel slices that some capsule of some t
  * touches (S = 0: no capsule touches the grid).  The dynamic field's sites all
@@ -131,8 +136,8 @@ int pcdf_composite_slab(const pcdf_grid *grid, int32_t T, int32_t H, const int32
  *   finish:  the fused z pass, composite min and float epilogue for every t. */
 int pcdf_composite_prepare(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, void *workspace,
                            size_t workspace_bytes, void *stream);
-int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, int32_t T, int32_t H,
-                          const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
+int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int32_t T,
+                          int32_t H, const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
                           size_t workspace_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------

@@ -41,10 +41,10 @@ def _declare(lib):
         "pcdf_static_workspace_bytes": [G, SZP],
         "pcdf_build_static_sdf": [G, P, P, P, P, SZ, P],
         "pcdf_composite_workspace_bytes": [G, I32, I32, P, SZP],
-        "pcdf_build_predicted_composite": [G, P, I32, I32, P, P, P, P, SZ, P],
+        "pcdf_build_predicted_composite": [G, P, P, I32, I32, P, P, P, P, SZ, P],
         "pcdf_composite_prepare": [G, I32, I32, P, P, SZ, P],
         "pcdf_composite_slab": [G, I32, I32, P, ctypes.POINTER(I32), ctypes.POINTER(I32)],
-        "pcdf_composite_finish": [G, P, I32, I32, P, P, P, P, SZ, P],
+        "pcdf_composite_finish": [G, P, P, I32, I32, P, P, P, P, SZ, P],
         "pcdf_scratch_workspace_bytes": [G, I32, I32, SZP],
         "pcdf_build_from_scratch": [G, P, I32, I32, P, P, P, P, SZ, P],
         "pcdf_query_cost": [G, P, I32, P, P, I64, F32, P, P, P],

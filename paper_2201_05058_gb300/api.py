@@ -113,13 +113,17 @@ def build_static_sdf(occ: torch.Tensor, grid, want_sdf: bool = True, out_sq=None
 
 
 def build_predicted_composite(static_sq: torch.Tensor, grid, caps, want_sq: bool = True, want_sdf: bool = True,
-                              out_sq=None, out_sdf=None):
+                              out_sq=None, out_sdf=None, static_sdf=None):
     """Composite fields comp[t] = min(static, capsules at t) for t < T (Sec. 6, 8).
 
-    static_sq: CUDA int32 [nz, ny, nx]; caps: host int32 [T][H][7] fixed point.
-    Returns (comp_sq int32 [T, nz, ny, nx] or None, comp_sdf fp32 or None)."""
+    static_sq: CUDA int32 [nz, ny, nx]; caps: host int32 [T][H][7] fixed point;
+    static_sdf: optional float field built with static_sq (reused where the
+    static field wins).  Returns (comp_sq int32 [T, nz, ny, nx] or None,
+    comp_sdf fp32 or None)."""
     shp = _shape(grid)
     _need(static_sq, "static_sq", torch.int32, shp)
+    if static_sdf is not None:
+        _need(static_sdf, "static_sdf", torch.float32, shp)
     caps = _caps_host(caps)
     T, H = int(caps.shape[0]), int(caps.shape[1])
     dev = static_sq.device
@@ -137,7 +141,8 @@ def build_predicted_composite(static_sq: torch.Tensor, grid, caps, want_sq: bool
         sdf = out_sdf if out_sdf is not None else torch.empty((T,) + shp, dtype=torch.float32, device=dev)
         _need(sdf, "comp_sdf", torch.float32, (T,) + shp)
     ws = _workspace(nbytes.value, dev)
-    _lib.check(lib.pcdf_build_predicted_composite(ctypes.byref(g), _ptr(static_sq), T, H, cp, _ptr(sq), _ptr(sdf),
+    _lib.check(lib.pcdf_build_predicted_composite(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), T, H, cp,
+                                                  _ptr(sq), _ptr(sdf),
                                                   _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(dev))),
                "pcdf_build_predicted_composite")
     return sq, sdf
@@ -179,12 +184,14 @@ def composite_prepare(grid, caps, workspace: torch.Tensor):
                "pcdf_composite_prepare")
 
 
-def composite_finish(static_sq, grid, caps, workspace: torch.Tensor, comp_sq=None, comp_sdf=None):
+def composite_finish(static_sq, grid, caps, workspace: torch.Tensor, comp_sq=None, comp_sdf=None, static_sdf=None):
     """Second stage: fused z pass + composite min + float epilogue into the given outputs."""
     shp = _shape(grid)
     caps = _caps_host(caps)
     T, H = int(caps.shape[0]), int(caps.shape[1])
     _need(static_sq, "static_sq", torch.int32, shp)
+    if static_sdf is not None:
+        _need(static_sdf, "static_sdf", torch.float32, shp)
     _need(workspace, "workspace", torch.uint8)
     if comp_sq is not None:
         _need(comp_sq, "comp_sq", torch.int32, (T,) + shp)
@@ -192,7 +199,8 @@ def composite_finish(static_sq, grid, caps, workspace: torch.Tensor, comp_sq=Non
         _need(comp_sdf, "comp_sdf", torch.float32, (T,) + shp)
     g = _cgrid(grid)
     cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
-    _lib.check(_lib.load().pcdf_composite_finish(ctypes.byref(g), _ptr(static_sq), T, H, cp, _ptr(comp_sq),
+    _lib.check(_lib.load().pcdf_composite_finish(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), T, H, cp,
+                                                 _ptr(comp_sq),
                                                  _ptr(comp_sdf), _ptr(workspace), workspace.numel(),
                                                  ctypes.c_void_p(_stream(static_sq.device))),
                "pcdf_composite_finish")

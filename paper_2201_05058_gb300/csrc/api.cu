@@ -241,8 +241,8 @@ int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "dynamic y pass");
 }
 
-int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, int T, const CompositePlan &p,
-                     int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st)
+int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int T,
+                     const CompositePlan &p, int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st)
 {
     cudaError_t e;
     if (p.S == 0) {
@@ -250,7 +250,7 @@ int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, int T, con
         return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "broadcast");
     }
     const int32_t *mid = plan_mid(p, workspace);
-    e = pcdf::launch_composite_z(static_sq, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, T, comp_sq, comp_sdf,
+    e = pcdf::launch_composite_z(static_sq, static_sdf, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, T, comp_sq, comp_sdf,
                                  grid->vox, st);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "composite z pass");
 }
@@ -313,9 +313,9 @@ int pcdf_composite_slab(const pcdf_grid *grid, int32_t T, int32_t H, const int32
     return PCDF_OK;
 }
 
-int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_sq, int32_t T, int32_t H,
-                                   const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
-                                   size_t workspace_bytes, void *stream)
+int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
+                                   int32_t T, int32_t H, const int32_t *caps, int32_t *comp_sq, float *comp_sdf,
+                                   void *workspace, size_t workspace_bytes, void *stream)
 {
     CompositePlan p;
     if (int rc = plan_composite(grid, T, H, caps, p))
@@ -326,7 +326,7 @@ int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_
         return rc;
     if (int rc = composite_prepare(grid, T, H, p, workspace, (cudaStream_t)stream))
         return rc;
-    return composite_finish(grid, static_sq, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
+    return composite_finish(grid, static_sq, static_sdf, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
 }
 
 int pcdf_composite_prepare(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, void *workspace,
@@ -340,8 +340,8 @@ int pcdf_composite_prepare(const pcdf_grid *grid, int32_t T, int32_t H, const in
     return composite_prepare(grid, T, H, p, workspace, (cudaStream_t)stream);
 }
 
-int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, int32_t T, int32_t H,
-                          const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
+int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int32_t T,
+                          int32_t H, const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
                           size_t workspace_bytes, void *stream)
 {
     CompositePlan p;
@@ -351,7 +351,7 @@ int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, int32
         return fail(PCDF_EINVAL, "static_sq and at least one output must be non-NULL");
     if (int rc = check_ws(p, workspace, workspace_bytes))
         return rc;
-    return composite_finish(grid, static_sq, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
+    return composite_finish(grid, static_sq, static_sdf, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
 }
 
 int pcdf_scratch_workspace_bytes(const pcdf_grid *grid, int32_t T, int32_t H, size_t *bytes)

@@ -270,137 +270,104 @@ __global__ void __launch_bounds__(128)
 // ---------------------------------------------------------------------------
 // k_composite_z
 // ---------------------------------------------------------------------------
+// Shared memory per thread, [slot][thread]: slots 1..S hold the staged slab
+// column (slab element e in slot e + 1); slot 0 and slot S + 1 give the
+// in-place stacks room for the sites just below and above the slab; then the
+// occupancy bits of the slab column.
+//
+// Set F (distance to free voxels, output at the voxels inside a human) runs
+// first, in place over the staged column, and writes its outputs directly;
+// the column is then reloaded and set O (distance to the humans, output
+// everywhere else) is built in place and walked along z.  Where the static
+// field is nearer than the humans the float output is the static float field
+// itself (same value, no square root).
 
-// Forward cursor over an envelope stack in shared memory ([entry][thread]);
-// the current and the next site are kept in registers.
-struct Cursor {
-    const uint32_t *stk;
-    int nthr, top, q;
-    int s, g, sn, gn;
-    __device__ __forceinline__ Cursor(const uint32_t *stk_, int nthr_, int top_) : stk(stk_), nthr(nthr_), top(top_), q(0)
-    {
-        s = g = sn = gn = 0;
-        if (top >= 0) {
-            s = site_of(stk[0]);
-            g = gval_of(stk[0]);
-        }
-        if (top >= 1) {
-            sn = site_of(stk[nthr]);
-            gn = gval_of(stk[nthr]);
-        }
-    }
-    // min over the envelope at z (z non-decreasing between calls); -1 if empty
-    __device__ __forceinline__ int eval(int z)
-    {
-        if (top < 0)
-            return -1;
-        int fc = parab(z, s, g);
-        while (q < top) {
-            const int fn = parab(z, sn, gn);
-            if (fn > fc)
-                break;
-            ++q;
-            s = sn;
-            g = gn;
-            fc = fn;
-            if (q < top) {
-                const uint32_t w = stk[(q + 1) * nthr];
-                sn = site_of(w);
-                gn = gval_of(w);
-            }
-        }
-        return fc;
-    }
-};
-
-// sign(S) sqrt(|S|) vox with the infinities, branch-free apart from the select
-__device__ __forceinline__ float sq_to_sdf_fast(int32_t v, float vox)
+template <bool kStaticSdf>
+__device__ __forceinline__ void emit_one(int z, int32_t sv, float sf, int d, int32_t *ocol, float *fcol, long long o,
+                                         float vox)
 {
-    const int32_t a = v < 0 ? -v : v;
-    float m = __fmul_rn(__fsqrt_rn(__int2float_rn(a)), vox);
-    m = a == kInf32 ? __int_as_float(0x7f800000) : m;
-    return __int_as_float(__float_as_int(m) | (v & (int32_t)0x80000000));
-}
-
-template <bool kCheck>
-__device__ __forceinline__ void emit_one(int z, int32_t sv, Cursor &O, Cursor &F, const uint32_t *mk, int zlo,
-                                         int nthr, int32_t *ocol, float *fcol, long long o, float vox)
-{
-    bool occz = false;
-    if (kCheck) {
-        const int e = z - zlo;
-        occz = (mk[(e >> 5) * nthr] >> (e & 31)) & 1u;
-    }
-    int32_t d;
-    if (occz) {
-        const int f = F.eval(z);
-        d = f < 0 ? -kInf32 : -f;
-    } else {
-        const int f = O.eval(z);
-        d = f < 0 ? kInf32 : f;
-    }
     const int32_t cv = min(sv, d);
     if (ocol)
         __stcs(ocol + o, cv);
-    if (fcol)
-        __stcs(fcol + o, sq_to_sdf_fast(cv, vox));
+    if (fcol) {
+        float f;
+        if (kStaticSdf && sv <= d)
+            f = sf;
+        else
+            f = sq_to_sdf_fast(cv, vox);
+        __stcs(fcol + o, f);
+    }
 }
 
-template <bool kCheck>
-__device__ __forceinline__ void emit_range(int z0, int z1, Cursor &O, Cursor &F, const uint32_t *mk, int zlo,
-                                           int nthr, const int32_t *scol, long long V2, int32_t *ocol, float *fcol,
-                                           float vox)
+// outputs for z in [z0, z1) that are not inside a human (kCheck: test the bits)
+template <bool kCheck, bool kStaticSdf>
+__device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, const uint32_t *mk, int zlo, int nthr,
+                                           const int32_t *scol, const float *sfcol, long long V2, int32_t *ocol,
+                                           float *fcol, float vox)
 {
     int z = z0;
     for (; z + 8 <= z1; z += 8) {
         int32_t sv[8];
+        float sf[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
             sv[i] = __ldg(scol + (long long)(z + i) * V2);
+            if (kStaticSdf)
+                sf[i] = __ldg(sfcol + (long long)(z + i) * V2);
+        }
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            emit_one<kCheck>(z + i, sv[i], O, F, mk, zlo, nthr, ocol, fcol, (long long)(z + i) * V2, vox);
+        for (int i = 0; i < 8; ++i) {
+            const int zz = z + i;
+            if (kCheck) {
+                const int e = zz - zlo;
+                if ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u)
+                    continue;
+            }
+            const int d = O.eval(zz);
+            emit_one<kStaticSdf>(zz, sv[i], kStaticSdf ? sf[i] : 0.f, d < 0 ? kInf32 : d, ocol, fcol,
+                                 (long long)zz * V2, vox);
+        }
     }
-    for (; z < z1; ++z)
-        emit_one<kCheck>(z, __ldg(scol + (long long)z * V2), O, F, mk, zlo, nthr, ocol, fcol, (long long)z * V2,
-                         vox);
+    for (; z < z1; ++z) {
+        if (kCheck) {
+            const int e = z - zlo;
+            if ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u)
+                continue;
+        }
+        const int d = O.eval(z);
+        emit_one<kStaticSdf>(z, __ldg(scol + (long long)z * V2), kStaticSdf ? __ldg(sfcol + (long long)z * V2) : 0.f,
+                             d < 0 ? kInf32 : d, ocol, fcol, (long long)z * V2, vox);
+    }
 }
 
-// Shared memory per thread, [entry][thread]: the staged slab column (S words,
-// reused in place as the set-O stack), the set-F stack (S + 2 words) and the
-// occupancy bits of the slab column.
-__global__ void k_composite_z(const int32_t *__restrict__ static_sq, const int32_t *__restrict__ dyn_mid, int nx,
-                              int ny, int nz, int zlo, int S, int T, int32_t *__restrict__ comp_sq,
-                              float *__restrict__ comp_sdf, float vox)
+template <bool kStaticSdf>
+__global__ void __launch_bounds__(128, 8)
+    k_composite_z(const int32_t *__restrict__ static_sq, const float *__restrict__ static_sdf,
+                  const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz, int zlo, int S, int T,
+                  int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox)
 {
     extern __shared__ uint32_t smem[];
     const int nthr = blockDim.x, tid = threadIdx.x;
     const long long V2 = (long long)nx * ny;
     const int t = blockIdx.x % T;
-    const long long c0 = (long long)(blockIdx.x / T) * nthr;
-    const long long c = c0 + tid;
-    const bool live = c < V2;
-    uint32_t *tile = smem + tid;
-    uint32_t *sF = smem + (size_t)S * nthr + tid;
-    uint32_t *mk = smem + (size_t)(2 * S + 2) * nthr + tid;
+    const long long c = (long long)(blockIdx.x / T) * nthr + tid;
+    if (c >= V2)
+        return;  // no block-level synchronisation below
+    uint32_t *tile = smem + tid;                              // slot k at tile[k * nthr]
+    uint32_t *mk = smem + (size_t)(S + 2) * nthr + tid;       // word w at mk[w * nthr]
     const int nw = (S + 31) >> 5;
+    const int32_t *dcol = dyn_mid + (long long)t * S * V2 + c;
 
-    // stage the slab column: S independent coalesced loads per thread
-    if (live) {
-        const int32_t *dcol = dyn_mid + (long long)t * S * V2 + c;
 #pragma unroll 8
-        for (int e = 0; e < S; ++e)
-            tile[e * nthr] = (uint32_t)__ldcs(dcol + (long long)e * V2);
-    }
-    if (!live)
-        return;
+    for (int e = 0; e < S; ++e)
+        tile[(e + 1) * nthr] = (uint32_t)__ldcs(dcol + (long long)e * V2);
 
     int firstOcc = S, lastOcc = -1;
     for (int w = 0; w < nw; ++w) {
         uint32_t bits = 0;
         const int e0 = w << 5, cnt = min(32, S - e0);
-        for (int bI = 0; bI < cnt; ++bI)
-            bits |= (uint32_t)((int32_t)tile[(e0 + bI) * nthr] < 0) << bI;
+        for (int b = 0; b < cnt; ++b)
+            bits |= (uint32_t)((int32_t)tile[(e0 + b + 1) * nthr] < 0) << b;
         mk[w * nthr] = bits;
         if (bits) {
             if (firstOcc == S)
@@ -408,81 +375,75 @@ __global__ void k_composite_z(const int32_t *__restrict__ static_sq, const int32
             lastOcc = e0 + 31 - __clz(bits);
         }
     }
-
-    // set F around the occupied run (before the tile is overwritten)
-    int topF = -1;
-    const int zo0 = zlo + firstOcc, zo1 = zlo + lastOcc;  // empty if lastOcc < 0
-    if (lastOcc >= 0) {
-        int a0 = 0, b0 = 0, a1 = 0, b1 = 0;
-        const int zr0 = max(zo0 - 1, 0), zr1 = min(zo1 + 1, nz - 1);
-        for (int z = zr0; z <= zr1; ++z) {
-            int g = 0;
-            const int e = z - zlo;
-            if (e >= 0 && e < S && ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u)) {
-                const int32_t v = (int32_t)tile[e * nthr];
-                g = v == -kInf32 ? -1 : -v;
-            }
-            if (g < 0)
-                continue;
-            while (topF >= 1 && dominated(a0, b0, a1, b1, z, g)) {
-                --topF;
-                a1 = a0;
-                b1 = b0;
-                if (topF >= 1) {
-                    const uint32_t x = sF[(topF - 1) * nthr];
-                    a0 = site_of(x);
-                    b0 = gval_of(x);
-                }
-            }
-            ++topF;
-            sF[topF * nthr] = pack_site(z, g);
-            a0 = a1;
-            b0 = b1;
-            a1 = z;
-            b1 = g;
-        }
-    }
-
-    // set O over the slab, built in place over the staged column: the entry
-    // written at step e lands in a slot <= e that has already been read
-    int topO = -1;
-    {
-        int a0 = 0, b0 = 0, a1 = 0, b1 = 0;
-        for (int e = 0; e < S; ++e) {
-            const int32_t v = (int32_t)tile[e * nthr];
-            const int g = v < 0 ? 0 : (v == kInf32 ? -1 : v);
-            if (g < 0)
-                continue;
-            const int z = zlo + e;
-            while (topO >= 1 && dominated(a0, b0, a1, b1, z, g)) {
-                --topO;
-                a1 = a0;
-                b1 = b0;
-                if (topO >= 1) {
-                    const uint32_t x = tile[(topO - 1) * nthr];
-                    a0 = site_of(x);
-                    b0 = gval_of(x);
-                }
-            }
-            ++topO;
-            tile[topO * nthr] = pack_site(z, g);
-            a0 = a1;
-            b0 = b1;
-            a1 = z;
-            b1 = g;
-        }
-    }
-
-    Cursor O(tile, nthr, topO), F(sF, nthr, topF);
     const long long V = V2 * nz;
     const int32_t *scol = static_sq + c;
+    const float *sfcol = kStaticSdf ? static_sdf + c : nullptr;
     int32_t *ocol = comp_sq ? comp_sq + (long long)t * V + c : nullptr;
     float *fcol = comp_sdf ? comp_sdf + (long long)t * V + c : nullptr;
-    // z below and above the occupied run need no occupancy test
+    auto occupied = [&](int z) {
+        const int e = z - zlo;
+        return e >= 0 && e < S && ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u);
+    };
+
+    const int zo0 = zlo + firstOcc, zo1 = zlo + lastOcc;
+    if (lastOcc >= 0) {
+        // set F over [zo0 - 1, zo1 + 1]; free voxels are sites only next to an
+        // occupied one.  Site z sits in slot z - zlo + 1, read before written.
+        const int zr0 = max(zo0 - 1, 0), zr1 = min(zo1 + 1, nz - 1);
+        EnvBuilder B(tile + (zr0 - zlo + 1) * nthr, nthr);
+        for (int z = zr0; z <= zr1; ++z) {
+            int g;
+            if (occupied(z)) {
+                const int32_t v = (int32_t)tile[(z - zlo + 1) * nthr];
+                if (v == -kInf32)
+                    continue;
+                g = -v;
+            } else {
+                if (!occupied(z - 1) && !occupied(z + 1))
+                    continue;
+                g = 0;
+            }
+            B.push(z, g);
+        }
+        EnvCursor F(tile + (zr0 - zlo + 1) * nthr, nthr, B.top);
+        for (int z = zo0; z <= zo1; ++z) {
+            if (!occupied(z))
+                continue;
+            const int f = F.eval(z);
+            const long long o = (long long)z * V2;
+            emit_one<kStaticSdf>(z, __ldg(scol + o), kStaticSdf ? __ldg(sfcol + o) : 0.f, f < 0 ? -kInf32 : -f,
+                                 ocol, fcol, o, vox);
+        }
+        // restore the staged column for set O
+#pragma unroll 8
+        for (int e = 0; e < S; ++e)
+            tile[(e + 1) * nthr] = (uint32_t)__ldg(dcol + (long long)e * V2);
+    }
+
+    // set O over the slab: sites are the free slab voxels with a finite
+    // partial and the ends of the occupied runs (zero distance)
+    EnvBuilder B(tile + nthr, nthr);
+    for (int e = 0; e < S; ++e) {
+        const int32_t v = (int32_t)tile[(e + 1) * nthr];
+        int g;
+        if (v >= 0) {
+            if (v == kInf32)
+                continue;
+            g = v;
+        } else {
+            const int z = zlo + e;
+            if (occupied(z - 1) && occupied(z + 1))
+                continue;
+            g = 0;
+        }
+        B.push(zlo + e, g);
+    }
+    EnvCursor O(tile + nthr, nthr, B.top);
+    // below the occupied run, the run (skipping its voxels), above it
     const int za = lastOcc >= 0 ? zo0 : nz, zb = lastOcc >= 0 ? zo1 + 1 : nz;
-    emit_range<false>(0, za, O, F, mk, zlo, nthr, scol, V2, ocol, fcol, vox);
-    emit_range<true>(za, zb, O, F, mk, zlo, nthr, scol, V2, ocol, fcol, vox);
-    emit_range<false>(zb, nz, O, F, mk, zlo, nthr, scol, V2, ocol, fcol, vox);
+    emit_range<false, kStaticSdf>(0, za, O, mk, zlo, nthr, scol, sfcol, V2, ocol, fcol, vox);
+    emit_range<true, kStaticSdf>(za, zb, O, mk, zlo, nthr, scol, sfcol, V2, ocol, fcol, vox);
+    emit_range<false, kStaticSdf>(zb, nz, O, mk, zlo, nthr, scol, sfcol, V2, ocol, fcol, vox);
 }
 
 __global__ void k_broadcast_static(const int32_t *__restrict__ static_sq, long long V, int T,
@@ -523,21 +484,31 @@ cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_z(const int32_t *static_sq, const int32_t *dyn_mid, int nx, int ny, int nz, int zlo,
-                               int S, int T, int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream)
+cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf, const int32_t *dyn_mid, int nx,
+                               int ny, int nz, int zlo, int S, int T, int32_t *comp_sq, float *comp_sdf, float vox,
+                               cudaStream_t stream)
 {
     const long long V2 = (long long)nx * ny;
-    const int words = 2 * S + 2 + (S + 31) / 32;
+    const int words = S + 2 + (S + 31) / 32;
     int nthr = 128;
     while (nthr > 32 && (size_t)nthr * words * sizeof(uint32_t) > 200 * 1024)
         nthr >>= 1;
     const size_t smem = (size_t)nthr * words * sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(k_composite_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
     const long long nblk = (V2 + nthr - 1) / nthr * T;
-    k_composite_z<<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, dyn_mid, nx, ny, nz, zlo, S, T, comp_sq,
-                                                          comp_sdf, vox);
+    cudaError_t e;
+    if (static_sdf) {
+        e = cudaFuncSetAttribute(k_composite_z<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        k_composite_z<true><<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, static_sdf, dyn_mid, nx, ny, nz, zlo,
+                                                                    S, T, comp_sq, comp_sdf, vox);
+    } else {
+        e = cudaFuncSetAttribute(k_composite_z<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        k_composite_z<false><<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, nullptr, dyn_mid, nx, ny, nz, zlo, S,
+                                                                     T, comp_sq, comp_sdf, vox);
+    }
     return cudaGetLastError();
 }
 

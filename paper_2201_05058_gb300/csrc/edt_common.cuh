@@ -29,6 +29,79 @@ __device__ __forceinline__ bool dominated(int s0, int g0, int s1, int g1, int s2
     return (f2 - f1) * (s1 - s0) <= (f1 - f0) * (s2 - s1);
 }
 
+// Forward cursor over an envelope stack in shared memory whose entry q lives
+// at stk[q * stride]; the current and next site are kept in registers.
+// eval(z) requires z to be non-decreasing between calls.
+struct EnvCursor {
+    const uint32_t *stk;
+    int stride, top, q;
+    int s, g, sn, gn;
+    __device__ __forceinline__ EnvCursor(const uint32_t *stk_, int stride_, int top_)
+        : stk(stk_), stride(stride_), top(top_), q(0), s(0), g(0), sn(0), gn(0)
+    {
+        if (top >= 0) {
+            s = site_of(stk[0]);
+            g = gval_of(stk[0]);
+        }
+        if (top >= 1) {
+            sn = site_of(stk[stride]);
+            gn = gval_of(stk[stride]);
+        }
+    }
+    // min over the envelope at z; -1 if the envelope is empty
+    __device__ __forceinline__ int eval(int z)
+    {
+        if (top < 0)
+            return -1;
+        int fc = parab(z, s, g);
+        while (q < top) {
+            const int fn = parab(z, sn, gn);
+            if (fn > fc)
+                break;
+            ++q;
+            s = sn;
+            g = gn;
+            fc = fn;
+            if (q < top) {
+                const uint32_t w = stk[(q + 1) * stride];
+                sn = site_of(w);
+                gn = gval_of(w);
+            }
+        }
+        return fc;
+    }
+};
+
+// Push site (e, g) onto a stack kept in shared memory (entry q at
+// stk[q * stride]) with the top two entries cached in registers, popping the
+// entries that the new site makes useless.
+struct EnvBuilder {
+    uint32_t *stk;
+    int stride, top;
+    int s0, g0, s1, g1;
+    __device__ __forceinline__ EnvBuilder(uint32_t *stk_, int stride_)
+        : stk(stk_), stride(stride_), top(-1), s0(0), g0(0), s1(0), g1(0) {}
+    __device__ __forceinline__ void push(int e, int g)
+    {
+        while (top >= 1 && dominated(s0, g0, s1, g1, e, g)) {
+            --top;
+            s1 = s0;
+            g1 = g0;
+            if (top >= 1) {
+                const uint32_t w = stk[(top - 1) * stride];
+                s0 = site_of(w);
+                g0 = gval_of(w);
+            }
+        }
+        ++top;
+        stk[top * stride] = pack_site(e, g);
+        s0 = s1;
+        g0 = g1;
+        s1 = e;
+        g1 = g;
+    }
+};
+
 // Is the centre of voxel (i, j, k), 16 * (i, j, k) + 8 in fixed point, inside
 // the closed capsule?  Squared distance to the segment against r^2 without
 // rounding: with s = (p-a).(b-a) and L = |b-a|^2 the nearest point is a
@@ -62,6 +135,15 @@ __device__ __forceinline__ float sq_to_sdf(int32_t s, float vox)
     const int32_t a = s < 0 ? -s : s;
     const float m = __fmul_rn(__fsqrt_rn(__int2float_rn(a)), vox);
     return s < 0 ? -m : m;
+}
+
+// The same value as sq_to_sdf with a select instead of branches.
+__device__ __forceinline__ float sq_to_sdf_fast(int32_t v, float vox)
+{
+    const int32_t a = v < 0 ? -v : v;
+    float m = __fmul_rn(__fsqrt_rn(__int2float_rn(a)), vox);
+    m = a == kInf32 ? __int_as_float(0x7f800000) : m;
+    return __int_as_float(__float_as_int(m) | (v & (int32_t)0x80000000));
 }
 
 }  // namespace pcdf

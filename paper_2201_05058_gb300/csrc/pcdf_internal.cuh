@@ -70,8 +70,11 @@ cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, 
 
 // z-pass of the dynamic field over the slab [zlo, zlo + S) fused with the
 // composite min against static_sq and the float epilogue, for all T.
-cudaError_t launch_composite_z(const int32_t *static_sq, const int32_t *dyn_mid, int nx, int ny, int nz, int zlo,
-                               int S, int T, int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream);
+// static_sdf (nullable) is the float field of static_sq; where the static
+// field wins the min it is copied instead of recomputed.
+cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf, const int32_t *dyn_mid, int nx,
+                               int ny, int nz, int zlo, int S, int T, int32_t *comp_sq, float *comp_sdf, float vox,
+                               cudaStream_t stream);
 
 // Copies static_sq into every t of comp (and its float field) when no capsule
 // touches the grid.

@@ -94,15 +94,18 @@ def test_static_edt_box_and_wall_structures():
 # ---------------------------------------------------------------------------
 
 def check_composite(occ, caps, grid):
-    d = dev()
-    static_sq, _ = pcdf.build_static_sdf(cuda(occ), grid)
-    comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, caps)
-    comp_sq = comp_sq.cpu().numpy()
-    comp_sdf = comp_sdf.cpu().numpy()
+    """Both float-epilogue variants (static float field reused or recomputed)
+    against the oracle."""
+    static_sq, static_sdf = pcdf.build_static_sdf(cuda(occ), grid)
     want = oracle.predicted_composite(oracle.edt(occ), caps)
-    for t in range(caps.shape[0]):
-        assert_equal_fields(comp_sq[t], want[t], f"comp_sq[{t}]")
-        assert_bits_equal(comp_sdf[t], oracle.sdf_from_sq(want[t], grid.vox), f"comp_sdf[{t}]")
+    for reuse in (False, True):
+        comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, caps,
+                                                           static_sdf=static_sdf if reuse else None)
+        comp_sq = comp_sq.cpu().numpy()
+        comp_sdf = comp_sdf.cpu().numpy()
+        for t in range(caps.shape[0]):
+            assert_equal_fields(comp_sq[t], want[t], f"comp_sq[{t}] reuse={reuse}")
+            assert_bits_equal(comp_sdf[t], oracle.sdf_from_sq(want[t], grid.vox), f"comp_sdf[{t}] reuse={reuse}")
     return comp_sq
 
 
@@ -181,7 +184,7 @@ def big_scene():
     sc = scenes.scene_composite(seed=0)
     grid = sc["grid"]
     static_sq, static_sdf = pcdf.build_static_sdf(cuda(sc["occ"]), grid)
-    comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, sc["caps"])
+    comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, sc["caps"], static_sdf=static_sdf)
     torch.cuda.synchronize()
     return sc, static_sq.cpu().numpy(), static_sdf.cpu().numpy(), comp_sq, comp_sdf
 
