@@ -40,39 +40,38 @@ __device__ __forceinline__ int32_t widen(int16_t v)
 }
 __device__ __forceinline__ int32_t widen(int32_t v) { return v; }
 
-// The merged envelope of a column: band k contributes entries
-// slots [lo_k + st_k, lo_k + st_k + len_k) of the column's tile.
+// The merged envelope of a column: band k contributes the entries in slots
+// [lo_k + st_k, lo_k + st_k + len_k) of the column's tile; global entry q of
+// band k sits in slot q + (lo_k + st_k - (len_0 + ... + len_{k-1})).
 struct Merged {
-    int lo[kBands], st[kBands], len[kBands];
-    int K;  // total entries
-    // slot of global entry q (0 <= q < K)
+    int c1, c2, c3, K;      // running entry counts after bands 0, 1, 2, 3
+    int b0, b1, b2, b3;     // slot offsets
+    __device__ __forceinline__ void init(const int (*seg)[kBands][kCols], int c, int wpb, int n)
+    {
+        const int l0 = seg[1][0][c], l1 = seg[1][1][c], l2 = seg[1][2][c], l3 = seg[1][3][c];
+        c1 = l0;
+        c2 = c1 + l1;
+        c3 = c2 + l2;
+        K = c3 + l3;
+        b0 = seg[0][0][c];
+        b1 = min(wpb * 32, n) + seg[0][1][c] - c1;
+        b2 = min(2 * wpb * 32, n) + seg[0][2][c] - c2;
+        b3 = min(3 * wpb * 32, n) + seg[0][3][c] - c3;
+    }
     __device__ __forceinline__ int slot(int q) const
     {
-#pragma unroll
-        for (int k = 0; k < kBands - 1; ++k) {
-            if (q < len[k])
-                return lo[k] + st[k] + q;
-            q -= len[k];
-        }
-        return lo[kBands - 1] + st[kBands - 1] + q;
+        return q + (q < c1 ? b0 : (q < c2 ? b1 : (q < c3 ? b2 : b3)));
     }
 };
-
-template <typename TIn>
-__device__ __forceinline__ void stage(uint32_t *tile, const TIn *col, long long stride, int a, int b)
-{
-#pragma unroll 8
-    for (int e = a; e < b; ++e)
-        tile[e * kCols] = (uint32_t)widen(col[(long long)e * stride]);
-}
+static_assert(kBands == 4, "Merged assumes four bands");
 
 template <typename TIn, bool kSdf>
 __global__ void __launch_bounds__(kCols * kBands)
     k_envelope_banded(const TIn *__restrict__ in, int32_t *__restrict__ out, float *__restrict__ sdf, float vox,
-                      int n, int nx, long long ncols, long long outer_stride, long long stride)
+                      int n, int nx, long long ncols, long long outer_stride, int stride)
 {
     extern __shared__ uint32_t smem[];
-    __shared__ int seg[3][kBands][kCols];  // per column: band start-in-band, length; then any-target flag
+    __shared__ int seg[2][kBands][kCols];  // per column and band: first surviving entry, number of entries
     const int c = threadIdx.x % kCols, band = threadIdx.x / kCols;
     const long long cl = (long long)blockIdx.x * kCols + c;
     const bool live = cl < ncols;
@@ -80,66 +79,85 @@ __global__ void __launch_bounds__(kCols * kBands)
     const TIn *col = in + base;
     uint32_t *tile = smem + c;                                  // element e at tile[e * kCols]
     uint32_t *mk = smem + (size_t)n * kCols + c;                // occupied bits, word w at mk[w * kCols]
-    const int bw = (n + kBands - 1) / kBands;                   // band width
-    const int e0 = min(band * bw, n), e1 = min(e0 + bw, n);
-
-    // stage this band's slots and the occupancy bits of its words
-    if (live)
-        stage(tile, col, stride, e0, e1);
-    __syncthreads();
     const int nw = (n + 31) >> 5;
-    if (live)
-        for (int w = band; w < nw; w += kBands) {
-            const int w0 = w << 5, cnt = min(32, n - w0);
+    const int wpb = (nw + kBands - 1) / kBands;                 // mask words per band
+    const int w0 = min(band * wpb, nw), w1 = min(w0 + wpb, nw);
+    const int e0 = min(w0 << 5, n), e1 = min(w1 << 5, n);
+
+    // stage this band's slots and their occupancy words
+    if (live) {
+        for (int w = w0; w < w1; ++w) {
+            const int a = w << 5, cnt = min(32, n - a);
             uint32_t occ = 0;
-            for (int i = 0; i < cnt; ++i)
-                occ |= (uint32_t)((int32_t)tile[(w0 + i) * kCols] < 0) << i;
+#pragma unroll 8
+            for (int i = 0; i < cnt; ++i) {
+                const int32_t v = widen(col[(a + i) * stride]);
+                tile[(a + i) * kCols] = (uint32_t)v;
+                occ |= (uint32_t)(v < 0) << i;
+            }
             mk[w * kCols] = occ;
         }
+    }
     __syncthreads();
-    auto occupied = [&](int e) { return (mk[(e >> 5) * kCols] >> (e & 31)) & 1u; };
+    auto valid = [&](int w) { const int cnt = n - (w << 5); return cnt >= 32 ? 0xffffffffu : ((1u << cnt) - 1u); };
+    auto occw = [&](int w) { return (w >= 0 && w < nw) ? mk[w * kCols] : 0u; };
 
     for (int set = 0; set < 2; ++set) {
-        // 0. does this band hold outputs of this set?  (re-stage for set F)
+        // targets: free voxels for set O, occupied voxels for set F
         bool mine = false;
         if (live)
-            for (int e = e0; e < e1; ++e)
-                mine |= set == 0 ? !occupied(e) : occupied(e);
+            for (int w = w0; w < w1; ++w) {
+                const uint32_t o = occw(w);
+                mine |= (set == 0 ? (~o & valid(w)) : o) != 0;
+            }
         if (!__syncthreads_or(mine))
             continue;
-        if (set == 1 && live)
-            stage(tile, col, stride, e0, e1);  // set O may have overwritten the slots
-        __syncthreads();
 
-        // 1. band envelope, in place over slots [e0, e1)
+        // 1. band envelope, in place over slots [e0, e1).  Sites: the targets
+        //    with a finite partial distance, and the run ends of the other
+        //    state (zero distance) next to a target.
         EnvBuilder B(tile + e0 * kCols, kCols);
-        if (live)
-            for (int e = e0; e < e1; ++e) {
-                int g;
-                const bool oc = occupied(e);
-                if (set == 0 ? !oc : oc) {
-                    const int32_t v = (int32_t)tile[e * kCols];
-                    if (v == kInf32 || v == -kInf32)
-                        continue;
-                    g = v < 0 ? -v : v;
+        if (live) {
+            for (int w = w0; w < w1; ++w) {
+                const uint32_t vm = valid(w);
+                const uint32_t o = occw(w), op = occw(w - 1), on = occw(w + 1);
+                const uint32_t vp = w > 0 ? 0xffffffffu : 0u, vn = w + 1 < nw ? valid(w + 1) : 0u;
+                uint32_t tgt, zs;
+                if (set == 0) {
+                    const uint32_t fr = ~o & vm, frp = ~op & vp, frn = ~on & vn;
+                    tgt = fr;
+                    zs = o & vm & ((fr << 1) | (frp >> 31) | (fr >> 1) | (frn << 31));
                 } else {
-                    const bool l = e > 0 && (set == 0 ? !occupied(e - 1) : occupied(e - 1));
-                    const bool r = e + 1 < n && (set == 0 ? !occupied(e + 1) : occupied(e + 1));
-                    if (!l && !r)
-                        continue;
-                    g = 0;
+                    tgt = o & vm;
+                    zs = ~o & vm & ((o << 1) | ((op & vp) >> 31) | (o >> 1) | ((on & vn) << 31));
+                    // set O overwrote the slots: restage the values of the targets
+                    for (uint32_t m = tgt; m; m &= m - 1) {
+                        const int e = (w << 5) + __ffs(m) - 1;
+                        tile[e * kCols] = (uint32_t)widen(col[e * stride]);
+                    }
                 }
-                B.push(e, g);
+                for (uint32_t m = tgt | zs; m; m &= m - 1) {
+                    const int i = __ffs(m) - 1, e = (w << 5) + i;
+                    int g = 0;
+                    if ((tgt >> i) & 1u) {
+                        const int32_t v = (int32_t)tile[e * kCols];
+                        const int32_t a = v < 0 ? -v : v;
+                        if (a == kInf32)
+                            continue;
+                        g = a;
+                    }
+                    B.push(e, g);
+                }
             }
+        }
         seg[0][band][c] = 0;
         seg[1][band][c] = B.top + 1;
         __syncthreads();
-
         // 2. merge the bands of the column (first thread of the column); the
         //    segment table lives in shared memory (indexed by band)
         if (band == 0 && live) {
             int *st = &seg[0][0][c], *len = &seg[1][0][c];  // band k at [k * kCols]
-            auto ent = [&](int k, int i) { return tile[(min(k * bw, n) + st[k * kCols] + i) * kCols]; };
+            auto ent = [&](int k, int i) { return tile[(min(k * wpb * 32, n) + st[k * kCols] + i) * kCols]; };
             for (int k = 1; k < kBands; ++k) {
                 for (;;) {
                     const int lk = len[k * kCols];
@@ -187,25 +205,11 @@ __global__ void __launch_bounds__(kCols * kBands)
         // 3. outputs of this band
         if (live && mine) {
             Merged M;
-            M.K = 0;
-#pragma unroll
-            for (int k = 0; k < kBands; ++k) {
-                M.lo[k] = min(k * bw, n);
-                M.st[k] = seg[0][k][c];
-                M.len[k] = seg[1][k][c];
-                M.K += M.len[k];
-            }
+            M.init(seg, c, wpb, n);
             int32_t *o = out + base;
             float *f = kSdf ? sdf + base : nullptr;
-            if (M.K == 0) {
-                for (int e = e0; e < e1; ++e)
-                    if (set == 0 ? !occupied(e) : occupied(e)) {
-                        const int32_t r = set == 0 ? kInf32 : -kInf32;
-                        o[(long long)e * stride] = r;
-                        if (kSdf)
-                            f[(long long)e * stride] = sq_to_sdf(r, vox);
-                    }
-            } else {
+            int q = 0, sc = 0, gc = 0, sn = 0, gn = 0;
+            if (M.K > 0) {
                 // first entry whose successor is not closer at e0
                 int lq = 0, hq = M.K - 1;
                 while (lq < hq) {
@@ -216,37 +220,46 @@ __global__ void __launch_bounds__(kCols * kBands)
                     else
                         hq = mid;
                 }
-                int q = lq;
+                q = lq;
                 uint32_t w = tile[M.slot(q) * kCols];
-                int sc = site_of(w), gc = gval_of(w);
-                int sn = 0, gn = 0;
+                sc = site_of(w);
+                gc = gval_of(w);
                 if (q + 1 < M.K) {
                     w = tile[M.slot(q + 1) * kCols];
                     sn = site_of(w);
                     gn = gval_of(w);
                 }
-                for (int e = e0; e < e1; ++e) {
-                    if (!(set == 0 ? !occupied(e) : occupied(e)))
-                        continue;
-                    int fc = parab(e, sc, gc);
-                    while (q + 1 < M.K) {
-                        const int fn = parab(e, sn, gn);
-                        if (fn > fc)
-                            break;
-                        ++q;
-                        sc = sn;
-                        gc = gn;
-                        fc = fn;
-                        if (q + 1 < M.K) {
-                            w = tile[M.slot(q + 1) * kCols];
-                            sn = site_of(w);
-                            gn = gval_of(w);
+            }
+            for (int w = w0; w < w1; ++w) {
+                const uint32_t ow = occw(w);
+                const uint32_t tgt = set == 0 ? (~ow & valid(w)) : ow;
+                for (uint32_t m = tgt; m; m &= m - 1) {
+                    const int e = (w << 5) + __ffs(m) - 1;
+                    int32_t r;
+                    if (M.K == 0) {
+                        r = kInf32;
+                    } else {
+                        int fc = parab(e, sc, gc);
+                        while (q + 1 < M.K) {
+                            const int fn = parab(e, sn, gn);
+                            if (fn > fc)
+                                break;
+                            ++q;
+                            sc = sn;
+                            gc = gn;
+                            fc = fn;
+                            if (q + 1 < M.K) {
+                                const uint32_t x = tile[M.slot(q + 1) * kCols];
+                                sn = site_of(x);
+                                gn = gval_of(x);
+                            }
                         }
+                        r = fc;
                     }
-                    const int32_t r = set == 0 ? fc : -fc;
-                    o[(long long)e * stride] = r;
+                    r = set == 0 ? r : -r;
+                    o[e * stride] = r;
                     if (kSdf)
-                        f[(long long)e * stride] = sq_to_sdf(r, vox);
+                        f[e * stride] = sq_to_sdf_fast(r, vox);
                 }
             }
         }
@@ -265,9 +278,10 @@ cudaError_t launch_banded(const TIn *in, int32_t *out, float *sdf, float vox, in
                                          (int)smem);
     if (e != cudaSuccess)
         return e;
+    // element offsets along the column stay below 2^31: n <= 512, stride <= 512 * 512
     const long long nblk = (ncols + kCols - 1) / kCols;
     k_envelope_banded<TIn, kSdf><<<(unsigned)nblk, kCols * kBands, smem, stream>>>(in, out, sdf, vox, n, nx, ncols,
-                                                                                    outer_stride, stride);
+                                                                                    outer_stride, (int)stride);
     return cudaGetLastError();
 }
 
