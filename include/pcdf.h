@@ -64,6 +64,7 @@ extern "C" {
 #define PCDF_EINVAL (-1)   /* bad size, pointer, alignment or capsule range */
 #define PCDF_ENOMEM (-2)   /* workspace smaller than the size query returned */
 #define PCDF_ECUDA (-3)    /* a CUDA launch or runtime call failed */
+#define PCDF_ETIMEOUT (-4) /* a bounded wait inside the batched kernel expired */
 
 #define PCDF_INF 2147483647
 #define PCDF_MAX_DIM 512
@@ -181,6 +182,61 @@ int pcdf_query_cost(const pcdf_grid *grid, const float *sdf, int32_t T, const fl
 int pcdf_query_cost_backward(const pcdf_grid *grid, const float *sdf, int32_t T, const float *spheres,
                              const int32_t *tidx, int64_t N, float eps, const float *grad_h, float *grad_c,
                              float *grad_r, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched environments in one persistent launch (an extension beyond the
+ * paper: many maps of uneven size, horizon and human count updated together).
+ *
+ * For every environment e: the static signed squared EDT of occ (as
+ * pcdf_build_static_sdf) and its T composite fields comp_sq[t] (as
+ * pcdf_build_predicted_composite), int32 only.  Results are bit-identical to
+ * the per-environment calls and independent of the tile shapes.
+ *
+ * pcdf_batch_create   builds the host-side plan (work items, capsule tables,
+ *                     workspace layout); allocates host memory only; reads
+ *                     each environment's HOST capsules; needs the current
+ *                     device to query occupancy.
+ * pcdf_batch_upload   copies the plan into the workspace (host-to-device
+ *                     copies on `stream`; not capturable; repeat it whenever
+ *                     the workspace or the environments' device pointers
+ *                     change).
+ * pcdf_batch_run      resets the counters and launches the persistent kernel:
+ *                     no host synchronisation, capturable in a CUDA graph.
+ * pcdf_batch_error    synchronises `stream` and reports PCDF_ETIMEOUT if a
+ *                     dependency wait inside the last run timed out (then the
+ *                     outputs are not valid), else PCDF_OK.
+ * pcdf_batch_autotune times every candidate tile shape (rows per row-pass
+ *                     item, slab slices per capsule item, time steps per
+ *                     composite item) with `reps` runs each, synchronising
+ *                     `stream`, and returns the fastest; the workspace must
+ *                     hold pcdf_batch_autotune_workspace_bytes().
+ * ------------------------------------------------------------------------- */
+typedef struct pcdf_env {
+    pcdf_grid grid;
+    int32_t T, H;
+    const int32_t *caps; /* HOST [T][H][7]; NULL iff H == 0 */
+    const uint8_t *occ;  /* device [nz][ny][nx] */
+    int32_t *comp_sq;    /* device [T][nz][ny][nx], out */
+} pcdf_env;
+
+typedef struct pcdf_batch_tiles {
+    int32_t row_rows;   /* rows per row-pass item (<= 0: 32) */
+    int32_t dyn_slices; /* slab slices per capsule-field item (<= 0: 1) */
+    int32_t comp_t;     /* time steps per composite item (<= 0: 1) */
+} pcdf_batch_tiles;
+
+typedef struct pcdf_batch pcdf_batch;
+
+int pcdf_batch_create(const pcdf_env *envs, int32_t n_env, const pcdf_batch_tiles *tiles, pcdf_batch **out);
+void pcdf_batch_destroy(pcdf_batch *batch);
+int pcdf_batch_workspace_bytes(const pcdf_batch *batch, size_t *bytes);
+int pcdf_batch_tiles_used(const pcdf_batch *batch, pcdf_batch_tiles *tiles);
+int pcdf_batch_upload(pcdf_batch *batch, void *workspace, size_t workspace_bytes, void *stream);
+int pcdf_batch_run(const pcdf_batch *batch, void *workspace, void *stream);
+int pcdf_batch_error(const pcdf_batch *batch, const void *workspace, void *stream, int32_t *code);
+int pcdf_batch_autotune_workspace_bytes(const pcdf_env *envs, int32_t n_env, size_t *bytes);
+int pcdf_batch_autotune(const pcdf_env *envs, int32_t n_env, void *workspace, size_t workspace_bytes, void *stream,
+                        int32_t reps, pcdf_batch_tiles *best, float *best_ms);
 
 #ifdef __cplusplus
 }

@@ -8,6 +8,8 @@ hand-written CUDA kernels of ``libpcdf.so`` behind the C ABI of
 ``include/pcdf.h``; PyTorch supplies device memory and streams only.
 """
 from .api import (  # noqa: F401
+    Batch,
+    batch_autotune,
     Grid,
     HingeCost,
     build_from_scratch,

@@ -20,6 +20,15 @@ class PcdfGrid(ctypes.Structure):
                 ("vox", ctypes.c_float), ("origin", ctypes.c_float * 3)]
 
 
+class PcdfEnv(ctypes.Structure):
+    _fields_ = [("grid", PcdfGrid), ("T", ctypes.c_int32), ("H", ctypes.c_int32), ("caps", ctypes.c_void_p),
+                ("occ", ctypes.c_void_p), ("comp_sq", ctypes.c_void_p)]
+
+
+class PcdfBatchTiles(ctypes.Structure):
+    _fields_ = [("row_rows", ctypes.c_int32), ("dyn_slices", ctypes.c_int32), ("comp_t", ctypes.c_int32)]
+
+
 EXPORTS = (
     "pcdf_last_error", "pcdf_version",
     "pcdf_static_workspace_bytes", "pcdf_build_static_sdf",
@@ -27,6 +36,9 @@ EXPORTS = (
     "pcdf_composite_prepare", "pcdf_composite_finish", "pcdf_composite_slab",
     "pcdf_scratch_workspace_bytes", "pcdf_build_from_scratch",
     "pcdf_query_cost", "pcdf_query_cost_backward",
+    "pcdf_batch_create", "pcdf_batch_destroy", "pcdf_batch_workspace_bytes", "pcdf_batch_tiles_used",
+    "pcdf_batch_upload", "pcdf_batch_run", "pcdf_batch_error", "pcdf_batch_autotune_workspace_bytes",
+    "pcdf_batch_autotune",
 )
 
 
@@ -50,6 +62,21 @@ def _declare(lib):
         "pcdf_query_cost": [G, P, I32, P, P, I64, F32, P, P, P],
         "pcdf_query_cost_backward": [G, P, I32, P, P, I64, F32, P, P, P, P],
     }
+    E = ctypes.POINTER(PcdfEnv)
+    TL = ctypes.POINTER(PcdfBatchTiles)
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig.update({
+        "pcdf_batch_create": [E, I32, TL, PP],
+        "pcdf_batch_workspace_bytes": [P, SZP],
+        "pcdf_batch_tiles_used": [P, TL],
+        "pcdf_batch_upload": [P, P, SZ, P],
+        "pcdf_batch_run": [P, P, P],
+        "pcdf_batch_error": [P, P, P, ctypes.POINTER(I32)],
+        "pcdf_batch_autotune_workspace_bytes": [E, I32, SZP],
+        "pcdf_batch_autotune": [E, I32, P, SZ, P, I32, TL, ctypes.POINTER(ctypes.c_float)],
+    })
+    lib.pcdf_batch_destroy.argtypes = [P]
+    lib.pcdf_batch_destroy.restype = None
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args

@@ -313,3 +313,105 @@ class HingeCost(torch.autograd.Function):
 def hinge_cost(centres, radii, sdf, tidx, eps, grid):
     """Differentiable hinge cost h[...] (autograd through HingeCost)."""
     return HingeCost.apply(centres, radii, sdf, tidx, float(eps), grid)
+
+
+# ---------------------------------------------------------------------------
+# batched environments: one persistent launch
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """Many environments updated by one persistent kernel launch.
+
+    envs: sequence of (grid, occ CUDA uint8 [nz,ny,nx], caps host int32
+    [T][H][7]).  Allocates the int32 composite outputs ``self.comp_sq[e]``
+    ([T_e, nz, ny, nx]) and the workspace from PyTorch, builds and uploads the
+    plan.  ``run()`` enqueues the counter reset and the launch on the current
+    stream (capturable in a CUDA graph); ``error()`` synchronises and returns
+    the kernel's status code (0 = ok)."""
+
+    def __init__(self, envs, tiles=None, device=None):
+        self._lib = _lib.load()
+        self.device = device if device is not None else envs[0][1].device
+        self._caps = []
+        self.comp_sq = []
+        arr = (_lib.PcdfEnv * len(envs))()
+        for i, (grid, occ, caps) in enumerate(envs):
+            _need(occ, f"occ[{i}]", torch.uint8, _shape(grid))
+            c = _caps_host(caps)
+            self._caps.append(c)
+            T, H = int(c.shape[0]), int(c.shape[1])
+            out = torch.empty((T,) + _shape(grid), dtype=torch.int32, device=self.device)
+            self.comp_sq.append(out)
+            arr[i].grid = _cgrid(grid)
+            arr[i].T = T
+            arr[i].H = H
+            arr[i].caps = c.ctypes.data if H > 0 else None
+            arr[i].occ = occ.data_ptr()
+            arr[i].comp_sq = out.data_ptr()
+        self._envs = arr
+        self._occ = [e[1] for e in envs]
+        t = _lib.PcdfBatchTiles(*(tiles or (0, 0, 0)))
+        h = ctypes.c_void_p()
+        _lib.check(self._lib.pcdf_batch_create(arr, len(envs), ctypes.byref(t), ctypes.byref(h)), "pcdf_batch_create")
+        self._h = h
+        nbytes = ctypes.c_size_t(0)
+        _lib.check(self._lib.pcdf_batch_workspace_bytes(h, ctypes.byref(nbytes)), "pcdf_batch_workspace_bytes")
+        self.workspace = _workspace(nbytes.value, self.device)
+        _lib.check(self._lib.pcdf_batch_upload(h, _ptr(self.workspace), self.workspace.numel(),
+                                               ctypes.c_void_p(_stream(self.device))), "pcdf_batch_upload")
+
+    @property
+    def tiles(self):
+        t = _lib.PcdfBatchTiles()
+        _lib.check(self._lib.pcdf_batch_tiles_used(self._h, ctypes.byref(t)), "pcdf_batch_tiles_used")
+        return (t.row_rows, t.dyn_slices, t.comp_t)
+
+    def run(self):
+        _lib.check(self._lib.pcdf_batch_run(self._h, _ptr(self.workspace), ctypes.c_void_p(_stream(self.device))),
+                   "pcdf_batch_run")
+
+    def error(self) -> int:
+        code = ctypes.c_int32(0)
+        _lib.check(self._lib.pcdf_batch_error(self._h, _ptr(self.workspace), ctypes.c_void_p(_stream(self.device)),
+                                              ctypes.byref(code)), "pcdf_batch_error")
+        return code.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pcdf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_autotune(envs, reps: int = 3, device=None):
+    """Time every candidate tile shape of the batched kernel on these
+    environments; returns ((row_rows, dyn_slices, comp_t), ms)."""
+    lib = _lib.load()
+    device = device if device is not None else envs[0][1].device
+    arr = (_lib.PcdfEnv * len(envs))()
+    keep = []
+    for i, (grid, occ, caps) in enumerate(envs):
+        c = _caps_host(caps)
+        keep.append(c)
+        T, H = int(c.shape[0]), int(c.shape[1])
+        out = torch.empty((T,) + _shape(grid), dtype=torch.int32, device=device)
+        keep.append(out)
+        arr[i].grid = _cgrid(grid)
+        arr[i].T = T
+        arr[i].H = H
+        arr[i].caps = c.ctypes.data if H > 0 else None
+        arr[i].occ = occ.data_ptr()
+        arr[i].comp_sq = out.data_ptr()
+    nbytes = ctypes.c_size_t(0)
+    _lib.check(lib.pcdf_batch_autotune_workspace_bytes(arr, len(envs), ctypes.byref(nbytes)), "autotune workspace")
+    ws = _workspace(nbytes.value, device)
+    best = _lib.PcdfBatchTiles()
+    ms = ctypes.c_float(0)
+    _lib.check(lib.pcdf_batch_autotune(arr, len(envs), _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(device)),
+                                       int(reps), ctypes.byref(best), ctypes.byref(ms)), "pcdf_batch_autotune")
+    return (best.row_rows, best.dyn_slices, best.comp_t), ms.value

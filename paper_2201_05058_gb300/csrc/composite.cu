@@ -1,449 +1,33 @@
-// Predicted composite fields (Sec. 6 composition, Sec. 8 sequence of fields)
-// on sm_103a.
-//
-// The field of the humans at time t is the exact signed EDT of the voxels
-// inside their capsules; its sites all lie in the z-slab [zlo, zlo + S) that
-// the capsules touch.  Two kernels build the composite of every t:
-//
-//  k_dyn_xy      one CTA per (slab slice, t): the exact x-interval of each
-//                capsule on every row of the slice, then per column x the
-//                y lower envelopes of the row distances to those intervals.
-//                Output: the 2-D partial field of the slice (signed int32),
-//                with no row-pass intermediate in memory.
-//  k_composite_z thread per (column (x, y), t): the z envelope of the slab's
-//                2-D partials, evaluated at every z, min with the static
-//                field, float epilogue; the T CTAs that share a static column
-//                block run together so that block is read from DRAM once.
+// Predicted composite fields (Sec. 6, Sec. 8) on sm_103a: stand-alone
+// kernels and launchers; the algorithms are described in composite.cuh.
 #include <cuda_runtime.h>
 
-#include "edt_common.cuh"
+#include "composite.cuh"
 
 namespace pcdf {
 namespace {
-
-// ---------------------------------------------------------------------------
-// k_dyn_xy
-// ---------------------------------------------------------------------------
-// Shared memory: rows[ny][H + 1] = interval count, then the merged maximal
-// occupied runs of the row as (xa << 16 | xb); then a stack of `cap` words per
-// thread, laid out [entry][thread].
-
-__device__ __forceinline__ bool row_inside(const int32_t *r, int x)
-{
-    const int cnt = r[0];
-    for (int i = 1; i <= cnt; ++i)
-        if (x >= (r[i] >> 16) && x <= (r[i] & 0xFFFF))
-            return true;
-    return false;
-}
-
-// squared distance along the row from x to the nearest occupied voxel (-1: none)
-__device__ __forceinline__ int row_g_occ(const int32_t *r, int x)
-{
-    const int cnt = r[0];
-    if (cnt == 0)
-        return -1;
-    int d = 1 << 20;
-    for (int i = 1; i <= cnt; ++i) {
-        const int a = r[i] >> 16, b = r[i] & 0xFFFF;
-        const int di = x < a ? a - x : (x > b ? x - b : 0);
-        d = min(d, di);
-    }
-    return d * d;
-}
-
-// squared distance along the row from an occupied x to the nearest free voxel
-// (-1: the whole row is occupied); runs are maximal, so the neighbours of the
-// run holding x are free
-__device__ __forceinline__ int row_g_free(const int32_t *r, int x, int nx)
-{
-    const int cnt = r[0];
-    for (int i = 1; i <= cnt; ++i) {
-        const int a = r[i] >> 16, b = r[i] & 0xFFFF;
-        if (x >= a && x <= b) {
-            int d = 1 << 20;
-            if (a - 1 >= 0)
-                d = x - a + 1;
-            if (b + 1 <= nx - 1)
-                d = min(d, b - x + 1);
-            return d == (1 << 20) ? -1 : d * d;
-        }
-    }
-    return 0;
-}
 
 __global__ void __launch_bounds__(128)
     k_dyn_xy(const __grid_constant__ CapBatch caps, int H, int nx, int ny, int zlo, int S, int t0, int cap,
              int32_t *__restrict__ dyn_mid)
 {
     extern __shared__ __align__(16) int32_t sm[];
-    __shared__ int s_ylo, s_yhi;
-    const int s = blockIdx.x, tl = blockIdx.y, z = zlo + s;
-    const int nthr = blockDim.x, tid = threadIdx.x;
-    const int rw = H + 1;
-    int32_t *rows = sm;
-    uint32_t *stk = reinterpret_cast<uint32_t *>(sm + ny * rw) + tid;  // entry q at stk[q * nthr]
-    if (tid == 0) {
-        s_ylo = ny;
-        s_yhi = -1;
-    }
-    __syncthreads();
-
-    // rows: merged occupied runs of every capsule crossing this slice
-    for (int y = tid; y < ny; y += nthr) {
-        int32_t *r = rows + y * rw;
-        int cnt = 0;
-        for (int h = 0; h < H; ++h) {
-            const CapInfo &ci = caps.caps[tl * H + h];
-            if (ci.lo[0] > ci.hi[0] || z < ci.lo[2] || z > ci.hi[2] || y < ci.lo[1] || y > ci.hi[1])
-                continue;
-            // the capsule is convex, so its voxels on this row form one run
-            int xa = -1, xb = -2;
-            for (int x = ci.lo[0]; x <= ci.hi[0]; ++x) {
-                if (capsule_contains(ci, x, y, z)) {
-                    if (xa < 0)
-                        xa = x;
-                    xb = x;
-                } else if (xa >= 0) {
-                    break;
-                }
-            }
-            if (xa < 0)
-                continue;
-            int i = cnt;
-            while (i > 0 && (r[i] >> 16) > xa) {
-                r[i + 1] = r[i];
-                --i;
-            }
-            r[i + 1] = (xa << 16) | xb;
-            ++cnt;
-        }
-        int m = 0;  // merge overlapping or touching runs
-        for (int i = 1; i <= cnt; ++i) {
-            const int a = r[i] >> 16, b = r[i] & 0xFFFF;
-            if (m > 0 && a <= (r[m] & 0xFFFF) + 1) {
-                if (b > (r[m] & 0xFFFF))
-                    r[m] = (r[m] & ~0xFFFF) | b;
-            } else {
-                r[++m] = r[i];
-            }
-        }
-        r[0] = m;
-        if (m) {
-            atomicMin(&s_ylo, y);
-            atomicMax(&s_yhi, y);
-        }
-    }
-    __syncthreads();
-    const int ylo = s_ylo, yhi = s_yhi;
-    const int t = t0 + tl;
-    const long long V2 = (long long)nx * ny;
-
-    for (int x = tid; x < nx; x += nthr) {
-        int32_t *oc = dyn_mid + ((long long)t * S + s) * V2 + x;  // element y at oc[y * nx]
-        if (yhi < 0) {
-            for (int y = 0; y < ny; ++y)
-                oc[(long long)y * nx] = kInf32;
-            continue;
-        }
-        int fo = ny, lo_ = -1;  // first / last occupied row of this column
-        for (int y = ylo; y <= yhi; ++y)
-            if (row_inside(rows + y * rw, x)) {
-                if (fo == ny)
-                    fo = y;
-                lo_ = y;
-            }
-
-        // distances to free voxels at the occupied voxels (set F).  Free rows
-        // matter only next to an occupied row: the nearest free voxel of any
-        // occupied voxel is the first free row out of its run.
-        if (lo_ >= 0) {
-            const int y0 = max(fo - 1, 0), y1 = min(lo_ + 1, ny - 1);
-            int top = -1, s0 = 0, g0 = 0, s1 = 0, g1 = 0;
-            bool prev_occ = false;  // y0 - 1 lies before the first occupied row
-            bool cur_occ = y0 >= ylo && y0 <= yhi && row_inside(rows + y0 * rw, x);
-            for (int y = y0; y <= y1; ++y) {
-                const bool next_occ = y + 1 <= y1 && y + 1 >= ylo && y + 1 <= yhi && row_inside(rows + (y + 1) * rw, x);
-                int g;
-                if (cur_occ)
-                    g = row_g_free(rows + y * rw, x, nx);
-                else
-                    g = (prev_occ || next_occ) ? 0 : -1;
-                prev_occ = cur_occ;
-                cur_occ = next_occ;
-                if (g < 0)
-                    continue;
-                while (top >= 1 && dominated(s0, g0, s1, g1, y, g)) {
-                    --top;
-                    s1 = s0;
-                    g1 = g0;
-                    if (top >= 1) {
-                        const uint32_t w = stk[(top - 1) * nthr];
-                        s0 = site_of(w);
-                        g0 = gval_of(w);
-                    }
-                }
-                ++top;
-                stk[top * nthr] = pack_site(y, g);
-                s0 = s1;
-                g0 = g1;
-                s1 = y;
-                g1 = g;
-            }
-            int q = 0, sc = 0, gc = 0;
-            if (top >= 0) {
-                const uint32_t w = stk[0];
-                sc = site_of(w);
-                gc = gval_of(w);
-            }
-            for (int y = fo; y <= lo_; ++y) {
-                if (!row_inside(rows + y * rw, x))
-                    continue;
-                int32_t r = -kInf32;
-                if (top >= 0) {
-                    int fc = parab(y, sc, gc);
-                    while (q < top) {
-                        const uint32_t w = stk[(q + 1) * nthr];
-                        const int fn = parab(y, site_of(w), gval_of(w));
-                        if (fn > fc)
-                            break;
-                        ++q;
-                        sc = site_of(w);
-                        gc = gval_of(w);
-                        fc = fn;
-                    }
-                    r = -fc;
-                }
-                oc[(long long)y * nx] = r;
-            }
-        }
-
-        // distances to occupied voxels at the free voxels (set O): sites are
-        // the rows holding a run (g = 0 where x is inside one)
-        int top = -1, s0 = 0, g0 = 0, s1 = 0, g1 = 0;
-        for (int y = ylo; y <= yhi; ++y) {
-            const int g = row_g_occ(rows + y * rw, x);
-            if (g < 0)
-                continue;
-            while (top >= 1 && dominated(s0, g0, s1, g1, y, g)) {
-                --top;
-                s1 = s0;
-                g1 = g0;
-                if (top >= 1) {
-                    const uint32_t w = stk[(top - 1) * nthr];
-                    s0 = site_of(w);
-                    g0 = gval_of(w);
-                }
-            }
-            ++top;
-            stk[top * nthr] = pack_site(y, g);
-            s0 = s1;
-            g0 = g1;
-            s1 = y;
-            g1 = g;
-        }
-        int q = 0, sc = 0, gc = 0;
-        {
-            const uint32_t w = stk[0];  // top >= 0: some row of [ylo, yhi] holds a run
-            sc = site_of(w);
-            gc = gval_of(w);
-        }
-        for (int y = 0; y < ny; ++y) {
-            if (y >= fo && y <= lo_ && row_inside(rows + y * rw, x))
-                continue;
-            int fc = parab(y, sc, gc);
-            while (q < top) {
-                const uint32_t w = stk[(q + 1) * nthr];
-                const int fn = parab(y, site_of(w), gval_of(w));
-                if (fn > fc)
-                    break;
-                ++q;
-                sc = site_of(w);
-                gc = gval_of(w);
-                fc = fn;
-            }
-            oc[(long long)y * nx] = fc;
-        }
-    }
+    comp::dyn_xy_slice(caps.caps + blockIdx.y * H, H, nx, ny, zlo, S, t0 + (int)blockIdx.y, (int)blockIdx.x, cap,
+                       dyn_mid, sm);
 }
 
-// ---------------------------------------------------------------------------
-// k_composite_z
-// ---------------------------------------------------------------------------
-// Shared memory per thread, [slot][thread]: slots 1..S hold the staged slab
-// column (slab element e in slot e + 1); slot 0 and slot S + 1 give the
-// in-place stacks room for the sites just below and above the slab; then the
-// occupancy bits of the slab column.
-//
-// Set F (distance to free voxels, output at the voxels inside a human) runs
-// first, in place over the staged column, and writes its outputs directly;
-// the column is then reloaded and set O (distance to the humans, output
-// everywhere else) is built in place and walked along z.  Where the static
-// field is nearer than the humans the float output is the static float field
-// itself (same value, no square root).
-
-template <bool kStaticSdf>
-__device__ __forceinline__ void emit_one(int z, int32_t sv, float sf, int d, int32_t *ocol, float *fcol, long long o,
-                                         float vox)
-{
-    const int32_t cv = min(sv, d);
-    if (ocol)
-        __stcs(ocol + o, cv);
-    if (fcol) {
-        float f;
-        if (kStaticSdf && sv <= d)
-            f = sf;
-        else
-            f = sq_to_sdf_fast(cv, vox);
-        __stcs(fcol + o, f);
-    }
-}
-
-// outputs for z in [z0, z1) that are not inside a human (kCheck: test the bits)
-template <bool kCheck, bool kStaticSdf>
-__device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, const uint32_t *mk, int zlo, int nthr,
-                                           const int32_t *scol, const float *sfcol, long long V2, int32_t *ocol,
-                                           float *fcol, float vox)
-{
-    int z = z0;
-    for (; z + 8 <= z1; z += 8) {
-        int32_t sv[8];
-        float sf[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            sv[i] = __ldg(scol + (long long)(z + i) * V2);
-            if (kStaticSdf)
-                sf[i] = __ldg(sfcol + (long long)(z + i) * V2);
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int zz = z + i;
-            if (kCheck) {
-                const int e = zz - zlo;
-                if ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u)
-                    continue;
-            }
-            const int d = O.eval(zz);
-            emit_one<kStaticSdf>(zz, sv[i], kStaticSdf ? sf[i] : 0.f, d < 0 ? kInf32 : d, ocol, fcol,
-                                 (long long)zz * V2, vox);
-        }
-    }
-    for (; z < z1; ++z) {
-        if (kCheck) {
-            const int e = z - zlo;
-            if ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u)
-                continue;
-        }
-        const int d = O.eval(z);
-        emit_one<kStaticSdf>(z, __ldg(scol + (long long)z * V2), kStaticSdf ? __ldg(sfcol + (long long)z * V2) : 0.f,
-                             d < 0 ? kInf32 : d, ocol, fcol, (long long)z * V2, vox);
-    }
-}
-
-template <bool kStaticSdf>
+// CTAs are ordered t-fastest, so the T CTAs of one column block run together
+// and read the static column block from DRAM once.
+template <bool kSq, bool kSdfOut, bool kStaticSdf>
 __global__ void __launch_bounds__(128, 8)
     k_composite_z(const int32_t *__restrict__ static_sq, const float *__restrict__ static_sdf,
                   const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz, int zlo, int S, int T,
                   int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox)
 {
     extern __shared__ uint32_t smem[];
-    const int nthr = blockDim.x, tid = threadIdx.x;
-    const long long V2 = (long long)nx * ny;
-    const int t = blockIdx.x % T;
-    const long long c = (long long)(blockIdx.x / T) * nthr + tid;
-    if (c >= V2)
-        return;  // no block-level synchronisation below
-    uint32_t *tile = smem + tid;                              // slot k at tile[k * nthr]
-    uint32_t *mk = smem + (size_t)(S + 2) * nthr + tid;       // word w at mk[w * nthr]
-    const int nw = (S + 31) >> 5;
-    const int32_t *dcol = dyn_mid + (long long)t * S * V2 + c;
-
-#pragma unroll 8
-    for (int e = 0; e < S; ++e)
-        tile[(e + 1) * nthr] = (uint32_t)__ldcs(dcol + (long long)e * V2);
-
-    int firstOcc = S, lastOcc = -1;
-    for (int w = 0; w < nw; ++w) {
-        uint32_t bits = 0;
-        const int e0 = w << 5, cnt = min(32, S - e0);
-        for (int b = 0; b < cnt; ++b)
-            bits |= (uint32_t)((int32_t)tile[(e0 + b + 1) * nthr] < 0) << b;
-        mk[w * nthr] = bits;
-        if (bits) {
-            if (firstOcc == S)
-                firstOcc = e0 + __ffs(bits) - 1;
-            lastOcc = e0 + 31 - __clz(bits);
-        }
-    }
-    const long long V = V2 * nz;
-    const int32_t *scol = static_sq + c;
-    const float *sfcol = kStaticSdf ? static_sdf + c : nullptr;
-    int32_t *ocol = comp_sq ? comp_sq + (long long)t * V + c : nullptr;
-    float *fcol = comp_sdf ? comp_sdf + (long long)t * V + c : nullptr;
-    auto occupied = [&](int z) {
-        const int e = z - zlo;
-        return e >= 0 && e < S && ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u);
-    };
-
-    const int zo0 = zlo + firstOcc, zo1 = zlo + lastOcc;
-    if (lastOcc >= 0) {
-        // set F over [zo0 - 1, zo1 + 1]; free voxels are sites only next to an
-        // occupied one.  Site z sits in slot z - zlo + 1, read before written.
-        const int zr0 = max(zo0 - 1, 0), zr1 = min(zo1 + 1, nz - 1);
-        EnvBuilder B(tile + (zr0 - zlo + 1) * nthr, nthr);
-        for (int z = zr0; z <= zr1; ++z) {
-            int g;
-            if (occupied(z)) {
-                const int32_t v = (int32_t)tile[(z - zlo + 1) * nthr];
-                if (v == -kInf32)
-                    continue;
-                g = -v;
-            } else {
-                if (!occupied(z - 1) && !occupied(z + 1))
-                    continue;
-                g = 0;
-            }
-            B.push(z, g);
-        }
-        EnvCursor F(tile + (zr0 - zlo + 1) * nthr, nthr, B.top);
-        for (int z = zo0; z <= zo1; ++z) {
-            if (!occupied(z))
-                continue;
-            const int f = F.eval(z);
-            const long long o = (long long)z * V2;
-            emit_one<kStaticSdf>(z, __ldg(scol + o), kStaticSdf ? __ldg(sfcol + o) : 0.f, f < 0 ? -kInf32 : -f,
-                                 ocol, fcol, o, vox);
-        }
-        // restore the staged column for set O
-#pragma unroll 8
-        for (int e = 0; e < S; ++e)
-            tile[(e + 1) * nthr] = (uint32_t)__ldg(dcol + (long long)e * V2);
-    }
-
-    // set O over the slab: sites are the free slab voxels with a finite
-    // partial and the ends of the occupied runs (zero distance)
-    EnvBuilder B(tile + nthr, nthr);
-    for (int e = 0; e < S; ++e) {
-        const int32_t v = (int32_t)tile[(e + 1) * nthr];
-        int g;
-        if (v >= 0) {
-            if (v == kInf32)
-                continue;
-            g = v;
-        } else {
-            const int z = zlo + e;
-            if (occupied(z - 1) && occupied(z + 1))
-                continue;
-            g = 0;
-        }
-        B.push(zlo + e, g);
-    }
-    EnvCursor O(tile + nthr, nthr, B.top);
-    // below the occupied run, the run (skipping its voxels), above it
-    const int za = lastOcc >= 0 ? zo0 : nz, zb = lastOcc >= 0 ? zo1 + 1 : nz;
-    emit_range<false, kStaticSdf>(0, za, O, mk, zlo, nthr, scol, sfcol, V2, ocol, fcol, vox);
-    emit_range<true, kStaticSdf>(za, zb, O, mk, zlo, nthr, scol, sfcol, V2, ocol, fcol, vox);
-    emit_range<false, kStaticSdf>(zb, nz, O, mk, zlo, nthr, scol, sfcol, V2, ocol, fcol, vox);
+    comp::composite_block<kSq, kSdfOut, kStaticSdf, false>(static_sq, static_sdf, dyn_mid, nx, ny, nz, zlo, S,
+                                                           (int)(blockIdx.x % T), (long long)(blockIdx.x / T) * blockDim.x,
+                                                           comp_sq, comp_sdf, vox, smem);
 }
 
 __global__ void k_broadcast_static(const int32_t *__restrict__ static_sq, long long V, int T,
@@ -484,6 +68,20 @@ cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, 
     return cudaGetLastError();
 }
 
+template <bool kSq, bool kSdfOut, bool kStaticSdf>
+cudaError_t launch_cz(int nblk, int nthr, size_t smem, const int32_t *static_sq, const float *static_sdf,
+                      const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int T, int32_t *comp_sq,
+                      float *comp_sdf, float vox, cudaStream_t stream)
+{
+    auto kern = k_composite_z<kSq, kSdfOut, kStaticSdf>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, static_sdf, dyn_mid, nx, ny, nz, zlo, S, T, comp_sq,
+                                                 comp_sdf, vox);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf, const int32_t *dyn_mid, int nx,
                                int ny, int nz, int zlo, int S, int T, int32_t *comp_sq, float *comp_sdf, float vox,
                                cudaStream_t stream)
@@ -494,22 +92,21 @@ cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf
     while (nthr > 32 && (size_t)nthr * words * sizeof(uint32_t) > 200 * 1024)
         nthr >>= 1;
     const size_t smem = (size_t)nthr * words * sizeof(uint32_t);
-    const long long nblk = (V2 + nthr - 1) / nthr * T;
-    cudaError_t e;
-    if (static_sdf) {
-        e = cudaFuncSetAttribute(k_composite_z<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        k_composite_z<true><<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, static_sdf, dyn_mid, nx, ny, nz, zlo,
-                                                                    S, T, comp_sq, comp_sdf, vox);
-    } else {
-        e = cudaFuncSetAttribute(k_composite_z<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        k_composite_z<false><<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, nullptr, dyn_mid, nx, ny, nz, zlo, S,
-                                                                     T, comp_sq, comp_sdf, vox);
-    }
-    return cudaGetLastError();
+    const int nblk = (int)((V2 + nthr - 1) / nthr * T);
+#define PCDF_CZ(a, b, c)                                                                                            \
+    return launch_cz<a, b, c>(nblk, nthr, smem, static_sq, static_sdf, dyn_mid, nx, ny, nz, zlo, S, T, comp_sq,     \
+                              comp_sdf, vox, stream)
+    const bool sq = comp_sq != nullptr, sd = comp_sdf != nullptr, st = static_sdf != nullptr && sd;
+    if (sq && sd && st)
+        PCDF_CZ(true, true, true);
+    if (sq && sd)
+        PCDF_CZ(true, true, false);
+    if (sq)
+        PCDF_CZ(true, false, false);
+    if (st)
+        PCDF_CZ(false, true, true);
+    PCDF_CZ(false, true, false);
+#undef PCDF_CZ
 }
 
 cudaError_t launch_broadcast_static(const int32_t *static_sq, long long V, int T, int32_t *comp_sq,

@@ -1,0 +1,250 @@
+// Host-side helpers of the C ABI: argument checks, capsule tables and the
+// plan (slab, workspace layout) of a composite request.  Host code only.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "host.h"
+
+namespace pcdf {
+namespace host {
+
+thread_local char g_err[512] = "";
+
+const char *last_error() { return g_err; }
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(PCDF_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int check_grid(const pcdf_grid *g)
+{
+    if (!g)
+        return fail(PCDF_EINVAL, "grid is NULL");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nx > PCDF_MAX_DIM || g->ny > PCDF_MAX_DIM ||
+        g->nz > PCDF_MAX_DIM)
+        return fail(PCDF_EINVAL, "grid dims %d x %d x %d outside [1, %d]", g->nx, g->ny, g->nz, PCDF_MAX_DIM);
+    if (!std::isfinite(g->vox) || !(g->vox > 0.f))
+        return fail(PCDF_EINVAL, "voxel size must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(g->origin[a]))
+            return fail(PCDF_EINVAL, "origin must be finite");
+    return PCDF_OK;
+}
+
+long long nvox(const pcdf_grid *g) { return (long long)g->nx * g->ny * g->nz; }
+
+// floor(a / b) for b > 0
+long long floordiv(long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Capsule ranges and the voxel-index bounding box of its voxel centres: a
+// centre 16 i + 8 can lie within r of the segment only if it lies within
+// [min(a, b) - r, max(a, b) + r] on every axis.
+int make_capinfo(const pcdf_grid *g, int T, int H, const int32_t *caps, std::vector<pcdf::CapInfo> &out,
+                 int *zlo, int *zhi)
+{
+    const int n[3] = {g->nx, g->ny, g->nz};
+    out.resize((size_t)T * H);
+    *zlo = n[2];
+    *zhi = -1;
+    for (long long q = 0; q < (long long)T * H; ++q) {
+        const int32_t *c = caps + 7 * q;
+        for (int a = 0; a < 6; ++a)
+            if (c[a] < PCDF_CAP_MIN || c[a] > PCDF_CAP_MAX)
+                return fail(PCDF_EINVAL, "capsule %lld coordinate %d = %d outside [%d, %d]", q, a, c[a],
+                            PCDF_CAP_MIN, PCDF_CAP_MAX);
+        if (c[6] < 0 || c[6] > PCDF_CAP_MAX_R)
+            return fail(PCDF_EINVAL, "capsule %lld radius %d outside [0, %d]", q, c[6], PCDF_CAP_MAX_R);
+        pcdf::CapInfo &ci = out[q];
+        std::memset(&ci, 0, sizeof(ci));
+        bool empty = false;
+        for (int a = 0; a < 3; ++a) {
+            ci.a[a] = c[a];
+            ci.b[a] = c[3 + a];
+            const long long mn = std::min(c[a], c[3 + a]) - (long long)c[6];
+            const long long mx = std::max(c[a], c[3 + a]) + (long long)c[6];
+            long long lo = floordiv(mn - 8 + 15, 16);  // ceil((mn - 8) / 16)
+            long long hi = floordiv(mx - 8, 16);
+            lo = std::max(lo, 0LL);
+            hi = std::min(hi, (long long)n[a] - 1);
+            ci.lo[a] = (int32_t)lo;
+            ci.hi[a] = (int32_t)hi;
+            empty |= lo > hi;
+        }
+        ci.r = c[6];
+        if (empty) {
+            for (int a = 0; a < 3; ++a) {
+                ci.lo[a] = 1;
+                ci.hi[a] = 0;
+            }
+            continue;
+        }
+        *zlo = std::min(*zlo, ci.lo[2]);
+        *zhi = std::max(*zhi, ci.hi[2]);
+    }
+    return PCDF_OK;
+}
+
+int check_caps_args(int T, int H, const int32_t *caps)
+{
+    if (T < 1 || T > PCDF_MAX_T)
+        return fail(PCDF_EINVAL, "T = %d outside [1, %d]", T, PCDF_MAX_T);
+    if (H < 0 || H > PCDF_MAX_H)
+        return fail(PCDF_EINVAL, "H = %d outside [0, %d]", H, PCDF_MAX_H);
+    if (H > 0 && !caps)
+        return fail(PCDF_EINVAL, "caps is NULL with H = %d", H);
+    return PCDF_OK;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Static (or union) signed EDT of one grid: row pass (mode 0 or 1 with the
+// capsules of one t), y envelope, z envelope with optional float epilogue.
+int run_full_edt(const pcdf_grid *g, int mode, const uint8_t *occ, const pcdf::CapBatch *caps, int H, int32_t *sq,
+                 float *sdf, void *ws, cudaStream_t st)
+{
+    const long long V = nvox(g);
+    int16_t *g16 = (int16_t *)ws;
+    int32_t *mid = (int32_t *)((char *)ws + align_up((size_t)V * sizeof(int16_t)));
+    cudaError_t e = pcdf::launch_pass_x(mode, occ, caps, H, g->nx, g->ny, 0, g->nz, 1, g16, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "row pass");
+    const long long slice = (long long)g->nx * g->ny;
+    e = pcdf::launch_envelope_i16(g16, mid, g->ny, g->nx, (long long)g->nx * g->nz, slice, g->nx, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "y pass");
+    e = pcdf::launch_envelope_i32(mid, sq, sdf, g->vox, g->nz, g->nx, slice, g->nx, slice, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "z pass");
+    return PCDF_OK;
+}
+
+size_t full_edt_ws(const pcdf_grid *g)
+{
+    const long long V = nvox(g);
+    return align_up((size_t)V * sizeof(int16_t)) + align_up((size_t)V * sizeof(int32_t));
+}
+
+
+
+int plan_composite(const pcdf_grid *grid, int T, int H, const int32_t *caps, CompositePlan &p)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (int rc = check_caps_args(T, H, caps))
+        return rc;
+    if (H > 0)
+        if (int rc = make_capinfo(grid, T, H, caps, p.ci, &p.zlo, &p.zhi))
+            return rc;
+    p.S = p.zhi >= p.zlo ? p.zhi - p.zlo + 1 : 0;
+    p.slab = (long long)T * p.S * grid->nx * grid->ny;
+    // stack bound of the analytic kernel: rows holding a run (<= sum of the
+    // capsules' y extents) plus two free rows per run (one run per capsule)
+    int ext_max = 0;
+    for (int t = 0; t < T; ++t) {
+        int ext = 0;
+        for (int h = 0; h < H; ++h) {
+            const pcdf::CapInfo &c = p.ci[(size_t)t * H + h];
+            if (c.lo[0] <= c.hi[0])
+                ext += c.hi[1] - c.lo[1] + 1;
+        }
+        ext_max = std::max(ext_max, ext);
+    }
+    p.cap = std::min(ext_max + 2 * H + 2, grid->ny + 2);
+    p.fused = H <= pcdf::kMaxCapsPerLaunch && pcdf::dyn_xy_fits(grid->ny, H, p.cap);
+    if (p.S == 0)
+        p.need = 0;
+    else if (p.fused)
+        p.need = align_up((size_t)p.slab * sizeof(int32_t));
+    else
+        p.need = align_up((size_t)p.slab * sizeof(int16_t)) + align_up((size_t)p.slab * sizeof(int32_t));
+    return PCDF_OK;
+}
+
+int32_t *plan_mid(const CompositePlan &p, void *workspace)
+{
+    return p.fused ? (int32_t *)workspace
+                   : (int32_t *)((char *)workspace + align_up((size_t)p.slab * sizeof(int16_t)));
+}
+
+int check_ws(const CompositePlan &p, void *workspace, size_t workspace_bytes)
+{
+    if (p.S == 0)
+        return PCDF_OK;
+    if (!workspace || !aligned(workspace, kAlign))
+        return fail(PCDF_EINVAL, "workspace must be non-NULL and %zu-byte aligned", kAlign);
+    if (workspace_bytes < p.need)
+        return fail(PCDF_ENOMEM, "workspace %zu bytes < %zu needed", workspace_bytes, p.need);
+    return PCDF_OK;
+}
+
+int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &p, void *workspace,
+                      cudaStream_t st)
+{
+    if (p.S == 0)
+        return PCDF_OK;
+    int32_t *mid = plan_mid(p, workspace);
+    const long long sliceN = (long long)grid->nx * grid->ny;
+    // capsules travel as kernel parameters, in chunks of whole time steps
+    const int t_chunk = std::max(1, pcdf::kMaxCapsPerLaunch / std::max(H, 1));
+    static thread_local pcdf::CapBatch batch;
+    if (p.fused) {
+        for (int t0 = 0; t0 < T; t0 += t_chunk) {
+            const int nt = std::min(t_chunk, T - t0);
+            batch.count = nt * H;
+            std::memcpy(batch.caps, p.ci.data() + (size_t)t0 * H, sizeof(pcdf::CapInfo) * nt * H);
+            cudaError_t e = pcdf::launch_dyn_xy(&batch, H, grid->nx, grid->ny, p.zlo, p.S, t0, nt, p.cap, mid, st);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "dynamic x+y pass");
+        }
+        return PCDF_OK;
+    }
+    int16_t *g16 = (int16_t *)workspace;
+    for (int t0 = 0; t0 < T; t0 += t_chunk) {
+        const int nt = std::min(t_chunk, T - t0);
+        batch.count = nt * H;
+        std::memcpy(batch.caps, p.ci.data() + (size_t)t0 * H, sizeof(pcdf::CapInfo) * nt * H);
+        cudaError_t e = pcdf::launch_pass_x(2, nullptr, &batch, H, grid->nx, grid->ny, p.zlo, p.S, nt,
+                                            g16 + (long long)t0 * p.S * sliceN, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "dynamic row pass");
+    }
+    cudaError_t e = pcdf::launch_envelope_i16(g16, mid, grid->ny, grid->nx, (long long)grid->nx * T * p.S, sliceN,
+                                              grid->nx, st);
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "dynamic y pass");
+}
+
+int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int T,
+                     const CompositePlan &p, int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st)
+{
+    cudaError_t e;
+    if (p.S == 0) {
+        e = pcdf::launch_broadcast_static(static_sq, nvox(grid), T, comp_sq, comp_sdf, grid->vox, st);
+        return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "broadcast");
+    }
+    const int32_t *mid = plan_mid(p, workspace);
+    e = pcdf::launch_composite_z(static_sq, static_sdf, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, T, comp_sq, comp_sdf,
+                                 grid->vox, st);
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "composite z pass");
+}
+
+
+}  // namespace host
+}  // namespace pcdf

@@ -98,15 +98,17 @@ def check_composite(occ, caps, grid):
     against the oracle."""
     static_sq, static_sdf = pcdf.build_static_sdf(cuda(occ), grid)
     want = oracle.predicted_composite(oracle.edt(occ), caps)
-    for reuse in (False, True):
-        comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, caps,
+    for reuse, want_sq in ((False, True), (True, True), (True, False)):
+        comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, caps, want_sq=want_sq,
                                                            static_sdf=static_sdf if reuse else None)
-        comp_sq = comp_sq.cpu().numpy()
         comp_sdf = comp_sdf.cpu().numpy()
         for t in range(caps.shape[0]):
-            assert_equal_fields(comp_sq[t], want[t], f"comp_sq[{t}] reuse={reuse}")
+            if want_sq:
+                assert_equal_fields(comp_sq[t].cpu().numpy(), want[t], f"comp_sq[{t}] reuse={reuse}")
             assert_bits_equal(comp_sdf[t], oracle.sdf_from_sq(want[t], grid.vox), f"comp_sdf[{t}] reuse={reuse}")
-    return comp_sq
+        if want_sq:
+            out = comp_sq.cpu().numpy()
+    return out
 
 
 @pytest.mark.parametrize("seed", [0, 5])
