@@ -56,6 +56,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
     ap.add_argument("--profile-case", choices=["composite", "static", "scratch", "query"], default=None,
                     help="run one small untimed case of the named stage (for ncu captures) and exit")
     ap.add_argument("--profile-T", type=int, default=4, help="horizon of the --profile-case composite")
@@ -228,6 +229,60 @@ def run_reference(args):
 # native arm
 # ---------------------------------------------------------------------------
 
+def bench_batched(dev, seed, steps):
+    """64 ragged environments (per-axis sizes 64-320 x 64-320 x 64-128, T 5-30,
+    1-4 humans, 4 cm voxels), int32 composite fields: one graph-captured
+    persistent launch with autotuned tiles, against 64 separate per-environment
+    calls on the same stream."""
+    import torch
+
+    import paper_2201_05058_gb300 as pcdf
+    envs = scenes.scene_batch(seed=seed)
+    dev_envs = [(e["grid"], torch.from_numpy(e["occ"]).to(dev), e["caps"]) for e in envs]
+    vox_t = sum(e["grid"].nvox * e["caps"].shape[0] for e in envs)
+    tiles, tune_ms = pcdf.batch_autotune(dev_envs, reps=2)
+    b = pcdf.Batch(dev_envs, tiles=tiles)
+    b.run()
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run()
+    g.replay()
+    torch.cuda.synchronize(dev)
+    k = max(3, min(steps, 10))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for a, z in ev:
+        a.record()
+        g.replay()
+        z.record()
+    torch.cuda.synchronize(dev)
+    graph_ms = float(np.mean([a.elapsed_time(z) for a, z in ev]))
+    status = b.error()
+    # the same work as separate calls (static + composite per environment)
+    statics = [torch.empty(gr.shape, dtype=torch.int32, device=dev) for gr, _, _ in dev_envs]
+
+    def separate():
+        for (gr, occ, caps), st, out in zip(dev_envs, statics, b.comp_sq):
+            pcdf.build_static_sdf(occ, gr, want_sdf=False, out_sq=st)
+            pcdf.build_predicted_composite(st, gr, caps, want_sdf=False, out_sq=out)
+
+    separate()
+    torch.cuda.synchronize(dev)
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for a, z in ev2:
+        a.record()
+        separate()
+        z.record()
+    torch.cuda.synchronize(dev)
+    sep_ms = float(np.mean([a.elapsed_time(z) for a, z in ev2]))
+    b.close()
+    return {"workload": "64 ragged environments, 64-320 x 64-320 x 64-128 voxels, T 5-30, 1-4 humans, int32 fields",
+            "voxel_fields": int(vox_t), "graph_ms": graph_ms, "gvox_s": vox_t / (graph_ms * 1e-3) / 1e9,
+            "separate_calls_ms": sep_ms, "separate_gvox_s": vox_t / (sep_ms * 1e-3) / 1e9,
+            "tiles": {"row_rows": tiles[0], "dyn_slices": tiles[1], "comp_t": tiles[2]},
+            "autotune_best_ms": tune_ms, "status": status}
+
+
 def run_native(args):
     import torch
 
@@ -384,6 +439,8 @@ def run_native(args):
            "ms_per_step": e2e_total / k_e2e,
            "what": "H2D occupancy (pinned) + capsules, static + composite, D2H of the T float fields (pinned)"}
 
+    batched = bench_batched(dev, rank_seed(args.seed, rank), args.steps) if not args.no_batched else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc)
@@ -401,7 +458,7 @@ def run_native(args):
             "composite_only": {"ms": comp_avg, "gvox_s": T * V / (comp_avg * 1e-3) / 1e9},
             "from_scratch": {"ms": scr_avg, "gvox_s": T * V / (scr_avg * 1e-3) / 1e9,
                              "composite_speedup": scr_avg / comp_avg},
-            "query": query, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "query": query, "batched": batched, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
