@@ -238,6 +238,82 @@ int pcdf_batch_autotune_workspace_bytes(const pcdf_env *envs, int32_t n_env, siz
 int pcdf_batch_autotune(const pcdf_env *envs, int32_t n_env, void *workspace, size_t workspace_bytes, void *stream,
                         int32_t reps, pcdf_batch_tiles *best, float *best_ms);
 
+/* ---------------------------------------------------------------------------
+ * Learned surrogate of the dynamic field: a BF16 MLP with FP32 accumulation
+ * (an extension beyond the paper).  16 inputs (PCDF_MLP_IN features, then
+ * zero pads) -> 256 -> 256 -> 256 -> 1, ReLU after the hidden layers.
+ *
+ * State: one device buffer of pcdf_mlp_state_bytes(), 256-byte aligned,
+ * holding the FP32 parameter vector, the two Adam moments and the gradient
+ * (each PCDF_MLP_PARAMS_PAD floats, in that order), then the BF16 copies of the
+ * weight matrices (PCDF_MLP_BF16_WEIGHTS values).  Parameter vector order:
+ * W1 [256][16], b1 [256], W2 [256][256], b2, W3 [256][256], b3, w4 [256], b4;
+ * the BF16 copies hold W1, W2, W3, w4 in the same layouts.  Layer l computes
+ * relu(x W_l^T + b_l); activations and input gradients are stored in BF16.
+ *
+ * x: device BF16 bits [M][16] (16-byte aligned); y, target: device FP32 [M].
+ * Workspace: pcdf_mlp_workspace_bytes(M), 256-byte aligned.
+ * pcdf_mlp_backward runs the forward pass (y), the loss mean((y - t)^2)
+ * (added to *loss if non-NULL, after zeroing it) and overwrites the gradient.
+ * pcdf_mlp_adam applies one Adam step (bias-corrected, step >= 1) to the FP32
+ * parameters and refreshes the BF16 copies.
+ * ------------------------------------------------------------------------- */
+#define PCDF_MLP_IN 11
+#define PCDF_MLP_IN_PAD 16
+#define PCDF_MLP_WIDTH 256
+#define PCDF_MLP_PARAMS 136193
+#define PCDF_MLP_PARAMS_PAD 136196
+#define PCDF_MLP_BF16_WEIGHTS 135424
+
+int pcdf_mlp_state_bytes(size_t *bytes);
+int pcdf_mlp_workspace_bytes(int64_t M, size_t *bytes);
+int pcdf_mlp_init(void *state, uint64_t seed, void *stream);
+int pcdf_mlp_forward(const void *state, const uint16_t *x, int64_t M, float *y, void *workspace,
+                     size_t workspace_bytes, void *stream);
+int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64_t M, float *y, float *loss,
+                      void *workspace, size_t workspace_bytes, void *stream);
+int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, int32_t step, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Surrogate queries (an extension beyond the paper).
+ *
+ * Features of a point p (metres) at time index t of a horizon T for one
+ * capsule (a, b, r): p - grid centre scaled by 2 / largest grid extent;
+ * 2 t / (T - 1) - 1 (0 if T == 1); p - a and p - b in units of 2 m; r in units
+ * of 2 m; five zeros.  (The capsule's end points enter relative to the point.)
+ *
+ * pcdf_surrogate_samples  M training rows from exact dynamic fields
+ *     fields  device fp32 [n_fields][nz][ny][nx] (float fields of one capsule
+ *             each, e.g. composites with an empty static map);
+ *     caps    device int32 [n_fields][7], tf device int32 [n_fields] (time
+ *             index of each field for the t feature, horizon T);
+ *     point i: with probability `near` within 1 m of the capsule axis, else
+ *     uniform in the grid; a counter hash of (seed, i) draws it;
+ *     x out device BF16 bits [M][16]; target out device fp32 [M] (trilinear
+ *     value of the field at the point).
+ * pcdf_surrogate_features  rows (q * H + h) for sphere q and capsule h of time
+ *     clamp(tidx[q], 0, T - 1); caps device int32 [T][H][7]; x out [N * H][16].
+ * pcdf_surrogate_finish  from the network outputs y [N * H] (device fp32):
+ *     d = min(trilinear(static_sdf), min_h y[q * H + h]); where
+ *     |d - (eps + r)| < band the query is answered exactly (corner voxels of
+ *     its cell from static_sq and an exact local search over the capsules'
+ *     voxels, interpolated like pcdf_query_cost: same bits as the exact
+ *     composite path); h[q] = max(0, eps + r - d) (device fp32 [N]), d_out
+ *     (nullable) the distance used; n_fallback (device int32, nullable) the
+ *     number of exact answers.  caps_host: HOST int32 [T][H][7].  Workspace:
+ *     pcdf_surrogate_finish_workspace_bytes(T, H, N).
+ * ------------------------------------------------------------------------- */
+int pcdf_surrogate_samples(const pcdf_grid *grid, const float *fields, const int32_t *caps, const int32_t *tf,
+                           int32_t n_fields, int32_t T, int64_t M, uint64_t seed, float near, uint16_t *x,
+                           float *target, void *stream);
+int pcdf_surrogate_features(const pcdf_grid *grid, const float *spheres, const int32_t *tidx, int64_t N, int32_t T,
+                            int32_t H, const int32_t *caps, uint16_t *x, void *stream);
+int pcdf_surrogate_finish_workspace_bytes(int32_t T, int32_t H, int64_t N, size_t *bytes);
+int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
+                          const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
+                          const int32_t *caps_host, const float *y, float eps, float band, float *h, float *d_out,
+                          int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,11 @@ hand-written CUDA kernels of ``libpcdf.so`` behind the C ABI of
 ``include/pcdf.h``; PyTorch supplies device memory and streams only.
 """
 from .api import (  # noqa: F401
+    SurrogateMLP,
+    surrogate_features,
+    surrogate_finish,
+    surrogate_query,
+    surrogate_samples,
     Batch,
     batch_autotune,
     Grid,

@@ -39,6 +39,9 @@ EXPORTS = (
     "pcdf_batch_create", "pcdf_batch_destroy", "pcdf_batch_workspace_bytes", "pcdf_batch_tiles_used",
     "pcdf_batch_upload", "pcdf_batch_run", "pcdf_batch_error", "pcdf_batch_autotune_workspace_bytes",
     "pcdf_batch_autotune",
+    "pcdf_mlp_state_bytes", "pcdf_mlp_workspace_bytes", "pcdf_mlp_init", "pcdf_mlp_forward", "pcdf_mlp_backward",
+    "pcdf_mlp_adam", "pcdf_surrogate_samples", "pcdf_surrogate_features", "pcdf_surrogate_finish_workspace_bytes",
+    "pcdf_surrogate_finish",
 )
 
 
@@ -74,6 +77,19 @@ def _declare(lib):
         "pcdf_batch_error": [P, P, P, ctypes.POINTER(I32)],
         "pcdf_batch_autotune_workspace_bytes": [E, I32, SZP],
         "pcdf_batch_autotune": [E, I32, P, SZ, P, I32, TL, ctypes.POINTER(ctypes.c_float)],
+    })
+    U64, F32 = ctypes.c_uint64, ctypes.c_float
+    sig.update({
+        "pcdf_mlp_state_bytes": [SZP],
+        "pcdf_mlp_workspace_bytes": [I64, SZP],
+        "pcdf_mlp_init": [P, U64, P],
+        "pcdf_mlp_forward": [P, P, I64, P, P, SZ, P],
+        "pcdf_mlp_backward": [P, P, P, I64, P, P, P, SZ, P],
+        "pcdf_mlp_adam": [P, F32, F32, F32, F32, I32, P],
+        "pcdf_surrogate_samples": [G, P, P, P, I32, I32, I64, U64, F32, P, P, P],
+        "pcdf_surrogate_features": [G, P, P, I64, I32, I32, P, P, P],
+        "pcdf_surrogate_finish_workspace_bytes": [I32, I32, I64, SZP],
+        "pcdf_surrogate_finish": [G, P, P, P, P, I64, I32, I32, P, P, F32, F32, P, P, P, P, SZ, P],
     })
     lib.pcdf_batch_destroy.argtypes = [P]
     lib.pcdf_batch_destroy.restype = None

@@ -415,3 +415,177 @@ def batch_autotune(envs, reps: int = 3, device=None):
     _lib.check(lib.pcdf_batch_autotune(arr, len(envs), _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(device)),
                                        int(reps), ctypes.byref(best), ctypes.byref(ms)), "pcdf_batch_autotune")
     return (best.row_rows, best.dyn_slices, best.comp_t), ms.value
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate of the dynamic field (BF16 MLP, FP32 accumulation)
+# ---------------------------------------------------------------------------
+
+MLP_IN, MLP_IN_PAD, MLP_WIDTH = 11, 16, 256
+MLP_PARAMS, MLP_PARAMS_PAD, MLP_BF16 = 136193, 136196, 135424
+# element offsets in the FP32 parameter vector and in the BF16 weight copies
+_P_OFF = {"W1": (0, (256, 16)), "b1": (4096, (256,)), "W2": (4352, (256, 256)), "b2": (69888, (256,)),
+          "W3": (70144, (256, 256)), "b3": (135680, (256,)), "w4": (135936, (256,)), "b4": (136192, ())}
+_H_OFF = {"W1": (0, (256, 16)), "W2": (4096, (256, 256)), "W3": (69632, (256, 256)), "w4": (135168, (256,))}
+
+
+class SurrogateMLP:
+    """State of the surrogate network in one device buffer (FP32 parameters,
+    Adam moments, gradient, BF16 weight copies; layout in include/pcdf.h)."""
+
+    def __init__(self, device, seed: int = 0):
+        self._lib = _lib.load()
+        self.device = torch.device(device)
+        n = ctypes.c_size_t(0)
+        _lib.check(self._lib.pcdf_mlp_state_bytes(ctypes.byref(n)), "pcdf_mlp_state_bytes")
+        self.state = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        self.step = 0
+        self._ws = None
+        self.reset(seed)
+
+    def reset(self, seed: int):
+        _lib.check(self._lib.pcdf_mlp_init(_ptr(self.state), int(seed), ctypes.c_void_p(_stream(self.device))),
+                   "pcdf_mlp_init")
+        self.step = 0
+
+    def _workspace(self, M):
+        n = ctypes.c_size_t(0)
+        _lib.check(self._lib.pcdf_mlp_workspace_bytes(int(M), ctypes.byref(n)), "pcdf_mlp_workspace_bytes")
+        if self._ws is None or self._ws.numel() < n.value:
+            self._ws = _workspace(n.value, self.device)
+        return self._ws
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        """x: CUDA bfloat16 [M, 16] -> y float32 [M]."""
+        _need(x, "x", torch.bfloat16)
+        M = x.shape[0]
+        y = torch.empty(M, dtype=torch.float32, device=self.device)
+        ws = self._workspace(M)
+        _lib.check(self._lib.pcdf_mlp_forward(_ptr(self.state), _ptr(x), M, _ptr(y), _ptr(ws), ws.numel(),
+                                              ctypes.c_void_p(_stream(self.device))), "pcdf_mlp_forward")
+        return y
+
+    def backward(self, x: torch.Tensor, target: torch.Tensor):
+        """Forward + loss + gradient (into the state).  Returns (y, loss[1])."""
+        _need(x, "x", torch.bfloat16)
+        _need(target, "target", torch.float32)
+        M = x.shape[0]
+        y = torch.empty(M, dtype=torch.float32, device=self.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        ws = self._workspace(M)
+        _lib.check(self._lib.pcdf_mlp_backward(_ptr(self.state), _ptr(x), _ptr(target), M, _ptr(y), _ptr(loss),
+                                               _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(self.device))),
+                   "pcdf_mlp_backward")
+        return y, loss
+
+    def adam(self, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step += 1
+        _lib.check(self._lib.pcdf_mlp_adam(_ptr(self.state), float(lr), float(beta1), float(beta2), float(eps),
+                                           self.step, ctypes.c_void_p(_stream(self.device))), "pcdf_mlp_adam")
+
+    def train_step(self, x, target, lr):
+        _, loss = self.backward(x, target)
+        self.adam(lr)
+        return loss
+
+    def _f32(self, region):
+        off = {"master": 0, "m": 4, "v": 8, "grad": 12}[region] * MLP_PARAMS_PAD
+        return self.state[off:off + 4 * MLP_PARAMS_PAD].view(torch.float32)
+
+    def _bf16(self):
+        off = 16 * MLP_PARAMS_PAD
+        return self.state[off:off + 2 * MLP_BF16].view(torch.bfloat16)
+
+    def params(self):
+        """dict of float64 numpy arrays as the network computes with them: the
+        BF16 weight copies and the FP32 biases."""
+        master = self._f32("master").detach().cpu().double().numpy()
+        half = self._bf16().detach().cpu().float().double().numpy()
+        out = {}
+        for k, (o, shp) in _P_OFF.items():
+            if k in _H_OFF:
+                ho, _ = _H_OFF[k]
+                out[k] = half[ho:ho + int(np.prod(shp))].reshape(shp)
+            else:
+                out[k] = master[o:o + max(1, int(np.prod(shp)))].reshape(shp)
+        return out
+
+    def grads(self):
+        g = self._f32("grad").detach().cpu().double().numpy()
+        return {k: g[o:o + max(1, int(np.prod(shp)))].reshape(shp) for k, (o, shp) in _P_OFF.items()}
+
+    def save(self, path):
+        torch.save({"state": self.state.cpu(), "step": self.step}, path)
+
+    def load(self, path):
+        d = torch.load(path, map_location="cpu")
+        if d["state"].numel() != self.state.numel():
+            raise ValueError("checkpoint size does not match the network state")
+        self.state.copy_(d["state"].to(self.device))
+        self.step = int(d["step"])
+
+
+def surrogate_samples(grid, fields, caps, tf, T, M, seed, near=0.5):
+    """Training rows from exact dynamic fields (see pcdf_surrogate_samples)."""
+    _need(fields, "fields", torch.float32)
+    _need(caps, "caps", torch.int32)
+    _need(tf, "tf", torch.int32)
+    dev = fields.device
+    x = torch.empty((M, MLP_IN_PAD), dtype=torch.bfloat16, device=dev)
+    t = torch.empty(M, dtype=torch.float32, device=dev)
+    g = _cgrid(grid)
+    _lib.check(_lib.load().pcdf_surrogate_samples(ctypes.byref(g), _ptr(fields), _ptr(caps), _ptr(tf),
+                                                  int(fields.shape[0]), int(T), int(M), int(seed), float(near),
+                                                  _ptr(x), _ptr(t), ctypes.c_void_p(_stream(dev))),
+               "pcdf_surrogate_samples")
+    return x, t
+
+
+def surrogate_features(grid, spheres, tidx, T, caps_dev):
+    """Network rows (sphere q, human h) -> CUDA bfloat16 [N * H, 16]."""
+    _need(spheres, "spheres", torch.float32)
+    _need(tidx, "tidx", torch.int32)
+    _need(caps_dev, "caps", torch.int32)
+    H = int(caps_dev.shape[1])
+    N = spheres.numel() // 4
+    dev = spheres.device
+    x = torch.empty((N * H, MLP_IN_PAD), dtype=torch.bfloat16, device=dev)
+    g = _cgrid(grid)
+    _lib.check(_lib.load().pcdf_surrogate_features(ctypes.byref(g), _ptr(spheres), _ptr(tidx), N, int(T), H,
+                                                   _ptr(caps_dev), _ptr(x), ctypes.c_void_p(_stream(dev))),
+               "pcdf_surrogate_features")
+    return x
+
+
+def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band):
+    """Hinge cost from the network outputs with exact answers near the
+    threshold.  Returns (h, d, n_fallback[1])."""
+    caps = _caps_host(caps)
+    H = int(caps.shape[1])
+    N = spheres.numel() // 4
+    dev = spheres.device
+    h = torch.empty(tidx.shape, dtype=torch.float32, device=dev)
+    d = torch.empty(tidx.shape, dtype=torch.float32, device=dev)
+    nfb = torch.zeros(1, dtype=torch.int32, device=dev)
+    n = ctypes.c_size_t(0)
+    lib = _lib.load()
+    _lib.check(lib.pcdf_surrogate_finish_workspace_bytes(int(T), H, N, ctypes.byref(n)), "surrogate workspace")
+    ws = _workspace(n.value, dev)
+    g = _cgrid(grid)
+    _lib.check(lib.pcdf_surrogate_finish(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), _ptr(spheres),
+                                         _ptr(tidx), N, int(T), H, caps.ctypes.data_as(ctypes.c_void_p), _ptr(y),
+                                         float(eps), float(band), _ptr(h), _ptr(d), _ptr(nfb), _ptr(ws), ws.numel(),
+                                         ctypes.c_void_p(_stream(dev))), "pcdf_surrogate_finish")
+    return h, d, nfb
+
+
+def surrogate_query(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps, band, caps_dev=None):
+    """Hinge cost of every sphere through the network, exact within `band`
+    of the threshold.  Returns (h, d, n_fallback[1])."""
+    caps = _caps_host(caps)
+    if caps_dev is None:
+        caps_dev = torch.from_numpy(caps).to(spheres.device)
+    T = int(caps.shape[0])
+    x = surrogate_features(grid, spheres, tidx, T, caps_dev)
+    y = model.forward(x)
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band)

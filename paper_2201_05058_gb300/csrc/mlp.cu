@@ -1,0 +1,582 @@
+// BF16 multilayer perceptron with FP32 accumulation on sm_103a tensor cores:
+// the learned surrogate of the dynamic (human) distance field.
+//
+// Network: 16 inputs (11 features, 5 zero pads) -> 256 -> 256 -> 256 -> 1, ReLU
+// after the three hidden layers.  Weights live as FP32 master copies (Adam) and
+// BF16 copies (GEMM operands); activations and back-propagated gradients are
+// stored in BF16, every product is accumulated in FP32.
+//
+// Kernels:
+//   k_gemm     C(m,n) = sum_k A(m,k) B(k,n) with mma.sync m16n8k16 (BF16 in, FP32
+//              accumulate), operands staged in shared memory; the epilogue
+//              adds the bias and applies ReLU (forward), multiplies by the
+//              ReLU mask of the layer below (input gradient) or accumulates
+//              FP32 into a weight gradient (split over the batch).
+//   k_head     the 256 -> 1 output layer, the squared-error loss and its
+//              gradient with respect to the last hidden layer.
+//   k_colsum   bias gradients (column sums of a BF16 gradient matrix).
+//   k_adam     Adam update of the FP32 master copy and refresh of the BF16 copy.
+//   k_init     counter-hash uniform initialisation (fan-in scaled).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "host.h"
+
+using namespace pcdf::host;
+
+namespace pcdf {
+namespace mlp {
+
+constexpr int kW = PCDF_MLP_WIDTH;   // 256
+constexpr int kIn = PCDF_MLP_IN_PAD; // 16
+
+// element offsets of the FP32 parameter vector
+constexpr long long oW1 = 0, oB1 = oW1 + (long long)kW * kIn, oW2 = oB1 + kW, oB2 = oW2 + (long long)kW * kW,
+                    oW3 = oB2 + kW, oB3 = oW3 + (long long)kW * kW, oW4 = oB3 + kW, oB4 = oW4 + kW,
+                    kP = oB4 + 1, kPpad = (kP + 3) / 4 * 4;
+// element offsets of the BF16 weight copies
+constexpr long long hW1 = 0, hW2 = hW1 + (long long)kW * kIn, hW3 = hW2 + (long long)kW * kW,
+                    hW4 = hW3 + (long long)kW * kW, kH = hW4 + kW;
+static_assert(kP == PCDF_MLP_PARAMS, "parameter count");
+static_assert(kH == PCDF_MLP_BF16_WEIGHTS, "bf16 weight count");
+
+// state layout (bytes): master, adam m, adam v, grad (FP32 [kPpad] each), bf16 weights
+constexpr size_t sMaster = 0, sM = 4 * kPpad, sV = 8 * kPpad, sGrad = 12 * kPpad, sHalf = 16 * kPpad,
+                 kStateBytes = sHalf + 2 * kH;
+
+using bf16 = __nv_bfloat16;
+
+// ---------------------------------------------------------------------------
+// GEMM
+// ---------------------------------------------------------------------------
+constexpr int BM = 64, BN = 64, BK = 32, PADK = 8;
+
+enum Epi { kBiasRelu = 0, kMask = 1, kAtomic = 2 };
+
+struct GemmArgs {
+    const bf16 *A, *B;
+    int lda, ldb, M, N, K, k_split;
+    const float *bias;   // kBiasRelu
+    const bf16 *mask;    // kMask: output zero where mask <= 0
+    int ldm;
+    bf16 *out_h;         // kBiasRelu, kMask
+    float *out_f;        // kAtomic
+    int ldo;
+};
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Stage a 64 x BK tile whose element (r, k) is at P[r * ld + k] (kT = false)
+// or P[k * ld + r] (kT = true) into S[r][k]; out-of-range elements are zero.
+template <bool kT>
+__device__ __forceinline__ void stage_tile(bf16 (*S)[BK + PADK], const bf16 *__restrict__ P, int ld, int r0, int R,
+                                           int k0, int k1)
+{
+    const bf16 zero = __float2bfloat16_rn(0.f);
+    for (int v = threadIdx.x; v < BM * BK / 8; v += blockDim.x) {
+        if (!kT) {
+            const int r = v / (BK / 8), kq = (v % (BK / 8)) * 8;
+            const int gr = r0 + r, gk = k0 + kq;
+            if (gr < R && gk + 8 <= k1) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(P + (long long)gr * ld + gk);
+                *reinterpret_cast<uint4 *>(&S[r][kq]) = q;
+            } else {
+                for (int j = 0; j < 8; ++j)
+                    S[r][kq + j] = (gr < R && gk + j < k1) ? P[(long long)gr * ld + gk + j] : zero;
+            }
+        } else {
+            const int k = v / (BM / 8), rq = (v % (BM / 8)) * 8;
+            const int gk = k0 + k, gr = r0 + rq;
+            if (gk < k1 && gr + 8 <= R) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(P + (long long)gk * ld + gr);
+                const bf16 *e = reinterpret_cast<const bf16 *>(&q);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    S[rq + j][k] = e[j];
+            } else {
+                for (int j = 0; j < 8; ++j)
+                    S[rq + j][k] = (gk < k1 && gr + j < R) ? P[(long long)gk * ld + gr + j] : zero;
+            }
+        }
+    }
+}
+
+template <bool kTA, bool kTB, int kEpi>
+__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g)
+{
+    __shared__ __align__(16) bf16 As[BM][BK + PADK];
+    __shared__ __align__(16) bf16 Bs[BN][BK + PADK];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * g.k_split, ke = min(g.K, kb + g.k_split);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp >> 1, wn = warp & 1, gid = lane >> 2, tig = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                acc[i][j][q] = 0.f;
+
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        stage_tile<kTA>(As, g.A, g.lda, m0, g.M, k0, ke);
+        stage_tile<kTB>(Bs, g.B, g.ldb, n0, g.N, k0, ke);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = wm * 32 + mt * 16 + gid, c = kk + tig * 2;
+                a[mt][0] = *reinterpret_cast<const uint32_t *>(&As[r][c]);
+                a[mt][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][c]);
+                a[mt][2] = *reinterpret_cast<const uint32_t *>(&As[r][c + 8]);
+                a[mt][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][c + 8]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int n = wn * 32 + nt * 8 + gid, k = kk + tig * 2;
+                b[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][k]);
+                b[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][k + 8]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+                    mma16816(acc[mt][nt], a[mt], b[nt]);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = m0 + wm * 32 + mt * 16 + gid + (q >= 2 ? 8 : 0);
+                const int c = n0 + wn * 32 + nt * 8 + tig * 2 + (q & 1);
+                if (r >= g.M || c >= g.N)
+                    continue;
+                const float v = acc[mt][nt][q];
+                if (kEpi == kBiasRelu) {
+                    g.out_h[(long long)r * g.ldo + c] = __float2bfloat16_rn(fmaxf(v + g.bias[c], 0.f));
+                } else if (kEpi == kMask) {
+                    const float m = __bfloat162float(g.mask[(long long)r * g.ldm + c]);
+                    g.out_h[(long long)r * g.ldo + c] = __float2bfloat16_rn(m > 0.f ? v : 0.f);
+                } else {
+                    atomicAdd(g.out_f + (long long)r * g.ldo + c, v);
+                }
+            }
+}
+
+template <bool kTA, bool kTB, int kEpi>
+cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st)
+{
+    const dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, splits);
+    k_gemm<kTA, kTB, kEpi><<<grid, 128, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// output layer, loss, bias gradients, Adam, initialisation
+// ---------------------------------------------------------------------------
+constexpr int kHeadRows = 64;  // rows per CTA of k_head (8 warps x 8 rows)
+
+// y[m] = H3[m] . w4 + b4.  With a target: loss += (y - t)^2 / M,
+// dy = 2 (y - t) / M, dZ3[m][k] = dy * w4[k] where H3[m][k] > 0, and the
+// gradients of w4 and b4 accumulate (per CTA in shared memory, then atomics).
+__global__ void __launch_bounds__(256)
+    k_head(const bf16 *__restrict__ H3, const bf16 *__restrict__ w4h, const float *__restrict__ b4, long long M,
+           float *__restrict__ y, const float *__restrict__ target, bf16 *__restrict__ dZ3, float *__restrict__ gw4,
+           float *__restrict__ gb4, float *__restrict__ loss, float inv_m)
+{
+    __shared__ float s_gw[kW];
+    __shared__ float s_gb, s_loss;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kW; k += blockDim.x)
+        s_gw[k] = 0.f;
+    if (threadIdx.x == 0)
+        s_gb = s_loss = 0.f;
+    __syncthreads();
+    float w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        w[j] = __bfloat162float(w4h[lane * 8 + j]);
+    float gw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float gb = 0.f, ls = 0.f;
+    for (int i = warp; i < kHeadRows; i += blockDim.x / 32) {
+        const long long m = (long long)blockIdx.x * kHeadRows + i;
+        if (m >= M)
+            break;
+        const uint4 q = *reinterpret_cast<const uint4 *>(H3 + m * kW + lane * 8);
+        const bf16 *h = reinterpret_cast<const bf16 *>(&q);
+        float hv[8], s = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            hv[j] = __bfloat162float(h[j]);
+            s = fmaf(hv[j], w[j], s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float yv = s + b4[0];
+        if (lane == 0)
+            y[m] = yv;
+        if (target) {
+            const float e = yv - target[m];
+            const float dy = 2.f * e * inv_m;
+            ls += e * e * inv_m;
+            gb += dy;
+            bf16 dz[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                dz[j] = __float2bfloat16_rn(hv[j] > 0.f ? dy * w[j] : 0.f);
+                gw[j] = fmaf(dy, hv[j], gw[j]);
+            }
+            *reinterpret_cast<uint4 *>(dZ3 + m * kW + lane * 8) = *reinterpret_cast<const uint4 *>(dz);
+        }
+    }
+    if (target) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            atomicAdd(&s_gw[lane * 8 + j], gw[j]);
+        if (lane == 0) {
+            atomicAdd(&s_gb, gb);
+            atomicAdd(&s_loss, ls);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kW; k += blockDim.x)
+            atomicAdd(gw4 + k, s_gw[k]);
+        if (threadIdx.x == 0) {
+            atomicAdd(gb4, s_gb);
+            if (loss)
+                atomicAdd(loss, s_loss);
+        }
+    }
+}
+
+// grad_b[n] += sum_m dZ[m][n] over a block of rows
+__global__ void __launch_bounds__(256) k_colsum(const bf16 *__restrict__ dZ, long long M, float *__restrict__ gb)
+{
+    const int n = threadIdx.x;  // blockDim = kW
+    const long long m0 = (long long)blockIdx.x * 256, m1 = min(M, m0 + 256);
+    float s = 0.f;
+    for (long long m = m0; m < m1; ++m)
+        s += __bfloat162float(dZ[m * kW + n]);
+    atomicAdd(gb + n, s);
+}
+
+__device__ __forceinline__ long long half_index(long long i)
+{
+    if (i < oB1)
+        return hW1 + (i - oW1);
+    if (i >= oW2 && i < oB2)
+        return hW2 + (i - oW2);
+    if (i >= oW3 && i < oB3)
+        return hW3 + (i - oW3);
+    if (i >= oW4 && i < oB4)
+        return hW4 + (i - oW4);
+    return -1;
+}
+
+__global__ void k_adam(float *__restrict__ p, float *__restrict__ mo, float *__restrict__ ve,
+                       const float *__restrict__ g, bf16 *__restrict__ h, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kP)
+        return;
+    // input columns 11..15 of the first layer stay zero
+    if (i < oB1 && (i % kIn) >= PCDF_MLP_IN)
+        return;
+    const float gi = g[i];
+    const float m = b1 * mo[i] + (1.f - b1) * gi;
+    const float v = b2 * ve[i] + (1.f - b2) * gi * gi;
+    mo[i] = m;
+    ve[i] = v;
+    const float pn = p[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    p[i] = pn;
+    const long long hi = half_index(i);
+    if (hi >= 0)
+        h[hi] = __float2bfloat16_rn(pn);
+}
+
+__device__ __forceinline__ uint32_t hash32(uint64_t x)
+{
+    // splitmix64 finaliser
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return (uint32_t)(x >> 32);
+}
+
+// weights uniform in +-sqrt(6 / fan_in) (fan-in of the real inputs), biases 0,
+// Adam moments 0
+__global__ void k_init(float *__restrict__ p, float *__restrict__ mo, float *__restrict__ ve, bf16 *__restrict__ h,
+                       unsigned long long seed)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kP)
+        return;
+    float fan = 0.f;
+    if (i < oB1)
+        fan = (i % kIn) < PCDF_MLP_IN ? (float)PCDF_MLP_IN : 0.f;
+    else if ((i >= oW2 && i < oB2) || (i >= oW3 && i < oB3) || (i >= oW4 && i < oB4))
+        fan = (float)kW;
+    float v = 0.f;
+    if (fan > 0.f) {
+        const float u = (hash32(seed * 0x100000001B3ull + (unsigned long long)i) + 0.5f) * (1.f / 4294967296.f);
+        v = (2.f * u - 1.f) * sqrtf(6.f / fan);
+    }
+    p[i] = v;
+    mo[i] = 0.f;
+    ve[i] = 0.f;
+    const long long hi = half_index(i);
+    if (hi >= 0)
+        h[hi] = __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct State {
+    float *p, *m, *v, *g;
+    bf16 *h;
+    explicit State(void *s)
+    {
+        char *b = (char *)s;
+        p = (float *)(b + sMaster);
+        m = (float *)(b + sM);
+        v = (float *)(b + sV);
+        g = (float *)(b + sGrad);
+        h = (bf16 *)(b + sHalf);
+    }
+};
+
+struct Acts {
+    bf16 *H1, *H2, *H3, *dA, *dB;
+    float *y;
+};
+
+size_t ws_bytes(long long M) { return 5 * align_up((size_t)M * kW * 2) + align_up((size_t)M * 4); }
+
+Acts carve(void *ws, long long M)
+{
+    char *b = (char *)ws;
+    const size_t a = align_up((size_t)M * kW * 2);
+    Acts r;
+    r.H1 = (bf16 *)b;
+    r.H2 = (bf16 *)(b + a);
+    r.H3 = (bf16 *)(b + 2 * a);
+    r.dA = (bf16 *)(b + 3 * a);
+    r.dB = (bf16 *)(b + 4 * a);
+    r.y = (float *)(b + 5 * a);
+    return r;
+}
+
+GemmArgs fwd_args(const bf16 *X, int K, const bf16 *W, const float *bias, bf16 *out, long long M)
+{
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = X;
+    g.lda = K;
+    g.B = W;
+    g.ldb = K;
+    g.M = (int)M;
+    g.N = kW;
+    g.K = K;
+    g.k_split = K;
+    g.bias = bias;
+    g.out_h = out;
+    g.ldo = kW;
+    return g;
+}
+
+int forward(const State &S, const bf16 *x, long long M, const Acts &A, cudaStream_t st)
+{
+    cudaError_t e = gemm<false, false, kBiasRelu>(fwd_args(x, kIn, S.h + hW1, S.p + oB1, A.H1, M), 1, st);
+    if (e == cudaSuccess)
+        e = gemm<false, false, kBiasRelu>(fwd_args(A.H1, kW, S.h + hW2, S.p + oB2, A.H2, M), 1, st);
+    if (e == cudaSuccess)
+        e = gemm<false, false, kBiasRelu>(fwd_args(A.H2, kW, S.h + hW3, S.p + oB3, A.H3, M), 1, st);
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp forward");
+}
+
+// dX = dZ W with the ReLU mask of X (layer input); dZ [M][kW], W [kW][Kin]
+cudaError_t back_input(const bf16 *dZ, const bf16 *W, int Kin, const bf16 *X, bf16 *dX, long long M, cudaStream_t st)
+{
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = dZ;
+    g.lda = kW;
+    g.B = W;      // B(k = n_out, n = k_in) at W[k * Kin + n]
+    g.ldb = Kin;
+    g.M = (int)M;
+    g.N = Kin;
+    g.K = kW;
+    g.k_split = kW;
+    g.mask = X;
+    g.ldm = Kin;
+    g.out_h = dX;
+    g.ldo = Kin;
+    return gemm<false, true, kMask>(g, 1, st);
+}
+
+// gW[n][k] += sum_m dZ[m][n] X[m][k]
+cudaError_t back_weight(const bf16 *dZ, const bf16 *X, int Kin, float *gW, long long M, cudaStream_t st)
+{
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = dZ;     // A(m' = n, k' = m) at dZ[k' * kW + m']
+    g.lda = kW;
+    g.B = X;      // B(k' = m, n' = k) at X[k' * Kin + n']
+    g.ldb = Kin;
+    g.M = kW;
+    g.N = Kin;
+    g.K = (int)M;
+    int splits = (int)std::min<long long>(128, (M + 2047) / 2048);
+    splits = std::max(splits, 1);
+    g.k_split = (int)(((M + splits - 1) / splits + BK - 1) / BK * BK);
+    splits = (int)((M + g.k_split - 1) / g.k_split);
+    g.out_f = gW;
+    g.ldo = Kin;
+    return gemm<true, true, kAtomic>(g, splits, st);
+}
+
+}  // namespace mlp
+}  // namespace pcdf
+
+using namespace pcdf::mlp;
+
+extern "C" {
+
+int pcdf_mlp_state_bytes(size_t *bytes)
+{
+    if (!bytes)
+        return fail(PCDF_EINVAL, "bytes is NULL");
+    *bytes = kStateBytes;
+    return PCDF_OK;
+}
+
+int pcdf_mlp_workspace_bytes(int64_t M, size_t *bytes)
+{
+    if (!bytes || M < 0)
+        return fail(PCDF_EINVAL, "bytes is NULL or M < 0");
+    *bytes = ws_bytes(M);
+    return PCDF_OK;
+}
+
+int pcdf_mlp_init(void *state, uint64_t seed, void *stream)
+{
+    if (!state || !aligned(state, kAlign))
+        return fail(PCDF_EINVAL, "state must be non-NULL and %zu-byte aligned", kAlign);
+    State S(state);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(S.g, 0, 4 * kPpad, st);
+    if (e == cudaSuccess) {
+        k_init<<<(unsigned)((kP + 255) / 256), 256, 0, st>>>(S.p, S.m, S.v, S.h, (unsigned long long)seed);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp init");
+}
+
+int pcdf_mlp_forward(const void *state, const uint16_t *x, int64_t M, float *y, void *workspace,
+                     size_t workspace_bytes, void *stream)
+{
+    if (!state || (M > 0 && (!x || !y || !workspace)))
+        return fail(PCDF_EINVAL, "state, x, y and workspace must be non-NULL");
+    if (M < 0 || M > (1LL << 31) - 1)
+        return fail(PCDF_EINVAL, "M out of range");
+    if (M == 0)
+        return PCDF_OK;
+    if (!aligned(x, 16) || !aligned(workspace, kAlign) || !aligned(state, kAlign))
+        return fail(PCDF_EINVAL, "x must be 16-byte aligned, state and workspace %zu-byte aligned", kAlign);
+    if (workspace_bytes < ws_bytes(M))
+        return fail(PCDF_ENOMEM, "workspace %zu bytes < %zu needed", workspace_bytes, ws_bytes(M));
+    State S(const_cast<void *>(state));
+    Acts A = carve(workspace, M);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = forward(S, (const bf16 *)x, M, A, st))
+        return rc;
+    k_head<<<(unsigned)((M + kHeadRows - 1) / kHeadRows), 256, 0, st>>>(A.H3, S.h + hW4, S.p + oB4, M, y, nullptr,
+                                                                        nullptr, nullptr, nullptr, nullptr, 0.f);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp head");
+}
+
+int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64_t M, float *y, float *loss,
+                      void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!state || !x || !target || !y || !workspace)
+        return fail(PCDF_EINVAL, "state, x, target, y and workspace must be non-NULL");
+    if (M < 1 || M > (1LL << 31) - 1)
+        return fail(PCDF_EINVAL, "M out of range");
+    if (!aligned(x, 16) || !aligned(workspace, kAlign) || !aligned(state, kAlign))
+        return fail(PCDF_EINVAL, "x must be 16-byte aligned, state and workspace %zu-byte aligned", kAlign);
+    if (workspace_bytes < ws_bytes(M))
+        return fail(PCDF_ENOMEM, "workspace %zu bytes < %zu needed", workspace_bytes, ws_bytes(M));
+    State S(state);
+    Acts A = carve(workspace, M);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bf16 *X = (const bf16 *)x;
+    cudaError_t e = cudaMemsetAsync(S.g, 0, 4 * kPpad, st);
+    if (e == cudaSuccess && loss)
+        e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "mlp backward reset");
+    if (int rc = forward(S, X, M, A, st))
+        return rc;
+    k_head<<<(unsigned)((M + kHeadRows - 1) / kHeadRows), 256, 0, st>>>(A.H3, S.h + hW4, S.p + oB4, M, y, target,
+                                                                        A.dA, S.g + oW4, S.g + oB4, loss,
+                                                                        1.f / (float)M);
+    e = cudaGetLastError();
+    const unsigned cs = (unsigned)((M + 255) / 256);
+    // layer 3: Z3 = H2 W3^T + b3
+    if (e == cudaSuccess) {
+        k_colsum<<<cs, kW, 0, st>>>(A.dA, M, S.g + oB3);
+        e = back_weight(A.dA, A.H2, kW, S.g + oW3, M, st);
+    }
+    if (e == cudaSuccess)
+        e = back_input(A.dA, S.h + hW3, kW, A.H2, A.dB, M, st);
+    // layer 2
+    if (e == cudaSuccess) {
+        k_colsum<<<cs, kW, 0, st>>>(A.dB, M, S.g + oB2);
+        e = back_weight(A.dB, A.H1, kW, S.g + oW2, M, st);
+    }
+    if (e == cudaSuccess)
+        e = back_input(A.dB, S.h + hW2, kW, A.H1, A.dA, M, st);
+    // layer 1 (the input needs no gradient)
+    if (e == cudaSuccess) {
+        k_colsum<<<cs, kW, 0, st>>>(A.dA, M, S.g + oB1);
+        e = back_weight(A.dA, X, kIn, S.g + oW1, M, st);
+    }
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp backward");
+}
+
+int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, int32_t step, void *stream)
+{
+    if (!state || step < 1)
+        return fail(PCDF_EINVAL, "state must be non-NULL and step >= 1");
+    State S(state);
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    cudaStream_t st = (cudaStream_t)stream;
+    k_adam<<<(unsigned)((kP + 255) / 256), 256, 0, st>>>(S.p, S.m, S.v, S.g, S.h, lr, beta1, beta2, eps, c1, c2);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp adam");
+}
+
+}  // extern "C"

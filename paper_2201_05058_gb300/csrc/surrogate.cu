@@ -1,0 +1,450 @@
+// Surrogate distance queries with an exact fallback (sm_103a).
+//
+// The learned part predicts, per human capsule, the dynamic field value at a
+// point; a query's distance is the min over the humans and the trilinear
+// static field.  Where that prediction lies within `band` of the hinge
+// threshold eps + r the prediction could flip the collision decision, so the
+// query is answered exactly instead: the eight corner voxels of its cell get
+// their exact composite values (static squared EDT from the static field; the
+// dynamic squared EDT by a local search over the capsules' voxels, bounded as
+// described at exact_dyn_sq) and are interpolated by the same code as the
+// exact cost query, giving bit-identical results on those queries.
+//
+// Kernels:
+//   k_sur_samples   training samples (features, target) drawn from exact
+//                   dynamic fields with a counter-hash generator;
+//   k_sur_features  query features, one row per (sphere, human);
+//   k_sur_combine   min over humans and static field, hinge, fallback list;
+//   k_sur_fallback  exact answers for the listed queries (warp per query).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "edt_common.cuh"
+#include "host.h"
+#include "trilinear.cuh"
+
+using namespace pcdf::host;
+
+namespace pcdf {
+namespace sur {
+
+using bf16 = __nv_bfloat16;
+constexpr float kLen = 2.0f;  // metres: scale of the point-to-endpoint features
+
+struct FeatGrid {
+    QueryGrid g;
+    float centre[3];
+    float scale;  // 2 / largest grid extent
+};
+
+__device__ __forceinline__ float fixed_to_m(int32_t v, float origin, float vox)
+{
+    return __fadd_rn(origin, __fmul_rn((float)v, __fdiv_rn(vox, 16.f)));
+}
+
+// Features of point p at time index t (horizon T) for one capsule:
+// p scaled to [-1, 1] by the grid, t scaled to [-1, 1], p - a and p - b in
+// units of kLen, the radius in units of kLen, then zero padding.
+__device__ __forceinline__ void features(const FeatGrid &G, float px, float py, float pz, int t, int T,
+                                         const int32_t *cap, bf16 *out)
+{
+    const float p[3] = {px, py, pz};
+    float f[16];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        f[a] = (p[a] - G.centre[a]) * G.scale;
+    f[3] = T > 1 ? 2.f * (float)t / (float)(T - 1) - 1.f : 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f[4 + a] = (p[a] - fixed_to_m(cap[a], G.g.origin[a], G.g.vox)) * (1.f / kLen);
+        f[7 + a] = (p[a] - fixed_to_m(cap[3 + a], G.g.origin[a], G.g.vox)) * (1.f / kLen);
+    }
+    f[10] = (float)cap[6] * (G.g.vox / 16.f) * (1.f / kLen);
+#pragma unroll
+    for (int a = 11; a < 16; ++a)
+        f[a] = 0.f;
+    bf16 h[16];
+#pragma unroll
+    for (int a = 0; a < 16; ++a)
+        h[a] = __float2bfloat16_rn(f[a]);
+    reinterpret_cast<uint4 *>(out)[0] = reinterpret_cast<const uint4 *>(h)[0];
+    reinterpret_cast<uint4 *>(out)[1] = reinterpret_cast<const uint4 *>(h)[1];
+}
+
+__device__ __forceinline__ uint32_t hash32(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return (uint32_t)(x >> 32);
+}
+__device__ __forceinline__ float uni(uint64_t seed, long long i, int k)
+{
+    return (hash32(seed ^ ((uint64_t)i * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)k << 56)) + 0.5f) *
+           (1.f / 4294967296.f);
+}
+
+// Sample i: a field j (exact dynamic field of one capsule at time index tf[j]),
+// a point uniform in the grid (probability 1 - near) or within 1 m of the
+// capsule axis, the field's trilinear value there as the target.
+__global__ void k_sur_samples(FeatGrid G, const float *__restrict__ fields, const int32_t *__restrict__ caps,
+                              const int32_t *__restrict__ tf, int n_fields, int T, long long M,
+                              unsigned long long seed, float near, bf16 *__restrict__ x, float *__restrict__ target)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M)
+        return;
+    const int j = min((int)(uni(seed, i, 0) * n_fields), n_fields - 1);
+    const int32_t *cap = caps + 7 * j;
+    const float ext[3] = {G.g.n[0] * G.g.vox, G.g.n[1] * G.g.vox, G.g.n[2] * G.g.vox};
+    float p[3];
+    if (uni(seed, i, 1) >= near) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            p[a] = G.g.origin[a] + uni(seed, i, 2 + a) * ext[a];
+    } else {
+        const float s = uni(seed, i, 2);
+        const float u = 2.f * uni(seed, i, 3) - 1.f, phi = 6.2831853f * uni(seed, i, 4);
+        const float rad = uni(seed, i, 5) * 1.0f;
+        const float w = sqrtf(fmaxf(0.f, 1.f - u * u));
+        const float dir[3] = {w * cosf(phi), w * sinf(phi), u};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float am = fixed_to_m(cap[a], G.g.origin[a], G.g.vox);
+            const float bm = fixed_to_m(cap[3 + a], G.g.origin[a], G.g.vox);
+            p[a] = am + s * (bm - am) + rad * dir[a];
+            p[a] = fminf(fmaxf(p[a], G.g.origin[a]), G.g.origin[a] + ext[a]);
+        }
+    }
+    const long long V = (long long)G.g.n[0] * G.g.n[1] * G.g.n[2];
+    const Sample r = trilinear(G.g, fields + (long long)j * V, make_float4(p[0], p[1], p[2], 0.f), false);
+    target[i] = r.d;
+    features(G, p[0], p[1], p[2], tf[j], T, cap, x + i * 16);
+}
+
+__global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, const int32_t *__restrict__ tidx,
+                               long long N, int T, int H, const int32_t *__restrict__ caps, bf16 *__restrict__ x)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * H)
+        return;
+    const long long q = i / H;
+    const int h = (int)(i % H);
+    const float4 s = spheres[q];
+    const int t = min(max(tidx[q], 0), T - 1);
+    features(G, s.x, s.y, s.z, t, T, caps + 7 * ((long long)t * H + h), x + i * 16);
+}
+
+__global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
+                              long long N, int H, const float *__restrict__ y, float eps, float band,
+                              float *__restrict__ h, float *__restrict__ d_out, int *__restrict__ list,
+                              int *__restrict__ count)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool fb = false;
+    if (q < N) {
+        const float4 s = spheres[q];
+        float dyn = __int_as_float(0x7f800000);
+        for (int k = 0; k < H; ++k)
+            dyn = fminf(dyn, y[q * H + k]);
+        const float ds = trilinear(g, static_sdf, s, false).d;
+        const float d = fminf(ds, dyn);
+        const float thr = eps + s.w;
+        fb = fabsf(d - thr) < band;
+        const float hv = thr - d;
+        h[q] = hv > 0.f ? hv : 0.f;
+        if (d_out)
+            d_out[q] = d;
+    }
+    // warp-aggregated append to the fallback list
+    const unsigned m = __ballot_sync(0xffffffffu, fb);
+    if (m) {
+        const int lane = threadIdx.x & 31;
+        int base = 0;
+        if (lane == __ffs(m) - 1)
+            base = atomicAdd(count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (fb)
+            list[base + __popc(m & ((1u << lane) - 1u))] = (int)q;
+    }
+}
+
+// --- exact dynamic squared distance at one voxel, warp-cooperative ---------
+
+__device__ __forceinline__ int warp_min(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ bool inside_any(const CapInfo *caps, int H, int i, int j, int k)
+{
+    for (int c = 0; c < H; ++c)
+        if (caps[c].lo[0] <= caps[c].hi[0] && capsule_contains(caps[c], i, j, k))
+            return true;
+    return false;
+}
+
+// min |v - u|^2 over the voxels u of the box [lo, hi] (clipped to the grid)
+// that satisfy pred(u); the warp's lanes split the box
+template <class Pred>
+__device__ __forceinline__ int box_search(const int (&v)[3], int lo0, int lo1, int lo2, int hi0, int hi1, int hi2,
+                                          int best, Pred pred)
+{
+    const int lane = threadIdx.x & 31;
+    const int nxb = hi0 - lo0 + 1, nyb = hi1 - lo1 + 1, nzb = hi2 - lo2 + 1;
+    if (nxb <= 0 || nyb <= 0 || nzb <= 0)
+        return best;
+    const long long tot = (long long)nxb * nyb * nzb;
+    for (long long e = lane; e < tot; e += 32) {
+        const int i = lo0 + (int)(e % nxb), j = lo1 + (int)((e / nxb) % nyb), k = lo2 + (int)(e / ((long long)nxb * nyb));
+        const int d = (i - v[0]) * (i - v[0]) + (j - v[1]) * (j - v[1]) + (k - v[2]) * (k - v[2]);
+        if (d < best && pred(i, j, k))
+            best = d;
+    }
+    return warp_min(best);
+}
+
+// Exact dynamic squared EDT at voxel v (signed, as the composite kernels).
+// Outside every capsule: min over the capsules c of the squared distance to
+// c's voxels.  If q is the point of capsule c nearest to v's centre at
+// continuous distance d (voxel units), every point u of the convex capsule
+// satisfies |v - u|^2 >= d^2 + |u - q|^2, and some voxel of c lies within
+// d + sqrt(3) of v (a ball of radius sqrt(3)/2 around the point sqrt(3)/2
+// inside q holds a lattice point when r >= sqrt(3)/2), so the nearest voxel
+// lies within sqrt((d + sqrt(3))^2 - d^2) of q.  The search box covers that
+// ball with a margin; capsules that are thin, cut by the grid boundary, or
+// whose result breaks the d + sqrt(3) bound are searched over their whole
+// in-grid bounding box instead.  Inside some capsule: minus the squared
+// distance to the nearest voxel outside all capsules, by growing shells.
+__device__ int exact_dyn_sq(const QueryGrid &g, const CapInfo *caps, int H, const int (&v)[3])
+{
+    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    if (inside_any(caps, H, v[0], v[1], v[2])) {
+        int best = kInf32;
+        for (int rad = 1; rad <= max(n0, max(n1, n2)); ++rad) {
+            if ((long long)rad * rad >= best && best != kInf32)
+                break;
+            // the two faces of the shell along each axis (cube faces overlap, harmless)
+            for (int face = 0; face < 6; ++face) {
+                const int ax = face >> 1, sg = (face & 1) ? 1 : -1;
+                int lo[3] = {v[0] - rad, v[1] - rad, v[2] - rad}, hi[3] = {v[0] + rad, v[1] + rad, v[2] + rad};
+                lo[ax] = hi[ax] = v[ax] + sg * rad;
+                best = box_search(v, max(lo[0], 0), max(lo[1], 0), max(lo[2], 0), min(hi[0], n0 - 1),
+                                  min(hi[1], n1 - 1), min(hi[2], n2 - 1), best,
+                                  [&](int i, int j, int k) { return !inside_any(caps, H, i, j, k); });
+            }
+        }
+        return best == kInf32 ? -kInf32 : -best;
+    }
+    int best = kInf32;
+    const float pv[3] = {16.f * v[0] + 8.f, 16.f * v[1] + 8.f, 16.f * v[2] + 8.f};
+    for (int c = 0; c < H; ++c) {
+        const CapInfo &C = caps[c];
+        if (C.lo[0] > C.hi[0])
+            continue;
+        bool full = C.r < 14;  // r < sqrt(3)/2 voxel (16ths)
+        for (int a = 0; a < 3; ++a) {
+            const int mn = min(C.a[a], C.b[a]) - C.r, mx = max(C.a[a], C.b[a]) + C.r;
+            const int ulo = (mn - 8 + 15 + 16 * 4096) / 16 - 4096, uhi = (mx - 8 + 16 * 4096) / 16 - 4096;
+            full |= ulo < 0 || uhi > g.n[a] - 1;  // cut by the grid boundary
+        }
+        int lo[3], hi[3];
+        float dv = 0.f;
+        if (!full) {
+            float ab[3], w[3], L = 0.f, s = 0.f;
+            for (int a = 0; a < 3; ++a) {
+                ab[a] = (float)(C.b[a] - C.a[a]);
+                w[a] = pv[a] - (float)C.a[a];
+                L += ab[a] * ab[a];
+                s += w[a] * ab[a];
+            }
+            const float tpar = L > 0.f ? fminf(fmaxf(s / L, 0.f), 1.f) : 0.f;
+            float q[3], dd = 0.f;
+            for (int a = 0; a < 3; ++a) {
+                q[a] = (float)C.a[a] + tpar * ab[a];
+                dd += (pv[a] - q[a]) * (pv[a] - q[a]);
+            }
+            const float dist = sqrtf(dd);
+            dv = fmaxf(dist - (float)C.r, 0.f) / 16.f;  // voxel units
+            const float R = sqrtf(2.f * 1.7320508f * dv + 3.f) + 2.f;
+            for (int a = 0; a < 3; ++a) {
+                const float qs = dist > 0.f ? q[a] + (pv[a] - q[a]) * ((float)C.r / dist) : q[a];
+                const float qv = (qs - 8.f) / 16.f;
+                lo[a] = max((int)floorf(qv - R), C.lo[a]);
+                hi[a] = min((int)ceilf(qv + R), C.hi[a]);
+            }
+        }
+        int bc = kInf32;
+        if (!full) {
+            bc = box_search(v, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], kInf32,
+                            [&](int i, int j, int k) { return capsule_contains(C, i, j, k); });
+            const float bound = dv + 1.7320508f + 0.01f;
+            if (bc == kInf32 || (float)bc > bound * bound)
+                full = true;
+        }
+        if (full)
+            bc = box_search(v, C.lo[0], C.lo[1], C.lo[2], C.hi[0], C.hi[1], C.hi[2], kInf32,
+                            [&](int i, int j, int k) { return capsule_contains(C, i, j, k); });
+        best = min(best, bc);
+    }
+    return best;
+}
+
+__global__ void k_sur_fallback(QueryGrid g, const int32_t *__restrict__ static_sq,
+                               const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
+                               const int32_t *__restrict__ tidx, int T, int H, const CapInfo *__restrict__ caps,
+                               float eps, const int *__restrict__ list, const int *__restrict__ count,
+                               float *__restrict__ h, float *__restrict__ d_out)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int n = *count;
+    for (long long w = warp; w < n; w += nwarps) {
+        const long long q = list[w];
+        const float4 s = spheres[q];
+        const int t = min(max(tidx[q], 0), T - 1);
+        const Cell cl = locate(g, s);
+        float c[2][2][2];
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int v[3] = {dx ? cl.i1[0] : cl.i0[0], dy ? cl.i1[1] : cl.i0[1], dz ? cl.i1[2] : cl.i0[2]};
+                    const long long o = ((long long)v[2] * g.n[1] + v[1]) * g.n[0] + v[0];
+                    const int32_t sv = static_sq[o];
+                    const int32_t dv = exact_dyn_sq(g, caps + (long long)t * H, H, v);
+                    c[dz][dy][dx] = sv <= dv ? static_sdf[o] : sq_to_sdf_fast(min(sv, dv), g.vox);
+                }
+        if (lane == 0) {
+            const Sample r = interpolate(cl, c, false);
+            const float hv = (eps + s.w) - r.d;
+            h[q] = hv > 0.f ? hv : 0.f;
+            if (d_out)
+                d_out[q] = r.d;
+        }
+    }
+}
+
+FeatGrid feat_grid(const pcdf_grid *grid)
+{
+    FeatGrid G;
+    G.g.n[0] = grid->nx;
+    G.g.n[1] = grid->ny;
+    G.g.n[2] = grid->nz;
+    for (int a = 0; a < 3; ++a)
+        G.g.origin[a] = grid->origin[a];
+    G.g.vox = grid->vox;
+    const float ext[3] = {grid->nx * grid->vox, grid->ny * grid->vox, grid->nz * grid->vox};
+    for (int a = 0; a < 3; ++a)
+        G.centre[a] = grid->origin[a] + 0.5f * ext[a];
+    G.scale = 2.f / std::max(ext[0], std::max(ext[1], ext[2]));
+    return G;
+}
+
+}  // namespace sur
+}  // namespace pcdf
+
+using namespace pcdf::sur;
+
+extern "C" {
+
+int pcdf_surrogate_samples(const pcdf_grid *grid, const float *fields, const int32_t *caps, const int32_t *tf,
+                           int32_t n_fields, int32_t T, int64_t M, uint64_t seed, float near, uint16_t *x,
+                           float *target, void *stream)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (!fields || !caps || !tf || !x || !target || n_fields < 1 || T < 1 || M < 0)
+        return fail(PCDF_EINVAL, "bad surrogate sample arguments");
+    if (!aligned(x, 16))
+        return fail(PCDF_EINVAL, "x must be 16-byte aligned");
+    if (M == 0)
+        return PCDF_OK;
+    k_sur_samples<<<(unsigned)((M + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        feat_grid(grid), fields, caps, tf, n_fields, T, M, (unsigned long long)seed, near, (bf16 *)x, target);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "surrogate samples");
+}
+
+int pcdf_surrogate_features(const pcdf_grid *grid, const float *spheres, const int32_t *tidx, int64_t N, int32_t T,
+                            int32_t H, const int32_t *caps, uint16_t *x, void *stream)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (N < 0 || T < 1 || H < 1 || (N > 0 && (!spheres || !tidx || !caps || !x)))
+        return fail(PCDF_EINVAL, "bad surrogate feature arguments");
+    if (!aligned(spheres, 16) || !aligned(x, 16))
+        return fail(PCDF_EINVAL, "spheres and x must be 16-byte aligned");
+    const long long R = N * H;
+    if (R == 0)
+        return PCDF_OK;
+    k_sur_features<<<(unsigned)((R + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        feat_grid(grid), (const float4 *)spheres, tidx, N, T, H, caps, (bf16 *)x);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "surrogate features");
+}
+
+int pcdf_surrogate_finish_workspace_bytes(int32_t T, int32_t H, int64_t N, size_t *bytes)
+{
+    if (!bytes || T < 1 || H < 1 || N < 0)
+        return fail(PCDF_EINVAL, "bad arguments");
+    *bytes = align_up(sizeof(int)) + align_up((size_t)N * sizeof(int)) + align_up((size_t)T * H * sizeof(pcdf::CapInfo));
+    return PCDF_OK;
+}
+
+int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
+                          const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
+                          const int32_t *caps_host, const float *y, float eps, float band, float *h, float *d_out,
+                          int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (N < 0 || T < 1 || H < 1 || !caps_host)
+        return fail(PCDF_EINVAL, "bad surrogate arguments");
+    if (N == 0)
+        return PCDF_OK;
+    if (!static_sq || !static_sdf || !spheres || !tidx || !y || !h || !workspace)
+        return fail(PCDF_EINVAL, "required pointer is NULL");
+    if (!aligned(spheres, 16) || !aligned(workspace, kAlign))
+        return fail(PCDF_EINVAL, "spheres must be 16-byte aligned, workspace %zu-byte aligned", kAlign);
+    size_t need = 0;
+    pcdf_surrogate_finish_workspace_bytes(T, H, N, &need);
+    if (workspace_bytes < need)
+        return fail(PCDF_ENOMEM, "workspace %zu bytes < %zu needed", workspace_bytes, need);
+    std::vector<pcdf::CapInfo> ci;
+    int zlo = 0, zhi = -1;
+    if (int rc = make_capinfo(grid, T, H, caps_host, ci, &zlo, &zhi))
+        return rc;
+    char *ws = (char *)workspace;
+    int *count = (int *)ws;
+    int *list = (int *)(ws + align_up(sizeof(int)));
+    pcdf::CapInfo *dcaps = (pcdf::CapInfo *)(ws + align_up(sizeof(int)) + align_up((size_t)N * sizeof(int)));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dcaps, ci.data(), ci.size() * sizeof(pcdf::CapInfo), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "surrogate setup");
+    const FeatGrid G = feat_grid(grid);
+    k_sur_combine<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(G.g, static_sdf, (const float4 *)spheres, N, H, y, eps,
+                                                              band, h, d_out, list, count);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_sur_fallback<<<sms * 8, 256, 0, st>>>(G.g, static_sq, static_sdf, (const float4 *)spheres, tidx, T, H, dcaps,
+                                           eps, list, count, h, d_out);
+    if (n_fallback)
+        e = cudaMemcpyAsync(n_fallback, count, sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "surrogate finish");
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+"""The learned surrogate: its tensor-core forward and backward against the
+fp64 oracle, the exactness of the fallback, and what training buys."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenes
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+pcdf = pytest.importorskip("paper_2201_05058_gb300")
+from paper_2201_05058_gb300 import surrogate as sg  # noqa: E402
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda", 0)
+
+
+def rand_x(M, rng, d):
+    x = np.zeros((M, 16), np.float32)
+    x[:, :11] = rng.normal(0.0, 0.7, size=(M, 11))
+    return torch.from_numpy(x).to(d).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("M", [300, 4096])
+def test_mlp_forward_and_gradients_match_oracle(M):
+    d = dev()
+    rng = np.random.default_rng(M)
+    net = pcdf.SurrogateMLP(d, seed=3)
+    x = rand_x(M, rng, d)
+    t = torch.from_numpy(rng.normal(size=M).astype(np.float32)).to(d)
+    y, loss = net.backward(x, t)
+    torch.cuda.synchronize()
+    P = net.params()
+    xo = x.float().cpu().double().numpy()
+    want_loss, G, want_y = omlp.loss_and_grad(P, xo, t.cpu().double().numpy(), rounding=True)
+    yg = y.cpu().double().numpy()
+    assert np.max(np.abs(yg - want_y)) <= 2e-2 * max(1.0, np.max(np.abs(want_y)))
+    assert abs(float(loss.item()) - want_loss) <= 1e-2 * want_loss
+    got = net.grads()
+    for k in G:
+        a = np.asarray(G[k], np.float64).ravel()
+        b = np.asarray(got[k], np.float64).ravel()
+        if k == "W1":  # the five zero input columns have zero gradient
+            b = b.reshape(256, 16)[:, :11].ravel()
+            a = a.reshape(256, 16)[:, :11].ravel()
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(a) + 1e-9, k
+    # the forward pass alone gives the same outputs
+    y2 = net.forward(x)
+    assert torch.equal(y2, y)
+
+
+def test_adam_step():
+    d = dev()
+    rng = np.random.default_rng(1)
+    net = pcdf.SurrogateMLP(d, seed=4)
+    x = rand_x(1024, rng, d)
+    t = torch.from_numpy(rng.normal(size=1024).astype(np.float32)).to(d)
+    net.backward(x, t)
+    p0 = net._f32("master").clone()
+    g = net._f32("grad").clone()
+    net.adam(1e-3)
+    p1 = net._f32("master")
+    # first Adam step: m = 0.1 g, v = 0.001 g^2, bias-corrected -> p - lr g / (|g| + eps)
+    want = p0 - 1e-3 * g / (g.abs() + 1e-8)
+    live = torch.ones_like(g, dtype=torch.bool)
+    live[:4096] = (torch.arange(4096, device=d) % 16) < 11  # zero input columns stay
+    live[136193:] = False
+    assert torch.allclose(p1[live], want[live], atol=1e-6, rtol=1e-4)
+    # the BF16 copy follows the master copy
+    half = net._bf16()
+    assert torch.equal(half[4096:4096 + 65536], p1[4352:4352 + 65536].to(torch.bfloat16))
+
+
+def scene_set(seeds, grid_only=False):
+    out = [scenes.scene_small_walking(seed=s, T=20, H=1) for s in seeds]
+    return out
+
+
+def exact_query(sc, d, sph, tidx, eps):
+    grid = sc["grid"]
+    static_sq, static_sdf = pcdf.build_static_sdf(torch.from_numpy(sc["occ"]).to(d), grid)
+    _, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, sc["caps"], want_sq=False, static_sdf=static_sdf)
+    h = pcdf.query_cost(comp_sdf, grid, sph, tidx, eps)
+    # exact distance from the same kernel (an eps above every distance in the
+    # grid keeps the hinge linear; 16 m keeps the fp32 resolution near 2e-6 m)
+    big = 16.0
+    hb = pcdf.query_cost(comp_sdf, grid, sph, tidx, big)
+    dd = (big + sph[..., 3]) - hb
+    return static_sq, static_sdf, h, dd
+
+
+def test_fallback_everywhere_is_bit_exact():
+    d = dev()
+    sc = scenes.scene_small_walking(seed=77, T=20, H=1)
+    grid = sc["grid"]
+    rng = np.random.default_rng(2)
+    sph_np, tidx_np = scenes.spheres_along_paths(grid, 16, 40, 8, rng, T=20)
+    sph = torch.from_numpy(sph_np).to(d)
+    tidx = torch.from_numpy(tidx_np).to(d)
+    static_sq, static_sdf, h_ex, _ = exact_query(sc, d, sph, tidx, 0.2)
+    net = pcdf.SurrogateMLP(d, seed=5)  # untrained: every answer must come from the fallback
+    h, _, nfb = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=1.0e9)
+    assert int(nfb.item()) == sph_np.size // 4
+    assert torch.equal(h, h_ex)
+
+
+def test_fallback_exact_with_several_humans():
+    d = dev()
+    sc = scenes.scene_small_walking(seed=78, T=6, H=3)
+    grid = sc["grid"]
+    rng = np.random.default_rng(3)
+    sph_np = scenes.spheres_uniform(grid, 3000, rng)
+    tidx_np = rng.integers(0, 6, 3000).astype(np.int32)
+    sph = torch.from_numpy(sph_np).to(d)
+    tidx = torch.from_numpy(tidx_np).to(d)
+    static_sq, static_sdf, h_ex, _ = exact_query(sc, d, sph, tidx, 0.2)
+    net = pcdf.SurrogateMLP(d, seed=6)
+    h, _, nfb = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=1.0e9)
+    assert int(nfb.item()) == 3000
+    assert torch.equal(h, h_ex)
+    # and the oracle agrees with both (within the cost tolerance)
+    comp = oracle.predicted_composite(oracle.edt(sc["occ"]), sc["caps"])
+    sdf_o = np.stack([oracle.sdf_from_sq(comp[t], grid.vox) for t in range(6)])
+    want, _ = oracle.hinge_cost(sdf_o, grid.origin, grid.vox, sph_np, tidx_np, 0.2)
+    assert np.max(np.abs(h.cpu().numpy() - want)) <= 1e-5
+
+
+def test_training_gains_and_decisions_stay_identical():
+    """Train on 40 scenes x 20 steps; on held-out scenes the trained network
+    needs far fewer exact answers than an untrained one at a band that covers
+    its validation error, and every collision decision equals the exact one."""
+    d = dev()
+    train_sc = scene_set(range(2000, 2040))
+    grid = train_sc[0]["grid"]
+    fields, caps, tf = sg.exact_dynamic_fields(grid, [s["caps"] for s in train_sc], d)
+    net = pcdf.SurrogateMLP(d, seed=11)
+    hist = sg.train(net, grid, fields, caps, tf, 20, steps=600, batch=16384, lr=2e-3, log_every=100)
+    assert hist[-1][1] < 0.1 * hist[0][1]
+
+    def evaluate(model, seeds, band=None):
+        res = []
+        for s in seeds:
+            sc = scenes.scene_small_walking(seed=s, T=20, H=1)
+            rng = np.random.default_rng(s)
+            sph_np, tidx_np = scenes.spheres_along_paths(grid, 64, 40, 8, rng, T=20)
+            sph = torch.from_numpy(sph_np).to(d)
+            tidx = torch.from_numpy(tidx_np).to(d)
+            static_sq, static_sdf, h_ex, d_ex = exact_query(sc, d, sph, tidx, 0.2)
+            h, dp, nfb = pcdf.surrogate_query(model, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2,
+                                              band=0.0 if band is None else band)
+            res.append((h, dp, nfb, h_ex, d_ex))
+        return res
+
+    def band_of(model):
+        res = evaluate(model, range(3000, 3004))
+        dp = torch.cat([r[1].reshape(-1) for r in res])
+        de = torch.cat([r[4].reshape(-1) for r in res])
+        return sg.band_from_errors(dp, de)
+
+    band = band_of(net)
+    untrained = pcdf.SurrogateMLP(d, seed=12)
+    band_u = band_of(untrained)
+    test = evaluate(net, range(3100, 3104), band)
+    test_u = evaluate(untrained, range(3100, 3104), band_u)
+    n = sum(r[0].numel() for r in test)
+    fb = sum(int(r[2].item()) for r in test) / n
+    fb_u = sum(int(r[2].item()) for r in test_u) / n
+    for h, dp, nfb, h_ex, d_ex in test + test_u:
+        assert torch.equal(h > 0, h_ex > 0)
+    assert fb < 0.5 * fb_u
+    assert fb < 0.5
