@@ -57,6 +57,7 @@ def parse_args(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
     ap.add_argument("--profile-case", choices=["composite", "static", "scratch", "query"], default=None,
                     help="run one small untimed case of the named stage (for ncu captures) and exit")
     ap.add_argument("--profile-T", type=int, default=4, help="horizon of the --profile-case composite")
@@ -283,6 +284,100 @@ def bench_batched(dev, seed, steps):
             "autotune_best_ms": tune_ms, "status": status}
 
 
+def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=65536):
+    """Learned surrogate: trained on the exact fields of n_train_scenes 64^3
+    scenes (5 cm voxels, one human walking over T = 20 steps) with n_samples
+    samples, then 1M trajectory-sphere queries per plan step on held-out scenes:
+    error against the exact composite field, fallback fraction, decision
+    identity, and the time of the surrogate path against the exact paths."""
+    import torch
+
+    import paper_2201_05058_gb300 as pcdf
+    from paper_2201_05058_gb300 import surrogate as sg
+
+    def ev_time(fn, k=5):
+        fn()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, z in ev:
+            a.record()
+            fn()
+            z.record()
+        torch.cuda.synchronize(dev)
+        return float(np.median([a.elapsed_time(z) for a, z in ev]))
+
+    T = 20
+    train_sc = [scenes.scene_small_walking(seed=seed + 1000 + i, T=T, H=1) for i in range(n_train_scenes)]
+    grid = train_sc[0]["grid"]
+    t0 = time.perf_counter()
+    fields, caps, tf = sg.exact_dynamic_fields(grid, [s["caps"] for s in train_sc], dev)
+    torch.cuda.synchronize(dev)
+    t_fields = time.perf_counter() - t0
+    net = pcdf.SurrogateMLP(dev, seed=seed + 17)
+    steps = max(1, n_samples // batch)
+    t0 = time.perf_counter()
+    hist = sg.train(net, grid, fields, caps, tf, T, steps=steps, batch=batch, lr=2e-3, log_every=max(1, steps // 8))
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    del fields
+
+    def queries(s):
+        sc = scenes.scene_small_walking(seed=s, T=T, H=1)
+        rng = np.random.default_rng(s)
+        sph, tidx = scenes.spheres_along_paths(grid, 1024, 40, 25, rng, T=T)  # 1,024,000 spheres
+        return sc, torch.from_numpy(sph).to(dev), torch.from_numpy(tidx).to(dev)
+
+    def exact(sc, sph, tidx):
+        occ = torch.from_numpy(sc["occ"]).to(dev)
+        st_sq, st_sdf = pcdf.build_static_sdf(occ, grid)
+        _, comp = pcdf.build_predicted_composite(st_sq, grid, sc["caps"], want_sq=False, static_sdf=st_sdf)
+        big = 16.0
+        d = (big + sph[..., 3]) - pcdf.query_cost(comp, grid, sph, tidx, big)
+        return occ, st_sq, st_sdf, comp, d
+
+    # band from validation scenes
+    errs = []
+    for s in range(seed + 5000, seed + 5002):
+        sc, sph, tidx = queries(s)
+        _, st_sq, st_sdf, _, d_ex = exact(sc, sph, tidx)
+        _, d_pr, _ = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.0)
+        errs.append((d_pr - d_ex).abs().reshape(-1))
+    band = sg.band_from_errors(torch.cat(errs), torch.zeros_like(torch.cat(errs)))
+    # held-out test scenes
+    stats = []
+    for s in range(seed + 6000, seed + 6002):
+        sc, sph, tidx = queries(s)
+        occ, st_sq, st_sdf, comp, d_ex = exact(sc, sph, tidx)
+        h_ex = pcdf.query_cost(comp, grid, sph, tidx, 0.2)
+        _, d_pr, _ = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.0)
+        h, _, nfb = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band)
+        e = (d_pr - d_ex).abs()
+        stats.append((float(e.max()), float(e.mean()), int(nfb.item()) / sph.numel() * 4,
+                      bool(torch.equal(h > 0, h_ex > 0)), int((h > 0).sum())))
+    # timing on the last test scene: one plan step of 1M queries
+    caps_dev = torch.from_numpy(np.ascontiguousarray(sc["caps"])).to(dev)
+    t_sur = ev_time(lambda: pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band,
+                                                 caps_dev=caps_dev))
+
+    def exact_composite():
+        _, cs = pcdf.build_predicted_composite(st_sq, grid, sc["caps"], want_sq=False, static_sdf=st_sdf)
+        pcdf.query_cost(cs, grid, sph, tidx, 0.2)
+
+    def exact_scratch():
+        _, fs = pcdf.build_from_scratch(occ, grid, sc["caps"])
+        pcdf.query_cost(fs, grid, sph, tidx, 0.2)
+
+    t_comp = ev_time(exact_composite)
+    t_scr = ev_time(exact_scratch)
+    return {"workload": f"MLP 16-256-256-256-1 bf16/fp32, trained on {n_train_scenes} 64^3 scenes x T=20 "
+                        f"({steps * batch} samples); 1,024,000 sphere queries per plan step on held-out scenes",
+            "train_s": t_train, "fields_s": t_fields, "loss_first": hist[0][1], "loss_last": hist[-1][1],
+            "band_m": band, "max_err_m": max(x[0] for x in stats), "mean_err_m": float(np.mean([x[1] for x in stats])),
+            "fallback_frac": float(np.mean([x[2] for x in stats])), "decisions_identical": all(x[3] for x in stats),
+            "surrogate_ms": t_sur, "exact_composite_ms": t_comp, "exact_scratch_ms": t_scr,
+            "speedup_vs_scratch": t_scr / t_sur, "speedup_vs_composite": t_comp / t_sur}
+
+
 def run_native(args):
     import torch
 
@@ -440,6 +535,7 @@ def run_native(args):
            "what": "H2D occupancy (pinned) + capsules, static + composite, D2H of the T float fields (pinned)"}
 
     batched = bench_batched(dev, rank_seed(args.seed, rank), args.steps) if not args.no_batched else None
+    surrogate = bench_surrogate(dev, rank_seed(args.seed, rank)) if not args.no_surrogate else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -458,7 +554,7 @@ def run_native(args):
             "composite_only": {"ms": comp_avg, "gvox_s": T * V / (comp_avg * 1e-3) / 1e9},
             "from_scratch": {"ms": scr_avg, "gvox_s": T * V / (scr_avg * 1e-3) / 1e9,
                              "composite_speedup": scr_avg / comp_avg},
-            "query": query, "batched": batched, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "query": query, "batched": batched, "surrogate": surrogate, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -295,7 +295,10 @@ int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, in
  *     clamp(tidx[q], 0, T - 1); caps device int32 [T][H][7]; x out [N * H][16].
  * pcdf_surrogate_finish  from the network outputs y [N * H] (device fp32):
  *     d = min(trilinear(static_sdf), min_h y[q * H + h]); where
- *     |d - (eps + r)| < band the query is answered exactly (corner voxels of
+ *     |d - (eps + r)| < band and the humans can matter in the query's cell
+ *     (min_h y - band - 2 sqrt(3) vox does not exceed every static corner
+ *     value; `band` must bound the network's error) the query is answered
+ *     exactly (corner voxels of
  *     its cell from static_sq and an exact local search over the capsules'
  *     voxels, interpolated like pcdf_query_cost: same bits as the exact
  *     composite path); h[q] = max(0, eps + r - d) (device fp32 [N]), d_out

@@ -139,6 +139,12 @@ __global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, c
     features(G, s.x, s.y, s.z, t, T, caps + 7 * ((long long)t * H + h), x + i * 16);
 }
 
+// A query needs the exact answer only if the prediction is within `band` of
+// the threshold and the humans can matter in its cell.  They cannot when the
+// predicted dynamic distance, less the band (the network's error bound) and
+// less 2 sqrt(3) voxels (how far the signed voxel field can change across a
+// cell), still exceeds every static corner value: then the static field is
+// the min at all eight corners and its interpolation is the exact distance.
 __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
                               long long N, int H, const float *__restrict__ y, float eps, float band,
                               float *__restrict__ h, float *__restrict__ d_out, int *__restrict__ list,
@@ -151,10 +157,26 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
         float dyn = __int_as_float(0x7f800000);
         for (int k = 0; k < H; ++k)
             dyn = fminf(dyn, y[q * H + k]);
-        const float ds = trilinear(g, static_sdf, s, false).d;
+        const Cell cl = locate(g, s);
+        const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+        float c[2][2][2], smax = __int_as_float(0xff800000);
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const float v = __ldg(static_sdf + (dz ? cl.i1[2] : cl.i0[2]) * sz + (dy ? cl.i1[1] : cl.i0[1]) * sy +
+                                          (dx ? cl.i1[0] : cl.i0[0]));
+                    c[dz][dy][dx] = v;
+                    smax = fmaxf(smax, v);
+                }
+        const float ds = interpolate(cl, c, false).d;
         const float d = fminf(ds, dyn);
         const float thr = eps + s.w;
-        fb = fabsf(d - thr) < band;
+        const float lip = 2.f * 1.7320508f * g.vox;
+        const bool static_certain = dyn - band - lip > smax;
+        fb = fabsf(d - thr) < band && !static_certain;
         const float hv = thr - d;
         h[q] = hv > 0.f ? hv : 0.f;
         if (d_out)

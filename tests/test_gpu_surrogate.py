@@ -139,7 +139,7 @@ def test_training_gains_and_decisions_stay_identical():
     grid = train_sc[0]["grid"]
     fields, caps, tf = sg.exact_dynamic_fields(grid, [s["caps"] for s in train_sc], d)
     net = pcdf.SurrogateMLP(d, seed=11)
-    hist = sg.train(net, grid, fields, caps, tf, 20, steps=600, batch=16384, lr=2e-3, log_every=100)
+    hist = sg.train(net, grid, fields, caps, tf, 20, steps=1500, batch=32768, lr=2e-3, log_every=100)
     assert hist[-1][1] < 0.1 * hist[0][1]
 
     def evaluate(model, seeds, band=None):
@@ -172,5 +172,6 @@ def test_training_gains_and_decisions_stay_identical():
     fb_u = sum(int(r[2].item()) for r in test_u) / n
     for h, dp, nfb, h_ex, d_ex in test + test_u:
         assert torch.equal(h > 0, h_ex > 0)
-    assert fb < 0.5 * fb_u
-    assert fb < 0.5
+    info = f"band {band:.4f} m (untrained {band_u:.3f}), fallback {fb:.4f} (untrained {fb_u:.4f}), loss {hist}"
+    assert fb < 0.5 * fb_u, info
+    assert fb < 0.25, info
