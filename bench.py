@@ -335,14 +335,19 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
         d = (big + sph[..., 3]) - pcdf.query_cost(comp, grid, sph, tidx, big)
         return occ, st_sq, st_sdf, comp, d
 
-    # band from validation scenes
-    errs = []
+    # bands from validation scenes: the decision band (every wrong predicted
+    # decision falls inside it) and the error bound (largest error)
+    dps, des, thrs = [], [], []
     for s in range(seed + 5000, seed + 5002):
         sc, sph, tidx = queries(s)
         _, st_sq, st_sdf, _, d_ex = exact(sc, sph, tidx)
         _, d_pr, _ = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.0)
-        errs.append((d_pr - d_ex).abs().reshape(-1))
-    band = sg.band_from_errors(torch.cat(errs), torch.zeros_like(torch.cat(errs)))
+        dps.append(d_pr.reshape(-1))
+        des.append(d_ex.reshape(-1))
+        thrs.append((0.2 + sph[..., 3]).reshape(-1))
+    dps, des, thrs = torch.cat(dps), torch.cat(des), torch.cat(thrs)
+    band = sg.band_from_decisions(dps, des, thrs)
+    err_bound = sg.band_from_errors(dps, des)
     # held-out test scenes
     stats = []
     for s in range(seed + 6000, seed + 6002):
@@ -350,14 +355,18 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
         occ, st_sq, st_sdf, comp, d_ex = exact(sc, sph, tidx)
         h_ex = pcdf.query_cost(comp, grid, sph, tidx, 0.2)
         _, d_pr, _ = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.0)
-        h, _, nfb = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band)
+        h, _, nfb = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band,
+                                         err_bound=err_bound)
         e = (d_pr - d_ex).abs()
         stats.append((float(e.max()), float(e.mean()), int(nfb.item()) / sph.numel() * 4,
                       bool(torch.equal(h > 0, h_ex > 0)), int((h > 0).sum())))
     # timing on the last test scene: one plan step of 1M queries
     caps_dev = torch.from_numpy(np.ascontiguousarray(sc["caps"])).to(dev)
     t_sur = ev_time(lambda: pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band,
-                                                 caps_dev=caps_dev))
+                                                 caps_dev=caps_dev, err_bound=err_bound))
+    x_q = pcdf.surrogate_features(grid, sph, tidx, T, caps_dev)
+    t_feat = ev_time(lambda: pcdf.surrogate_features(grid, sph, tidx, T, caps_dev))
+    t_mlp = ev_time(lambda: net.forward(x_q))
 
     def exact_composite():
         _, cs = pcdf.build_predicted_composite(st_sq, grid, sc["caps"], want_sq=False, static_sdf=st_sdf)
@@ -372,9 +381,10 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
     return {"workload": f"MLP 16-256-256-256-1 bf16/fp32, trained on {n_train_scenes} 64^3 scenes x T=20 "
                         f"({steps * batch} samples); 1,024,000 sphere queries per plan step on held-out scenes",
             "train_s": t_train, "fields_s": t_fields, "loss_first": hist[0][1], "loss_last": hist[-1][1],
-            "band_m": band, "max_err_m": max(x[0] for x in stats), "mean_err_m": float(np.mean([x[1] for x in stats])),
+            "band_m": band, "err_bound_m": err_bound, "max_err_m": max(x[0] for x in stats), "mean_err_m": float(np.mean([x[1] for x in stats])),
             "fallback_frac": float(np.mean([x[2] for x in stats])), "decisions_identical": all(x[3] for x in stats),
-            "surrogate_ms": t_sur, "exact_composite_ms": t_comp, "exact_scratch_ms": t_scr,
+            "surrogate_ms": t_sur, "features_ms": t_feat, "mlp_forward_ms": t_mlp,
+            "mlp_tflops": 2 * 136193 * sph.numel() / 4 / (t_mlp * 1e-3) / 1e12, "exact_composite_ms": t_comp, "exact_scratch_ms": t_scr,
             "speedup_vs_scratch": t_scr / t_sur, "speedup_vs_composite": t_comp / t_sur}
 
 

@@ -296,8 +296,9 @@ int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, in
  * pcdf_surrogate_finish  from the network outputs y [N * H] (device fp32):
  *     d = min(trilinear(static_sdf), min_h y[q * H + h]); where
  *     |d - (eps + r)| < band and the humans can matter in the query's cell
- *     (min_h y - band - 2 sqrt(3) vox does not exceed every static corner
- *     value; `band` must bound the network's error) the query is answered
+ *     (min_h y - err_bound - 2 sqrt(3) vox does not exceed every static
+ *     corner value; err_bound must bound the network's error) the query is
+ *     answered
  *     exactly (corner voxels of
  *     its cell from static_sq and an exact local search over the capsules'
  *     voxels, interpolated like pcdf_query_cost: same bits as the exact
@@ -314,8 +315,9 @@ int pcdf_surrogate_features(const pcdf_grid *grid, const float *spheres, const i
 int pcdf_surrogate_finish_workspace_bytes(int32_t T, int32_t H, int64_t N, size_t *bytes);
 int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                           const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
-                          const int32_t *caps_host, const float *y, float eps, float band, float *h, float *d_out,
-                          int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream);
+                          const int32_t *caps_host, const float *y, float eps, float band, float err_bound,
+                          float *h, float *d_out, int32_t *n_fallback, void *workspace, size_t workspace_bytes,
+                          void *stream);
 
 #ifdef __cplusplus
 }

@@ -557,9 +557,11 @@ def surrogate_features(grid, spheres, tidx, T, caps_dev):
     return x
 
 
-def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band):
+def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound=None):
     """Hinge cost from the network outputs with exact answers near the
-    threshold.  Returns (h, d, n_fallback[1])."""
+    threshold (err_bound: bound on the network error, default band).
+    Returns (h, d, n_fallback[1])."""
+    err_bound = band if err_bound is None else err_bound
     caps = _caps_host(caps)
     H = int(caps.shape[1])
     N = spheres.numel() // 4
@@ -574,18 +576,20 @@ def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps
     g = _cgrid(grid)
     _lib.check(lib.pcdf_surrogate_finish(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), _ptr(spheres),
                                          _ptr(tidx), N, int(T), H, caps.ctypes.data_as(ctypes.c_void_p), _ptr(y),
-                                         float(eps), float(band), _ptr(h), _ptr(d), _ptr(nfb), _ptr(ws), ws.numel(),
+                                         float(eps), float(band), float(err_bound), _ptr(h), _ptr(d), _ptr(nfb),
+                                         _ptr(ws), ws.numel(),
                                          ctypes.c_void_p(_stream(dev))), "pcdf_surrogate_finish")
     return h, d, nfb
 
 
-def surrogate_query(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps, band, caps_dev=None):
+def surrogate_query(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps, band, caps_dev=None,
+                    err_bound=None):
     """Hinge cost of every sphere through the network, exact within `band`
-    of the threshold.  Returns (h, d, n_fallback[1])."""
+    of the threshold where the humans can matter.  Returns (h, d, n_fallback[1])."""
     caps = _caps_host(caps)
     if caps_dev is None:
         caps_dev = torch.from_numpy(caps).to(spheres.device)
     T = int(caps.shape[0])
     x = surrogate_features(grid, spheres, tidx, T, caps_dev)
     y = model.forward(x)
-    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band)
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound)

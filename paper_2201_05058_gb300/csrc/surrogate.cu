@@ -141,12 +141,12 @@ __global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, c
 
 // A query needs the exact answer only if the prediction is within `band` of
 // the threshold and the humans can matter in its cell.  They cannot when the
-// predicted dynamic distance, less the band (the network's error bound) and
+// predicted dynamic distance, less `err` (a bound on the network's error) and
 // less 2 sqrt(3) voxels (how far the signed voxel field can change across a
 // cell), still exceeds every static corner value: then the static field is
 // the min at all eight corners and its interpolation is the exact distance.
 __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
-                              long long N, int H, const float *__restrict__ y, float eps, float band,
+                              long long N, int H, const float *__restrict__ y, float eps, float band, float err,
                               float *__restrict__ h, float *__restrict__ d_out, int *__restrict__ list,
                               int *__restrict__ count)
 {
@@ -175,7 +175,7 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
         const float d = fminf(ds, dyn);
         const float thr = eps + s.w;
         const float lip = 2.f * 1.7320508f * g.vox;
-        const bool static_certain = dyn - band - lip > smax;
+        const bool static_certain = dyn - err - lip > smax;
         fb = fabsf(d - thr) < band && !static_certain;
         const float hv = thr - d;
         h[q] = hv > 0.f ? hv : 0.f;
@@ -195,7 +195,7 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
     }
 }
 
-// --- exact dynamic squared distance at one voxel, warp-cooperative ---------
+// --- exact dynamic squared distances at the corners of a cell -----------
 
 __device__ __forceinline__ int warp_min(int v)
 {
@@ -213,110 +213,149 @@ __device__ __forceinline__ bool inside_any(const CapInfo *caps, int H, int i, in
     return false;
 }
 
-// min |v - u|^2 over the voxels u of the box [lo, hi] (clipped to the grid)
-// that satisfy pred(u); the warp's lanes split the box
+// For every voxel u of the box [lo, hi] with pred(u), lower best[c] to
+// |v_c - u|^2 for the corners c in `mask`.  Lanes take the x positions of a
+// row; rows are walked in order; the minima are reduced over the warp.
 template <class Pred>
-__device__ __forceinline__ int box_search(const int (&v)[3], int lo0, int lo1, int lo2, int hi0, int hi1, int hi2,
-                                          int best, Pred pred)
+__device__ __forceinline__ void scan_box(const int (&v)[8][3], unsigned mask, const int (&lo)[3], const int (&hi)[3],
+                                         int (&best)[8], Pred pred)
 {
     const int lane = threadIdx.x & 31;
-    const int nxb = hi0 - lo0 + 1, nyb = hi1 - lo1 + 1, nzb = hi2 - lo2 + 1;
-    if (nxb <= 0 || nyb <= 0 || nzb <= 0)
-        return best;
-    const long long tot = (long long)nxb * nyb * nzb;
-    for (long long e = lane; e < tot; e += 32) {
-        const int i = lo0 + (int)(e % nxb), j = lo1 + (int)((e / nxb) % nyb), k = lo2 + (int)(e / ((long long)nxb * nyb));
-        const int d = (i - v[0]) * (i - v[0]) + (j - v[1]) * (j - v[1]) + (k - v[2]) * (k - v[2]);
-        if (d < best && pred(i, j, k))
-            best = d;
-    }
-    return warp_min(best);
+    for (int k = lo[2]; k <= hi[2]; ++k)
+        for (int j = lo[1]; j <= hi[1]; ++j)
+            for (int i = lo[0] + lane; i <= hi[0]; i += 32) {
+                if (!pred(i, j, k))
+                    continue;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if (!((mask >> c) & 1u))
+                        continue;
+                    const int d = (i - v[c][0]) * (i - v[c][0]) + (j - v[c][1]) * (j - v[c][1]) +
+                                  (k - v[c][2]) * (k - v[c][2]);
+                    best[c] = min(best[c], d);
+                }
+            }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        best[c] = warp_min(best[c]);
 }
 
-// Exact dynamic squared EDT at voxel v (signed, as the composite kernels).
-// Outside every capsule: min over the capsules c of the squared distance to
-// c's voxels.  If q is the point of capsule c nearest to v's centre at
+// Exact dynamic squared EDT (signed, as the composite kernels) at the eight
+// corners v_c of a cell.
+//
+// A corner outside every capsule: min over the capsules C of the squared
+// distance to C's voxels.  If q is the point of C nearest to v's centre at
 // continuous distance d (voxel units), every point u of the convex capsule
-// satisfies |v - u|^2 >= d^2 + |u - q|^2, and some voxel of c lies within
+// satisfies |v - u|^2 >= d^2 + |u - q|^2, and some voxel of C lies within
 // d + sqrt(3) of v (a ball of radius sqrt(3)/2 around the point sqrt(3)/2
 // inside q holds a lattice point when r >= sqrt(3)/2), so the nearest voxel
-// lies within sqrt((d + sqrt(3))^2 - d^2) of q.  The search box covers that
-// ball with a margin; capsules that are thin, cut by the grid boundary, or
-// whose result breaks the d + sqrt(3) bound are searched over their whole
-// in-grid bounding box instead.  Inside some capsule: minus the squared
-// distance to the nearest voxel outside all capsules, by growing shells.
-__device__ int exact_dyn_sq(const QueryGrid &g, const CapInfo *caps, int H, const int (&v)[3])
+// lies within sqrt((d + sqrt(3))^2 - d^2) of q.  One box covers those balls
+// for all eight corners with a margin; capsules that are thin, cut by the grid
+// boundary, or whose result breaks the d + sqrt(3) bound at some corner are
+// searched over their whole in-grid bounding box instead.
+// A corner inside some capsule: minus the squared distance to the nearest
+// voxel outside all capsules, searched in growing cube shells.
+__device__ void exact_cell_dyn(const QueryGrid &g, const CapInfo *caps, int H, const int (&v)[8][3], int (&out)[8])
 {
-    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-    if (inside_any(caps, H, v[0], v[1], v[2])) {
-        int best = kInf32;
-        for (int rad = 1; rad <= max(n0, max(n1, n2)); ++rad) {
-            if ((long long)rad * rad >= best && best != kInf32)
+    const int n[3] = {g.n[0], g.n[1], g.n[2]};
+    unsigned ext = 0;
+    for (int c = 0; c < 8; ++c) {
+        out[c] = kInf32;
+        if (!inside_any(caps, H, v[c][0], v[c][1], v[c][2]))
+            ext |= 1u << c;
+    }
+    // interior corners (rare: corners within the humans)
+    for (int c = 0; c < 8; ++c) {
+        if ((ext >> c) & 1u)
+            continue;
+        int best[8];
+        for (int q = 0; q < 8; ++q)
+            best[q] = kInf32;
+        for (int rad = 1; rad <= max(n[0], max(n[1], n[2])); ++rad) {
+            if (best[c] != kInf32 && (long long)rad * rad >= best[c])
                 break;
-            // the two faces of the shell along each axis (cube faces overlap, harmless)
             for (int face = 0; face < 6; ++face) {
                 const int ax = face >> 1, sg = (face & 1) ? 1 : -1;
-                int lo[3] = {v[0] - rad, v[1] - rad, v[2] - rad}, hi[3] = {v[0] + rad, v[1] + rad, v[2] + rad};
-                lo[ax] = hi[ax] = v[ax] + sg * rad;
-                best = box_search(v, max(lo[0], 0), max(lo[1], 0), max(lo[2], 0), min(hi[0], n0 - 1),
-                                  min(hi[1], n1 - 1), min(hi[2], n2 - 1), best,
-                                  [&](int i, int j, int k) { return !inside_any(caps, H, i, j, k); });
+                int lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = max(v[c][a] - rad, 0);
+                    hi[a] = min(v[c][a] + rad, n[a] - 1);
+                }
+                const int f = v[c][ax] + sg * rad;
+                if (f < 0 || f > n[ax] - 1)
+                    continue;
+                lo[ax] = hi[ax] = f;
+                scan_box(v, 1u << c, lo, hi, best, [&](int i, int j, int k) { return !inside_any(caps, H, i, j, k); });
             }
         }
-        return best == kInf32 ? -kInf32 : -best;
+        out[c] = best[c] == kInf32 ? -kInf32 : -best[c];
     }
-    int best = kInf32;
-    const float pv[3] = {16.f * v[0] + 8.f, 16.f * v[1] + 8.f, 16.f * v[2] + 8.f};
-    for (int c = 0; c < H; ++c) {
-        const CapInfo &C = caps[c];
+    if (!ext)
+        return;
+    for (int cc = 0; cc < H; ++cc) {
+        const CapInfo &C = caps[cc];
         if (C.lo[0] > C.hi[0])
             continue;
-        bool full = C.r < 14;  // r < sqrt(3)/2 voxel (16ths)
+        bool full = C.r < 14;  // r < sqrt(3)/2 voxel, in 16ths
         for (int a = 0; a < 3; ++a) {
             const int mn = min(C.a[a], C.b[a]) - C.r, mx = max(C.a[a], C.b[a]) + C.r;
             const int ulo = (mn - 8 + 15 + 16 * 4096) / 16 - 4096, uhi = (mx - 8 + 16 * 4096) / 16 - 4096;
-            full |= ulo < 0 || uhi > g.n[a] - 1;  // cut by the grid boundary
+            full |= ulo < 0 || uhi > n[a] - 1;  // cut by the grid boundary
         }
-        int lo[3], hi[3];
-        float dv = 0.f;
+        int best[8];
+        for (int c = 0; c < 8; ++c)
+            best[c] = kInf32;
+        float bound[8];
         if (!full) {
-            float ab[3], w[3], L = 0.f, s = 0.f;
-            for (int a = 0; a < 3; ++a) {
-                ab[a] = (float)(C.b[a] - C.a[a]);
-                w[a] = pv[a] - (float)C.a[a];
-                L += ab[a] * ab[a];
-                s += w[a] * ab[a];
+            int lo[3] = {1 << 20, 1 << 20, 1 << 20}, hi[3] = {-(1 << 20), -(1 << 20), -(1 << 20)};
+            const float ab[3] = {(float)(C.b[0] - C.a[0]), (float)(C.b[1] - C.a[1]), (float)(C.b[2] - C.a[2])};
+            const float L = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+            for (int c = 0; c < 8; ++c) {
+                bound[c] = 0.f;
+                if (!((ext >> c) & 1u))
+                    continue;
+                const float pv[3] = {16.f * v[c][0] + 8.f, 16.f * v[c][1] + 8.f, 16.f * v[c][2] + 8.f};
+                float w[3], s = 0.f;
+                for (int a = 0; a < 3; ++a) {
+                    w[a] = pv[a] - (float)C.a[a];
+                    s += w[a] * ab[a];
+                }
+                const float tpar = L > 0.f ? fminf(fmaxf(s / L, 0.f), 1.f) : 0.f;
+                float q[3], dd = 0.f;
+                for (int a = 0; a < 3; ++a) {
+                    q[a] = (float)C.a[a] + tpar * ab[a];
+                    dd += (pv[a] - q[a]) * (pv[a] - q[a]);
+                }
+                const float dist = sqrtf(dd);
+                const float dv = fmaxf(dist - (float)C.r, 0.f) / 16.f;  // voxel units
+                bound[c] = dv + 1.7320508f + 0.01f;
+                const float R = sqrtf(2.f * 1.7320508f * dv + 3.f) + 2.f;
+                for (int a = 0; a < 3; ++a) {
+                    const float qs = dist > 0.f ? q[a] + (pv[a] - q[a]) * ((float)C.r / dist) : q[a];
+                    const float qv = (qs - 8.f) / 16.f;
+                    lo[a] = min(lo[a], (int)floorf(qv - R));
+                    hi[a] = max(hi[a], (int)ceilf(qv + R));
+                }
             }
-            const float tpar = L > 0.f ? fminf(fmaxf(s / L, 0.f), 1.f) : 0.f;
-            float q[3], dd = 0.f;
             for (int a = 0; a < 3; ++a) {
-                q[a] = (float)C.a[a] + tpar * ab[a];
-                dd += (pv[a] - q[a]) * (pv[a] - q[a]);
+                lo[a] = max(lo[a], C.lo[a]);
+                hi[a] = min(hi[a], C.hi[a]);
             }
-            const float dist = sqrtf(dd);
-            dv = fmaxf(dist - (float)C.r, 0.f) / 16.f;  // voxel units
-            const float R = sqrtf(2.f * 1.7320508f * dv + 3.f) + 2.f;
-            for (int a = 0; a < 3; ++a) {
-                const float qs = dist > 0.f ? q[a] + (pv[a] - q[a]) * ((float)C.r / dist) : q[a];
-                const float qv = (qs - 8.f) / 16.f;
-                lo[a] = max((int)floorf(qv - R), C.lo[a]);
-                hi[a] = min((int)ceilf(qv + R), C.hi[a]);
-            }
+            scan_box(v, ext, lo, hi, best, [&](int i, int j, int k) { return capsule_contains(C, i, j, k); });
+            for (int c = 0; c < 8; ++c)
+                if (((ext >> c) & 1u) && (best[c] == kInf32 || (float)best[c] > bound[c] * bound[c]))
+                    full = true;
         }
-        int bc = kInf32;
-        if (!full) {
-            bc = box_search(v, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], kInf32,
-                            [&](int i, int j, int k) { return capsule_contains(C, i, j, k); });
-            const float bound = dv + 1.7320508f + 0.01f;
-            if (bc == kInf32 || (float)bc > bound * bound)
-                full = true;
+        if (full) {
+            for (int c = 0; c < 8; ++c)
+                best[c] = kInf32;
+            const int lo[3] = {C.lo[0], C.lo[1], C.lo[2]}, hi[3] = {C.hi[0], C.hi[1], C.hi[2]};
+            scan_box(v, ext, lo, hi, best, [&](int i, int j, int k) { return capsule_contains(C, i, j, k); });
         }
-        if (full)
-            bc = box_search(v, C.lo[0], C.lo[1], C.lo[2], C.hi[0], C.hi[1], C.hi[2], kInf32,
-                            [&](int i, int j, int k) { return capsule_contains(C, i, j, k); });
-        best = min(best, bc);
+        for (int c = 0; c < 8; ++c)
+            if ((ext >> c) & 1u)
+                out[c] = min(out[c], best[c]);
     }
-    return best;
 }
 
 __global__ void k_sur_fallback(QueryGrid g, const int32_t *__restrict__ static_sq,
@@ -334,17 +373,21 @@ __global__ void k_sur_fallback(QueryGrid g, const int32_t *__restrict__ static_s
         const float4 s = spheres[q];
         const int t = min(max(tidx[q], 0), T - 1);
         const Cell cl = locate(g, s);
-        float c[2][2][2];
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int v[3] = {dx ? cl.i1[0] : cl.i0[0], dy ? cl.i1[1] : cl.i0[1], dz ? cl.i1[2] : cl.i0[2]};
-                    const long long o = ((long long)v[2] * g.n[1] + v[1]) * g.n[0] + v[0];
-                    const int32_t sv = static_sq[o];
-                    const int32_t dv = exact_dyn_sq(g, caps + (long long)t * H, H, v);
-                    c[dz][dy][dx] = sv <= dv ? static_sdf[o] : sq_to_sdf_fast(min(sv, dv), g.vox);
-                }
+        int v[8][3];
+        for (int c = 0; c < 8; ++c) {
+            v[c][0] = (c & 1) ? cl.i1[0] : cl.i0[0];
+            v[c][1] = (c & 2) ? cl.i1[1] : cl.i0[1];
+            v[c][2] = (c & 4) ? cl.i1[2] : cl.i0[2];
+        }
+        int dyn[8];
+        exact_cell_dyn(g, caps + (long long)t * H, H, v, dyn);
         if (lane == 0) {
+            float c[2][2][2];
+            for (int k = 0; k < 8; ++k) {
+                const long long o = ((long long)v[k][2] * g.n[1] + v[k][1]) * g.n[0] + v[k][0];
+                const int32_t sv = static_sq[o];
+                c[(k >> 2) & 1][(k >> 1) & 1][k & 1] = sv <= dyn[k] ? static_sdf[o] : sq_to_sdf_fast(min(sv, dyn[k]), g.vox);
+            }
             const Sample r = interpolate(cl, c, false);
             const float hv = (eps + s.w) - r.d;
             h[q] = hv > 0.f ? hv : 0.f;
@@ -423,7 +466,8 @@ int pcdf_surrogate_finish_workspace_bytes(int32_t T, int32_t H, int64_t N, size_
 
 int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                           const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
-                          const int32_t *caps_host, const float *y, float eps, float band, float *h, float *d_out,
+                          const int32_t *caps_host, const float *y, float eps, float band, float err_bound,
+                          float *h, float *d_out,
                           int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream)
 {
     if (int rc = check_grid(grid))
@@ -456,7 +500,7 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
         return cuda_fail(e, "surrogate setup");
     const FeatGrid G = feat_grid(grid);
     k_sur_combine<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(G.g, static_sdf, (const float4 *)spheres, N, H, y, eps,
-                                                              band, h, d_out, list, count);
+                                                              band, err_bound, h, d_out, list, count);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

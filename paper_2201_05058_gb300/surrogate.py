@@ -56,3 +56,14 @@ def band_from_errors(d_pred, d_exact, margin=1.5, floor=0.05):
     err = err[torch.isfinite(err)]
     m = float(err.max().item()) if err.numel() else 0.0
     return max(floor, margin * m)
+
+
+def band_from_decisions(d_pred, d_exact, thr, margin=1.5, floor=0.05):
+    """The smallest band that would have sent to the exact path every
+    validation query whose predicted decision (d < thr) was wrong, with a
+    margin: max |d_pred - thr| over those queries."""
+    wrong = (d_pred < thr) != (d_exact < thr)
+    gap = (d_pred - thr).abs()[wrong]
+    gap = gap[torch.isfinite(gap)]
+    m = float(gap.max().item()) if gap.numel() else 0.0
+    return max(floor, margin * m)

@@ -167,6 +167,24 @@ def test_training_gains_and_decisions_stay_identical():
     band_u = band_of(untrained)
     test = evaluate(net, range(3100, 3104), band)
     test_u = evaluate(untrained, range(3100, 3104), band_u)
+    # the decision band (tighter) with the error bound kept for the
+    # static-certain test still gives identical decisions
+    res = evaluate(net, range(3000, 3004))
+    dps = torch.cat([r[1].reshape(-1) for r in res])
+    des = torch.cat([r[4].reshape(-1) for r in res])
+    thr = 0.2 + torch.cat([torch.from_numpy(scenes.spheres_along_paths(grid, 64, 40, 8, np.random.default_rng(s), T=20)[0])
+                           .to(d)[..., 3].reshape(-1) for s in range(3000, 3004)])
+    band_d = sg.band_from_decisions(dps, des, thr)
+    for s in range(3100, 3104):
+        sc = scenes.scene_small_walking(seed=s, T=20, H=1)
+        rng = np.random.default_rng(s)
+        sph_np, tidx_np = scenes.spheres_along_paths(grid, 64, 40, 8, rng, T=20)
+        sph = torch.from_numpy(sph_np).to(d)
+        tidx = torch.from_numpy(tidx_np).to(d)
+        static_sq, static_sdf, h_ex, _ = exact_query(sc, d, sph, tidx, 0.2)
+        h, _, _ = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=band_d,
+                                       err_bound=band)
+        assert torch.equal(h > 0, h_ex > 0)
     n = sum(r[0].numel() for r in test)
     fb = sum(int(r[2].item()) for r in test) / n
     fb_u = sum(int(r[2].item()) for r in test_u) / n
