@@ -294,7 +294,10 @@ int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, in
  * pcdf_surrogate_features  rows (q * H + h) for sphere q and capsule h of time
  *     clamp(tidx[q], 0, T - 1); caps device int32 [T][H][7]; x out [N * H][16].
  * pcdf_surrogate_finish  from the network outputs y [N * H] (device fp32):
- *     d = min(trilinear(static_sdf), min_h y[q * H + h]); where
+ *     d = trilinear over the query's cell of min(static corner value,
+ *     min_h (y[q * H + h] + u_h . (corner - p))), u_h the unit vector from
+ *     capsule h's nearest axis point to p (the dynamic value extrapolated to
+ *     the corners along its distance gradient); where
  *     |d - (eps + r)| < band and the humans can matter in the query's cell
  *     (min_h y - err_bound - 2 sqrt(3) vox does not exceed every static
  *     corner value; err_bound must bound the network's error) the query is

@@ -139,6 +139,12 @@ __global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, c
     features(G, s.x, s.y, s.z, t, T, caps + 7 * ((long long)t * H + h), x + i * 16);
 }
 
+// The prediction is made like the exact distance: the eight corners of the
+// query's cell get min(static corner value, predicted dynamic value there) and
+// are interpolated.  The dynamic value at a corner is extrapolated from the
+// network's value at the point along the distance gradient of each capsule
+// (the unit vector from the nearest axis point), then the min over humans.
+//
 // A query needs the exact answer only if the prediction is within `band` of
 // the threshold and the humans can matter in its cell.  They cannot when the
 // predicted dynamic distance, less `err` (a bound on the network's error) and
@@ -146,7 +152,8 @@ __global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, c
 // cell), still exceeds every static corner value: then the static field is
 // the min at all eight corners and its interpolation is the exact distance.
 __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
-                              long long N, int H, const float *__restrict__ y, float eps, float band, float err,
+                              const int32_t *__restrict__ tidx, int T, const CapInfo *__restrict__ caps, long long N,
+                              int H, const float *__restrict__ y, float eps, float band, float err,
                               float *__restrict__ h, float *__restrict__ d_out, int *__restrict__ list,
                               int *__restrict__ count)
 {
@@ -154,12 +161,10 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
     bool fb = false;
     if (q < N) {
         const float4 s = spheres[q];
-        float dyn = __int_as_float(0x7f800000);
-        for (int k = 0; k < H; ++k)
-            dyn = fminf(dyn, y[q * H + k]);
+        const int t = min(max(tidx[q], 0), T - 1);
         const Cell cl = locate(g, s);
         const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
-        float c[2][2][2], smax = __int_as_float(0xff800000);
+        float c[2][2][2], dync[2][2][2], smax = __int_as_float(0xff800000);
 #pragma unroll
         for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
@@ -170,9 +175,51 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
                                           (dx ? cl.i1[0] : cl.i0[0]));
                     c[dz][dy][dx] = v;
                     smax = fmaxf(smax, v);
+                    dync[dz][dy][dx] = __int_as_float(0x7f800000);
                 }
-        const float ds = interpolate(cl, c, false).d;
-        const float d = fminf(ds, dyn);
+        const float p[3] = {s.x, s.y, s.z};
+        const float k16 = g.vox / 16.f;
+        float dyn = __int_as_float(0x7f800000);
+        for (int k = 0; k < H; ++k) {
+            const float yk = y[q * H + k];
+            dyn = fminf(dyn, yk);
+            const CapInfo &C = caps[(long long)t * H + k];
+            float ab[3], w[3], L = 0.f, sd = 0.f;
+            for (int a = 0; a < 3; ++a) {
+                const float am = g.origin[a] + (float)C.a[a] * k16;
+                ab[a] = (float)(C.b[a] - C.a[a]) * k16;
+                w[a] = p[a] - am;
+                L += ab[a] * ab[a];
+                sd += w[a] * ab[a];
+            }
+            const float tp = L > 0.f ? fminf(fmaxf(sd / L, 0.f), 1.f) : 0.f;
+            float u[3], nn = 0.f;
+            for (int a = 0; a < 3; ++a) {
+                u[a] = w[a] - tp * ab[a];
+                nn += u[a] * u[a];
+            }
+            const float inv = nn > 1e-12f ? rsqrtf(nn) : 0.f;
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int iv[3] = {dx ? cl.i1[0] : cl.i0[0], dy ? cl.i1[1] : cl.i0[1], dz ? cl.i1[2] : cl.i0[2]};
+                        float proj = 0.f;
+                        for (int a = 0; a < 3; ++a)
+                            proj += u[a] * inv * (g.origin[a] + ((float)iv[a] + 0.5f) * g.vox - p[a]);
+                        dync[dz][dy][dx] = fminf(dync[dz][dy][dx], yk + proj);
+                    }
+        }
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx)
+                    c[dz][dy][dx] = fminf(c[dz][dy][dx], dync[dz][dy][dx]);
+        const float d = interpolate(cl, c, false).d;
         const float thr = eps + s.w;
         const float lip = 2.f * 1.7320508f * g.vox;
         const bool static_certain = dyn - err - lip > smax;
@@ -499,8 +546,9 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
     if (e != cudaSuccess)
         return cuda_fail(e, "surrogate setup");
     const FeatGrid G = feat_grid(grid);
-    k_sur_combine<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(G.g, static_sdf, (const float4 *)spheres, N, H, y, eps,
-                                                              band, err_bound, h, d_out, list, count);
+    k_sur_combine<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(G.g, static_sdf, (const float4 *)spheres, tidx, T,
+                                                              dcaps, N, H, y, eps, band, err_bound, h, d_out, list,
+                                                              count);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
