@@ -99,6 +99,23 @@ int pcdf_static_workspace_bytes(const pcdf_grid *grid, size_t *bytes);
 int pcdf_build_static_sdf(const pcdf_grid *grid, const uint8_t *occ, int32_t *static_sq, float *static_sdf,
                           void *workspace, size_t workspace_bytes, void *stream);
 
+/* Allocation-free variant of pcdf_build_static_sdf (the paper has no
+ * counterpart; it exists for callers that cannot allocate device memory when
+ * they need the field, such as real-time loops that forbid allocation after
+ * start-up or hosts whose device memory belongs to another runtime).  Same
+ * arguments and result as pcdf_build_static_sdf, without a workspace: the
+ * scratch is a fixed array inside the library (about 12 MB on every device
+ * that loads it, held until exit), so grids are limited to
+ * PCDF_NOALLOC_MAX_VOXELS voxels (larger grids fail with PCDF_EINVAL and
+ * nothing is enqueued).  Allocates nothing.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race on it and must be serialised
+ * by the caller.  No part of the array needs to start at zero. */
+#define PCDF_NOALLOC_MAX_VOXELS 2097152
+int pcdf_build_static_sdf_noalloc(const pcdf_grid *grid, const uint8_t *occ, int32_t *static_sq, float *static_sdf,
+                                  void *stream);
+
 /* ---------------------------------------------------------------------------
  * Predicted composite fields (Sec. 6 composition; Sec. 8 sequence of n fields).
  *

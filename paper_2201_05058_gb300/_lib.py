@@ -31,7 +31,7 @@ class PcdfBatchTiles(ctypes.Structure):
 
 EXPORTS = (
     "pcdf_last_error", "pcdf_version",
-    "pcdf_static_workspace_bytes", "pcdf_build_static_sdf",
+    "pcdf_static_workspace_bytes", "pcdf_build_static_sdf", "pcdf_build_static_sdf_noalloc",
     "pcdf_composite_workspace_bytes", "pcdf_build_predicted_composite",
     "pcdf_composite_prepare", "pcdf_composite_finish", "pcdf_composite_slab",
     "pcdf_scratch_workspace_bytes", "pcdf_build_from_scratch",
@@ -55,6 +55,7 @@ def _declare(lib):
     sig = {
         "pcdf_static_workspace_bytes": [G, SZP],
         "pcdf_build_static_sdf": [G, P, P, P, P, SZ, P],
+        "pcdf_build_static_sdf_noalloc": [G, P, P, P, P],
         "pcdf_composite_workspace_bytes": [G, I32, I32, P, SZP],
         "pcdf_build_predicted_composite": [G, P, P, I32, I32, P, P, P, P, SZ, P],
         "pcdf_composite_prepare": [G, I32, I32, P, P, SZ, P],
