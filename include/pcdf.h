@@ -258,7 +258,7 @@ int pcdf_batch_autotune(const pcdf_env *envs, int32_t n_env, void *workspace, si
 /* ---------------------------------------------------------------------------
  * Learned surrogate of the dynamic field: a BF16 MLP with FP32 accumulation
  * (an extension beyond the paper).  16 inputs (PCDF_MLP_IN features, then
- * zero pads) -> 256 -> 256 -> 256 -> 1, ReLU after the hidden layers.
+ * zero pads; the weights of the pad inputs stay zero) -> 256 -> 256 -> 256 -> 1, ReLU after the hidden layers.
  *
  * State: one device buffer of pcdf_mlp_state_bytes(), 256-byte aligned,
  * holding the FP32 parameter vector, the two Adam moments and the gradient
@@ -275,7 +275,7 @@ int pcdf_batch_autotune(const pcdf_env *envs, int32_t n_env, void *workspace, si
  * pcdf_mlp_adam applies one Adam step (bias-corrected, step >= 1) to the FP32
  * parameters and refreshes the BF16 copies.
  * ------------------------------------------------------------------------- */
-#define PCDF_MLP_IN 11
+#define PCDF_MLP_IN 13
 #define PCDF_MLP_IN_PAD 16
 #define PCDF_MLP_WIDTH 256
 #define PCDF_MLP_PARAMS 136193
@@ -297,7 +297,11 @@ int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, in
  * Features of a point p (metres) at time index t of a horizon T for one
  * capsule (a, b, r): p - grid centre scaled by 2 / largest grid extent;
  * 2 t / (T - 1) - 1 (0 if T == 1); p - a and p - b in units of 2 m; r in units
- * of 2 m; five zeros.  (The capsule's end points enter relative to the point.)
+ * of 2 m; the continuous signed distance |p - n| - r from p to the capsule
+ * (n the nearest axis point) in units of 2 m; the axis parameter of n scaled
+ * to [-1, 1]; three zeros.  (The capsule enters relative to the point; the
+ * network learns the exact voxel field's departure from the continuous
+ * distance.)
  *
  * pcdf_surrogate_samples  M training rows from exact dynamic fields
  *     fields  device fp32 [n_fields][nz][ny][nx] (float fields of one capsule

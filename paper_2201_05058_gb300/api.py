@@ -421,7 +421,7 @@ def batch_autotune(envs, reps: int = 3, device=None):
 # learned surrogate of the dynamic field (BF16 MLP, FP32 accumulation)
 # ---------------------------------------------------------------------------
 
-MLP_IN, MLP_IN_PAD, MLP_WIDTH = 11, 16, 256
+MLP_IN, MLP_IN_PAD, MLP_WIDTH = 13, 16, 256
 MLP_PARAMS, MLP_PARAMS_PAD, MLP_BF16 = 136193, 136196, 135424
 # element offsets in the FP32 parameter vector and in the BF16 weight copies
 _P_OFF = {"W1": (0, (256, 16)), "b1": (4096, (256,)), "W2": (4352, (256, 256)), "b2": (69888, (256,)),

@@ -47,7 +47,9 @@ __device__ __forceinline__ float fixed_to_m(int32_t v, float origin, float vox)
 
 // Features of point p at time index t (horizon T) for one capsule:
 // p scaled to [-1, 1] by the grid, t scaled to [-1, 1], p - a and p - b in
-// units of kLen, the radius in units of kLen, then zero padding.
+// units of kLen, the radius in units of kLen, the continuous signed distance
+// from p to the capsule (|p - nearest axis point| - r) in units of kLen and
+// the axis parameter of that nearest point scaled to [-1, 1], then zeros.
 __device__ __forceinline__ void features(const FeatGrid &G, float px, float py, float pz, int t, int T,
                                          const int32_t *cap, bf16 *out)
 {
@@ -57,14 +59,31 @@ __device__ __forceinline__ void features(const FeatGrid &G, float px, float py, 
     for (int a = 0; a < 3; ++a)
         f[a] = (p[a] - G.centre[a]) * G.scale;
     f[3] = T > 1 ? 2.f * (float)t / (float)(T - 1) - 1.f : 0.f;
+    float w[3], ab[3], L = 0.f, sd = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        f[4 + a] = (p[a] - fixed_to_m(cap[a], G.g.origin[a], G.g.vox)) * (1.f / kLen);
-        f[7 + a] = (p[a] - fixed_to_m(cap[3 + a], G.g.origin[a], G.g.vox)) * (1.f / kLen);
+        const float am = fixed_to_m(cap[a], G.g.origin[a], G.g.vox);
+        const float bm = fixed_to_m(cap[3 + a], G.g.origin[a], G.g.vox);
+        f[4 + a] = (p[a] - am) * (1.f / kLen);
+        f[7 + a] = (p[a] - bm) * (1.f / kLen);
+        w[a] = p[a] - am;
+        ab[a] = bm - am;
+        L += ab[a] * ab[a];
+        sd += w[a] * ab[a];
     }
-    f[10] = (float)cap[6] * (G.g.vox / 16.f) * (1.f / kLen);
+    const float r = (float)cap[6] * (G.g.vox / 16.f);
+    f[10] = r * (1.f / kLen);
+    const float sp = L > 0.f ? fminf(fmaxf(sd / L, 0.f), 1.f) : 0.f;
+    float nn = 0.f;
 #pragma unroll
-    for (int a = 11; a < 16; ++a)
+    for (int a = 0; a < 3; ++a) {
+        const float e = w[a] - sp * ab[a];
+        nn += e * e;
+    }
+    f[11] = (sqrtf(nn) - r) * (1.f / kLen);
+    f[12] = 2.f * sp - 1.f;
+#pragma unroll
+    for (int a = 13; a < 16; ++a)
         f[a] = 0.f;
     bf16 h[16];
 #pragma unroll
