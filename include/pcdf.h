@@ -310,17 +310,20 @@ int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, in
  *             index of each field for the t feature, horizon T);
  *     point i: with probability `near` within 1 m of the capsule axis, else
  *     uniform in the grid; a counter hash of (seed, i) draws it;
- *     x out device BF16 bits [M][16]; target out device fp32 [M] (trilinear
- *     value of the field at the point).
+ *     x out device BF16 bits [M][16]; target out device fp32 [M]: the
+ *     trilinear value of the field at the point minus the continuous signed
+ *     distance from the point to the capsule (the network learns that
+ *     departure).
  * pcdf_surrogate_features  rows (q * H + h) for sphere q and capsule h of time
  *     clamp(tidx[q], 0, T - 1); caps device int32 [T][H][7]; x out [N * H][16].
  * pcdf_surrogate_finish  from the network outputs y [N * H] (device fp32):
+ *     with D_h = continuous signed distance to capsule h + y[q * H + h],
  *     d = trilinear over the query's cell of min(static corner value,
- *     min_h (y[q * H + h] + u_h . (corner - p))), u_h the unit vector from
+ *     min_h (D_h + u_h . (corner - p))), u_h the unit vector from
  *     capsule h's nearest axis point to p (the dynamic value extrapolated to
  *     the corners along its distance gradient); where
  *     |d - (eps + r)| < band and the humans can matter in the query's cell
- *     (min_h y - err_bound - 2 sqrt(3) vox does not exceed every static
+ *     (min_h D_h - err_bound - 2 sqrt(3) vox does not exceed every static
  *     corner value; err_bound must bound the network's error) the query is
  *     answered
  *     exactly (corner voxels of

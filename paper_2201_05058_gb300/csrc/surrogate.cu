@@ -45,43 +45,64 @@ __device__ __forceinline__ float fixed_to_m(int32_t v, float origin, float vox)
     return __fadd_rn(origin, __fmul_rn((float)v, __fdiv_rn(vox, 16.f)));
 }
 
-// Features of point p at time index t (horizon T) for one capsule:
-// p scaled to [-1, 1] by the grid, t scaled to [-1, 1], p - a and p - b in
-// units of kLen, the radius in units of kLen, the continuous signed distance
-// from p to the capsule (|p - nearest axis point| - r) in units of kLen and
-// the axis parameter of that nearest point scaled to [-1, 1], then zeros.
-__device__ __forceinline__ void features(const FeatGrid &G, float px, float py, float pz, int t, int T,
-                                         const int32_t *cap, bf16 *out)
+// Continuous geometry of one capsule seen from point p (metres): the signed
+// distance |p - n| - r to its surface (n the nearest axis point), the axis
+// parameter of n in [0, 1] and the unit vector from n to p (zero on the axis).
+struct CapGeo {
+    float dist, s, u[3];
+};
+
+__device__ __forceinline__ CapGeo capsule_geo(const QueryGrid &g, const float (&p)[3], const int32_t *cap)
 {
-    const float p[3] = {px, py, pz};
-    float f[16];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        f[a] = (p[a] - G.centre[a]) * G.scale;
-    f[3] = T > 1 ? 2.f * (float)t / (float)(T - 1) - 1.f : 0.f;
     float w[3], ab[3], L = 0.f, sd = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float am = fixed_to_m(cap[a], G.g.origin[a], G.g.vox);
-        const float bm = fixed_to_m(cap[3 + a], G.g.origin[a], G.g.vox);
-        f[4 + a] = (p[a] - am) * (1.f / kLen);
-        f[7 + a] = (p[a] - bm) * (1.f / kLen);
+        const float am = fixed_to_m(cap[a], g.origin[a], g.vox);
+        const float bm = fixed_to_m(cap[3 + a], g.origin[a], g.vox);
         w[a] = p[a] - am;
         ab[a] = bm - am;
         L += ab[a] * ab[a];
         sd += w[a] * ab[a];
     }
-    const float r = (float)cap[6] * (G.g.vox / 16.f);
-    f[10] = r * (1.f / kLen);
-    const float sp = L > 0.f ? fminf(fmaxf(sd / L, 0.f), 1.f) : 0.f;
+    CapGeo r;
+    r.s = L > 0.f ? fminf(fmaxf(sd / L, 0.f), 1.f) : 0.f;
     float nn = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float e = w[a] - sp * ab[a];
-        nn += e * e;
+        r.u[a] = w[a] - r.s * ab[a];
+        nn += r.u[a] * r.u[a];
     }
-    f[11] = (sqrtf(nn) - r) * (1.f / kLen);
-    f[12] = 2.f * sp - 1.f;
+    const float len = sqrtf(nn);
+    const float inv = len > 1e-6f ? 1.f / len : 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        r.u[a] *= inv;
+    r.dist = len - (float)cap[6] * (g.vox / 16.f);
+    return r;
+}
+
+// Features of point p at time index t (horizon T) for one capsule:
+// p scaled to [-1, 1] by the grid, t scaled to [-1, 1], p - a and p - b in
+// units of kLen, the radius in units of kLen, the continuous signed distance
+// to the capsule in units of kLen and the axis parameter of its nearest point
+// scaled to [-1, 1], then zeros.  The network's output is the exact field's
+// departure from that continuous distance (its target in training).
+__device__ __forceinline__ void features(const FeatGrid &G, const float (&p)[3], int t, int T, const int32_t *cap,
+                                         const CapGeo &geo, bf16 *out)
+{
+    float f[16];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        f[a] = (p[a] - G.centre[a]) * G.scale;
+    f[3] = T > 1 ? 2.f * (float)t / (float)(T - 1) - 1.f : 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f[4 + a] = (p[a] - fixed_to_m(cap[a], G.g.origin[a], G.g.vox)) * (1.f / kLen);
+        f[7 + a] = (p[a] - fixed_to_m(cap[3 + a], G.g.origin[a], G.g.vox)) * (1.f / kLen);
+    }
+    f[10] = (float)cap[6] * (G.g.vox / 16.f) * (1.f / kLen);
+    f[11] = geo.dist * (1.f / kLen);
+    f[12] = 2.f * geo.s - 1.f;
 #pragma unroll
     for (int a = 13; a < 16; ++a)
         f[a] = 0.f;
@@ -141,8 +162,9 @@ __global__ void k_sur_samples(FeatGrid G, const float *__restrict__ fields, cons
     }
     const long long V = (long long)G.g.n[0] * G.g.n[1] * G.g.n[2];
     const Sample r = trilinear(G.g, fields + (long long)j * V, make_float4(p[0], p[1], p[2], 0.f), false);
-    target[i] = r.d;
-    features(G, p[0], p[1], p[2], tf[j], T, cap, x + i * 16);
+    const CapGeo geo = capsule_geo(G.g, p, cap);
+    target[i] = r.d - geo.dist;
+    features(G, p, tf[j], T, cap, geo, x + i * 16);
 }
 
 __global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, const int32_t *__restrict__ tidx,
@@ -155,14 +177,18 @@ __global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, c
     const int h = (int)(i % H);
     const float4 s = spheres[q];
     const int t = min(max(tidx[q], 0), T - 1);
-    features(G, s.x, s.y, s.z, t, T, caps + 7 * ((long long)t * H + h), x + i * 16);
+    const float p[3] = {s.x, s.y, s.z};
+    const int32_t *cap = caps + 7 * ((long long)t * H + h);
+    features(G, p, t, T, cap, capsule_geo(G.g, p, cap), x + i * 16);
 }
 
 // The prediction is made like the exact distance: the eight corners of the
 // query's cell get min(static corner value, predicted dynamic value there) and
-// are interpolated.  The dynamic value at a corner is extrapolated from the
-// network's value at the point along the distance gradient of each capsule
-// (the unit vector from the nearest axis point), then the min over humans.
+// are interpolated.  The dynamic value of a capsule at the point is its
+// continuous distance plus the network's output (the learned departure of the
+// exact voxel field from it); at a corner it is extrapolated along the
+// capsule's distance gradient (the unit vector from the nearest axis point),
+// then the min over humans.
 //
 // A query needs the exact answer only if the prediction is within `band` of
 // the threshold and the humans can matter in its cell.  They cannot when the
@@ -197,27 +223,13 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
                     dync[dz][dy][dx] = __int_as_float(0x7f800000);
                 }
         const float p[3] = {s.x, s.y, s.z};
-        const float k16 = g.vox / 16.f;
         float dyn = __int_as_float(0x7f800000);
         for (int k = 0; k < H; ++k) {
-            const float yk = y[q * H + k];
-            dyn = fminf(dyn, yk);
             const CapInfo &C = caps[(long long)t * H + k];
-            float ab[3], w[3], L = 0.f, sd = 0.f;
-            for (int a = 0; a < 3; ++a) {
-                const float am = g.origin[a] + (float)C.a[a] * k16;
-                ab[a] = (float)(C.b[a] - C.a[a]) * k16;
-                w[a] = p[a] - am;
-                L += ab[a] * ab[a];
-                sd += w[a] * ab[a];
-            }
-            const float tp = L > 0.f ? fminf(fmaxf(sd / L, 0.f), 1.f) : 0.f;
-            float u[3], nn = 0.f;
-            for (int a = 0; a < 3; ++a) {
-                u[a] = w[a] - tp * ab[a];
-                nn += u[a] * u[a];
-            }
-            const float inv = nn > 1e-12f ? rsqrtf(nn) : 0.f;
+            const int32_t cp[7] = {C.a[0], C.a[1], C.a[2], C.b[0], C.b[1], C.b[2], C.r};
+            const CapGeo geo = capsule_geo(g, p, cp);
+            const float yk = y[q * H + k] + geo.dist;  // residual + continuous distance
+            dyn = fminf(dyn, yk);
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
@@ -226,8 +238,9 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
                     for (int dx = 0; dx < 2; ++dx) {
                         const int iv[3] = {dx ? cl.i1[0] : cl.i0[0], dy ? cl.i1[1] : cl.i0[1], dz ? cl.i1[2] : cl.i0[2]};
                         float proj = 0.f;
+#pragma unroll
                         for (int a = 0; a < 3; ++a)
-                            proj += u[a] * inv * (g.origin[a] + ((float)iv[a] + 0.5f) * g.vox - p[a]);
+                            proj += geo.u[a] * (g.origin[a] + ((float)iv[a] + 0.5f) * g.vox - p[a]);
                         dync[dz][dy][dx] = fminf(dync[dz][dy][dx], yk + proj);
                     }
         }

@@ -135,6 +135,15 @@ def test_composite_ragged_grid_and_edge_capsules():
     check_composite(occ, caps, grid)
 
 
+def test_composite_odd_slice_size():
+    # nx * ny odd: one column per thread (the paired-column kernel needs it even)
+    grid = scenes.Grid(33, 17, 30, 0.05)
+    rng = np.random.default_rng(8)
+    occ, _ = scenes.boxes_occupancy(grid, 5, rng)
+    caps = scenes.walking_capsules(grid, 2, 3, rng)
+    check_composite(occ, caps, grid)
+
+
 def test_composite_no_humans_and_humans_outside():
     sc = scenes.scene_small(seed=1)
     grid = sc["grid"]
