@@ -143,7 +143,8 @@ int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_
 
 /* The z-slab [zlo, zlo + S) of voxel slices that some capsule of some t
  * touches (S = 0: no capsule touches the grid).  The dynamic field's sites all
- * lie in it; the workspace holds one int32 per slab voxel per t. */
+ * lie in it; the workspace holds one int32 per slab voxel per t and one
+ * int32 per column (x, y): the largest static value of the column. */
 int pcdf_composite_slab(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, int32_t *zlo,
                         int32_t *S);
 
@@ -151,7 +152,11 @@ int pcdf_composite_slab(const pcdf_grid *grid, int32_t T, int32_t H, const int32
  * overlap or time them separately (same arguments and workspace; the
  * workspace carries the dynamic intermediate from the first to the second):
  *   prepare: the capsule row pass and y pass over the z-slab the capsules touch;
- *   finish:  the fused z pass, composite min and float epilogue for every t. */
+ *   finish:  the static column maxima, then the fused z pass, composite min
+ *            and float epilogue for every t (where a column's largest static
+ *            value is no larger than the humans' least 2-D partial, or a z lies
+ *            far enough from the slab, the output is the static field without
+ *            evaluating the humans' envelope). */
 int pcdf_composite_prepare(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, void *workspace,
                            size_t workspace_bytes, void *stream);
 int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int32_t T,

@@ -21,13 +21,21 @@ __global__ void __launch_bounds__(128)
 template <bool kSq, bool kSdfOut, bool kStaticSdf>
 __global__ void __launch_bounds__(128, 8)
     k_composite_z(const int32_t *__restrict__ static_sq, const float *__restrict__ static_sdf,
-                  const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz, int zlo, int S, int T,
-                  int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox)
+                  const int32_t *__restrict__ colmax, const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz,
+                  int zlo, int S, int T, int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox,
+                  int vec)
 {
     extern __shared__ uint32_t smem[];
-    comp::composite_block<kSq, kSdfOut, kStaticSdf, false>(static_sq, static_sdf, dyn_mid, nx, ny, nz, zlo, S,
-                                                           (int)(blockIdx.x % T), (long long)(blockIdx.x / T) * blockDim.x,
-                                                           comp_sq, comp_sdf, vox, smem);
+    comp::composite_block_short<kSq, kSdfOut, kStaticSdf>(static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S,
+                                                          (int)(blockIdx.x % T),
+                                                          (long long)(blockIdx.x / T) * blockDim.x, comp_sq, comp_sdf,
+                                                          vox, vec != 0, smem);
+}
+
+__global__ void __launch_bounds__(128) k_colmax(const int32_t *__restrict__ sq, long long V2, int nz,
+                                                int32_t *__restrict__ colmax)
+{
+    comp::colmax_block(sq, V2, nz, colmax);
 }
 
 __global__ void k_broadcast_static(const int32_t *__restrict__ static_sq, long long V, int T,
@@ -68,23 +76,36 @@ cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, 
     return cudaGetLastError();
 }
 
+namespace {
+
 template <bool kSq, bool kSdfOut, bool kStaticSdf>
 cudaError_t launch_cz(int nblk, int nthr, size_t smem, const int32_t *static_sq, const float *static_sdf,
-                      const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int T, int32_t *comp_sq,
-                      float *comp_sdf, float vox, cudaStream_t stream)
+                      const int32_t *colmax, const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int T,
+                      int32_t *comp_sq, float *comp_sdf, float vox, int vec, cudaStream_t stream)
 {
     auto kern = k_composite_z<kSq, kSdfOut, kStaticSdf>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    kern<<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, static_sdf, dyn_mid, nx, ny, nz, zlo, S, T, comp_sq,
-                                                 comp_sdf, vox);
+    kern<<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S, T,
+                                                 comp_sq, comp_sdf, vox, vec);
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf, const int32_t *dyn_mid, int nx,
-                               int ny, int nz, int zlo, int S, int T, int32_t *comp_sq, float *comp_sdf, float vox,
-                               cudaStream_t stream)
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+cudaError_t launch_colmax(const int32_t *sq, int nx, int ny, int nz, int32_t *colmax, cudaStream_t stream)
+{
+    const long long V2 = (long long)nx * ny;
+    k_colmax<<<(unsigned)((V2 + 31) / 32), 128, 0, stream>>>(sq, V2, nz, colmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf, const int32_t *colmax,
+                               const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int T,
+                               int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream)
 {
     const long long V2 = (long long)nx * ny;
     const int words = S + 2 + (S + 31) / 32;
@@ -93,10 +114,14 @@ cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf
         nthr >>= 1;
     const size_t smem = (size_t)nthr * words * sizeof(uint32_t);
     const int nblk = (int)((V2 + nthr - 1) / nthr * T);
-#define PCDF_CZ(a, b, c)                                                                                            \
-    return launch_cz<a, b, c>(nblk, nthr, smem, static_sq, static_sdf, dyn_mid, nx, ny, nz, zlo, S, T, comp_sq,     \
-                              comp_sdf, vox, stream)
     const bool sq = comp_sq != nullptr, sd = comp_sdf != nullptr, st = static_sdf != nullptr && sd;
+    // 16-byte copies of all-static column blocks: every plane and column
+    // block starts on a 16-byte boundary
+    const int vec = V2 % 4 == 0 && aligned16(static_sq) && (!st || aligned16(static_sdf)) &&
+                    (!sq || aligned16(comp_sq)) && (!sd || aligned16(comp_sdf));
+#define PCDF_CZ(a, b, c)                                                                                            \
+    return launch_cz<a, b, c>(nblk, nthr, smem, static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S, T,      \
+                              comp_sq, comp_sdf, vox, vec, stream)
     if (sq && sd && st)
         PCDF_CZ(true, true, true);
     if (sq && sd)

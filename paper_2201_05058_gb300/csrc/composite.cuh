@@ -11,10 +11,19 @@
 //                y lower envelopes of the row distances to those intervals.
 //                Output: the 2-D partial field of the slice (signed int32),
 //                with no row-pass intermediate in memory.
+//  k_colmax     the largest static value of every column (x, y).
 //  k_composite_z thread per (column (x, y), t): the z envelope of the slab's
 //                2-D partials, evaluated at every z, min with the static
 //                field, float epilogue; the T CTAs that share a static column
 //                block run together so that block is read from DRAM once.
+//
+// The humans' field of a column is never below gmin, the least 2-D partial of
+// its slab, and at z outside the slab it is at least gmin plus the squared
+// distance to the slab.  Where the column's largest static value does not
+// exceed that bound the composite is the static field: a column with
+// colmax <= gmin is a copy of the static column, a CTA of such columns copies
+// its block with 16-byte accesses, and other columns evaluate the envelope
+// only in the z window around the slab where the humans can be nearer.
 #pragma once
 
 #include "edt_common.cuh"
@@ -306,8 +315,6 @@ struct Out {
     }
 };
 
-// outputs for z in [z0, z1) outside the humans (kCheck: skip the occupied
-// slab voxels, whose outputs set F wrote); offsets z * V2 stay below 2^31
 template <bool kCoherent, class T>
 __device__ __forceinline__ T ldx(const T *p)
 {
@@ -316,9 +323,15 @@ __device__ __forceinline__ T ldx(const T *p)
     return __ldg(p);
 }
 
-template <bool kCheck, bool kEmpty, bool kCoherent, class O_t>
-__device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, const uint32_t *mk, int zlo, int nthr,
-                                           const int32_t *scol, const float *sfcol, int V2, const O_t &out)
+// Outputs for z in [z0, z1).  kEval: the humans' distance is the envelope O
+// where useO holds (else +INF: the static field); kCheck: skip the occupied
+// slab voxels where useMk holds (set F wrote them).  Lanes of a warp that
+// share the bounds keep the loads and stores of a z coalesced; offsets
+// z * V2 stay below 2^31.
+template <bool kCheck, bool kEval, bool kCoherent, class O_t>
+__device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, bool useO, const uint32_t *mk, bool useMk,
+                                           int zlo, int nthr, const int32_t *scol, const float *sfcol, int V2,
+                                           const O_t &out)
 {
     constexpr bool kStaticSdf = O_t::kHaveStatic;
     int z = z0;
@@ -334,39 +347,42 @@ __device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, const u
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int zz = z + i;
-            if (kCheck) {
+            if (kCheck && useMk) {
                 const int e = zz - zlo;
                 if ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u)
                     continue;
             }
-            const int32_t d = kEmpty ? kInf32 : O.eval(zz);
+            const int32_t d = (kEval && useO) ? O.eval(zz) : kInf32;
             out.put(zz * V2, sv[i], kStaticSdf ? sf[i] : 0.f, d);
         }
     }
     for (; z < z1; ++z) {
-        if (kCheck) {
+        if (kCheck && useMk) {
             const int e = z - zlo;
             if ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u)
                 continue;
         }
-        const int32_t d = kEmpty ? kInf32 : O.eval(z);
+        const int32_t d = (kEval && useO) ? O.eval(z) : kInf32;
         out.put(z * V2, ldx<kCoherent>(scol + z * V2), kStaticSdf ? ldx<kCoherent>(sfcol + z * V2) : 0.f, d);
     }
 }
 
+// Outputs of one column over [0, nz) with the column's own bounds: below
+// its occupied run, the run (skipping its voxels), above it; `empty`: set O
+// has no site.
 template <bool kCoherent, class O_t>
 __device__ __forceinline__ void emit_all(int za, int zb, int nz, bool empty, EnvCursor &O, const uint32_t *mk,
                                          int zlo, int nthr, const int32_t *scol, const float *sfcol, int V2,
                                          const O_t &out)
 {
     if (empty) {
-        emit_range<false, true, kCoherent>(0, za, O, mk, zlo, nthr, scol, sfcol, V2, out);
-        emit_range<true, true, kCoherent>(za, zb, O, mk, zlo, nthr, scol, sfcol, V2, out);
-        emit_range<false, true, kCoherent>(zb, nz, O, mk, zlo, nthr, scol, sfcol, V2, out);
+        emit_range<false, false, kCoherent>(0, za, O, false, mk, false, zlo, nthr, scol, sfcol, V2, out);
+        emit_range<true, false, kCoherent>(za, zb, O, false, mk, true, zlo, nthr, scol, sfcol, V2, out);
+        emit_range<false, false, kCoherent>(zb, nz, O, false, mk, false, zlo, nthr, scol, sfcol, V2, out);
     } else {
-        emit_range<false, false, kCoherent>(0, za, O, mk, zlo, nthr, scol, sfcol, V2, out);
-        emit_range<true, false, kCoherent>(za, zb, O, mk, zlo, nthr, scol, sfcol, V2, out);
-        emit_range<false, false, kCoherent>(zb, nz, O, mk, zlo, nthr, scol, sfcol, V2, out);
+        emit_range<false, true, kCoherent>(0, za, O, true, mk, false, zlo, nthr, scol, sfcol, V2, out);
+        emit_range<true, true, kCoherent>(za, zb, O, true, mk, true, zlo, nthr, scol, sfcol, V2, out);
+        emit_range<false, true, kCoherent>(zb, nz, O, true, mk, false, zlo, nthr, scol, sfcol, V2, out);
     }
 }
 
@@ -375,53 +391,95 @@ struct OutT : Out<kSq, kSdfOut, kStaticSdf> {
     static constexpr bool kHaveStatic = kStaticSdf;
 };
 
-// The CTA computes columns [col0, col0 + blockDim.x) of time t; smem holds
-// blockDim.x * (S + 2 + ceil(S / 32)) words.
-template <bool kSq, bool kSdfOut, bool kStaticSdf, bool kCoherent>
-__device__ __forceinline__ void composite_block(const int32_t *__restrict__ static_sq,
-                                                const float *__restrict__ static_sdf,
-                                                const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz, int zlo,
-                                                int S, int t, long long col0, int32_t *__restrict__ comp_sq,
-                                                float *__restrict__ comp_sdf, float vox, uint32_t *smem)
+// Largest value of each column c of a field [nz][V2]: warp w of the CTA reads
+// the z quarter w of 32 consecutive columns (lane = column).
+__device__ __forceinline__ void colmax_block(const int32_t *__restrict__ sq, long long V2, int nz,
+                                             int32_t *__restrict__ colmax)
 {
-    const int nthr = blockDim.x, tid = threadIdx.x;
-    const long long V2 = (long long)nx * ny;
-    const long long c = col0 + tid;
-    if (c >= V2)
-        return;  // no block-level synchronisation below
-    uint32_t *tile = smem + tid;                              // slot k at tile[k * nthr]
-    uint32_t *mk = smem + (size_t)(S + 2) * nthr + tid;       // word w at mk[w * nthr]
-    const int nw = (S + 31) >> 5;
-    const int32_t *dcol = dyn_mid + (long long)t * S * V2 + c;
-
+    __shared__ int32_t part[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long c = (long long)blockIdx.x * 32 + lane;
+    const int z0 = (int)((long long)nz * w / 4), z1 = (int)((long long)nz * (w + 1) / 4);
+    int32_t m = INT32_MIN;
+    if (c < V2) {
+        const int32_t *col = sq + c;
 #pragma unroll 8
-    for (int e = 0; e < S; ++e)
-        tile[(e + 1) * nthr] = (uint32_t)(kCoherent ? __ldcg(dcol + (long long)e * V2) : __ldcs(dcol + (long long)e * V2));
+        for (int z = z0; z < z1; ++z)
+            m = max(m, __ldg(col + (long long)z * V2));
+    }
+    part[w][lane] = m;
+    __syncthreads();
+    if (w == 0 && c < V2)
+        colmax[c] = max(max(part[0][lane], part[1][lane]), max(part[2][lane], part[3][lane]));
+}
 
-    int firstOcc = S, lastOcc = -1;
-    for (int w = 0; w < nw; ++w) {
-        uint32_t bits = 0;
-        const int e0 = w << 5, cnt = min(32, S - e0);
-        for (int b = 0; b < cnt; ++b)
-            bits |= (uint32_t)((int32_t)tile[(e0 + b + 1) * nthr] < 0) << b;
-        mk[w * nthr] = bits;
-        if (bits) {
-            if (firstOcc == S)
-                firstOcc = e0 + __ffs(bits) - 1;
-            lastOcc = e0 + 31 - __clz(bits);
+// The static field as the composite of time t on columns [col0, col0 + ncols)
+// (ncols a multiple of 4): 16-byte loads and stores, thread tid on the column
+// quad tid % nq of the planes tid / nq, tid / nq + nthr / nq, ...  Needs
+// V2 % 4 == 0, col0 % 4 == 0 and 16-byte aligned fields.
+template <bool kSq, bool kSdfOut, bool kStaticSdf, bool kCoherent>
+__device__ __forceinline__ void copy_static_block(const int32_t *__restrict__ static_sq,
+                                                  const float *__restrict__ static_sdf, long long V2, int nz,
+                                                  long long col0, int ncols, int32_t *__restrict__ osq,
+                                                  float *__restrict__ osdf, float vox)
+{
+    const int nq = ncols >> 2;
+    const int zstep = blockDim.x / nq;
+    const int qd = threadIdx.x % nq, zfirst = threadIdx.x / nq;
+    if (zfirst >= zstep)
+        return;
+    const long long base = col0 + 4 * qd;
+#pragma unroll 4
+    for (int z = zfirst; z < nz; z += zstep) {
+        const long long o = (long long)z * V2 + base;
+        const int4 sv = ldx<kCoherent>(reinterpret_cast<const int4 *>(static_sq + o));
+        if (kSq)
+            __stcs(reinterpret_cast<int4 *>(osq + o), sv);
+        if (kSdfOut) {
+            float4 f;
+            if (kStaticSdf)
+                f = ldx<kCoherent>(reinterpret_cast<const float4 *>(static_sdf + o));
+            else
+                f = make_float4(sq_to_sdf_fast(sv.x, vox), sq_to_sdf_fast(sv.y, vox), sq_to_sdf_fast(sv.z, vox),
+                                sq_to_sdf_fast(sv.w, vox));
+            __stcs(reinterpret_cast<float4 *>(osdf + o), f);
         }
     }
-    const long long V = V2 * nz;
-    const int32_t *scol = static_sq + c;
-    const float *sfcol = kStaticSdf ? static_sdf + c : nullptr;
-    OutT<kSq, kSdfOut, kStaticSdf> out;
-    out.ocol = kSq ? comp_sq + (long long)t * V + c : nullptr;
-    out.fcol = kSdfOut ? comp_sdf + (long long)t * V + c : nullptr;
-    out.vox = vox;
+}
+
+// Sets F and O of the column staged in tile (slot e + 1 holds slab element
+// e).  occ: some slab voxel of the column may lie inside a human; then mk
+// receives the occupancy bits, set F is built in place over the staged
+// column, its outputs (the occupied voxels) are written and the column is
+// staged again.  Set O is then built in place.  Returns the top of the set O
+// stack (-1: no site); [za, zb) is the z range of the occupied voxels
+// ([nz, nz) if none).
+template <bool kCoherent, class O_t>
+__device__ __forceinline__ int build_sets(uint32_t *tile, uint32_t *mk, bool occ, int nthr, int S, int nz, int zlo,
+                                          const int32_t *scol, const float *sfcol, const int32_t *dcol, long long V2,
+                                          const O_t &out, int &za, int &zb)
+{
+    constexpr bool kStaticSdf = O_t::kHaveStatic;
+    const int nw = (S + 31) >> 5;
     const int V2i = (int)V2;
+    int firstOcc = S, lastOcc = -1;
+    if (occ) {
+        for (int w = 0; w < nw; ++w) {
+            uint32_t bits = 0;
+            const int e0 = w << 5, cnt = min(32, S - e0);
+            for (int b = 0; b < cnt; ++b)
+                bits |= (uint32_t)((int32_t)tile[(e0 + b + 1) * nthr] < 0) << b;
+            mk[w * nthr] = bits;
+            if (bits) {
+                if (firstOcc == S)
+                    firstOcc = e0 + __ffs(bits) - 1;
+                lastOcc = e0 + 31 - __clz(bits);
+            }
+        }
+    }
     auto occupied = [&](int z) {
         const int e = z - zlo;
-        return e >= 0 && e < S && ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u);
+        return occ && e >= 0 && e < S && ((mk[(e >> 5) * nthr] >> (e & 31)) & 1u);
     };
 
     const int zo0 = zlo + firstOcc, zo1 = zlo + lastOcc;
@@ -476,10 +534,155 @@ __device__ __forceinline__ void composite_block(const int32_t *__restrict__ stat
         }
         B.push(zlo + e, g);
     }
-    EnvCursor O(tile + nthr, nthr, B.top);
-    // below the occupied run, the run (skipping its voxels), above it
-    const int za = lastOcc >= 0 ? zo0 : nz, zb = lastOcc >= 0 ? zo1 + 1 : nz;
-    emit_all<kCoherent>(za, zb, nz, B.top < 0, O, mk, zlo, nthr, scol, sfcol, V2i, out);
+    za = lastOcc >= 0 ? zo0 : nz;
+    zb = lastOcc >= 0 ? zo1 + 1 : nz;
+    return B.top;
+}
+
+// The CTA computes columns [col0, col0 + blockDim.x) of time t, one column
+// per thread with the column's own z ranges (used inside the batched kernel;
+// no block-level synchronisation); smem holds
+// blockDim.x * (S + 2 + ceil(S / 32)) words.
+template <bool kSq, bool kSdfOut, bool kStaticSdf, bool kCoherent>
+__device__ __forceinline__ void composite_block(const int32_t *__restrict__ static_sq,
+                                                const float *__restrict__ static_sdf,
+                                                const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz, int zlo,
+                                                int S, int t, long long col0, int32_t *__restrict__ comp_sq,
+                                                float *__restrict__ comp_sdf, float vox, uint32_t *smem)
+{
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const long long V2 = (long long)nx * ny;
+    const long long c = col0 + tid;
+    if (c >= V2)
+        return;
+    uint32_t *tile = smem + tid;                              // slot k at tile[k * nthr]
+    uint32_t *mk = smem + (size_t)(S + 2) * nthr + tid;       // word w at mk[w * nthr]
+    const int32_t *dcol = dyn_mid + (long long)t * S * V2 + c;
+
+#pragma unroll 8
+    for (int e = 0; e < S; ++e)
+        tile[(e + 1) * nthr] = (uint32_t)(kCoherent ? __ldcg(dcol + (long long)e * V2) : __ldcs(dcol + (long long)e * V2));
+
+    const long long V = V2 * nz;
+    const int32_t *scol = static_sq + c;
+    const float *sfcol = kStaticSdf ? static_sdf + c : nullptr;
+    OutT<kSq, kSdfOut, kStaticSdf> out;
+    out.ocol = kSq ? comp_sq + (long long)t * V + c : nullptr;
+    out.fcol = kSdfOut ? comp_sdf + (long long)t * V + c : nullptr;
+    out.vox = vox;
+    int za, zb;
+    const int top = build_sets<kCoherent>(tile, mk, true, nthr, S, nz, zlo, scol, sfcol, dcol, V2, out, za, zb);
+    EnvCursor O(tile + nthr, nthr, top);
+    emit_all<kCoherent>(za, zb, nz, top < 0, O, mk, zlo, nthr, scol, sfcol, (int)V2, out);
+}
+
+// The CTA of k_composite_z: columns [col0, col0 + blockDim.x) of time t with
+// the static shortcuts.  colmax: the largest static value of every column;
+// vec: the CTA may copy with 16-byte accesses.  Block-wide barriers: every
+// thread of the CTA calls.
+//  * every column static (colmax <= gmin): the CTA copies the static block;
+//  * else each column with dynamic influence has a window [w0, w1) (the slab
+//    and every z less than R slices from it, R the least integer with
+//    gmin + R^2 >= colmax; beyond it the static field wins).  All threads
+//    work over the union of the windows, so every lane of a warp runs the
+//    same z loops and the accesses of a z stay coalesced: copies outside it,
+//    the envelope inside it (+INF for the static columns).
+template <bool kSq, bool kSdfOut, bool kStaticSdf>
+__device__ __forceinline__ void composite_block_short(const int32_t *__restrict__ static_sq,
+                                                      const float *__restrict__ static_sdf,
+                                                      const int32_t *__restrict__ colmax,
+                                                      const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz,
+                                                      int zlo, int S, int t, long long col0,
+                                                      int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf,
+                                                      float vox, bool vec, uint32_t *smem)
+{
+    __shared__ int s_w0, s_w1, s_occ;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const long long V2 = (long long)nx * ny;
+    const long long c = col0 + tid;
+    const bool live = c < V2;
+    uint32_t *tile = smem + tid;                              // slot k at tile[k * nthr]
+    uint32_t *mk = smem + (size_t)(S + 2) * nthr + tid;       // word w at mk[w * nthr]
+    const int32_t *dcol = dyn_mid + (long long)t * S * V2 + c;
+    const long long V = V2 * nz;
+    if (tid == 0) {
+        s_w0 = nz;
+        s_w1 = 0;
+        s_occ = 0;
+    }
+
+    int32_t gmin = kInf32;
+    if (live) {
+#pragma unroll 8
+        for (int e = 0; e < S; ++e) {
+            const int32_t v = __ldcs(dcol + (long long)e * V2);
+            tile[(e + 1) * nthr] = (uint32_t)v;
+            gmin = min(gmin, v);
+        }
+    }
+    // the humans' field of the column is >= gmin everywhere
+    const int32_t cmax = live ? __ldg(colmax + c) : kInf32;
+    const bool col_static = cmax <= gmin;
+    const int32_t *scol = static_sq + c;
+    const float *sfcol = kStaticSdf ? static_sdf + c : nullptr;
+    OutT<kSq, kSdfOut, kStaticSdf> out;
+    out.ocol = kSq ? comp_sq + (long long)t * V + c : nullptr;
+    out.fcol = kSdfOut ? comp_sdf + (long long)t * V + c : nullptr;
+    out.vox = vox;
+    const int V2i = (int)V2;
+    if (__syncthreads_and(!live || col_static)) {
+        if (vec) {
+            copy_static_block<kSq, kSdfOut, kStaticSdf, false>(
+                static_sq, static_sdf, V2, nz, col0, (int)min((long long)nthr, V2 - col0),
+                kSq ? comp_sq + (long long)t * V : nullptr, kSdfOut ? comp_sdf + (long long)t * V : nullptr, vox);
+        } else if (live) {
+            EnvCursor none(tile, nthr, -1);
+            emit_range<false, false, false>(0, nz, none, false, mk, false, zlo, nthr, scol, sfcol, V2i, out);
+        }
+        return;
+    }
+
+    const bool dyn = live && !col_static;
+    const bool occ = dyn && gmin < 0;  // some slab voxel of the column lies inside a human
+    if (dyn) {
+        int w0 = 0, w1 = nz;
+        const long long diff = (long long)cmax - gmin;  // > 0
+        if (diff < (long long)nz * nz) {
+            int R = (int)sqrtf((float)diff);
+            while ((long long)R * R < diff)
+                ++R;
+            while (R > 1 && (long long)(R - 1) * (R - 1) >= diff)
+                --R;
+            w0 = max(zlo - R + 1, 0);
+            w1 = min(zlo + S + R - 1, nz);
+        }
+        atomicMin(&s_w0, w0);
+        atomicMax(&s_w1, w1);
+        if (occ)
+            s_occ = 1;
+    }
+    __syncthreads();
+    const int ww0 = s_w0, ww1 = s_w1;  // some column is dynamic: ww0 <= zlo, ww1 >= zlo + S
+    const bool any_occ = s_occ != 0;
+    if (!live)
+        return;  // no block-level synchronisation below
+
+    int top = -1;  // set O stack top (-1: no site, or a static column)
+    if (dyn) {
+        int za, zb;
+        top = build_sets<false>(tile, mk, occ, nthr, S, nz, zlo, scol, sfcol, dcol, V2, out, za, zb);
+    }
+    EnvCursor O(tile + nthr, nthr, top);
+    const bool useO = top >= 0;
+    const int sa = zlo, sb = zlo + S;
+    emit_range<false, false, false>(0, ww0, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out);
+    emit_range<false, true, false>(ww0, sa, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out);
+    if (any_occ)  // skip the occupied slab voxels (set F wrote them)
+        emit_range<true, true, false>(sa, sb, O, useO, mk, occ, zlo, nthr, scol, sfcol, V2i, out);
+    else
+        emit_range<false, true, false>(sa, sb, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out);
+    emit_range<false, true, false>(sb, ww1, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out);
+    emit_range<false, false, false>(ww1, nz, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out);
 }
 
 }  // namespace comp

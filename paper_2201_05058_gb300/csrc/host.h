@@ -37,6 +37,7 @@ struct CompositePlan {
     bool fused = false;  // analytic x+y kernel (else row pass + y envelope)
     int cap = 0;         // its per-thread stack capacity
     size_t need = 0;     // workspace bytes
+    size_t colmax_off = 0;  // workspace offset of the static column maxima
 };
 
 int plan_composite(const pcdf_grid *grid, int T, int H, const int32_t *caps, CompositePlan &p);

@@ -175,6 +175,10 @@ int plan_composite(const pcdf_grid *grid, int T, int H, const int32_t *caps, Com
         p.need = align_up((size_t)p.slab * sizeof(int32_t));
     else
         p.need = align_up((size_t)p.slab * sizeof(int16_t)) + align_up((size_t)p.slab * sizeof(int32_t));
+    if (p.S > 0) {  // column maxima of the static field
+        p.colmax_off = p.need;
+        p.need += align_up((size_t)grid->nx * grid->ny * sizeof(int32_t));
+    }
     return PCDF_OK;
 }
 
@@ -240,8 +244,12 @@ int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const floa
         return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "broadcast");
     }
     const int32_t *mid = plan_mid(p, workspace);
-    e = pcdf::launch_composite_z(static_sq, static_sdf, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, T, comp_sq, comp_sdf,
-                                 grid->vox, st);
+    int32_t *colmax = (int32_t *)((char *)workspace + p.colmax_off);
+    e = pcdf::launch_colmax(static_sq, grid->nx, grid->ny, grid->nz, colmax, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "static column maxima");
+    e = pcdf::launch_composite_z(static_sq, static_sdf, colmax, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, T,
+                                 comp_sq, comp_sdf, grid->vox, st);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "composite z pass");
 }
 

@@ -136,11 +136,40 @@ def test_composite_ragged_grid_and_edge_capsules():
 
 
 def test_composite_odd_slice_size():
-    # nx * ny odd: one column per thread (the paired-column kernel needs it even)
+    # nx * ny not a multiple of 4: all-static column blocks are copied one
+    # column per thread instead of with 16-byte accesses
     grid = scenes.Grid(33, 17, 30, 0.05)
     rng = np.random.default_rng(8)
     occ, _ = scenes.boxes_occupancy(grid, 5, rng)
     caps = scenes.walking_capsules(grid, 2, 3, rng)
+    check_composite(occ, caps, grid)
+
+
+def test_composite_unaligned_outputs_and_far_humans():
+    """Outputs that start 4 bytes past a 16-byte boundary take the per-column
+    copy of all-static blocks; a human in one corner of a wide room leaves
+    most column blocks all-static, so the copies carry most of the field."""
+    grid = scenes.Grid(96, 80, 40, 0.05)
+    rng = np.random.default_rng(21)
+    occ, _ = scenes.boxes_occupancy(grid, 6, rng)
+    caps = np.array([[[160, 160, 60, 160, 160, 500, 70]],
+                     [[240, 200, 60, 250, 220, 500, 70]]], np.int32)
+    static_sq, static_sdf = pcdf.build_static_sdf(cuda(occ), grid)
+    want = oracle.predicted_composite(oracle.edt(occ), caps)
+    T, n = caps.shape[0], grid.nvox
+    ws = pcdf.composite_workspace(grid, caps, static_sq.device)
+    for reuse in (False, True):
+        buf_sq = torch.zeros(T * n + 1, dtype=torch.int32, device=static_sq.device)
+        buf_sdf = torch.zeros(T * n + 1, dtype=torch.float32, device=static_sq.device)
+        comp_sq = buf_sq[1:].view((T,) + grid.shape)
+        comp_sdf = buf_sdf[1:].view((T,) + grid.shape)
+        pcdf.composite_prepare(grid, caps, ws)
+        pcdf.composite_finish(static_sq, grid, caps, ws, comp_sq, comp_sdf, static_sdf=static_sdf if reuse else None)
+        for t in range(T):
+            assert_equal_fields(comp_sq[t].cpu().numpy(), want[t], f"comp_sq[{t}] unaligned")
+            assert_bits_equal(comp_sdf[t].cpu().numpy(), oracle.sdf_from_sq(want[t], grid.vox),
+                              f"comp_sdf[{t}] unaligned")
+    # the same request with aligned outputs (16-byte block copies)
     check_composite(occ, caps, grid)
 
 
@@ -166,6 +195,10 @@ def test_composite_degenerate_maps():
     # capsule covering the whole grid: no free voxel anywhere at that t
     big = np.array([[[160, 144, 176, 160, 144, 176, 8000]]], np.int32)
     comp = check_composite(scenes.random_occupancy(grid.shape, 0.1, np.random.default_rng(0)), big, grid)
+    assert np.all(comp == -oracle.INF32)
+    # static map with no free voxel: every column maximum is -INF, every
+    # column a copy of the static field
+    comp = check_composite(np.ones(grid.shape, np.uint8), caps, grid)
     assert np.all(comp == -oracle.INF32)
 
 
