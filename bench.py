@@ -93,21 +93,26 @@ def sources_sha(names):
 
 
 def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if none
-    of the sources the kernel is compiled from changed since the capture."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.txt: one line per kernel or stage, `name sources=a,b
+    sha=<hex> bytes=<n>`), if none of the sources it is compiled from changed
+    since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f).get(kernel)
-    if not d:
-        return None
-    try:
-        if sources_sha(d["sources"]) != d["sources_sha"]:
-            return None
-    except OSError:
-        return None
-    return float(d["dram_bytes_per_launch"])
+        for line in f:
+            parts = line.split()
+            if not parts or parts[0] != kernel:
+                continue
+            kv = dict(x.split("=", 1) for x in parts[1:] if "=" in x)
+            try:
+                if sources_sha(kv["sources"].split(",")) != kv["sha"]:
+                    return None
+            except (OSError, KeyError):
+                return None
+            return float(kv["bytes"])
+    return None
 
 
 # ---------------------------------------------------------------------------
