@@ -74,6 +74,24 @@ def rank_seed(seed: int, rank: int) -> int:
     return seed + 1000 * rank
 
 
+def slowest_rank_ms(ms: float, world: int, device) -> float:
+    """The job's time for a timed region: the largest of the ranks' times (one
+    all-reduce MAX over the default process group; the local time at world 1)."""
+    if world == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gvox_s(world: int, steps: int, T: int, V: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank updates its own T fields of V voxels
+    per step (weak scaling), over the slowest rank's time."""
+    return world * steps * T * V / (total_ms * 1e-3) / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -468,15 +486,12 @@ def run_native(args):
     step_ms, z_ms = timed(step, args.steps, extra_events=True)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    total_ms = float(sum(step_ms))
+    total_ms = slowest_rank_ms(float(sum(step_ms)), world, dev)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = world * args.steps * T * V / (total_ms * 1e-3) / 1e9
+    value = job_gvox_s(world, args.steps, T, V, total_ms)
 
     # composite stage alone and the from-scratch comparator (same inputs)
     def comp_only(_=None):
@@ -547,13 +562,8 @@ def run_native(args):
     e2e_step()
     k_e2e = max(3, min(args.steps, 10))
     e2e_ms, _ = timed(e2e_step, k_e2e)
-    e2e_total = float(sum(e2e_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e = {"value": world * k_e2e * T * V / (e2e_total * 1e-3) / 1e9, "unit": "Gvox/s",
+    e2e_total = slowest_rank_ms(float(sum(e2e_ms)), world, dev)
+    e2e = {"value": job_gvox_s(world, k_e2e, T, V, e2e_total), "unit": "Gvox/s",
            "h2d_bytes_per_step": int(occ_h.numel() + caps.nbytes), "d2h_bytes_per_step": int(out_h.numel() * 4),
            "ms_per_step": e2e_total / k_e2e,
            "what": "H2D occupancy (pinned) + capsules, static + composite, D2H of the T float fields (pinned)"}
