@@ -28,6 +28,10 @@
 
 #include "edt_common.cuh"
 
+#ifndef PCDF_EMIT_CHUNK
+#define PCDF_EMIT_CHUNK 8  // static values prefetched per lane in the z loops
+#endif
+
 namespace pcdf {
 namespace comp {
 
@@ -334,18 +338,19 @@ __device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, bool us
                                            const O_t &out)
 {
     constexpr bool kStaticSdf = O_t::kHaveStatic;
+    constexpr int kC = PCDF_EMIT_CHUNK;
     int z = z0;
-    for (; z + 8 <= z1; z += 8) {
-        int32_t sv[8];
-        float sf[8];
+    for (; z + kC <= z1; z += kC) {
+        int32_t sv[kC];
+        float sf[kC];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < kC; ++i) {
             sv[i] = ldx<kCoherent>(scol + (z + i) * V2);
             if (kStaticSdf)
                 sf[i] = ldx<kCoherent>(sfcol + (z + i) * V2);
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < kC; ++i) {
             const int zz = z + i;
             if (kCheck && useMk) {
                 const int e = zz - zlo;
@@ -390,6 +395,16 @@ template <bool kSq, bool kSdfOut, bool kStaticSdf>
 struct OutT : Out<kSq, kSdfOut, kStaticSdf> {
     static constexpr bool kHaveStatic = kStaticSdf;
 };
+
+// 4-byte asynchronous copy global -> shared (no register staging); the
+// thread's copies complete at cp_async_wait_all.
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Largest value of each column c of a field [nz][V2]: warp w of the CTA reads
 // the z quarter w of 32 consecutive columns (lane = column).
@@ -611,17 +626,18 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
         s_occ = 0;
     }
 
+    // stage the slab column with every load in flight at once
     int32_t gmin = kInf32;
+    const int32_t cmax = live ? __ldg(colmax + c) : kInf32;
     if (live) {
+        for (int e = 0; e < S; ++e)
+            cp_async4(tile + (e + 1) * nthr, dcol + (long long)e * V2);
+        cp_async_wait_all();
 #pragma unroll 8
-        for (int e = 0; e < S; ++e) {
-            const int32_t v = __ldcs(dcol + (long long)e * V2);
-            tile[(e + 1) * nthr] = (uint32_t)v;
-            gmin = min(gmin, v);
-        }
+        for (int e = 0; e < S; ++e)
+            gmin = min(gmin, (int32_t)tile[(e + 1) * nthr]);
     }
     // the humans' field of the column is >= gmin everywhere
-    const int32_t cmax = live ? __ldg(colmax + c) : kInf32;
     const bool col_static = cmax <= gmin;
     const int32_t *scol = static_sq + c;
     const float *sfcol = kStaticSdf ? static_sdf + c : nullptr;

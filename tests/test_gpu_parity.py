@@ -94,18 +94,22 @@ def test_static_edt_box_and_wall_structures():
 # ---------------------------------------------------------------------------
 
 def check_composite(occ, caps, grid):
-    """Both float-epilogue variants (static float field reused or recomputed)
-    against the oracle."""
+    """Every output variant against the oracle: the static float field reused
+    or recomputed, the int32 field with or without the float field, the
+    float field alone."""
     static_sq, static_sdf = pcdf.build_static_sdf(cuda(occ), grid)
     want = oracle.predicted_composite(oracle.edt(occ), caps)
-    for reuse, want_sq in ((False, True), (True, True), (True, False)):
-        comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, caps, want_sq=want_sq,
+    out = None
+    for reuse, want_sq, want_sdf in ((False, True, True), (True, True, True), (True, False, True),
+                                     (False, True, False)):
+        comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, caps, want_sq=want_sq, want_sdf=want_sdf,
                                                            static_sdf=static_sdf if reuse else None)
-        comp_sdf = comp_sdf.cpu().numpy()
         for t in range(caps.shape[0]):
             if want_sq:
                 assert_equal_fields(comp_sq[t].cpu().numpy(), want[t], f"comp_sq[{t}] reuse={reuse}")
-            assert_bits_equal(comp_sdf[t], oracle.sdf_from_sq(want[t], grid.vox), f"comp_sdf[{t}] reuse={reuse}")
+            if want_sdf:
+                assert_bits_equal(comp_sdf[t].cpu().numpy(), oracle.sdf_from_sq(want[t], grid.vox),
+                                  f"comp_sdf[{t}] reuse={reuse}")
         if want_sq:
             out = comp_sq.cpu().numpy()
     return out
@@ -147,8 +151,9 @@ def test_composite_odd_slice_size():
 
 def test_composite_unaligned_outputs_and_far_humans():
     """Outputs that start 4 bytes past a 16-byte boundary take the per-column
-    copy of all-static blocks; a human in one corner of a wide room leaves
-    most column blocks all-static, so the copies carry most of the field."""
+    copies of the static planes; aligned outputs take the 16-byte block
+    copies.  A human in one corner of a wide room leaves most column blocks
+    all-static, so the copies carry most of the field."""
     grid = scenes.Grid(96, 80, 40, 0.05)
     rng = np.random.default_rng(21)
     occ, _ = scenes.boxes_occupancy(grid, 6, rng)
@@ -169,7 +174,14 @@ def test_composite_unaligned_outputs_and_far_humans():
             assert_equal_fields(comp_sq[t].cpu().numpy(), want[t], f"comp_sq[{t}] unaligned")
             assert_bits_equal(comp_sdf[t].cpu().numpy(), oracle.sdf_from_sq(want[t], grid.vox),
                               f"comp_sdf[{t}] unaligned")
-    # the same request with aligned outputs (16-byte block copies)
+    # aligned outputs: 16-byte copies of the all-static planes
+    comp_sq = torch.empty((T,) + grid.shape, dtype=torch.int32, device=static_sq.device)
+    comp_sdf = torch.empty((T,) + grid.shape, dtype=torch.float32, device=static_sq.device)
+    pcdf.composite_prepare(grid, caps, ws)
+    pcdf.composite_finish(static_sq, grid, caps, ws, comp_sq, comp_sdf, static_sdf=static_sdf)
+    for t in range(T):
+        assert_equal_fields(comp_sq[t].cpu().numpy(), want[t], f"comp_sq[{t}] aligned")
+        assert_bits_equal(comp_sdf[t].cpu().numpy(), oracle.sdf_from_sq(want[t], grid.vox), f"comp_sdf[{t}] aligned")
     check_composite(occ, caps, grid)
 
 
