@@ -93,6 +93,7 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
                                              int s, int cap, int32_t *__restrict__ dyn_mid, int32_t *sm)
 {
     __shared__ int s_ylo, s_yhi;
+    __shared__ uint32_t s_rowbits[(PCDF_MAX_DIM + 31) / 32];  // rows holding a run
     const int z = zlo + s;
     const int nthr = blockDim.x, tid = threadIdx.x;
     const int rw = H + 1;
@@ -102,6 +103,8 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
         s_ylo = ny;
         s_yhi = -1;
     }
+    for (int w = tid; w < (ny + 31) / 32; w += nthr)
+        s_rowbits[w] = 0;
     __syncthreads();
 
     // rows: merged occupied runs of every capsule crossing this slice
@@ -147,6 +150,7 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
         if (m) {
             atomicMin(&s_ylo, y);
             atomicMax(&s_yhi, y);
+            atomicOr(&s_rowbits[y >> 5], 1u << (y & 31));
         }
     }
     __syncthreads();
@@ -161,11 +165,14 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
             continue;
         }
         int fo = ny, lo_ = -1;  // first / last occupied row of this column
-        for (int y = ylo; y <= yhi; ++y)
-            if (row_inside(rows + y * rw, x)) {
-                if (fo == ny)
-                    fo = y;
-                lo_ = y;
+        for (int w = ylo >> 5; w <= yhi >> 5; ++w)
+            for (uint32_t b = s_rowbits[w]; b; b &= b - 1) {
+                const int y = (w << 5) + __ffs(b) - 1;
+                if (row_inside(rows + y * rw, x)) {
+                    if (fo == ny)
+                        fo = y;
+                    lo_ = y;
+                }
             }
 
         // distances to free voxels at the occupied voxels (set F).  Free rows
@@ -173,7 +180,7 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
         // occupied voxel is the first free row out of its run.
         if (lo_ >= 0) {
             const int y0 = max(fo - 1, 0), y1 = min(lo_ + 1, ny - 1);
-            int top = -1, s0 = 0, g0 = 0, s1 = 0, g1 = 0;
+            EnvBuilder B(stk, nthr);
             bool prev_occ = false;  // y0 - 1 lies before the first occupied row
             bool cur_occ = y0 >= ylo && y0 <= yhi && row_inside(rows + y0 * rw, x);
             for (int y = y0; y <= y1; ++y) {
@@ -185,99 +192,39 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
                     g = (prev_occ || next_occ) ? 0 : -1;
                 prev_occ = cur_occ;
                 cur_occ = next_occ;
-                if (g < 0)
-                    continue;
-                while (top >= 1 && dominated(s0, g0, s1, g1, y, g)) {
-                    --top;
-                    s1 = s0;
-                    g1 = g0;
-                    if (top >= 1) {
-                        const uint32_t w = stk[(top - 1) * nthr];
-                        s0 = site_of(w);
-                        g0 = gval_of(w);
-                    }
-                }
-                ++top;
-                stk[top * nthr] = pack_site(y, g);
-                s0 = s1;
-                g0 = g1;
-                s1 = y;
-                g1 = g;
+                if (g >= 0)
+                    B.push(y, g);
             }
-            int q = 0, sc = 0, gc = 0;
-            if (top >= 0) {
-                const uint32_t w = stk[0];
-                sc = site_of(w);
-                gc = gval_of(w);
-            }
+            EnvCursor F(stk, nthr, B.top);
             for (int y = fo; y <= lo_; ++y) {
                 if (!row_inside(rows + y * rw, x))
                     continue;
-                int32_t r = -kInf32;
-                if (top >= 0) {
-                    int fc = parab(y, sc, gc);
-                    while (q < top) {
-                        const uint32_t w = stk[(q + 1) * nthr];
-                        const int fn = parab(y, site_of(w), gval_of(w));
-                        if (fn > fc)
-                            break;
-                        ++q;
-                        sc = site_of(w);
-                        gc = gval_of(w);
-                        fc = fn;
-                    }
-                    r = -fc;
-                }
-                oc[(long long)y * nx] = r;
+                const int f = F.eval(y);
+                oc[(long long)y * nx] = f < 0 ? -kInf32 : -f;
             }
         }
 
         // distances to occupied voxels at the free voxels (set O): sites are
         // the rows holding a run (g = 0 where x is inside one)
-        int top = -1, s0 = 0, g0 = 0, s1 = 0, g1 = 0;
-        for (int y = ylo; y <= yhi; ++y) {
-            const int g = row_g_occ(rows + y * rw, x);
-            if (g < 0)
-                continue;
-            while (top >= 1 && dominated(s0, g0, s1, g1, y, g)) {
-                --top;
-                s1 = s0;
-                g1 = g0;
-                if (top >= 1) {
-                    const uint32_t w = stk[(top - 1) * nthr];
-                    s0 = site_of(w);
-                    g0 = gval_of(w);
-                }
+        EnvBuilder B(stk, nthr);
+        for (int w = ylo >> 5; w <= yhi >> 5; ++w)
+            for (uint32_t b = s_rowbits[w]; b; b &= b - 1) {
+                const int y = (w << 5) + __ffs(b) - 1;
+                B.push(y, row_g_occ(rows + y * rw, x));
             }
-            ++top;
-            stk[top * nthr] = pack_site(y, g);
-            s0 = s1;
-            g0 = g1;
-            s1 = y;
-            g1 = g;
-        }
-        int q = 0, sc = 0, gc = 0;
-        {
-            const uint32_t w = stk[0];  // top >= 0: some row of [ylo, yhi] holds a run
-            sc = site_of(w);
-            gc = gval_of(w);
-        }
-        for (int y = 0; y < ny; ++y) {
-            if (y >= fo && y <= lo_ && row_inside(rows + y * rw, x))
-                continue;
-            int fc = parab(y, sc, gc);
-            while (q < top) {
-                const uint32_t w = stk[(q + 1) * nthr];
-                const int fn = parab(y, site_of(w), gval_of(w));
-                if (fn > fc)
-                    break;
-                ++q;
-                sc = site_of(w);
-                gc = gval_of(w);
-                fc = fn;
-            }
-            oc[(long long)y * nx] = fc;
-        }
+        EnvCursor O(stk, nthr, B.top);  // B.top >= 0: some row of [ylo, yhi] holds a run
+        // rows before the column's occupied range, the range (skipping its
+        // occupied rows, which set F wrote), rows after it
+        const int ya = min(fo, ny), yb = lo_ >= 0 ? lo_ + 1 : ny;
+#pragma unroll 4
+        for (int y = 0; y < ya; ++y)
+            oc[(long long)y * nx] = O.eval(y);
+        for (int y = ya; y < yb; ++y)
+            if (!row_inside(rows + y * rw, x))
+                oc[(long long)y * nx] = O.eval(y);
+#pragma unroll 4
+        for (int y = yb; y < ny; ++y)
+            oc[(long long)y * nx] = O.eval(y);
     }
 }
 
