@@ -442,9 +442,16 @@ def run_native(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    side = torch.cuda.Stream(device=dev)
+
     def step(z_events=None):
+        # as pcdf.predicted_fields: the capsules' x+y pass (independent of the
+        # static field) on a side stream, overlapping the static build
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            pcdf.composite_prepare(grid, caps, ws)
         pcdf.build_static_sdf(occ, grid, out_sq=static_sq, out_sdf=static_sdf)
-        pcdf.composite_prepare(grid, caps, ws)
+        stream.wait_stream(side)
         if z_events:
             z_events[0].record(stream)
         pcdf.composite_finish(static_sq, grid, caps, ws, comp_sq, comp_sdf, static_sdf=static_sdf)
@@ -554,9 +561,8 @@ def run_native(args):
 
     def e2e_step(_=None):
         occ_d.copy_(occ_h, non_blocking=True)
-        pcdf.build_static_sdf(occ_d, grid, out_sq=static_sq, out_sdf=static_sdf)
-        pcdf.build_predicted_composite(static_sq, grid, caps, out_sq=comp_sq, out_sdf=comp_sdf,
-                                       static_sdf=static_sdf)
+        pcdf.predicted_fields(occ_d, grid, caps, workspace=ws, out_static_sq=static_sq, out_static_sdf=static_sdf,
+                              out_sq=comp_sq, out_sdf=comp_sdf)
         out_h.copy_(comp_sdf, non_blocking=True)
 
     e2e_step()

@@ -22,6 +22,7 @@ from .api import (  # noqa: F401
     build_static_sdf,
     capsule_fixed,
     composite_finish,
+    predicted_fields,
     composite_prepare,
     composite_slab,
     composite_workspace,

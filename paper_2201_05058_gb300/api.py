@@ -206,6 +206,46 @@ def composite_finish(static_sq, grid, caps, workspace: torch.Tensor, comp_sq=Non
                "pcdf_composite_finish")
 
 
+_side_streams = {}
+
+
+def _side_stream(dev):
+    st = _side_streams.get(dev.index)
+    if st is None:
+        st = torch.cuda.Stream(device=dev)
+        _side_streams[dev.index] = st
+    return st
+
+
+def predicted_fields(occ: torch.Tensor, grid, caps, workspace=None, out_static_sq=None, out_static_sdf=None,
+                     out_sq=None, out_sdf=None):
+    """One map update (Sec. 6, Sec. 8): the static field of `occ` and the T
+    composite fields with the capsules `caps` (host int32 [T][H][7]).
+
+    The capsules' x+y pass does not depend on the static field, so it runs
+    on a side stream while the static field is built on the current stream;
+    the current stream then waits for it and runs the fused z pass.  Returns
+    (static_sq, static_sdf, comp_sq, comp_sdf); `workspace` (from
+    composite_workspace) and the outputs may be passed in to reuse them."""
+    dev = occ.device
+    caps = _caps_host(caps)
+    T = int(caps.shape[0])
+    shp = _shape(grid)
+    ws = workspace if workspace is not None else composite_workspace(grid, caps, dev)
+    sq = out_sq if out_sq is not None else torch.empty((T,) + shp, dtype=torch.int32, device=dev)
+    sdf = out_sdf if out_sdf is not None else torch.empty((T,) + shp, dtype=torch.float32, device=dev)
+    main = torch.cuda.current_stream(dev)
+    side = _side_stream(dev)
+    side.wait_stream(main)
+    with torch.cuda.stream(side):
+        composite_prepare(grid, caps, ws)
+    ws.record_stream(side)
+    st_sq, st_sdf = build_static_sdf(occ, grid, out_sq=out_static_sq, out_sdf=out_static_sdf)
+    main.wait_stream(side)
+    composite_finish(st_sq, grid, caps, ws, sq, sdf, static_sdf=st_sdf)
+    return st_sq, st_sdf, sq, sdf
+
+
 def build_from_scratch(occ: torch.Tensor, grid, caps, want_sdf: bool = True, out_sq=None, out_sdf=None):
     """The comparator: full signed EDT of (occ OR capsules at t) for every t."""
     shp = _shape(grid)

@@ -401,3 +401,38 @@ def test_query_edge_cases():
         s2, f2 = pcdf.build_static_sdf(cuda(np.full(grid.shape, fill, np.uint8)), grid)
         hh = pcdf.query_cost(f2, grid, cuda(sph[:2]), cuda(tid[:2]), 0.2).cpu().numpy()
         assert np.all(hh == expect)
+
+
+def test_predicted_fields_overlapped_and_graph_captured():
+    """The one-call update (capsule x+y pass on a side stream, overlapping the
+    static build) equals the oracle, also when captured in a CUDA graph and
+    replayed on a new occupancy in the same buffers."""
+    sc = scenes.scene_small_walking(seed=31, T=6, H=2)
+    grid, caps = sc["grid"], sc["caps"]
+    d = torch.device("cuda", 0)
+    occ = cuda(sc["occ"])
+    st_sq, st_sdf, sq, sdf = pcdf.predicted_fields(occ, grid, caps)
+    want = oracle.predicted_composite(oracle.edt(sc["occ"]), caps)
+    for t in range(caps.shape[0]):
+        assert_equal_fields(sq[t].cpu().numpy(), want[t], f"comp_sq[{t}]")
+        assert_bits_equal(sdf[t].cpu().numpy(), oracle.sdf_from_sq(want[t], grid.vox), f"comp_sdf[{t}]")
+    assert_equal_fields(st_sq.cpu().numpy(), oracle.edt(sc["occ"]), "static")
+    ws = pcdf.composite_workspace(grid, caps, d)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(device=d)
+    s.wait_stream(torch.cuda.current_stream(d))
+    with torch.cuda.stream(s):
+        pcdf.predicted_fields(occ, grid, caps, workspace=ws, out_static_sq=st_sq, out_static_sdf=st_sdf,
+                              out_sq=sq, out_sdf=sdf)  # warm-up outside the capture
+        with torch.cuda.graph(g, stream=s):
+            pcdf.predicted_fields(occ, grid, caps, workspace=ws, out_static_sq=st_sq, out_static_sdf=st_sdf,
+                                  out_sq=sq, out_sdf=sdf)
+    torch.cuda.current_stream(d).wait_stream(s)
+    occ2 = scenes.scene_small_walking(seed=32, T=6, H=2)["occ"]
+    occ.copy_(cuda(occ2))
+    sq.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    want2 = oracle.predicted_composite(oracle.edt(occ2), caps)
+    for t in range(caps.shape[0]):
+        assert_equal_fields(sq[t].cpu().numpy(), want2[t], f"replayed comp_sq[{t}]")
