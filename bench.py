@@ -384,15 +384,26 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
         occ, st_sq, st_sdf, comp, d_ex = exact(sc, sph, tidx)
         h_ex = pcdf.query_cost(comp, grid, sph, tidx, 0.2)
         _, d_pr, _ = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.0)
+        cws = pcdf.composite_workspace(grid, sc["caps"], dev)
+        pcdf.composite_prepare(grid, sc["caps"], cws)
         h, _, nfb = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band,
-                                         err_bound=err_bound)
+                                         err_bound=err_bound, comp_workspace=cws)
         e = (d_pr - d_ex).abs()
         stats.append((float(e.max()), float(e.mean()), int(nfb.item()) / sph.numel() * 4,
                       bool(torch.equal(h > 0, h_ex > 0)), int((h > 0).sum())))
     # timing on the last test scene: one plan step of 1M queries
     caps_dev = torch.from_numpy(np.ascontiguousarray(sc["caps"])).to(dev)
-    t_sur = ev_time(lambda: pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band,
-                                                 caps_dev=caps_dev, err_bound=err_bound))
+
+    def surrogate_path():
+        # exact answers from the capsule-slab partials (the composite's first
+        # stage, run for this plan step's capsules)
+        pcdf.composite_prepare(grid, sc["caps"], cws)
+        pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band, caps_dev=caps_dev,
+                             err_bound=err_bound, comp_workspace=cws)
+
+    t_sur = ev_time(surrogate_path)
+    t_sur_local = ev_time(lambda: pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2,
+                                                       band=band, caps_dev=caps_dev, err_bound=err_bound))
     x_q = pcdf.surrogate_features(grid, sph, tidx, T, caps_dev)
     t_feat = ev_time(lambda: pcdf.surrogate_features(grid, sph, tidx, T, caps_dev))
     t_mlp = ev_time(lambda: net.forward(x_q))
@@ -412,7 +423,8 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
             "train_s": t_train, "fields_s": t_fields, "loss_first": hist[0][1], "loss_last": hist[-1][1],
             "band_m": band, "err_bound_m": err_bound, "max_err_m": max(x[0] for x in stats), "mean_err_m": float(np.mean([x[1] for x in stats])),
             "fallback_frac": float(np.mean([x[2] for x in stats])), "decisions_identical": all(x[3] for x in stats),
-            "surrogate_ms": t_sur, "features_ms": t_feat, "mlp_forward_ms": t_mlp,
+            "surrogate_ms": t_sur, "surrogate_local_search_ms": t_sur_local, "features_ms": t_feat,
+            "mlp_forward_ms": t_mlp,
             "mlp_tflops": 2 * 136193 * sph.numel() / 4 / (t_mlp * 1e-3) / 1e12, "exact_composite_ms": t_comp, "exact_scratch_ms": t_scr,
             "speedup_vs_scratch": t_scr / t_sur, "speedup_vs_composite": t_comp / t_sur}
 

@@ -351,6 +351,19 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
                           float *h, float *d_out, int32_t *n_fallback, void *workspace, size_t workspace_bytes,
                           void *stream);
 
+/* pcdf_surrogate_finish_slab  the same, with the exact answers taken from the
+ * 2-D partial field of the capsule slab that pcdf_composite_prepare left in
+ * comp_workspace (prepare run on the same grid, T, H and caps, earlier on the
+ * stream; comp_workspace_bytes >= pcdf_composite_workspace_bytes): each
+ * corner's dynamic value is the minimum over its column's slab sites, the
+ * integers the composite z pass produces, at a few loads per corner instead
+ * of a search over the capsules' voxels. */
+int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
+                               const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
+                               const int32_t *caps_host, const void *comp_workspace, size_t comp_workspace_bytes,
+                               const float *y, float eps, float band, float err_bound, float *h, float *d_out,
+                               int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

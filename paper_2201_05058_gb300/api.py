@@ -597,10 +597,13 @@ def surrogate_features(grid, spheres, tidx, T, caps_dev):
     return x
 
 
-def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound=None):
+def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound=None,
+                     comp_workspace=None):
     """Hinge cost from the network outputs with exact answers near the
-    threshold (err_bound: bound on the network error, default band).
-    Returns (h, d, n_fallback[1])."""
+    threshold (err_bound: bound on the network error, default band).  With
+    comp_workspace (after composite_prepare on the same grid and caps) the
+    exact answers come from its capsule-slab partials, else from a local
+    search over the capsules' voxels.  Returns (h, d, n_fallback[1])."""
     err_bound = band if err_bound is None else err_bound
     caps = _caps_host(caps)
     H = int(caps.shape[1])
@@ -614,22 +617,32 @@ def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps
     _lib.check(lib.pcdf_surrogate_finish_workspace_bytes(int(T), H, N, ctypes.byref(n)), "surrogate workspace")
     ws = _workspace(n.value, dev)
     g = _cgrid(grid)
-    _lib.check(lib.pcdf_surrogate_finish(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), _ptr(spheres),
-                                         _ptr(tidx), N, int(T), H, caps.ctypes.data_as(ctypes.c_void_p), _ptr(y),
-                                         float(eps), float(band), float(err_bound), _ptr(h), _ptr(d), _ptr(nfb),
-                                         _ptr(ws), ws.numel(),
-                                         ctypes.c_void_p(_stream(dev))), "pcdf_surrogate_finish")
+    cp = caps.ctypes.data_as(ctypes.c_void_p)
+    tail = (float(eps), float(band), float(err_bound), _ptr(h), _ptr(d), _ptr(nfb), _ptr(ws), ws.numel(),
+            ctypes.c_void_p(_stream(dev)))
+    if comp_workspace is None:
+        _lib.check(lib.pcdf_surrogate_finish(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), _ptr(spheres),
+                                             _ptr(tidx), N, int(T), H, cp, _ptr(y), *tail), "pcdf_surrogate_finish")
+    else:
+        _need(comp_workspace, "comp_workspace", torch.uint8)
+        _lib.check(lib.pcdf_surrogate_finish_slab(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), _ptr(spheres),
+                                                  _ptr(tidx), N, int(T), H, cp, _ptr(comp_workspace),
+                                                  comp_workspace.numel(), _ptr(y), *tail),
+                   "pcdf_surrogate_finish_slab")
     return h, d, nfb
 
 
 def surrogate_query(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps, band, caps_dev=None,
-                    err_bound=None):
+                    err_bound=None, comp_workspace=None):
     """Hinge cost of every sphere through the network, exact within `band`
-    of the threshold where the humans can matter.  Returns (h, d, n_fallback[1])."""
+    of the threshold where the humans can matter (from the capsule-slab
+    partials in comp_workspace when given, after composite_prepare).
+    Returns (h, d, n_fallback[1])."""
     caps = _caps_host(caps)
     if caps_dev is None:
         caps_dev = torch.from_numpy(caps).to(spheres.device)
     T = int(caps.shape[0])
     x = surrogate_features(grid, spheres, tidx, T, caps_dev)
     y = model.forward(x)
-    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound)
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound,
+                            comp_workspace)

@@ -476,6 +476,99 @@ __global__ void k_sur_fallback(QueryGrid g, const int32_t *__restrict__ static_s
     }
 }
 
+// The same exact answers from the 2-D partial field of the capsule slab that
+// pcdf_composite_prepare leaves in its workspace (dyn_mid[t][e][y][x] for the
+// slab slices zlo + e, e < S).  The dynamic value at a corner voxel is the
+// lower envelope of its column evaluated by brute force: outside the humans
+// min over slab slices z' of (z - z')^2 + g(z') (g the partial at a free
+// voxel, 0 at an occupied one); inside, minus min over the column of
+// (z - z')^2 + g(z') with g = 0 at free voxels (the slab's and the first
+// ones beyond it) and minus the partial at occupied ones.  The minima are
+// the ones the composite z pass takes, so the values are the same integers.
+// Warp per query; lanes over the slab slices of each of the cell's four
+// columns, both corner heights at once.
+__global__ void k_sur_fallback_slab(QueryGrid g, const int32_t *__restrict__ static_sq,
+                                    const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
+                                    const int32_t *__restrict__ tidx, int T, const int32_t *__restrict__ dyn_mid,
+                                    int zlo, int S, float eps, const int *__restrict__ list,
+                                    const int *__restrict__ count, float *__restrict__ h, float *__restrict__ d_out)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long V2 = (long long)g.n[0] * g.n[1];
+    const int nz = g.n[2];
+    const int n = *count;
+    for (long long w = warp; w < n; w += nwarps) {
+        const long long q = list[w];
+        const float4 s = spheres[q];
+        const int t = min(max(tidx[q], 0), T - 1);
+        const Cell cl = locate(g, s);
+        int dyn[8];
+#pragma unroll
+        for (int col = 0; col < 4; ++col) {
+            const int x = (col & 1) ? cl.i1[0] : cl.i0[0], y = (col & 2) ? cl.i1[1] : cl.i0[1];
+            const int32_t *pc = dyn_mid + (long long)t * S * V2 + (long long)y * g.n[0] + x;  // slice e at pc[e * V2]
+            int zc[2] = {cl.i0[2], cl.i1[2]};
+            bool inside[2];
+            int best[2] = {kInf32, kInf32};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e = zc[u] - zlo;
+                inside[u] = e >= 0 && e < S && __ldg(pc + (long long)e * V2) < 0;
+            }
+            for (int e = lane; e < S; e += 32) {
+                const int32_t P = __ldg(pc + (long long)e * V2);
+                const int zz = zlo + e;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int dz2 = (zc[u] - zz) * (zc[u] - zz);
+                    if (inside[u]) {
+                        if (P >= 0)
+                            best[u] = min(best[u], dz2);  // a free voxel
+                        else if (P != -kInf32)
+                            best[u] = min(best[u], dz2 - P);
+                    } else {
+                        if (P < 0)
+                            best[u] = min(best[u], dz2);  // an occupied voxel
+                        else if (P != kInf32)
+                            best[u] = min(best[u], dz2 + P);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                int b = warp_min(best[u]);
+                if (inside[u]) {
+                    // the free voxels next to the slab
+                    if (zlo - 1 >= 0)
+                        b = min(b, (zc[u] - (zlo - 1)) * (zc[u] - (zlo - 1)));
+                    if (zlo + S < nz)
+                        b = min(b, (zlo + S - zc[u]) * (zlo + S - zc[u]));
+                    b = b == kInf32 ? -kInf32 : -b;
+                }
+                dyn[col + 4 * u] = b;  // corner index: x bit 0, y bit 1, z bit 2
+            }
+        }
+        if (lane == 0) {
+            float c[2][2][2];
+            for (int k = 0; k < 8; ++k) {
+                const int vx = (k & 1) ? cl.i1[0] : cl.i0[0], vy = (k & 2) ? cl.i1[1] : cl.i0[1],
+                          vz = (k & 4) ? cl.i1[2] : cl.i0[2];
+                const long long o = ((long long)vz * g.n[1] + vy) * g.n[0] + vx;
+                const int32_t sv = static_sq[o];
+                c[(k >> 2) & 1][(k >> 1) & 1][k & 1] =
+                    sv <= dyn[k] ? static_sdf[o] : sq_to_sdf_fast(min(sv, dyn[k]), g.vox);
+            }
+            const Sample r = interpolate(cl, c, false);
+            const float hv = (eps + s.w) - r.d;
+            h[q] = hv > 0.f ? hv : 0.f;
+            if (d_out)
+                d_out[q] = r.d;
+        }
+    }
+}
+
 FeatGrid feat_grid(const pcdf_grid *grid)
 {
     FeatGrid G;
@@ -543,18 +636,18 @@ int pcdf_surrogate_finish_workspace_bytes(int32_t T, int32_t H, int64_t N, size_
     return PCDF_OK;
 }
 
-int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
-                          const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
-                          const int32_t *caps_host, const float *y, float eps, float band, float err_bound,
-                          float *h, float *d_out,
-                          int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream)
+}  // extern "C"
+
+namespace {
+
+// combine, then the exact answers: from the capsule slab's 2-D partials when
+// dyn_mid is given, else by local search over the capsules' voxels
+int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, const float *spheres,
+                     const int32_t *tidx, int64_t N, int32_t T, int32_t H, const int32_t *caps_host,
+                     const int32_t *dyn_mid, int zlo_slab, int S_slab, const float *y, float eps, float band,
+                     float err_bound, float *h, float *d_out, int32_t *n_fallback, void *workspace,
+                     size_t workspace_bytes, void *stream)
 {
-    if (int rc = check_grid(grid))
-        return rc;
-    if (N < 0 || T < 1 || H < 1 || !caps_host)
-        return fail(PCDF_EINVAL, "bad surrogate arguments");
-    if (N == 0)
-        return PCDF_OK;
     if (!static_sq || !static_sdf || !spheres || !tidx || !y || !h || !workspace)
         return fail(PCDF_EINVAL, "required pointer is NULL");
     if (!aligned(spheres, 16) || !aligned(workspace, kAlign))
@@ -584,13 +677,61 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_sur_fallback<<<sms * 8, 256, 0, st>>>(G.g, static_sq, static_sdf, (const float4 *)spheres, tidx, T, H, dcaps,
-                                           eps, list, count, h, d_out);
+    if (dyn_mid)
+        k_sur_fallback_slab<<<sms * 8, 256, 0, st>>>(G.g, static_sq, static_sdf, (const float4 *)spheres, tidx, T,
+                                                    dyn_mid, zlo_slab, S_slab, eps, list, count, h, d_out);
+    else
+        k_sur_fallback<<<sms * 8, 256, 0, st>>>(G.g, static_sq, static_sdf, (const float4 *)spheres, tidx, T, H,
+                                               dcaps, eps, list, count, h, d_out);
     if (n_fallback)
         e = cudaMemcpyAsync(n_fallback, count, sizeof(int), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
         e = cudaGetLastError();
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "surrogate finish");
+}
+
+}  // namespace
+
+extern "C" {
+
+int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
+                          const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
+                          const int32_t *caps_host, const float *y, float eps, float band, float err_bound,
+                          float *h, float *d_out,
+                          int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (N < 0 || T < 1 || H < 1 || !caps_host)
+        return fail(PCDF_EINVAL, "bad surrogate arguments");
+    if (N == 0)
+        return PCDF_OK;
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, nullptr, 0, 0, y, eps,
+                            band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes, stream);
+}
+
+int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
+                               const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
+                               const int32_t *caps_host, const void *comp_workspace, size_t comp_workspace_bytes,
+                               const float *y, float eps, float band, float err_bound, float *h, float *d_out,
+                               int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (N < 0 || T < 1 || H < 1 || !caps_host)
+        return fail(PCDF_EINVAL, "bad surrogate arguments");
+    CompositePlan p;
+    if (int rc = plan_composite(grid, T, H, caps_host, p))
+        return rc;
+    if (int rc = check_ws(p, const_cast<void *>(comp_workspace), comp_workspace_bytes))
+        return rc;
+    if (N == 0)
+        return PCDF_OK;
+    const int32_t *mid = p.S > 0 ? plan_mid(p, const_cast<void *>(comp_workspace)) : nullptr;
+    // no capsule in the grid: the dynamic field is +INF everywhere (an empty slab)
+    static const int32_t none = 0;
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, mid ? mid : &none, p.zlo,
+                            p.S, y, eps, band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes, stream);
 }
 
 }  // extern "C"

@@ -107,6 +107,13 @@ def test_fallback_everywhere_is_bit_exact():
     h, _, nfb = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=1.0e9)
     assert int(nfb.item()) == sph_np.size // 4
     assert torch.equal(h, h_ex)
+    # the same answers from the capsule-slab partials of the composite's first stage
+    ws = pcdf.composite_workspace(grid, sc["caps"], d)
+    pcdf.composite_prepare(grid, sc["caps"], ws)
+    h2, _, nfb2 = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=1.0e9,
+                                       comp_workspace=ws)
+    assert int(nfb2.item()) == sph_np.size // 4
+    assert torch.equal(h2, h_ex)
 
 
 def test_fallback_exact_with_several_humans():
@@ -123,11 +130,45 @@ def test_fallback_exact_with_several_humans():
     h, _, nfb = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=1.0e9)
     assert int(nfb.item()) == 3000
     assert torch.equal(h, h_ex)
+    ws = pcdf.composite_workspace(grid, sc["caps"], d)
+    pcdf.composite_prepare(grid, sc["caps"], ws)
+    h2, _, _ = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=1.0e9,
+                                    comp_workspace=ws)
+    assert torch.equal(h2, h_ex)
     # and the oracle agrees with both (within the cost tolerance)
     comp = oracle.predicted_composite(oracle.edt(sc["occ"]), sc["caps"])
     sdf_o = np.stack([oracle.sdf_from_sq(comp[t], grid.vox) for t in range(6)])
     want, _ = oracle.hinge_cost(sdf_o, grid.origin, grid.vox, sph_np, tidx_np, 0.2)
     assert np.max(np.abs(h.cpu().numpy() - want)) <= 1e-5
+
+
+def test_slab_fallback_edge_cases():
+    """Slab fallback with capsules cut by the grid boundary, touching the
+    floor and ceiling, a capsule covering the whole grid, and none at all."""
+    d = dev()
+    grid = scenes.Grid(40, 36, 30, 0.05)
+    rng = np.random.default_rng(9)
+    occ, _ = scenes.boxes_occupancy(grid, 6, rng)
+    caps_sets = [
+        np.array([[[-40, 100, 0, -40, 100, 480, 90], [300, 300, 8, 300, 300, 16, 60]],
+                  [[620, 560, 200, 640, 570, 470, 80], [100, 500, 470, 120, 520, 479, 40]]], np.int32),
+        np.array([[[320, 288, 240, 320, 288, 240, 8000]]], np.int32),
+        np.array([[[-8000, -8000, -8000, -8000, -8000, -7000, 80]]], np.int32),
+    ]
+    sph_np = scenes.spheres_uniform(grid, 2000, rng)
+    sph = torch.from_numpy(sph_np).to(d)
+    for caps in caps_sets:
+        T = caps.shape[0]
+        tidx = torch.from_numpy(rng.integers(0, T, 2000).astype(np.int32)).to(d)
+        static_sq, static_sdf = pcdf.build_static_sdf(torch.from_numpy(occ).to(d), grid)
+        _, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, caps, want_sq=False, static_sdf=static_sdf)
+        h_ex = pcdf.query_cost(comp_sdf, grid, sph, tidx, 0.2)
+        net = pcdf.SurrogateMLP(d, seed=7)
+        ws = pcdf.composite_workspace(grid, caps, d)
+        pcdf.composite_prepare(grid, caps, ws)
+        h, _, _ = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, caps, 0.2, band=1.0e9,
+                                       comp_workspace=ws)
+        assert torch.equal(h, h_ex)
 
 
 def test_training_gains_and_decisions_stay_identical():
