@@ -347,9 +347,9 @@ int pcdf_surrogate_features(const pcdf_grid *grid, const float *spheres, const i
 int pcdf_surrogate_finish_workspace_bytes(int32_t T, int32_t H, int64_t N, size_t *bytes);
 int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                           const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
-                          const int32_t *caps_host, const float *y, float eps, float band, float err_bound,
-                          float *h, float *d_out, int32_t *n_fallback, void *workspace, size_t workspace_bytes,
-                          void *stream);
+                          const int32_t *caps_host, const float *y, const int32_t *y_index, float eps, float band,
+                          float err_bound, float *h, float *d_out, int32_t *n_fallback, void *workspace,
+                          size_t workspace_bytes, void *stream);
 
 /* pcdf_surrogate_finish_slab  the same, with the exact answers taken from the
  * 2-D partial field of the capsule slab that pcdf_composite_prepare left in
@@ -361,8 +361,26 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
 int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                                const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
                                const int32_t *caps_host, const void *comp_workspace, size_t comp_workspace_bytes,
-                               const float *y, float eps, float band, float err_bound, float *h, float *d_out,
-                               int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream);
+                               const float *y, const int32_t *y_index, float eps, float band, float err_bound,
+                               float *h, float *d_out, int32_t *n_fallback, void *workspace, size_t workspace_bytes,
+                               void *stream);
+
+/* pcdf_surrogate_select  the rows the network must answer.  Row i = q * H + h
+ * (sphere q, capsule h of time clamp(tidx[q], 0, T - 1); caps DEVICE int32
+ * [T][H][7]) is skipped when its capsule cannot be nearer than the static
+ * field at any corner of the query's cell: the continuous distance from the
+ * sphere centre to the capsule, less the largest centre-to-corner distance of
+ * the cell and 1e-4 m, exceeds zero and every static corner value of
+ * static_sdf (the exact distance to a capsule's voxels is never below the
+ * continuous distance to the capsule).  Kept rows get their features in x
+ * (BF16 bits [<= N * H][16]) at slot y_index[i] (device int32 [N * H]; -1
+ * for a skipped row), slots taken in an unspecified order; *count (device
+ * int32) receives the number kept.  The network runs on x[0 .. *count) and
+ * pcdf_surrogate_finish(_slab) reads its output through y_index (a NULL
+ * y_index there means y holds every row in order). */
+int pcdf_surrogate_select(const pcdf_grid *grid, const float *static_sdf, const float *spheres, const int32_t *tidx,
+                          int64_t N, int32_t T, int32_t H, const int32_t *caps, uint16_t *x, int32_t *y_index,
+                          int32_t *count, void *stream);
 
 #ifdef __cplusplus
 }

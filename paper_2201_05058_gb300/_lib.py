@@ -41,7 +41,7 @@ EXPORTS = (
     "pcdf_batch_autotune",
     "pcdf_mlp_state_bytes", "pcdf_mlp_workspace_bytes", "pcdf_mlp_init", "pcdf_mlp_forward", "pcdf_mlp_backward",
     "pcdf_mlp_adam", "pcdf_surrogate_samples", "pcdf_surrogate_features", "pcdf_surrogate_finish_workspace_bytes",
-    "pcdf_surrogate_finish", "pcdf_surrogate_finish_slab",
+    "pcdf_surrogate_finish", "pcdf_surrogate_finish_slab", "pcdf_surrogate_select",
 )
 
 
@@ -90,8 +90,10 @@ def _declare(lib):
         "pcdf_surrogate_samples": [G, P, P, P, I32, I32, I64, U64, F32, P, P, P],
         "pcdf_surrogate_features": [G, P, P, I64, I32, I32, P, P, P],
         "pcdf_surrogate_finish_workspace_bytes": [I32, I32, I64, SZP],
-        "pcdf_surrogate_finish": [G, P, P, P, P, I64, I32, I32, P, P, F32, F32, F32, P, P, P, P, SZ, P],
-        "pcdf_surrogate_finish_slab": [G, P, P, P, P, I64, I32, I32, P, P, SZ, P, F32, F32, F32, P, P, P, P, SZ, P],
+        "pcdf_surrogate_finish": [G, P, P, P, P, I64, I32, I32, P, P, P, F32, F32, F32, P, P, P, P, SZ, P],
+        "pcdf_surrogate_finish_slab": [G, P, P, P, P, I64, I32, I32, P, P, SZ, P, P, F32, F32, F32, P, P, P, P, SZ,
+                                       P],
+        "pcdf_surrogate_select": [G, P, P, P, I64, I32, I32, P, P, P, P, P],
     })
     lib.pcdf_batch_destroy.argtypes = [P]
     lib.pcdf_batch_destroy.restype = None

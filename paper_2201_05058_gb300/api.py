@@ -597,8 +597,26 @@ def surrogate_features(grid, spheres, tidx, T, caps_dev):
     return x
 
 
+def surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev):
+    """Rows the network must answer (the others cannot beat the static field
+    in their cell).  Returns (x BF16 [kept rows][16], y_index int32 [N * H])."""
+    N = spheres.numel() // 4
+    H = int(caps_dev.shape[1])
+    dev = spheres.device
+    x = torch.empty((N * H, 16), dtype=torch.bfloat16, device=dev)
+    yi = torch.empty(N * H, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    _need(static_sdf, "static_sdf", torch.float32, _shape(grid))
+    _need(caps_dev, "caps", torch.int32)
+    g = _cgrid(grid)
+    _lib.check(_lib.load().pcdf_surrogate_select(ctypes.byref(g), _ptr(static_sdf), _ptr(spheres), _ptr(tidx), N,
+                                                 int(T), H, _ptr(caps_dev), _ptr(x), _ptr(yi), _ptr(cnt),
+                                                 ctypes.c_void_p(_stream(dev))), "pcdf_surrogate_select")
+    return x[: int(cnt.item())], yi
+
+
 def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound=None,
-                     comp_workspace=None):
+                     comp_workspace=None, y_index=None):
     """Hinge cost from the network outputs with exact answers near the
     threshold (err_bound: bound on the network error, default band).  With
     comp_workspace (after composite_prepare on the same grid and caps) the
@@ -622,12 +640,13 @@ def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps
             ctypes.c_void_p(_stream(dev)))
     if comp_workspace is None:
         _lib.check(lib.pcdf_surrogate_finish(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), _ptr(spheres),
-                                             _ptr(tidx), N, int(T), H, cp, _ptr(y), *tail), "pcdf_surrogate_finish")
+                                             _ptr(tidx), N, int(T), H, cp, _ptr(y), _ptr(y_index), *tail),
+                   "pcdf_surrogate_finish")
     else:
         _need(comp_workspace, "comp_workspace", torch.uint8)
         _lib.check(lib.pcdf_surrogate_finish_slab(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), _ptr(spheres),
                                                   _ptr(tidx), N, int(T), H, cp, _ptr(comp_workspace),
-                                                  comp_workspace.numel(), _ptr(y), *tail),
+                                                  comp_workspace.numel(), _ptr(y), _ptr(y_index), *tail),
                    "pcdf_surrogate_finish_slab")
     return h, d, nfb
 
@@ -642,7 +661,7 @@ def surrogate_query(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps
     if caps_dev is None:
         caps_dev = torch.from_numpy(caps).to(spheres.device)
     T = int(caps.shape[0])
-    x = surrogate_features(grid, spheres, tidx, T, caps_dev)
-    y = model.forward(x)
+    x, yi = surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev)
+    y = model.forward(x) if x.shape[0] else torch.empty(1, dtype=torch.float32, device=spheres.device)
     return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound,
-                            comp_workspace)
+                            comp_workspace, y_index=yi)

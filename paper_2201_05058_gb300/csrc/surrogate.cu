@@ -182,6 +182,68 @@ __global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, c
     features(G, p, t, T, cap, capsule_geo(G.g, p, cap), x + i * 16);
 }
 
+// Rows (sphere q, capsule h) that need the network.  The exact dynamic value
+// at a voxel outside the humans is at least the continuous distance from its
+// centre to the capsule (the nearest voxel centre inside lies in the solid),
+// and the continuous distance changes by at most |corner - p| between p and a
+// corner.  So when that distance at p, less the largest |corner - p| of the
+// query's cell and a rounding margin, exceeds every static corner value (and
+// zero), the static field is the min at all eight corners whatever the
+// network says: the row is skipped (y_index -1) and its capsule counts as
+// +INF.  The other rows get their features at slots taken in warp order.
+__global__ void k_sur_select(FeatGrid G, const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
+                             const int32_t *__restrict__ tidx, long long N, int T, int H,
+                             const int32_t *__restrict__ caps, bf16 *__restrict__ x, int32_t *__restrict__ y_index,
+                             int *__restrict__ count)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool need = false;
+    float p[3] = {0.f, 0.f, 0.f};
+    int t = 0;
+    const int32_t *cap = caps;
+    CapGeo geo{};
+    if (i < N * H) {
+        const long long q = i / H;
+        const int h = (int)(i % H);
+        const float4 s = spheres[q];
+        t = min(max(tidx[q], 0), T - 1);
+        p[0] = s.x;
+        p[1] = s.y;
+        p[2] = s.z;
+        cap = caps + 7 * ((long long)t * H + h);
+        geo = capsule_geo(G.g, p, cap);
+        const Cell cl = locate(G.g, s);
+        const long long sy = G.g.n[0], sz = (long long)G.g.n[0] * G.g.n[1];
+        float smax = 0.f, md2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            smax = fmaxf(smax, __ldg(static_sdf + ((k & 4) ? cl.i1[2] : cl.i0[2]) * sz +
+                                     ((k & 2) ? cl.i1[1] : cl.i0[1]) * sy + ((k & 1) ? cl.i1[0] : cl.i0[0])));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float c0 = G.g.origin[a] + ((float)cl.i0[a] + 0.5f) * G.g.vox;
+            const float c1 = G.g.origin[a] + ((float)cl.i1[a] + 0.5f) * G.g.vox;
+            const float m = fmaxf(fabsf(p[a] - c0), fabsf(p[a] - c1));
+            md2 += m * m;
+        }
+        need = !(geo.dist - sqrtf(md2) - 1e-4f > smax);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (m) {
+        if (lane == __ffs(m) - 1)
+            base = atomicAdd(count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    }
+    if (i < N * H) {
+        const int slot = base + __popc(m & ((1u << lane) - 1u));
+        y_index[i] = need ? slot : -1;
+        if (need)
+            features(G, p, t, T, cap, geo, x + (long long)slot * 16);
+    }
+}
+
 // The prediction is made like the exact distance: the eight corners of the
 // query's cell get min(static corner value, predicted dynamic value there) and
 // are interpolated.  The dynamic value of a capsule at the point is its
@@ -198,7 +260,8 @@ __global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, c
 // the min at all eight corners and its interpolation is the exact distance.
 __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
                               const int32_t *__restrict__ tidx, int T, const CapInfo *__restrict__ caps, long long N,
-                              int H, const float *__restrict__ y, float eps, float band, float err,
+                              int H, const float *__restrict__ y, const int32_t *__restrict__ y_index, float eps,
+                              float band, float err,
                               float *__restrict__ h, float *__restrict__ d_out, int *__restrict__ list,
                               int *__restrict__ count)
 {
@@ -228,7 +291,10 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
             const CapInfo &C = caps[(long long)t * H + k];
             const int32_t cp[7] = {C.a[0], C.a[1], C.a[2], C.b[0], C.b[1], C.b[2], C.r};
             const CapGeo geo = capsule_geo(g, p, cp);
-            const float yk = y[q * H + k] + geo.dist;  // residual + continuous distance
+            const long long yi = y_index ? (long long)y_index[q * H + k] : q * H + k;
+            if (yi < 0)
+                continue;  // the static field wins in the cell whatever this capsule
+            const float yk = y[yi] + geo.dist;  // residual + continuous distance
             dyn = fminf(dyn, yk);
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz)
@@ -628,6 +694,29 @@ int pcdf_surrogate_features(const pcdf_grid *grid, const float *spheres, const i
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "surrogate features");
 }
 
+int pcdf_surrogate_select(const pcdf_grid *grid, const float *static_sdf, const float *spheres, const int32_t *tidx,
+                          int64_t N, int32_t T, int32_t H, const int32_t *caps, uint16_t *x, int32_t *y_index,
+                          int32_t *count, void *stream)
+{
+    if (int rc = check_grid(grid))
+        return rc;
+    if (N < 0 || T < 1 || H < 1 || !count || (N > 0 && (!static_sdf || !spheres || !tidx || !caps || !x || !y_index)))
+        return fail(PCDF_EINVAL, "bad surrogate selection arguments");
+    if (!aligned(spheres, 16) || !aligned(x, 16))
+        return fail(PCDF_EINVAL, "spheres and x must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "surrogate selection");
+    const long long R = N * H;
+    if (R == 0)
+        return PCDF_OK;
+    k_sur_select<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(feat_grid(grid), static_sdf, (const float4 *)spheres, tidx,
+                                                             N, T, H, caps, (bf16 *)x, y_index, count);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "surrogate selection");
+}
+
 int pcdf_surrogate_finish_workspace_bytes(int32_t T, int32_t H, int64_t N, size_t *bytes)
 {
     if (!bytes || T < 1 || H < 1 || N < 0)
@@ -644,7 +733,8 @@ namespace {
 // dyn_mid is given, else by local search over the capsules' voxels
 int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, const float *spheres,
                      const int32_t *tidx, int64_t N, int32_t T, int32_t H, const int32_t *caps_host,
-                     const int32_t *dyn_mid, int zlo_slab, int S_slab, const float *y, float eps, float band,
+                     const int32_t *dyn_mid, int zlo_slab, int S_slab, const float *y, const int32_t *y_index,
+                     float eps, float band,
                      float err_bound, float *h, float *d_out, int32_t *n_fallback, void *workspace,
                      size_t workspace_bytes, void *stream)
 {
@@ -672,8 +762,8 @@ int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const floa
         return cuda_fail(e, "surrogate setup");
     const FeatGrid G = feat_grid(grid);
     k_sur_combine<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(G.g, static_sdf, (const float4 *)spheres, tidx, T,
-                                                              dcaps, N, H, y, eps, band, err_bound, h, d_out, list,
-                                                              count);
+                                                              dcaps, N, H, y, y_index, eps, band, err_bound, h, d_out,
+                                                              list, count);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -696,9 +786,9 @@ extern "C" {
 
 int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                           const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
-                          const int32_t *caps_host, const float *y, float eps, float band, float err_bound,
-                          float *h, float *d_out,
-                          int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream)
+                          const int32_t *caps_host, const float *y, const int32_t *y_index, float eps, float band,
+                          float err_bound, float *h, float *d_out, int32_t *n_fallback, void *workspace,
+                          size_t workspace_bytes, void *stream)
 {
     if (int rc = check_grid(grid))
         return rc;
@@ -706,15 +796,16 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
         return fail(PCDF_EINVAL, "bad surrogate arguments");
     if (N == 0)
         return PCDF_OK;
-    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, nullptr, 0, 0, y, eps,
-                            band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes, stream);
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, nullptr, 0, 0, y, y_index,
+                            eps, band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes, stream);
 }
 
 int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                                const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
                                const int32_t *caps_host, const void *comp_workspace, size_t comp_workspace_bytes,
-                               const float *y, float eps, float band, float err_bound, float *h, float *d_out,
-                               int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream)
+                               const float *y, const int32_t *y_index, float eps, float band, float err_bound,
+                               float *h, float *d_out, int32_t *n_fallback, void *workspace, size_t workspace_bytes,
+                               void *stream)
 {
     if (int rc = check_grid(grid))
         return rc;
@@ -731,7 +822,8 @@ int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, 
     // no capsule in the grid: the dynamic field is +INF everywhere (an empty slab)
     static const int32_t none = 0;
     return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, mid ? mid : &none, p.zlo,
-                            p.S, y, eps, band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes, stream);
+                            p.S, y, y_index, eps, band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes,
+                            stream);
 }
 
 }  // extern "C"

@@ -103,16 +103,19 @@ def test_fallback_everywhere_is_bit_exact():
     sph = torch.from_numpy(sph_np).to(d)
     tidx = torch.from_numpy(tidx_np).to(d)
     static_sq, static_sdf, h_ex, _ = exact_query(sc, d, sph, tidx, 0.2)
-    net = pcdf.SurrogateMLP(d, seed=5)  # untrained: every answer must come from the fallback
+    net = pcdf.SurrogateMLP(d, seed=5)
+    # untrained, band and error bound huge: every answer comes from the
+    # fallback, except where the static field provably wins the whole cell
+    # (the rows the selection skips), which is exact too
     h, _, nfb = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=1.0e9)
-    assert int(nfb.item()) == sph_np.size // 4
+    assert 0 < int(nfb.item()) <= sph_np.size // 4
     assert torch.equal(h, h_ex)
     # the same answers from the capsule-slab partials of the composite's first stage
     ws = pcdf.composite_workspace(grid, sc["caps"], d)
     pcdf.composite_prepare(grid, sc["caps"], ws)
     h2, _, nfb2 = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=1.0e9,
                                        comp_workspace=ws)
-    assert int(nfb2.item()) == sph_np.size // 4
+    assert int(nfb2.item()) == int(nfb.item())
     assert torch.equal(h2, h_ex)
 
 
@@ -128,7 +131,7 @@ def test_fallback_exact_with_several_humans():
     static_sq, static_sdf, h_ex, _ = exact_query(sc, d, sph, tidx, 0.2)
     net = pcdf.SurrogateMLP(d, seed=6)
     h, _, nfb = pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=1.0e9)
-    assert int(nfb.item()) == 3000
+    assert 0 < int(nfb.item()) <= 3000
     assert torch.equal(h, h_ex)
     ws = pcdf.composite_workspace(grid, sc["caps"], d)
     pcdf.composite_prepare(grid, sc["caps"], ws)
@@ -140,6 +143,35 @@ def test_fallback_exact_with_several_humans():
     sdf_o = np.stack([oracle.sdf_from_sq(comp[t], grid.vox) for t in range(6)])
     want, _ = oracle.hinge_cost(sdf_o, grid.origin, grid.vox, sph_np, tidx_np, 0.2)
     assert np.max(np.abs(h.cpu().numpy() - want)) <= 1e-5
+
+
+def test_row_selection_skips_only_static_cells():
+    """The selection keeps a row wherever the exact capsule field beats the
+    static field at some corner of the query's cell (the skip rule is a
+    proof, checked here against the exact fields)."""
+    d = dev()
+    sc = scenes.scene_small_walking(seed=79, T=8, H=2)
+    grid, caps = sc["grid"], sc["caps"]
+    rng = np.random.default_rng(4)
+    sph_np = scenes.spheres_uniform(grid, 4000, rng)
+    tidx_np = rng.integers(0, 8, 4000).astype(np.int32)
+    sph = torch.from_numpy(sph_np).to(d)
+    tidx = torch.from_numpy(tidx_np).to(d)
+    static_sq, static_sdf = pcdf.build_static_sdf(torch.from_numpy(sc["occ"]).to(d), grid)
+    x, yi = pcdf.surrogate_select(grid, static_sdf, sph, tidx, 8, torch.from_numpy(caps).to(d))
+    yi = yi.cpu().numpy().reshape(4000, 2)
+    kept = yi >= 0
+    assert 0 < kept.sum() < kept.size
+    assert np.array_equal(np.sort(yi[kept]), np.arange(kept.sum()))  # slots 0 .. kept - 1, each once
+    S = oracle.edt(sc["occ"])
+    dyns = [oracle.dynamic_field(grid.shape, caps[t]) for t in range(8)]
+    for q in np.nonzero(~kept.any(axis=1))[0][:300]:
+        dyn = dyns[tidx_np[q]]
+        u = (sph_np[q, :3].astype(np.float64) - np.asarray(grid.origin)) / grid.vox - 0.5
+        lo = [int(min(max(np.floor(u[a]), 0), grid.shape[2 - a] - 2)) for a in range(3)]
+        for k in range(8):
+            i, j, kk = lo[0] + (k & 1), lo[1] + ((k >> 1) & 1), lo[2] + ((k >> 2) & 1)
+            assert S[kk, j, i] <= dyn[kk, j, i], (q, k)
 
 
 def test_slab_fallback_edge_cases():
