@@ -409,6 +409,8 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
     t_mlp = ev_time(lambda: net.forward(x_q))
     x_sel, _ = pcdf.surrogate_select(grid, st_sdf, sph, tidx, T, caps_dev)
     t_mlp_sel = ev_time(lambda: net.forward(x_sel))
+    t_inf = ev_time(lambda: net.infer(x_q))
+    t_inf_sel = ev_time(lambda: net.infer(x_sel))
 
     def exact_composite():
         _, cs = pcdf.build_predicted_composite(st_sq, grid, sc["caps"], want_sq=False, static_sdf=st_sdf)
@@ -427,6 +429,8 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
             "fallback_frac": float(np.mean([x[2] for x in stats])), "decisions_identical": all(x[3] for x in stats),
             "surrogate_ms": t_sur, "surrogate_local_search_ms": t_sur_local, "features_ms": t_feat,
             "rows_to_network_frac": x_sel.shape[0] / (sph.numel() // 4), "mlp_forward_selected_ms": t_mlp_sel,
+            "mlp_infer_ms": t_inf, "mlp_infer_selected_ms": t_inf_sel,
+            "mlp_infer_tflops": 2 * 136193 * sph.numel() / 4 / (t_inf * 1e-3) / 1e12,
             "mlp_forward_ms": t_mlp,
             "mlp_tflops": 2 * 136193 * sph.numel() / 4 / (t_mlp * 1e-3) / 1e12, "exact_composite_ms": t_comp, "exact_scratch_ms": t_scr,
             "speedup_vs_scratch": t_scr / t_sur, "speedup_vs_composite": t_comp / t_sur}

@@ -292,6 +292,13 @@ int pcdf_mlp_workspace_bytes(int64_t M, size_t *bytes);
 int pcdf_mlp_init(void *state, uint64_t seed, void *stream);
 int pcdf_mlp_forward(const void *state, const uint16_t *x, int64_t M, float *y, void *workspace,
                      size_t workspace_bytes, void *stream);
+/* pcdf_mlp_infer  y = network(x) for M rows in one fused launch (no
+ * workspace): each CTA keeps a 64-row tile's activations in shared memory
+ * and streams the hidden weights; the products are accumulated in the same
+ * order and rounded at the same points as pcdf_mlp_forward, so y is
+ * bit-identical to it.  x device BF16 bits [M][16] (16-byte aligned), y
+ * device fp32 [M]. */
+int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);
 int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64_t M, float *y, float *loss,
                       void *workspace, size_t workspace_bytes, void *stream);
 int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, int32_t step, void *stream);

@@ -189,6 +189,184 @@ cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
+// fused inference: the whole network for a tile of rows in one CTA
+// ---------------------------------------------------------------------------
+// The activations of the tile stay in shared memory between layers; the
+// hidden weights stream through a double-buffered shared-memory chunk
+// (cp.async).  Per output element the k16 products are accumulated in the
+// same order as k_gemm and the epilogues and head do the same arithmetic as
+// k_gemm's bias+ReLU and k_head, so y is bit-identical to forward + head.
+constexpr int kIR = 64;           // rows per CTA
+constexpr int kIT = 256;          // threads: 8 warps, 2 (rows) x 4 (columns)
+constexpr int kKC = 32;           // K chunk of a hidden weight matrix
+constexpr int kActLd = kW + 8;    // row strides in bf16 (padding against bank conflicts)
+constexpr int kWLd = kKC + 8;
+constexpr int kInLd = kIn + 8;
+constexpr int kChunks = 2 * (kW / kKC);  // W2 then W3
+constexpr size_t kInferSmem =
+    ((size_t)kIR * kActLd + 2 * (size_t)kW * kWLd + (size_t)kIR * kInLd + (size_t)kW * kInLd) * sizeof(bf16);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+
+// 16-byte async copy; src_bytes 0 writes zeros
+__device__ __forceinline__ void cp16(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// one k16 step of the warp's 32 x 64 block: A rows from `a` (row stride lda,
+// columns k0 ..), B = W rows n (stride ldb, columns kb ..)
+__device__ __forceinline__ void warp_k16(float (&acc)[2][8][4], const bf16 *a, int lda, int k0, const bf16 *w,
+                                         int ldb, int kb, int wm, int wn, int lane)
+{
+    uint32_t af[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+        ldsm_x4(af[mt], a + (wm * 32 + mt * 16 + (lane & 15)) * lda + k0 + (lane >> 4) * 8);
+#pragma unroll
+    for (int np = 0; np < 4; ++np) {
+        uint32_t r[4];
+        ldsm_x4(r, w + (wn * 64 + np * 16 + (lane & 7) + ((lane >> 4) << 3)) * ldb + kb + ((lane >> 3) & 1) * 8);
+        const uint32_t b0[2] = {r[0], r[1]}, b1[2] = {r[2], r[3]};
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            mma16816(acc[mt][2 * np], af[mt], b0);
+            mma16816(acc[mt][2 * np + 1], af[mt], b1);
+        }
+    }
+}
+
+// act[r][c] = bf16(max(acc + bias[c], 0)) for the warp's block
+__device__ __forceinline__ void warp_epilogue(bf16 *act, const float (&acc)[2][8][4], const float *__restrict__ bias,
+                                              int wm, int wn, int lane)
+{
+    const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int hq = 0; hq < 2; ++hq) {
+                const int r = wm * 32 + mt * 16 + gid + 8 * hq;
+                const int c = wn * 64 + nt * 8 + tig * 2;
+                __nv_bfloat162 v;
+                v.x = __float2bfloat16_rn(fmaxf(acc[mt][nt][2 * hq] + __ldg(bias + c), 0.f));
+                v.y = __float2bfloat16_rn(fmaxf(acc[mt][nt][2 * hq + 1] + __ldg(bias + c + 1), 0.f));
+                *reinterpret_cast<__nv_bfloat162 *>(act + r * kActLd + c) = v;
+            }
+}
+
+__global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ wh, const float *__restrict__ p,
+                                                      const bf16 *__restrict__ x, long long M, float *__restrict__ y)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    bf16 *act = reinterpret_cast<bf16 *>(smem_raw);
+    bf16 *wbuf = act + kIR * kActLd;       // [2][kW][kWLd]
+    bf16 *xs = wbuf + 2 * kW * kWLd;       // [kIR][kInLd]
+    bf16 *w1s = xs + kIR * kInLd;          // [kW][kInLd]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wm = warp >> 2, wn = warp & 3;
+    const long long m0 = (long long)blockIdx.x * kIR;
+    const bf16 *W1 = wh + hW1, *W2 = wh + hW2, *W3 = wh + hW3;
+
+    // x tile (rows past M read as zeros) and W1: 16-byte pieces
+    for (int v = tid; v < kIR * 2; v += kIT) {
+        const int r = v >> 1, h = (v & 1) * 8;
+        const bool in = m0 + r < M;
+        cp16(xs + r * kInLd + h, x + (in ? (m0 + r) * kIn + h : 0), in ? 16 : 0);
+    }
+    for (int v = tid; v < kW * 2; v += kIT) {
+        const int n = v >> 1, h = (v & 1) * 8;
+        cp16(w1s + n * kInLd + h, W1 + n * kIn + h, 16);
+    }
+    cp_commit();
+    auto issue = [&](int g) {  // chunk g: W2 (g < 8) or W3, columns kKC * (g % 8) ..
+        const bf16 *W = g < kW / kKC ? W2 : W3;
+        const int kb = (g % (kW / kKC)) * kKC;
+        bf16 *dst = wbuf + (g & 1) * kW * kWLd;
+        for (int v = tid; v < kW * (kKC / 8); v += kIT) {
+            const int n = v / (kKC / 8), q = (v % (kKC / 8)) * 8;
+            cp16(dst + n * kWLd + q, W + n * kW + kb + q, 16);
+        }
+        cp_commit();
+    };
+    issue(0);
+
+    float acc[2][8][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                acc[mt][nt][q] = 0.f;
+    cp_wait_all();
+    __syncthreads();
+    // layer 1 (K = 16: one k16 step)
+    warp_k16(acc, xs, kInLd, 0, w1s, kInLd, 0, wm, wn, lane);
+    warp_epilogue(act, acc, p + oB1, wm, wn, lane);
+
+    // layers 2 and 3
+    for (int g = 0; g < kChunks; ++g) {
+        if (g % (kW / kKC) == 0) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        acc[mt][nt][q] = 0.f;
+        }
+        cp_wait_all();     // this thread's pieces of chunk g have landed
+        __syncthreads();   // everyone's have; chunk g - 1 and the layer input are done with
+        if (g + 1 < kChunks)
+            issue(g + 1);
+        const bf16 *wc = wbuf + (g & 1) * kW * kWLd;
+        const int k0 = (g % (kW / kKC)) * kKC;
+#pragma unroll
+        for (int kk = 0; kk < kKC; kk += 16)
+            warp_k16(acc, act, kActLd, k0 + kk, wc, kWLd, kk, wm, wn, lane);
+        if (g % (kW / kKC) == kW / kKC - 1) {
+            __syncthreads();  // every warp has read the layer input
+            warp_epilogue(act, acc, p + (g < kW / kKC ? oB2 : oB3), wm, wn, lane);
+        }
+    }
+    __syncthreads();
+
+    // head: the 256 -> 1 layer, as k_head (lane j owns columns 8 j .. 8 j + 7)
+    float w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        w[j] = __bfloat162float(wh[hW4 + lane * 8 + j]);
+    const float b4 = p[oB4];
+    for (int i = warp; i < kIR; i += kIT / 32) {
+        const long long m = m0 + i;
+        if (m >= M)
+            break;
+        const uint4 q = *reinterpret_cast<const uint4 *>(act + i * kActLd + lane * 8);
+        const bf16 *hh = reinterpret_cast<const bf16 *>(&q);
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            s = fmaf(__bfloat162float(hh[j]), w[j], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0)
+            y[m] = s + b4;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // output layer, loss, bias gradients, Adam, initialisation
 // ---------------------------------------------------------------------------
 constexpr int kHeadRows = 64;  // rows per CTA of k_head (8 warps x 8 rows)
@@ -514,6 +692,26 @@ int pcdf_mlp_forward(const void *state, const uint16_t *x, int64_t M, float *y, 
                                                                         nullptr, nullptr, nullptr, nullptr, 0.f);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp head");
+}
+
+int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, void *stream)
+{
+    if (!state || (M > 0 && (!x || !y)))
+        return fail(PCDF_EINVAL, "state, x and y must be non-NULL");
+    if (M < 0 || M > (1LL << 31) - 1)
+        return fail(PCDF_EINVAL, "M out of range");
+    if (M == 0)
+        return PCDF_OK;
+    if (!aligned(x, 16) || !aligned(state, kAlign))
+        return fail(PCDF_EINVAL, "x must be 16-byte aligned, state %zu-byte aligned", kAlign);
+    State S(const_cast<void *>(state));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
+    if (e == cudaSuccess) {
+        k_mlp_infer<<<(unsigned)((M + kIR - 1) / kIR), kIT, kInferSmem, st>>>(S.h, S.p, (const bf16 *)x, M, y);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp inference");
 }
 
 int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64_t M, float *y, float *loss,

@@ -49,9 +49,12 @@ def test_mlp_forward_and_gradients_match_oracle(M):
             b = b.reshape(256, 16)[:, :13].ravel()
             a = a.reshape(256, 16)[:, :13].ravel()
         assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(a) + 1e-9, k
-    # the forward pass alone gives the same outputs
+    # the forward pass alone gives the same outputs, and so does the fused
+    # inference kernel (tail tiles included)
     y2 = net.forward(x)
     assert torch.equal(y2, y)
+    assert torch.equal(net.infer(x), y)
+    assert torch.equal(net.infer(x[: M - 7]), y[: M - 7])
 
 
 def test_adam_step():
