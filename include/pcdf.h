@@ -163,6 +163,15 @@ int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const
                           int32_t H, const int32_t *caps, int32_t *comp_sq, float *comp_sdf, void *workspace,
                           size_t workspace_bytes, void *stream);
 
+/* The finish stage for the fields t = t0 .. t0 + nt - 1 only (0 <= t0,
+ * nt >= 1, t0 + nt <= T): the outputs are the same [T][nz][ny][nx] arrays,
+ * indexed by the absolute t, and only the range's fields are written.  A
+ * caller can copy finished fields to the host while later ones are computed
+ * (each call also recomputes the static column maxima). */
+int pcdf_composite_finish_range(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int32_t T,
+                                int32_t H, const int32_t *caps, int32_t t0, int32_t nt, int32_t *comp_sq,
+                                float *comp_sdf, void *workspace, size_t workspace_bytes, void *stream);
+
 /* ---------------------------------------------------------------------------
  * From-scratch comparator (Sec. 6 benchmark: a full exact EDT per subsequent
  * field instead of the composition).

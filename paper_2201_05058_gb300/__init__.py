@@ -24,6 +24,7 @@ from .api import (  # noqa: F401
     capsule_fixed,
     composite_finish,
     predicted_fields,
+    update_to_host,
     composite_prepare,
     composite_slab,
     composite_workspace,

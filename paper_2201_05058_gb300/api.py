@@ -184,8 +184,11 @@ def composite_prepare(grid, caps, workspace: torch.Tensor):
                "pcdf_composite_prepare")
 
 
-def composite_finish(static_sq, grid, caps, workspace: torch.Tensor, comp_sq=None, comp_sdf=None, static_sdf=None):
-    """Second stage: fused z pass + composite min + float epilogue into the given outputs."""
+def composite_finish(static_sq, grid, caps, workspace: torch.Tensor, comp_sq=None, comp_sdf=None, static_sdf=None,
+                     t_range=None):
+    """Second stage: fused z pass + composite min + float epilogue into the
+    given outputs ([T, ...] arrays); t_range = (t0, nt) writes only the
+    fields t0 .. t0 + nt - 1."""
     shp = _shape(grid)
     caps = _caps_host(caps)
     T, H = int(caps.shape[0]), int(caps.shape[1])
@@ -199,11 +202,18 @@ def composite_finish(static_sq, grid, caps, workspace: torch.Tensor, comp_sq=Non
         _need(comp_sdf, "comp_sdf", torch.float32, (T,) + shp)
     g = _cgrid(grid)
     cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
-    _lib.check(_lib.load().pcdf_composite_finish(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), T, H, cp,
-                                                 _ptr(comp_sq),
-                                                 _ptr(comp_sdf), _ptr(workspace), workspace.numel(),
-                                                 ctypes.c_void_p(_stream(static_sq.device))),
-               "pcdf_composite_finish")
+    if t_range is None:
+        _lib.check(_lib.load().pcdf_composite_finish(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), T, H, cp,
+                                                     _ptr(comp_sq), _ptr(comp_sdf), _ptr(workspace),
+                                                     workspace.numel(), ctypes.c_void_p(_stream(static_sq.device))),
+                   "pcdf_composite_finish")
+    else:
+        t0, nt = (int(v) for v in t_range)
+        _lib.check(_lib.load().pcdf_composite_finish_range(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), T, H,
+                                                           cp, t0, nt, _ptr(comp_sq), _ptr(comp_sdf),
+                                                           _ptr(workspace), workspace.numel(),
+                                                           ctypes.c_void_p(_stream(static_sq.device))),
+                   "pcdf_composite_finish_range")
 
 
 _side_streams = {}
@@ -244,6 +254,56 @@ def predicted_fields(occ: torch.Tensor, grid, caps, workspace=None, out_static_s
     main.wait_stream(side)
     composite_finish(st_sq, grid, caps, ws, sq, sdf, static_sdf=st_sdf)
     return st_sq, st_sdf, sq, sdf
+
+
+_copy_streams = {}
+
+
+def _copy_stream(dev):
+    st = _copy_streams.get(dev.index)
+    if st is None:
+        st = torch.cuda.Stream(device=dev)
+        _copy_streams[dev.index] = st
+    return st
+
+
+def update_to_host(occ_host: torch.Tensor, grid, caps, out_host: torch.Tensor, buffers: dict, chunk: int = 4):
+    """One map update with host buffers: the occupancy comes from pinned host
+    memory (uint8 [nz, ny, nx]) and the T float composite fields go to pinned
+    host memory (out_host fp32 [T, nz, ny, nx]).
+
+    `buffers` holds the device tensors, reused between calls: "occ" (uint8),
+    "static_sq", "static_sdf", "comp_sq" (optional), "comp_sdf" and
+    "workspace" (composite_workspace).  The static build and the capsule pass
+    overlap as in predicted_fields; the z pass then runs `chunk` time steps at
+    a time, and each finished chunk is copied to the host on a copy stream
+    while the next one is computed.  The current stream waits for every copy
+    (synchronise it before reading out_host)."""
+    caps = _caps_host(caps)
+    T = int(caps.shape[0])
+    occ_d, ws = buffers["occ"], buffers["workspace"]
+    st_sq, st_sdf = buffers["static_sq"], buffers["static_sdf"]
+    comp_sq, comp_sdf = buffers.get("comp_sq"), buffers["comp_sdf"]
+    dev = occ_d.device
+    if (out_host.is_cuda or out_host.dtype != torch.float32 or not out_host.is_contiguous()
+            or tuple(out_host.shape) != (T,) + _shape(grid)):
+        raise ValueError(f"out_host must be a contiguous host float32 tensor of shape {(T,) + _shape(grid)}")
+    main = torch.cuda.current_stream(dev)
+    occ_d.copy_(occ_host, non_blocking=True)
+    side = _side_stream(dev)
+    side.wait_stream(main)
+    with torch.cuda.stream(side):
+        composite_prepare(grid, caps, ws)
+    build_static_sdf(occ_d, grid, out_sq=st_sq, out_sdf=st_sdf)
+    main.wait_stream(side)
+    cp = _copy_stream(dev)
+    for t0 in range(0, T, chunk):
+        nt = min(chunk, T - t0)
+        composite_finish(st_sq, grid, caps, ws, comp_sq, comp_sdf, static_sdf=st_sdf, t_range=(t0, nt))
+        cp.wait_stream(main)
+        with torch.cuda.stream(cp):
+            out_host[t0:t0 + nt].copy_(comp_sdf[t0:t0 + nt], non_blocking=True)
+    main.wait_stream(cp)
 
 
 def build_from_scratch(occ: torch.Tensor, grid, caps, want_sdf: bool = True, out_sq=None, out_sdf=None):

@@ -82,7 +82,7 @@ int pcdf_build_predicted_composite(const pcdf_grid *grid, const int32_t *static_
         return rc;
     if (int rc = composite_prepare(grid, T, H, p, workspace, (cudaStream_t)stream))
         return rc;
-    return composite_finish(grid, static_sq, static_sdf, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
+    return composite_finish(grid, static_sq, static_sdf, 0, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
 }
 
 int pcdf_composite_prepare(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, void *workspace,
@@ -107,7 +107,23 @@ int pcdf_composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const
         return fail(PCDF_EINVAL, "static_sq and at least one output must be non-NULL");
     if (int rc = check_ws(p, workspace, workspace_bytes))
         return rc;
-    return composite_finish(grid, static_sq, static_sdf, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
+    return composite_finish(grid, static_sq, static_sdf, 0, T, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
+}
+
+int pcdf_composite_finish_range(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int32_t T,
+                                int32_t H, const int32_t *caps, int32_t t0, int32_t nt, int32_t *comp_sq,
+                                float *comp_sdf, void *workspace, size_t workspace_bytes, void *stream)
+{
+    CompositePlan p;
+    if (int rc = plan_composite(grid, T, H, caps, p))
+        return rc;
+    if (!static_sq || (!comp_sq && !comp_sdf))
+        return fail(PCDF_EINVAL, "static_sq and at least one output must be non-NULL");
+    if (t0 < 0 || nt < 1 || t0 + nt > T)
+        return fail(PCDF_EINVAL, "time range [%d, %d) outside [0, %d)", t0, t0 + nt, T);
+    if (int rc = check_ws(p, workspace, workspace_bytes))
+        return rc;
+    return composite_finish(grid, static_sq, static_sdf, t0, nt, p, comp_sq, comp_sdf, workspace, (cudaStream_t)stream);
 }
 
 int pcdf_scratch_workspace_bytes(const pcdf_grid *grid, int32_t T, int32_t H, size_t *bytes)

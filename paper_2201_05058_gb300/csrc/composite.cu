@@ -22,13 +22,13 @@ template <bool kSq, bool kSdfOut, bool kStaticSdf>
 __global__ void __launch_bounds__(128, 8)
     k_composite_z(const int32_t *__restrict__ static_sq, const float *__restrict__ static_sdf,
                   const int32_t *__restrict__ colmax, const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz,
-                  int zlo, int S, int T, int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox,
+                  int zlo, int S, int t0, int nt, int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox,
                   int vec)
 {
     extern __shared__ uint32_t smem[];
     comp::composite_block_short<kSq, kSdfOut, kStaticSdf>(static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S,
-                                                          (int)(blockIdx.x % T),
-                                                          (long long)(blockIdx.x / T) * blockDim.x, comp_sq, comp_sdf,
+                                                          t0 + (int)(blockIdx.x % nt),
+                                                          (long long)(blockIdx.x / nt) * blockDim.x, comp_sq, comp_sdf,
                                                           vox, vec != 0, smem);
 }
 
@@ -38,14 +38,14 @@ __global__ void __launch_bounds__(128) k_colmax(const int32_t *__restrict__ sq, 
     comp::colmax_block(sq, V2, nz, colmax);
 }
 
-__global__ void k_broadcast_static(const int32_t *__restrict__ static_sq, long long V, int T,
+__global__ void k_broadcast_static(const int32_t *__restrict__ static_sq, long long V, int t0, int nt,
                                    int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
         const int32_t s = __ldg(static_sq + v);
         const float f = sq_to_sdf(s, vox);
-        for (int t = 0; t < T; ++t) {
+        for (int t = t0; t < t0 + nt; ++t) {
             if (comp_sq)
                 __stcs(comp_sq + (long long)t * V + v, s);
             if (comp_sdf)
@@ -80,15 +80,15 @@ namespace {
 
 template <bool kSq, bool kSdfOut, bool kStaticSdf>
 cudaError_t launch_cz(int nblk, int nthr, size_t smem, const int32_t *static_sq, const float *static_sdf,
-                      const int32_t *colmax, const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int T,
-                      int32_t *comp_sq, float *comp_sdf, float vox, int vec, cudaStream_t stream)
+                      const int32_t *colmax, const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int t0,
+                      int nt, int32_t *comp_sq, float *comp_sdf, float vox, int vec, cudaStream_t stream)
 {
     auto kern = k_composite_z<kSq, kSdfOut, kStaticSdf>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    kern<<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S, T,
-                                                 comp_sq, comp_sdf, vox, vec);
+    kern<<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S, t0,
+                                                 nt, comp_sq, comp_sdf, vox, vec);
     return cudaGetLastError();
 }
 
@@ -104,7 +104,7 @@ cudaError_t launch_colmax(const int32_t *sq, int nx, int ny, int nz, int32_t *co
 }
 
 cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf, const int32_t *colmax,
-                               const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int T,
+                               const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int t0, int nt,
                                int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream)
 {
     const long long V2 = (long long)nx * ny;
@@ -113,14 +113,14 @@ cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf
     while (nthr > 32 && (size_t)nthr * words * sizeof(uint32_t) > 200 * 1024)
         nthr >>= 1;
     const size_t smem = (size_t)nthr * words * sizeof(uint32_t);
-    const int nblk = (int)((V2 + nthr - 1) / nthr * T);
+    const int nblk = (int)((V2 + nthr - 1) / nthr * nt);
     const bool sq = comp_sq != nullptr, sd = comp_sdf != nullptr, st = static_sdf != nullptr && sd;
     // 16-byte copies of all-static column blocks: every plane and column
     // block starts on a 16-byte boundary
     const int vec = V2 % 4 == 0 && aligned16(static_sq) && (!st || aligned16(static_sdf)) &&
                     (!sq || aligned16(comp_sq)) && (!sd || aligned16(comp_sdf));
 #define PCDF_CZ(a, b, c)                                                                                            \
-    return launch_cz<a, b, c>(nblk, nthr, smem, static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S, T,      \
+    return launch_cz<a, b, c>(nblk, nthr, smem, static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S, t0, nt, \
                               comp_sq, comp_sdf, vox, vec, stream)
     if (sq && sd && st)
         PCDF_CZ(true, true, true);
@@ -134,7 +134,7 @@ cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf
 #undef PCDF_CZ
 }
 
-cudaError_t launch_broadcast_static(const int32_t *static_sq, long long V, int T, int32_t *comp_sq,
+cudaError_t launch_broadcast_static(const int32_t *static_sq, long long V, int t0, int nt, int32_t *comp_sq,
                                     float *comp_sdf, float vox, cudaStream_t stream)
 {
     int dev = 0, sms = 0;
@@ -143,7 +143,7 @@ cudaError_t launch_broadcast_static(const int32_t *static_sq, long long V, int T
     long long nblk = (V + 255) / 256;
     if (nblk > (long long)sms * 8)
         nblk = (long long)sms * 8;
-    k_broadcast_static<<<(unsigned)nblk, 256, 0, stream>>>(static_sq, V, T, comp_sq, comp_sdf, vox);
+    k_broadcast_static<<<(unsigned)nblk, 256, 0, stream>>>(static_sq, V, t0, nt, comp_sq, comp_sdf, vox);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,8 @@ int32_t *plan_mid(const CompositePlan &p, void *workspace);
 int check_ws(const CompositePlan &p, void *workspace, size_t workspace_bytes);
 int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &p, void *workspace,
                       cudaStream_t st);
-int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int T,
+// fields t = t0 .. t0 + nt - 1 (outputs indexed by the absolute t)
+int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int t0, int nt,
                      const CompositePlan &p, int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st);
 
 }  // namespace host

@@ -72,18 +72,19 @@ cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, 
 cudaError_t launch_colmax(const int32_t *sq, int nx, int ny, int nz, int32_t *colmax, cudaStream_t stream);
 
 // z-pass of the dynamic field over the slab [zlo, zlo + S) fused with the
-// composite min against static_sq and the float epilogue, for all T.
+// composite min against static_sq and the float epilogue, for t = t0 ..
+// t0 + nt - 1 (outputs and slab indexed by the absolute t).
 // static_sdf (nullable) is the float field of static_sq; where the static
 // field wins the min it is copied instead of recomputed.  colmax holds the
 // column maxima of static_sq (launch_colmax): columns and z ranges where the
 // static field provably wins skip the envelope.
 cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf, const int32_t *colmax,
-                               const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int T,
+                               const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int t0, int nt,
                                int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream);
 
-// Copies static_sq into every t of comp (and its float field) when no capsule
-// touches the grid.
-cudaError_t launch_broadcast_static(const int32_t *static_sq, long long V, int T, int32_t *comp_sq,
+// Copies static_sq into t = t0 .. t0 + nt - 1 of comp (and its float field)
+// when no capsule touches the grid.
+cudaError_t launch_broadcast_static(const int32_t *static_sq, long long V, int t0, int nt, int32_t *comp_sq,
                                     float *comp_sdf, float vox, cudaStream_t stream);
 
 // query.cu

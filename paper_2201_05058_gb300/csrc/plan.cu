@@ -235,12 +235,12 @@ int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "dynamic y pass");
 }
 
-int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int T,
+int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int t0, int nt,
                      const CompositePlan &p, int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st)
 {
     cudaError_t e;
     if (p.S == 0) {
-        e = pcdf::launch_broadcast_static(static_sq, nvox(grid), T, comp_sq, comp_sdf, grid->vox, st);
+        e = pcdf::launch_broadcast_static(static_sq, nvox(grid), t0, nt, comp_sq, comp_sdf, grid->vox, st);
         return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "broadcast");
     }
     const int32_t *mid = plan_mid(p, workspace);
@@ -248,8 +248,8 @@ int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const floa
     e = pcdf::launch_colmax(static_sq, grid->nx, grid->ny, grid->nz, colmax, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "static column maxima");
-    e = pcdf::launch_composite_z(static_sq, static_sdf, colmax, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, T,
-                                 comp_sq, comp_sdf, grid->vox, st);
+    e = pcdf::launch_composite_z(static_sq, static_sdf, colmax, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, t0,
+                                 nt, comp_sq, comp_sdf, grid->vox, st);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "composite z pass");
 }
 

@@ -436,3 +436,25 @@ def test_predicted_fields_overlapped_and_graph_captured():
     want2 = oracle.predicted_composite(oracle.edt(occ2), caps)
     for t in range(caps.shape[0]):
         assert_equal_fields(sq[t].cpu().numpy(), want2[t], f"replayed comp_sq[{t}]")
+
+
+def test_update_to_host_chunks_equal_the_oracle():
+    """Host buffers in and out, fields copied in chunks while later ones are
+    computed; also a chunk size that does not divide T."""
+    sc = scenes.scene_small_walking(seed=33, T=7, H=2)
+    grid, caps = sc["grid"], sc["caps"]
+    d = torch.device("cuda", 0)
+    T = caps.shape[0]
+    bufs = {"occ": torch.empty(grid.shape, dtype=torch.uint8, device=d),
+            "static_sq": torch.empty(grid.shape, dtype=torch.int32, device=d),
+            "static_sdf": torch.empty(grid.shape, dtype=torch.float32, device=d),
+            "comp_sdf": torch.empty((T,) + grid.shape, dtype=torch.float32, device=d),
+            "workspace": pcdf.composite_workspace(grid, caps, d)}
+    occ_h = torch.from_numpy(sc["occ"]).pin_memory()
+    want = oracle.predicted_composite(oracle.edt(sc["occ"]), caps)
+    for chunk in (3, 7):
+        out_h = torch.full((T,) + grid.shape, float("nan"), dtype=torch.float32).pin_memory()
+        pcdf.update_to_host(occ_h, grid, caps, out_h, bufs, chunk=chunk)
+        torch.cuda.synchronize()
+        for t in range(T):
+            assert_bits_equal(out_h[t].numpy(), oracle.sdf_from_sq(want[t], grid.vox), f"host field {t}")
