@@ -70,6 +70,8 @@ def _load():
             lib.or_trilinear.restype = ctypes.c_double
             lib.or_hinge_cost.argtypes = [P, ctypes.c_int] + [ctypes.c_int] * 3 + [P, f32, P, P, i64, f32, P, P, P]
             lib.or_hinge_cost.restype = i64
+            lib.or_voxel_filter.argtypes = [ctypes.c_int] * 3 + [P, ctypes.c_int, P]
+            lib.or_collapse.argtypes = [ctypes.c_int] * 3 + [P, ctypes.c_int, ctypes.c_int, P]
             _lib = lib
     return _lib
 
@@ -217,3 +219,23 @@ def hinge_cost(sdf, origin, vox, spheres, tidx, eps, need_grad=False):
     if need_grad:
         return h, int(n_oob), gc, gr
     return h, int(n_oob)
+
+
+def voxel_filter(occ, min_neighbours: int = 5) -> np.ndarray:
+    """Sec. 8 clean-up: keep an occupied voxel iff at least min_neighbours of
+    its 26 in-grid neighbours are occupied."""
+    o = _c(occ, np.uint8)
+    nz, ny, nx = o.shape
+    out = np.empty_like(o)
+    _load().or_voxel_filter(nx, ny, nz, _ptr(o), int(min_neighbours), _ptr(out))
+    return out
+
+
+def collapse(occ, z0: int, z1: int) -> np.ndarray:
+    """Sec. 8 2-D map: uint8 [ny, nx], a column occupied iff some voxel of it
+    in slices [z0, z1) is."""
+    o = _c(occ, np.uint8)
+    nz, ny, nx = o.shape
+    out = np.empty((ny, nx), np.uint8)
+    _load().or_collapse(nx, ny, nz, _ptr(o), int(z0), int(z1), _ptr(out))
+    return out

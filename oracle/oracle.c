@@ -22,6 +22,11 @@
  *   - trilinear sampling, hinge obstacle cost and its gradient with respect to
  *     the sphere centre, in double precision (Sec. 7, hinge form of the
  *     robot-avoidance factor, applied to the environment field as in GPMP2).
+ *   - the static-map clean-up of Sec. 8: occupied voxels with fewer than a
+ *     given number of occupied voxels among their 26 neighbours are cleared.
+ *   - the 2-D map of Sec. 8: the 3-D grid collapsed over a range of slices
+ *     (a column is occupied if any of its voxels in the range is), whose EDT
+ *     is the 3-D EDT above on a grid one slice thick.
  *
  * Conventions (shared with the library by specification, not by code):
  *   grid index v = (k*ny + j)*nx + i, x fastest; voxel (i,j,k) has its centre
@@ -432,4 +437,37 @@ int64_t or_hinge_cost(const float *sdf, int T, int nx, int ny, int nz, const flo
             grad_r[q] = active ? 1.0 : 0.0;
     }
     return n_oob;
+}
+
+/* Sec. 8 voxel filter: out(v) = occ(v) and (number of occupied in-grid voxels
+ * among the 26 neighbours of v) >= min_neighbours. */
+void or_voxel_filter(int nx, int ny, int nz, const uint8_t *occ, int min_neighbours, uint8_t *out)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const size_t v = ((size_t)k * ny + j) * nx + i;
+                int n = 0;
+                for (int dk = -1; dk <= 1; ++dk)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        for (int di = -1; di <= 1; ++di) {
+                            const int a = i + di, b = j + dj, c = k + dk;
+                            if ((di || dj || dk) && a >= 0 && a < nx && b >= 0 && b < ny && c >= 0 && c < nz &&
+                                occ[((size_t)c * ny + b) * nx + a])
+                                ++n;
+                        }
+                out[v] = (uint8_t)(occ[v] && n >= min_neighbours);
+            }
+}
+
+/* Sec. 8 collapsed map: out[j][i] = 1 iff occ[k][j][i] for some k in [z0, z1). */
+void or_collapse(int nx, int ny, int nz, const uint8_t *occ, int z0, int z1, uint8_t *out)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            uint8_t o = 0;
+            for (int k = z0 < 0 ? 0 : z0; k < z1 && k < nz; ++k)
+                o |= occ[((size_t)k * ny + j) * nx + i] != 0;
+            out[(size_t)j * nx + i] = o;
+        }
 }

@@ -453,3 +453,62 @@ def test_hinge_gradient_matches_finite_differences_of_cost():
         assert gr[q] == 1.0
         checked += 1
     assert checked > 100
+
+
+# ---------------------------------------------------------------------------
+# Sec. 8 static-map clean-up and the collapsed 2-D map
+# ---------------------------------------------------------------------------
+
+def test_voxel_filter_closed_forms():
+    g = np.zeros((7, 7, 7), np.uint8)
+    g[3, 3, 3] = 1                                   # isolated: 0 neighbours
+    assert oracle.voxel_filter(g).sum() == 0
+    g[:] = 0
+    g[2:5, 2:5, 2:5] = 1                             # 3x3x3 cube: corners have 7 neighbours
+    assert np.array_equal(oracle.voxel_filter(g), g)
+    g[:] = 0
+    g[1:3, 1:3, 1:3] = 1                             # 2x2x2 cube: 7 neighbours each
+    assert np.array_equal(oracle.voxel_filter(g), g)
+    g[:] = 0
+    g[3, 3, :] = 1                                   # a line: at most 2 neighbours
+    assert oracle.voxel_filter(g).sum() == 0
+    g[:] = 0
+    g[3, 1:3, 1:3] = 1                               # 2x2 square: 3 neighbours each
+    assert oracle.voxel_filter(g).sum() == 0
+    assert np.array_equal(oracle.voxel_filter(g, 3), g)
+    assert oracle.voxel_filter(g, 4).sum() == 0
+    g[:] = 0
+    g[3, 1:4, 1:4] = 1                               # 3x3 square: corners 3, edges 5, centre 8
+    want = np.zeros_like(g)
+    want[3, 2, 1:4] = 1
+    want[3, 1:4, 2] = 1
+    assert np.array_equal(oracle.voxel_filter(g), want)
+    # the grid boundary is not occupied: a full grid keeps only voxels with >= 5
+    # in-grid neighbours (a corner of a 2x2x2 grid has 7)
+    assert oracle.voxel_filter(np.ones((2, 2, 2), np.uint8)).sum() == 8
+    assert oracle.voxel_filter(np.ones((1, 1, 4), np.uint8)).sum() == 0
+
+
+@pytest.mark.parametrize("shape,density,k", [((9, 11, 13), 0.3, 5), ((16, 16, 16), 0.1, 5), ((5, 1, 40), 0.6, 2),
+                                             ((12, 10, 8), 0.5, 0), ((12, 10, 8), 0.9, 26)])
+def test_voxel_filter_matches_a_convolution(shape, density, k):
+    from scipy import ndimage
+    g = (np.random.default_rng(len(shape) + k).random(shape) < density).astype(np.uint8)
+    n = ndimage.convolve(g.astype(np.int32), np.ones((3, 3, 3), np.int32), mode="constant", cval=0) - g
+    want = ((g == 1) & (n >= k)).astype(np.uint8)
+    assert np.array_equal(oracle.voxel_filter(g, k), want)
+
+
+def test_collapse_and_2d_edt():
+    from scipy import ndimage
+    rng = np.random.default_rng(7)
+    g = (rng.random((20, 31, 37)) < 0.02).astype(np.uint8)
+    for z0, z1 in ((0, 20), (3, 9), (-5, 4), (15, 40), (6, 6)):
+        want = g[max(z0, 0):max(min(z1, 20), 0)].any(axis=0).astype(np.uint8)
+        assert np.array_equal(oracle.collapse(g, z0, z1), want)
+    c = oracle.collapse(g, 2, 12)
+    S = oracle.edt(c[None])[0]
+    dO = ndimage.distance_transform_edt(c == 0)
+    dF = ndimage.distance_transform_edt(c == 1)
+    want = np.where(c == 0, np.rint(dO ** 2), -np.rint(dF ** 2)).astype(np.int64)
+    assert np.array_equal(S.astype(np.int64), want)
