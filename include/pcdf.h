@@ -117,6 +117,23 @@ int pcdf_build_static_sdf_noalloc(const pcdf_grid *grid, const uint8_t *occ, int
                                   void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Static-map utilities of the mapping pipeline (Sec. 8).
+ *
+ * pcdf_filter_voxels  clean-up of the static voxel map: out = occ with every
+ *     occupied voxel cleared whose 26 in-grid neighbours hold fewer than
+ *     min_neighbours (0..27) occupied voxels.  The paper clears voxels with
+ *     fewer than five connected voxels (min_neighbours = 5 reads "connected"
+ *     as the 26-neighbourhood).  occ, out: device uint8 [nz][ny][nx], nonzero
+ *     = occupied, distinct buffers; out holds 0/1.
+ * pcdf_collapse_2d  the 2-D map of the prediction module: out2d[j][i] = 1 iff
+ *     occ[k][j][i] != 0 for some k in [z0, z1) (clipped to the grid; an empty
+ *     range gives zeros).  out2d: device uint8 [ny][nx].  Its EDT is
+ *     pcdf_build_static_sdf on the grid {nx, ny, 1}.
+ * ------------------------------------------------------------------------- */
+int pcdf_filter_voxels(const pcdf_grid *grid, const uint8_t *occ, int32_t min_neighbours, uint8_t *out, void *stream);
+int pcdf_collapse_2d(const pcdf_grid *grid, const uint8_t *occ, int32_t z0, int32_t z1, uint8_t *out2d, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Predicted composite fields (Sec. 6 composition; Sec. 8 sequence of n fields).
  *
  * For t = 0..T-1:  comp[t] = min(S_static, S_dyn[t])  per voxel, where S_dyn[t]

@@ -24,6 +24,9 @@ from .api import (  # noqa: F401
     capsule_fixed,
     composite_finish,
     predicted_fields,
+    filter_voxels,
+    collapse_2d,
+    edt_2d,
     update_to_host,
     composite_prepare,
     composite_slab,

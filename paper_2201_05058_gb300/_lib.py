@@ -34,6 +34,7 @@ EXPORTS = (
     "pcdf_static_workspace_bytes", "pcdf_build_static_sdf", "pcdf_build_static_sdf_noalloc",
     "pcdf_composite_workspace_bytes", "pcdf_build_predicted_composite",
     "pcdf_composite_prepare", "pcdf_composite_finish", "pcdf_composite_finish_range", "pcdf_composite_slab",
+    "pcdf_filter_voxels", "pcdf_collapse_2d",
     "pcdf_scratch_workspace_bytes", "pcdf_build_from_scratch",
     "pcdf_query_cost", "pcdf_query_cost_backward",
     "pcdf_batch_create", "pcdf_batch_destroy", "pcdf_batch_workspace_bytes", "pcdf_batch_tiles_used",
@@ -62,6 +63,8 @@ def _declare(lib):
         "pcdf_composite_slab": [G, I32, I32, P, ctypes.POINTER(I32), ctypes.POINTER(I32)],
         "pcdf_composite_finish": [G, P, P, I32, I32, P, P, P, P, SZ, P],
         "pcdf_composite_finish_range": [G, P, P, I32, I32, P, I32, I32, P, P, P, SZ, P],
+        "pcdf_filter_voxels": [G, P, I32, P, P],
+        "pcdf_collapse_2d": [G, P, I32, I32, P, P],
         "pcdf_scratch_workspace_bytes": [G, I32, I32, SZP],
         "pcdf_build_from_scratch": [G, P, I32, I32, P, P, P, P, SZ, P],
         "pcdf_query_cost": [G, P, I32, P, P, I64, F32, P, P, P],

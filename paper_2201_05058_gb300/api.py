@@ -112,6 +112,41 @@ def build_static_sdf(occ: torch.Tensor, grid, want_sdf: bool = True, out_sq=None
     return sq, sdf
 
 
+def filter_voxels(occ: torch.Tensor, grid, min_neighbours: int = 5, out=None) -> torch.Tensor:
+    """Sec. 8 static-map clean-up: occupied voxels with fewer than
+    min_neighbours occupied voxels among their 26 neighbours are cleared.
+    occ: CUDA uint8 [nz, ny, nx]; returns uint8 0/1 of the same shape."""
+    shp = _shape(grid)
+    _need(occ, "occ", torch.uint8, shp)
+    out = out if out is not None else torch.empty_like(occ)
+    _need(out, "out", torch.uint8, shp)
+    g = _cgrid(grid)
+    _lib.check(_lib.load().pcdf_filter_voxels(ctypes.byref(g), _ptr(occ), int(min_neighbours), _ptr(out),
+                                              ctypes.c_void_p(_stream(occ.device))), "pcdf_filter_voxels")
+    return out
+
+
+def collapse_2d(occ: torch.Tensor, grid, z0: int, z1: int) -> torch.Tensor:
+    """Sec. 8 2-D map: uint8 [ny, nx], a column occupied iff one of its voxels
+    in slices [z0, z1) is."""
+    _need(occ, "occ", torch.uint8, _shape(grid))
+    out = torch.empty((grid.ny, grid.nx), dtype=torch.uint8, device=occ.device)
+    g = _cgrid(grid)
+    _lib.check(_lib.load().pcdf_collapse_2d(ctypes.byref(g), _ptr(occ), int(z0), int(z1), _ptr(out),
+                                            ctypes.c_void_p(_stream(occ.device))), "pcdf_collapse_2d")
+    return out
+
+
+def edt_2d(occ: torch.Tensor, grid, z0: int, z1: int, want_sdf: bool = True):
+    """The prediction module's 2-D EDT (Sec. 8): the signed squared EDT (and
+    float field) of the grid collapsed over slices [z0, z1).  Returns
+    (int32 [ny, nx], fp32 [ny, nx] or None)."""
+    c = collapse_2d(occ, grid, z0, z1)
+    g2 = Grid(grid.nx, grid.ny, 1, grid.vox, tuple(getattr(grid, "origin", (0.0, 0.0, 0.0))))
+    sq, sdf = build_static_sdf(c.view(1, grid.ny, grid.nx), g2, want_sdf=want_sdf)
+    return sq.view(grid.ny, grid.nx), (sdf.view(grid.ny, grid.nx) if sdf is not None else None)
+
+
 def build_predicted_composite(static_sq: torch.Tensor, grid, caps, want_sq: bool = True, want_sdf: bool = True,
                               out_sq=None, out_sdf=None, static_sdf=None):
     """Composite fields comp[t] = min(static, capsules at t) for t < T (Sec. 6, 8).
