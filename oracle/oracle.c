@@ -43,25 +43,31 @@
 
 #define OR_INF32 2147483647
 #define OR_BIG ((int64_t)1 << 60) /* "no site" marker inside the oracle */
+#define OR_CYLINDER (1 << 30)       /* radius-word flag: finite cylinder instead of capsule */
 
 /* ------------------------------------------------------------------------ */
 /* Capsule occupancy                                                         */
 /* ------------------------------------------------------------------------ */
 
 /* Is the fixed-point point p inside the closed capsule (segment a-b, radius r)?
+ * With the cylinder flag in the radius word: inside the closed finite
+ * cylinder of radius r around a-b, flat ends through a and b.
  * The squared distance from p to the segment is compared with r^2 exactly:
  *   projection parameter s = (p-a).(b-a), L = |b-a|^2;
  *   s <= 0 (or L == 0): nearest point is a;  s >= L: nearest point is b;
  *   otherwise |p-a|^2 - s^2/L <= r^2, multiplied through by L > 0. */
 int or_capsule_inside(int64_t px, int64_t py, int64_t pz, const int32_t *cap)
 {
+    const int cylinder = (cap[6] & OR_CYLINDER) != 0;
     const int64_t ax = cap[0], ay = cap[1], az = cap[2];
-    const int64_t bx = cap[3], by = cap[4], bz = cap[5], r = cap[6];
+    const int64_t bx = cap[3], by = cap[4], bz = cap[5], r = cap[6] & ~OR_CYLINDER;
     const int64_t wx = px - ax, wy = py - ay, wz = pz - az;
     const int64_t dx = bx - ax, dy = by - ay, dz = bz - az;
     const int64_t L = dx * dx + dy * dy + dz * dz;
     const int64_t s = wx * dx + wy * dy + wz * dz;
     const int64_t ww = wx * wx + wy * wy + wz * wz;
+    if (cylinder) /* closed finite cylinder (Sec. 6): 0 <= s <= L, distance to the line <= r */
+        return L > 0 && s >= 0 && s <= L && ww * L - s * s <= r * r * L;
     if (L == 0 || s <= 0)
         return ww <= r * r;
     if (s >= L) {

@@ -512,3 +512,72 @@ def test_collapse_and_2d_edt():
     dF = ndimage.distance_transform_edt(c == 1)
     want = np.where(c == 0, np.rint(dO ** 2), -np.rint(dF ** 2)).astype(np.int64)
     assert np.array_equal(S.astype(np.int64), want)
+
+
+# ---------------------------------------------------------------------------
+# cylinder primitive (Sec. 6's human primitive; radius-word flag)
+# ---------------------------------------------------------------------------
+
+CYL = 1 << 30
+
+
+def test_cylinder_predicate_upright_exact():
+    a, b, r = (104, 88, 24), (104, 88, 216), 40
+    cap = np.array([*a, *b, r | CYL], np.int32)
+    for k in range(16):
+        for j in range(12):
+            for i in range(14):
+                p = (16 * i + 8, 16 * j + 8, 16 * k + 8)
+                want = (p[0] - a[0]) ** 2 + (p[1] - a[1]) ** 2 <= r * r and a[2] <= p[2] <= b[2]
+                assert oracle.capsule_inside(p, cap) == want, (i, j, k)
+
+
+def test_cylinder_boundaries_and_caps():
+    cap = np.array([0, 0, 0, 0, 0, 160, 48 | CYL], np.int32)
+    capsule = np.array([0, 0, 0, 0, 0, 160, 48], np.int32)
+    assert oracle.capsule_inside((48, 0, 80), cap)          # on the side
+    assert not oracle.capsule_inside((48, 1, 80), cap)
+    assert oracle.capsule_inside((0, 0, 0), cap)            # on an end face
+    assert oracle.capsule_inside((30, 30, 160), cap)
+    assert not oracle.capsule_inside((0, 0, -1), cap)       # beyond the end: only the capsule holds it
+    assert oracle.capsule_inside((0, 0, -1), capsule)
+    assert not oracle.capsule_inside((0, 0, 161), cap)
+    zero = np.array([5, 5, 5, 5, 5, 5, 40 | CYL], np.int32)
+    assert not oracle.capsule_inside((5, 5, 5), zero)       # a zero-length axis holds nothing
+
+
+def test_cylinder_slanted_against_geometry_and_inside_capsule():
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        a = rng.integers(0, 400, 3)
+        b = a + rng.integers(-200, 200, 3)
+        r = int(rng.integers(8, 90))
+        cap = np.array([*a, *b, r | CYL], np.int32)
+        capsule = np.array([*a, *b, r], np.int32)
+        d = (b - a).astype(np.float64)
+        L = d @ d
+        for _ in range(300):
+            p = rng.integers(-100, 600, 3)
+            w = (p - a).astype(np.float64)
+            s = w @ d
+            dist2 = w @ w - s * s / L
+            inside = oracle.capsule_inside(tuple(int(v) for v in p), cap)
+            if inside:
+                assert oracle.capsule_inside(tuple(int(v) for v in p), capsule)
+            if abs(dist2 - r * r) > 1e-6 * r * r and min(abs(s), abs(s - L)) > 1e-9 * L:
+                assert inside == (0 <= s <= L and dist2 <= r * r)
+
+
+def test_cylinder_field_sandwich():
+    """EDT of the cylinder's voxels: an exterior voxel's distance is at least
+    its continuous distance to the solid (brute force on a small grid)."""
+    cap = np.array([[72, 72, 40, 72, 72, 200, 36 | CYL]], np.int32)
+    occ = oracle.capsule_occupancy((16, 10, 10), cap)
+    S = oracle.edt_brute(occ)
+    assert np.array_equal(S, oracle.edt(occ))
+    for k, j, i in np.argwhere(occ == 0)[::7]:
+        p = np.array([16 * i + 8, 16 * j + 8, 16 * k + 8], np.float64)
+        radial = max(np.hypot(p[0] - 72, p[1] - 72) - 36, 0.0)
+        axial = max(40 - p[2], p[2] - 200, 0.0)
+        cont = np.hypot(radial, axial) / 16.0
+        assert np.sqrt(S[k, j, i]) >= cont - 1e-9
