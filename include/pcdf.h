@@ -34,8 +34,10 @@
  *   measured from the grid corner, so the centre of voxel (i, j, k) is
  *   16 * (i, j, k) + 8.  A voxel belongs to the capsule iff its centre lies in
  *   the closed set of points within r of segment a-b (exact integer test).
- *   Coordinates must lie in [PCDF_CAP_MIN, PCDF_CAP_MAX] and 0 <= r <=
- *   PCDF_CAP_MAX_R.
+ *   With PCDF_CYLINDER set in the radius word the primitive is the closed
+ *   finite cylinder instead: points whose projection falls on the segment and
+ *   whose distance to its line is at most r.  Coordinates must lie in
+ *   [PCDF_CAP_MIN, PCDF_CAP_MAX] and 0 <= r <= PCDF_CAP_MAX_R.
  *
  *   Memory: device pointers are owned by the caller; the library keeps none
  *   past the call and allocates nothing.  Calls that need scratch take a
@@ -73,6 +75,10 @@ extern "C" {
 #define PCDF_CAP_MIN (-8192)
 #define PCDF_CAP_MAX 16384
 #define PCDF_CAP_MAX_R 8192
+/* OR-ed into a capsule's radius word: the primitive is the finite cylinder of
+ * radius r around segment a-b with flat ends at a and b (the paper's human
+ * primitive, Sec. 6) instead of the capsule; a != b is required. */
+#define PCDF_CYLINDER (1 << 30)
 
 typedef struct pcdf_grid {
     int32_t nx, ny, nz;

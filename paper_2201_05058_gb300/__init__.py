@@ -21,6 +21,7 @@ from .api import (  # noqa: F401
     build_from_scratch,
     build_predicted_composite,
     build_static_sdf,
+    CYLINDER,
     capsule_fixed,
     composite_finish,
     predicted_fields,

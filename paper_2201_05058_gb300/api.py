@@ -73,16 +73,25 @@ def _workspace(nbytes: int, dev) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
 
 
-def capsule_fixed(a_m, b_m, r_m, grid) -> np.ndarray:
+CYLINDER = 1 << 30  # radius-word flag of PCDF_CYLINDER
+
+
+def capsule_fixed(a_m, b_m, r_m, grid, cylinder: bool = False) -> np.ndarray:
     """Capsule(s) from metres to the library's 1/16-voxel fixed point.
 
-    a_m, b_m: [..., 3] segment end points (world metres); r_m: [...] radius.
-    Returns int32 [..., 7] (round half to even of (x - origin) / vox * 16)."""
+    a_m, b_m: [..., 3] segment end points (world metres); r_m: [...] radius
+    (per time step for a radius that grows over the horizon).  cylinder: the
+    finite cylinder with flat ends at a and b (the paper's primitive) instead
+    of the capsule.  Returns int32 [..., 7] (round half to even of
+    (x - origin) / vox * 16)."""
     o = np.asarray(getattr(grid, "origin", (0.0, 0.0, 0.0)), np.float64)
     a = np.rint((np.asarray(a_m, np.float64) - o) / grid.vox * 16.0)
     b = np.rint((np.asarray(b_m, np.float64) - o) / grid.vox * 16.0)
     r = np.rint(np.asarray(r_m, np.float64) / grid.vox * 16.0)[..., None]
-    return np.concatenate([a, b, r], axis=-1).astype(np.int32)
+    out = np.concatenate([a, b, r], axis=-1).astype(np.int32)
+    if cylinder:
+        out[..., 6] |= CYLINDER
+    return out
 
 
 # ---------------------------------------------------------------------------

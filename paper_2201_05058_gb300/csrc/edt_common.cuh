@@ -115,6 +115,8 @@ __device__ __forceinline__ bool capsule_contains(const CapInfo &c, int i, int j,
     const long long L = dx * dx + dy * dy + dz * dz;
     const long long s = wx * dx + wy * dy + wz * dz;
     const long long r2 = (long long)c.r * c.r;
+    if (c.cyl)  // projection on the segment, distance to the line at most r (L > 0)
+        return s >= 0 && s <= L && (wx * wx + wy * wy + wz * wz) * L - s * s <= r2 * L;
     if (L == 0 || s <= 0)
         return wx * wx + wy * wy + wz * wz <= r2;
     if (s >= L) {

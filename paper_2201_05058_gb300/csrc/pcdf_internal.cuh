@@ -22,7 +22,8 @@ struct alignas(16) CapInfo {
     int32_t r;
     int32_t lo[3];
     int32_t hi[3];
-    int32_t pad[3];
+    int32_t cyl;     // finite cylinder (flat ends) instead of a capsule
+    int32_t pad[2];
 };
 static_assert(sizeof(CapInfo) == 64, "CapInfo layout");
 

@@ -70,16 +70,22 @@ int make_capinfo(const pcdf_grid *g, int T, int H, const int32_t *caps, std::vec
             if (c[a] < PCDF_CAP_MIN || c[a] > PCDF_CAP_MAX)
                 return fail(PCDF_EINVAL, "capsule %lld coordinate %d = %d outside [%d, %d]", q, a, c[a],
                             PCDF_CAP_MIN, PCDF_CAP_MAX);
-        if (c[6] < 0 || c[6] > PCDF_CAP_MAX_R)
-            return fail(PCDF_EINVAL, "capsule %lld radius %d outside [0, %d]", q, c[6], PCDF_CAP_MAX_R);
+        const bool cyl = (c[6] & PCDF_CYLINDER) != 0;
+        const int32_t r = c[6] & ~PCDF_CYLINDER;
+        if (r < 0 || r > PCDF_CAP_MAX_R)
+            return fail(PCDF_EINVAL, "capsule %lld radius %d outside [0, %d]", q, r, PCDF_CAP_MAX_R);
+        if (cyl && c[0] == c[3] && c[1] == c[4] && c[2] == c[5])
+            return fail(PCDF_EINVAL, "cylinder %lld has a zero-length axis", q);
         pcdf::CapInfo &ci = out[q];
         std::memset(&ci, 0, sizeof(ci));
+        ci.cyl = cyl;
         bool empty = false;
         for (int a = 0; a < 3; ++a) {
             ci.a[a] = c[a];
             ci.b[a] = c[3 + a];
-            const long long mn = std::min(c[a], c[3 + a]) - (long long)c[6];
-            const long long mx = std::max(c[a], c[3 + a]) + (long long)c[6];
+            // the capsule's box also bounds the cylinder (a subset of it)
+            const long long mn = std::min(c[a], c[3 + a]) - (long long)r;
+            const long long mx = std::max(c[a], c[3 + a]) + (long long)r;
             long long lo = floordiv(mn - 8 + 15, 16);  // ceil((mn - 8) / 16)
             long long hi = floordiv(mx - 8, 16);
             lo = std::max(lo, 0LL);
@@ -88,7 +94,7 @@ int make_capinfo(const pcdf_grid *g, int T, int H, const int32_t *caps, std::vec
             ci.hi[a] = (int32_t)hi;
             empty |= lo > hi;
         }
-        ci.r = c[6];
+        ci.r = r;
         if (empty) {
             for (int a = 0; a < 3; ++a) {
                 ci.lo[a] = 1;

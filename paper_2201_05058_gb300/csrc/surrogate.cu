@@ -750,6 +750,9 @@ int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const floa
     int zlo = 0, zhi = -1;
     if (int rc = make_capinfo(grid, T, H, caps_host, ci, &zlo, &zhi))
         return rc;
+    for (const pcdf::CapInfo &c : ci)
+        if (c.cyl)
+            return fail(PCDF_EINVAL, "the surrogate models capsules only (a cylinder was given)");
     char *ws = (char *)workspace;
     int *count = (int *)ws;
     int *list = (int *)(ws + align_up(sizeof(int)));

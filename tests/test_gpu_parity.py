@@ -458,3 +458,40 @@ def test_update_to_host_chunks_equal_the_oracle():
         torch.cuda.synchronize()
         for t in range(T):
             assert_bits_equal(out_h[t].numpy(), oracle.sdf_from_sq(want[t], grid.vox), f"host field {t}")
+
+
+def test_cylinders_and_growing_radius():
+    """The paper's primitive (finite cylinder), mixed with capsules, with a
+    radius that grows over the horizon; composite, from-scratch and the
+    batched kernel against the oracle."""
+    grid = scenes.Grid(48, 44, 40, 0.05)
+    rng = np.random.default_rng(17)
+    occ, _ = scenes.boxes_occupancy(grid, 6, rng)
+    T = 5
+    a = np.array([[0.8 + 0.1 * t, 0.9, 0.25] for t in range(T)])
+    b = a + np.array([0.0, 0.0, 1.3])
+    r = 0.25 + 0.03 * np.arange(T)           # growing over the horizon
+    cyl = pcdf.capsule_fixed(a, b, r, grid, cylinder=True)
+    slanted = pcdf.capsule_fixed(a + [1.0, 0.7, 0.1], b + [1.3, 0.9, 0.0], r, grid, cylinder=True)
+    capsule = pcdf.capsule_fixed(a + [0.2, 1.2, 0.0], b + [0.2, 1.2, 0.0], r, grid)
+    caps = np.stack([cyl, slanted, capsule], axis=1)            # [T][3][7]
+    assert np.all(caps[:, :2, 6] & pcdf.CYLINDER)
+    check_composite(occ, caps, grid)
+    sq, _ = pcdf.build_from_scratch(cuda(occ), grid, caps, want_sdf=False)
+    want = oracle.from_scratch(occ, caps)
+    for t in range(T):
+        assert_equal_fields(sq[t].cpu().numpy(), want[t], f"scratch[{t}]")
+    b = pcdf.Batch([(grid, cuda(occ), caps)])
+    b.run()
+    assert b.error() == 0
+    comp = oracle.predicted_composite(oracle.edt(occ), caps)
+    assert np.array_equal(b.comp_sq[0].cpu().numpy(), comp)
+    b.close()
+    # the surrogate models capsules only
+    d = torch.device("cuda", 0)
+    static_sq, static_sdf = pcdf.build_static_sdf(cuda(occ), grid)
+    sph = torch.from_numpy(scenes.spheres_uniform(grid, 64, rng)).to(d)
+    tidx = torch.zeros(64, dtype=torch.int32, device=d)
+    y = torch.zeros(64 * 3, dtype=torch.float32, device=d)
+    with pytest.raises(RuntimeError):
+        pcdf.surrogate_finish(grid, static_sq, static_sdf, sph, tidx, T, caps, y, 0.2, 0.1)
