@@ -3,10 +3,10 @@
 //  k_voxel_filter  clears every occupied voxel with fewer than a given number
 //                  of occupied voxels among its 26 in-grid neighbours (the
 //                  paper clears voxels with fewer than five connected voxels).
-//                  A CTA owns a 32 x 8 tile of columns and a run of slices;
-//                  it stages one slice of the tile with its one-voxel halo at a
-//                  time in shared memory and keeps, per thread, the 3 x 3 sums
-//                  of the previous, current and next slice in registers.
+//                  A CTA owns a 32 x 8 tile of columns and 32 slices, staged
+//                  with their one-voxel halo in shared memory at once; each
+//                  thread then sweeps its column with the 3 x 3 sums of the
+//                  previous, current and next slice in registers.
 //  k_collapse      the 2-D map for the prediction module: a column is
 //                  occupied if any of its voxels in a slice range is.  Its EDT
 //                  is the static EDT of a grid one slice thick.
@@ -19,53 +19,52 @@ using namespace pcdf::host;
 namespace pcdf {
 namespace {
 
-constexpr int kFX = 32, kFY = 8, kFZ = 16;  // tile of a CTA: columns x, y; slices per CTA
+constexpr int kFX = 32, kFY = 8, kFZ = 32;  // tile of a CTA: columns x, y; slices per CTA
 constexpr int kHX = kFX + 2, kHY = kFY + 2;
 
+// The CTA stages its slices and their one-voxel halo (kFZ + 2 slices of
+// kHY x kHX bytes) with every load in flight at once, then each thread sweeps
+// its column keeping the 3 x 3 sums of three consecutive slices.
 __global__ void __launch_bounds__(kFX *kFY)
     k_voxel_filter(const uint8_t *__restrict__ occ, int nx, int ny, int nz, int min_n, uint8_t *__restrict__ out)
 {
-    __shared__ uint8_t plane[kHY][kHX];
+    __shared__ uint8_t tile[kFZ + 2][kHY][kHX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kFX + tx;
     const int x = blockIdx.x * kFX + tx, y = blockIdx.y * kFY + ty;
     const int z0 = blockIdx.z * kFZ, z1 = min(z0 + kFZ, nz);
     const long long V2 = (long long)nx * ny;
     const int x0 = blockIdx.x * kFX - 1, y0 = blockIdx.y * kFY - 1;
-
-    // 3 x 3 sum of slice z around (x, y) and the voxel itself (0 outside the grid)
-    auto slice = [&](int z, int &sum, int &self) {
-        __syncthreads();  // the previous slice has been read
-        for (int v = tid; v < kHX * kHY; v += kFX * kFY) {
-            const int hy = v / kHX, hx = v - hy * kHX;
-            const int gx = x0 + hx, gy = y0 + hy;
-            uint8_t o = 0;
-            if (z >= 0 && z < nz && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
-                o = __ldg(occ + z * V2 + (long long)gy * nx + gx) != 0;
-            plane[hy][hx] = o;
-        }
-        __syncthreads();
+    const int n = (z1 - z0 + 2) * kHY * kHX;
+    for (int v = tid; v < n; v += kFX * kFY) {
+        const int zz = v / (kHY * kHX), rem = v - zz * (kHY * kHX);
+        const int hy = rem / kHX, hx = rem - hy * kHX;
+        const int gx = x0 + hx, gy = y0 + hy, gz = z0 - 1 + zz;
+        uint8_t o = 0;
+        if (gz >= 0 && gz < nz && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+            o = __ldg(occ + gz * V2 + (long long)gy * nx + gx) != 0;
+        tile[zz][hy][hx] = o;
+    }
+    __syncthreads();
+    auto sum3 = [&](int zz) {
         int s = 0;
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx)
-                s += plane[ty + dy][tx + dx];
-        sum = s;
-        self = plane[ty + 1][tx + 1];
+                s += tile[zz][ty + dy][tx + dx];
+        return s;
     };
-
-    int s_prev, s_cur, s_next, o_prev, o_cur, o_next;
-    slice(z0 - 1, s_prev, o_prev);
-    slice(z0, s_cur, o_cur);
+    if (x >= nx || y >= ny)
+        return;  // no block-level synchronisation below
+    int s_prev = sum3(0), s_cur = sum3(1);
     for (int z = z0; z < z1; ++z) {
-        slice(z + 1, s_next, o_next);
-        if (x < nx && y < ny)
-            out[z * V2 + (long long)y * nx + x] = (uint8_t)(o_cur && s_prev + s_cur + s_next - 1 >= min_n);
+        const int zz = z - z0 + 1;
+        const int s_next = sum3(zz + 1);
+        const int o = tile[zz][ty + 1][tx + 1];
+        out[z * V2 + (long long)y * nx + x] = (uint8_t)(o && s_prev + s_cur + s_next - 1 >= min_n);
         s_prev = s_cur;
         s_cur = s_next;
-        o_cur = o_next;
     }
-    (void)o_prev;
 }
 
 __global__ void k_collapse(const uint8_t *__restrict__ occ, int nx, int ny, int z0, int z1,
