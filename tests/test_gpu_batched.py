@@ -111,3 +111,41 @@ def test_autotune_picks_a_candidate(batch_case):
     for e in range(len(envs)):
         assert np.array_equal(b.comp_sq[e].cpu().numpy(), want[e])
     b.close()
+
+
+def test_full_size_batch_matches_oracle_on_samples():
+    """The 64-environment batch at its full sizes (64-320 x 64-320 x 64-128,
+    T 5-30, 1-4 humans), in the launch configuration the benchmark times
+    (autotuned tiles, graph-captured run): whole fields of sampled
+    environments and time steps against the oracle, and voxels against the
+    definition."""
+    d = dev()
+    envs = scenes.scene_batch(seed=0)
+    dev_envs = [(e["grid"], torch.from_numpy(e["occ"]).to(d), e["caps"]) for e in envs]
+    tiles, _ = pcdf.batch_autotune(dev_envs, reps=1)
+    b = pcdf.Batch(dev_envs, tiles=tiles)
+    b.run()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run()
+    for f in b.comp_sq:
+        f.fill_(7)
+    g.replay()
+    torch.cuda.synchronize()
+    assert b.error() == 0
+    rng = np.random.default_rng(5)
+    largest = max(range(64), key=lambda e: envs[e]["grid"].nvox)
+    for e in sorted({largest, 0, 37}):
+        grid, occ, caps = envs[e]["grid"], envs[e]["occ"], envs[e]["caps"]
+        S = oracle.edt(occ)
+        T = caps.shape[0]
+        got = b.comp_sq[e].cpu().numpy()
+        for t in sorted({0, T - 1, int(rng.integers(0, T))}):
+            dyn_occ = oracle.capsule_occupancy(grid.shape, caps[t])
+            want = oracle.composite(S, oracle.edt(dyn_occ))
+            assert np.array_equal(got[t], want), f"environment {e}, t = {t}"
+            for _ in range(8):
+                k, j, i = (int(rng.integers(0, n)) for n in grid.shape)
+                assert got[t, k, j, i] == min(oracle.edt_at(occ, i, j, k), oracle.edt_at(dyn_occ, i, j, k))
+    b.close()
