@@ -388,9 +388,13 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
         pcdf.composite_prepare(grid, sc["caps"], cws)
         h, _, nfb = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band,
                                          err_bound=err_bound, comp_workspace=cws)
+        # the fallback band stated for this workload, 0.05 m
+        h05, _, nfb05 = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.05,
+                                             err_bound=err_bound, comp_workspace=cws)
         e = (d_pr - d_ex).abs()
         stats.append((float(e.max()), float(e.mean()), int(nfb.item()) / sph.numel() * 4,
-                      bool(torch.equal(h > 0, h_ex > 0)), int((h > 0).sum())))
+                      bool(torch.equal(h > 0, h_ex > 0)), int((h > 0).sum()),
+                      int(nfb05.item()) / sph.numel() * 4, int(((h05 > 0) != (h_ex > 0)).sum())))
     # timing on the last test scene: one plan step of 1M queries
     caps_dev = torch.from_numpy(np.ascontiguousarray(sc["caps"])).to(dev)
 
@@ -427,6 +431,9 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
             "train_s": t_train, "fields_s": t_fields, "loss_first": hist[0][1], "loss_last": hist[-1][1],
             "band_m": band, "err_bound_m": err_bound, "max_err_m": max(x[0] for x in stats), "mean_err_m": float(np.mean([x[1] for x in stats])),
             "fallback_frac": float(np.mean([x[2] for x in stats])), "decisions_identical": all(x[3] for x in stats),
+            "at_band_0_05_m": {"fallback_frac": float(np.mean([x[5] for x in stats])),
+                               "wrong_decisions": int(sum(x[6] for x in stats)),
+                               "queries": int(sph.numel() // 4 * len(stats))},
             "surrogate_ms": t_sur, "surrogate_local_search_ms": t_sur_local, "features_ms": t_feat,
             "rows_to_network_frac": x_sel.shape[0] / (sph.numel() // 4), "mlp_forward_selected_ms": t_mlp_sel,
             "mlp_infer_ms": t_inf, "mlp_infer_selected_ms": t_inf_sel,
