@@ -614,6 +614,29 @@ def run_native(args):
            "what": "H2D occupancy (pinned) + capsules, static + composite, D2H of the T float fields (pinned), "
                    "copies of finished 4-step chunks overlapping the next chunk's z pass"}
 
+    # a planner update: occupancy in from pinned host memory, the fields kept
+    # on the device, the hinge costs of a trajectory set (256 x 40 x 30
+    # spheres through the 256^3 room) computed there and read back
+    sph_p, tidx_p = scenes.spheres_along_paths(grid, 256, 40, 30, np.random.default_rng(45), T=T)
+    sph_pd = torch.from_numpy(sph_p).to(dev)
+    tid_pd = torch.from_numpy(tidx_p).to(dev)
+    h_host = torch.empty(tidx_p.shape, dtype=torch.float32).pin_memory()
+
+    def planner_step(_=None):
+        occ_d.copy_(occ_h, non_blocking=True)
+        pcdf.predicted_fields(occ_d, grid, caps, workspace=ws, out_static_sq=static_sq, out_static_sdf=static_sdf,
+                              out_sq=comp_sq, out_sdf=comp_sdf)
+        h_host.copy_(pcdf.query_cost(comp_sdf, grid, sph_pd, tid_pd, 0.2), non_blocking=True)
+
+    planner_step()
+    pl_ms, _ = timed(planner_step, k_e2e)
+    pl_total = slowest_rank_ms(float(sum(pl_ms)), world, dev)
+    e2e_planner = {"value": job_gvox_s(world, k_e2e, T, V, pl_total), "unit": "Gvox/s",
+                   "h2d_bytes_per_step": int(occ_h.numel() + caps.nbytes),
+                   "d2h_bytes_per_step": int(h_host.numel() * 4), "ms_per_step": pl_total / k_e2e,
+                   "what": "H2D occupancy (pinned) + capsules, static + composite kept on the device, hinge costs "
+                           "of 307,200 trajectory spheres on the 20 fields, D2H of the costs (pinned)"}
+
     batched = bench_batched(dev, rank_seed(args.seed, rank), args.steps) if not args.no_batched else None
     surrogate = bench_surrogate(dev, rank_seed(args.seed, rank)) if not args.no_surrogate else None
 
@@ -635,7 +658,7 @@ def run_native(args):
             "from_scratch": {"ms": scr_avg, "gvox_s": T * V / (scr_avg * 1e-3) / 1e9,
                              "composite_speedup": scr_avg / comp_avg},
             "query": query, "mapping": mapping, "batched": batched, "surrogate": surrogate, "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e,
+            "cpu_baseline": cpu, "e2e": e2e, "e2e_planner": e2e_planner,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
