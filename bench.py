@@ -415,6 +415,8 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
     t_mlp_sel = ev_time(lambda: net.forward(x_sel))
     t_inf = ev_time(lambda: net.infer(x_q))
     t_inf_sel = ev_time(lambda: net.infer(x_sel))
+    t_tc = ev_time(lambda: net.infer_tc(x_q))
+    t_tc_sel = ev_time(lambda: net.infer_tc(x_sel))
 
     def exact_composite():
         _, cs = pcdf.build_predicted_composite(st_sq, grid, sc["caps"], want_sq=False, static_sdf=st_sdf)
@@ -438,6 +440,8 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
             "rows_to_network_frac": x_sel.shape[0] / (sph.numel() // 4), "mlp_forward_selected_ms": t_mlp_sel,
             "mlp_infer_ms": t_inf, "mlp_infer_selected_ms": t_inf_sel,
             "mlp_infer_tflops": 2 * 136193 * sph.numel() / 4 / (t_inf * 1e-3) / 1e12,
+            "mlp_infer_tcgen05_ms": t_tc, "mlp_infer_tcgen05_selected_ms": t_tc_sel,
+            "mlp_infer_tcgen05_tflops": 2 * 136193 * sph.numel() / 4 / (t_tc * 1e-3) / 1e12,
             "mlp_forward_ms": t_mlp,
             "mlp_tflops": 2 * 136193 * sph.numel() / 4 / (t_mlp * 1e-3) / 1e12, "exact_composite_ms": t_comp, "exact_scratch_ms": t_scr,
             "speedup_vs_scratch": t_scr / t_sur, "speedup_vs_composite": t_comp / t_sur}

@@ -331,6 +331,15 @@ int pcdf_mlp_forward(const void *state, const uint16_t *x, int64_t M, float *y, 
  * bit-identical to it.  x device BF16 bits [M][16] (16-byte aligned), y
  * device fp32 [M]. */
 int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);
+
+/* pcdf_mlp_infer_tc  the same network on the 5th-generation tensor cores: one
+ * CTA per 128-row tile issues tcgen05.mma (BF16 operands in shared memory,
+ * FP32 accumulator in tensor memory), reads each layer back with tcgen05.ld
+ * for the bias, ReLU and BF16 rounding, and evaluates the head from tensor
+ * memory.  Same arithmetic up to the order of the FP32 sums (outputs within
+ * FP32 rounding of pcdf_mlp_infer, not bit-identical).  A tile whose
+ * bounded wait on the tensor cores expires (about a second) gets NaN. */
+int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);
 int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64_t M, float *y, float *loss,
                       void *workspace, size_t workspace_bytes, void *stream);
 int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, int32_t step, void *stream);

@@ -619,6 +619,16 @@ class SurrogateMLP:
                                             ctypes.c_void_p(_stream(self.device))), "pcdf_mlp_infer")
         return y
 
+    def infer_tc(self, x: torch.Tensor) -> torch.Tensor:
+        """forward on the tcgen05 tensor cores (FP32 accumulator in tensor
+        memory): y within FP32 rounding of forward.  x: CUDA bfloat16 [M, 16]."""
+        _need(x, "x", torch.bfloat16)
+        M = x.shape[0]
+        y = torch.empty(M, dtype=torch.float32, device=self.device)
+        _lib.check(self._lib.pcdf_mlp_infer_tc(_ptr(self.state), _ptr(x), M, _ptr(y),
+                                               ctypes.c_void_p(_stream(self.device))), "pcdf_mlp_infer_tc")
+        return y
+
     def backward(self, x: torch.Tensor, target: torch.Tensor):
         """Forward + loss + gradient (into the state).  Returns (y, loss[1])."""
         _need(x, "x", torch.bfloat16)
@@ -776,6 +786,6 @@ def surrogate_query(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps
         caps_dev = torch.from_numpy(caps).to(spheres.device)
     T = int(caps.shape[0])
     x, yi = surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev)
-    y = model.infer(x) if x.shape[0] else torch.empty(1, dtype=torch.float32, device=spheres.device)
+    y = model.infer_tc(x) if x.shape[0] else torch.empty(1, dtype=torch.float32, device=spheres.device)
     return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound,
                             comp_workspace, y_index=yi)

@@ -367,6 +367,262 @@ __global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ w
 }
 
 // ---------------------------------------------------------------------------
+// fused inference on the 5th-generation tensor cores (tcgen05 + TMEM)
+// ---------------------------------------------------------------------------
+// One CTA of 128 threads per 128-row tile.  Each layer is D[128 x 256] =
+// A[128 x K] B[256 x K]^T with D in tensor memory (256 fp32 columns, row r in
+// lane r): one thread issues tcgen05.mma (kind::f16, BF16 operands, FP32
+// accumulate) on operands in shared memory and commits to an mbarrier; the
+// four warps then read their 32 lanes back with tcgen05.ld, add the bias,
+// apply ReLU and store the BF16 activations as the next layer's A operand.
+// W2 and W3 pass through shared memory in 64-column chunks (cp.async).  The
+// head reads the last layer straight from tensor memory.
+//
+// Operand tiles use the canonical K-major layout without swizzling: 8 x 16
+// byte core matrices (8 rows of 8 BF16); element (r, k) of a tile with Kt
+// columns is at byte (r / 8) * Kt * 16 + (k / 8) * 128 + (r % 8) * 16 +
+// (k % 8) * 2, so K-adjacent core matrices are 128 bytes apart (leading byte
+// offset) and 8-row groups Kt * 16 bytes apart (stride byte offset).
+//
+// Waits on the mbarrier give up after about a second: the CTA then writes NaN
+// for its rows, and it frees its tensor memory on every path.
+namespace tc {
+
+constexpr int kM = 128, kThreads = 128, kKC = 64;
+constexpr uint32_t kCols = 256;
+constexpr uint32_t kBytesA = kM * kW * 2, kBytesB = kW * kKC * 2, kBytesX = kM * kIn * 2, kBytesW1 = kW * kIn * 2;
+constexpr size_t kSmem = 1024 + (size_t)kBytesA + kBytesB + kBytesX + kBytesW1;
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t kmaj(int r, int k, int Kt)
+{
+    return (uint32_t)((r >> 3) * Kt * 16 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start, leading and stride byte offsets (all
+// >> 4), the fixed 0b001 at bits 46-48, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16 (bits
+// 7-9 and 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kW >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kCols) : "memory");
+}
+
+// 32 consecutive fp32 columns of the calling thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity))
+        return true;
+    const uint64_t t0 = now_ns();
+    while (!mbar_try(bar, parity))
+        if (now_ns() - t0 > kWaitNs)
+            return false;
+    return true;
+}
+
+// relu(D + bias) of the thread's row as BF16 into the A operand tile
+__device__ __forceinline__ void epilogue(uint32_t tmem_row, const float *__restrict__ bias, unsigned char *sA, int r)
+{
+#pragma unroll 1
+    for (int c0 = 0; c0 < kW; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem_row + (uint32_t)c0, v);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            __align__(16) bf16 h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                h[j] = __float2bfloat16_rn(fmaxf(v[8 * g + j] + __ldg(bias + c0 + 8 * g + j), 0.f));
+            *reinterpret_cast<uint4 *>(sA + kmaj(r, c0 + 8 * g, kW)) = *reinterpret_cast<const uint4 *>(h);
+        }
+    }
+}
+
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    k_mlp_infer_tc(const bf16 *__restrict__ wh, const float *__restrict__ p, const bf16 *__restrict__ x, long long M,
+                   float *__restrict__ y)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t s_tmem;
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned operand area
+    unsigned char *sA = base, *sB = sA + tc::kBytesA, *sX = sB + tc::kBytesB, *sW1 = sX + tc::kBytesX;
+    const uint32_t aA = smem_u32(sA), aB = smem_u32(sB), aX = smem_u32(sX), aW1 = smem_u32(sW1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long m0 = (long long)blockIdx.x * tc::kM;
+    const bf16 *W1 = wh + hW1, *W2 = wh + hW2, *W3 = wh + hW3;
+
+    if (warp == 0)
+        tc::tmem_alloc(&s_tmem);
+    if (tid == 0)
+        tc::mbar_init(&bar);
+    // x tile (rows past M read as zeros) and W1, 16-byte pieces
+    for (int v = tid; v < tc::kM * 2; v += tc::kThreads) {
+        const int r = v >> 1, h = (v & 1) * 8;
+        const bool in = m0 + r < M;
+        cp16(sX + tc::kmaj(r, h, kIn), x + (in ? (m0 + r) * kIn + h : 0), in ? 16 : 0);
+    }
+    for (int v = tid; v < kW * 2; v += tc::kThreads) {
+        const int n = v >> 1, h = (v & 1) * 8;
+        cp16(sW1 + tc::kmaj(n, h, kIn), W1 + n * kIn + h, 16);
+    }
+    cp_commit();
+    cp_wait_all();
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+    const int r = tid;                                                  // row of the tile = TMEM lane
+    uint32_t phase = 0;
+    bool ok = true;
+
+    // layer 1: K = 16, one MMA
+    if (tid == 0) {
+        tc::mma(tmem, tc::sdesc(aX, 128, kIn * 16), tc::sdesc(aW1, 128, kIn * 16), 0u);
+        tc::commit(&bar);
+    }
+    ok = __syncthreads_and(tc::mbar_wait(&bar, phase));  // the same verdict in every thread
+    phase ^= 1u;
+    tc::fence_after();
+    if (ok)
+        tc::epilogue(tmem_row, p + oB1, sA, r);
+
+    for (int layer = 2; layer <= 3 && ok; ++layer) {
+        const bf16 *W = layer == 2 ? W2 : W3;
+        // the A tile is written and every lane of D has been read
+        tc::fence_proxy_async();
+        tc::fence_before();
+        __syncthreads();
+        for (int c = 0; c < kW / tc::kKC && ok; ++c) {
+            for (int v = tid; v < kW * (tc::kKC / 8); v += tc::kThreads) {
+                const int n = v / (tc::kKC / 8), q = (v % (tc::kKC / 8)) * 8;
+                cp16(sB + tc::kmaj(n, q, tc::kKC), W + n * kW + c * tc::kKC + q, 16);
+            }
+            cp_commit();
+            cp_wait_all();
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after();
+#pragma unroll
+                for (int kk = 0; kk < tc::kKC / 16; ++kk) {
+                    const int k0 = c * tc::kKC + kk * 16;
+                    tc::mma(tmem, tc::sdesc(aA + (uint32_t)(k0 / 8) * 128u, 128, kW * 16),
+                            tc::sdesc(aB + (uint32_t)(kk * 2) * 128u, 128, tc::kKC * 16), (c | kk) != 0);
+                }
+                tc::commit(&bar);
+            }
+            ok = tc::mbar_wait(&bar, phase);  // this chunk's products are done: sB may be refilled
+            phase ^= 1u;
+            ok = __syncthreads_and(ok);
+        }
+        tc::fence_after();
+        if (!ok)
+            break;
+        if (layer == 2) {
+            tc::epilogue(tmem_row, p + oB2, sA, r);
+        } else {
+            // head: relu(D + b3) rounded to BF16 (as stored between layers), then . w4 + b4
+            float acc = 0.f;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kW; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tmem_row + (uint32_t)c0, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float hv = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + __ldg(p + oB3 + c0 + j), 0.f)));
+                    acc = fmaf(hv, __bfloat162float(wh[hW4 + c0 + j]), acc);
+                }
+            }
+            if (m0 + r < M)
+                y[m0 + r] = acc + p[oB4];
+        }
+    }
+    if (!ok) {
+        // a wait expired: give the products in flight another bounded wait
+        // before the tensor memory is freed; this tile has no answer
+        (void)tc::mbar_wait(&bar, phase ^ 1u);
+        if (m0 + r < M)
+            y[m0 + r] = __int_as_float(0x7fc00000);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // output layer, loss, bias gradients, Adam, initialisation
 // ---------------------------------------------------------------------------
 constexpr int kHeadRows = 64;  // rows per CTA of k_head (8 warps x 8 rows)
@@ -712,6 +968,27 @@ int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, vo
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp inference");
+}
+
+int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y, void *stream)
+{
+    if (!state || (M > 0 && (!x || !y)))
+        return fail(PCDF_EINVAL, "state, x and y must be non-NULL");
+    if (M < 0 || M > (1LL << 31) - 1)
+        return fail(PCDF_EINVAL, "M out of range");
+    if (M == 0)
+        return PCDF_OK;
+    if (!aligned(x, 16) || !aligned(state, kAlign))
+        return fail(PCDF_EINVAL, "x must be 16-byte aligned, state %zu-byte aligned", kAlign);
+    State S(const_cast<void *>(state));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmem);
+    if (e == cudaSuccess) {
+        k_mlp_infer_tc<<<(unsigned)((M + tc::kM - 1) / tc::kM), tc::kThreads, tc::kSmem, st>>>(S.h, S.p,
+                                                                                               (const bf16 *)x, M, y);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp inference (tcgen05)");
 }
 
 int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64_t M, float *y, float *loss,

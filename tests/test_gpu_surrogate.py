@@ -55,6 +55,13 @@ def test_mlp_forward_and_gradients_match_oracle(M):
     assert torch.equal(y2, y)
     assert torch.equal(net.infer(x), y)
     assert torch.equal(net.infer(x[: M - 7]), y[: M - 7])
+    # the tcgen05 kernel: the same network up to the order of the FP32 sums
+    y_tc = net.infer_tc(x)
+    assert not torch.isnan(y_tc).any()
+    assert torch.allclose(y_tc, y, rtol=0, atol=1e-5 * max(1.0, float(y.abs().max())))
+    assert np.max(np.abs(y_tc.cpu().double().numpy() - want_y)) <= 2e-2 * max(1.0, np.max(np.abs(want_y)))
+    y_tc2 = net.infer_tc(x[: M - 7])
+    assert torch.allclose(y_tc2, y[: M - 7], rtol=0, atol=1e-5 * max(1.0, float(y.abs().max())))
 
 
 def test_adam_step():
