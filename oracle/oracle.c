@@ -10,8 +10,9 @@
  * of the method (Sec. 6 "Mapping - Predicted Composite Distance Fields" and
  * the GPMP2 obstacle factor of Sec. 7):
  *
- *   - capsule occupancy: exact int64 point-to-segment test.  The paper's human
- *     primitive is a cylinder (Sec. 6); this build reads it as a capsule.
+ *   - capsule occupancy: exact int64 point-to-segment test, and the paper's
+ *     own human primitive, the finite cylinder (Sec. 6), selected by a flag
+ *     in the radius word.
  *   - signed squared Euclidean distance transform (EDT), by its definition
  *     (brute-force minimum over all in-grid voxels of the opposite state) and
  *     by the separable lower-envelope algorithm of Meijster, Roerdink and
