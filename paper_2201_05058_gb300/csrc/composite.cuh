@@ -216,15 +216,11 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
         // rows before the column's occupied range, the range (skipping its
         // occupied rows, which set F wrote), rows after it
         const int ya = min(fo, ny), yb = lo_ >= 0 ? lo_ + 1 : ny;
-#pragma unroll 4
-        for (int y = 0; y < ya; ++y)
-            oc[(long long)y * nx] = O.eval(y);
+        O.fill(0, ya, oc, nx);
         for (int y = ya; y < yb; ++y)
             if (!row_inside(rows + y * rw, x))
                 oc[(long long)y * nx] = O.eval(y);
-#pragma unroll 4
-        for (int y = yb; y < ny; ++y)
-            oc[(long long)y * nx] = O.eval(y);
+        O.fill(yb, ny, oc, nx);
     }
 }
 

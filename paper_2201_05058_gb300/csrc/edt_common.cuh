@@ -70,6 +70,51 @@ struct EnvCursor {
         }
         return fc;
     }
+    __device__ __forceinline__ bool next_wins(int z) const { return q < top && parab(z, sn, gn) <= parab(z, s, g); }
+    __device__ __forceinline__ void advance()
+    {
+        ++q;
+        s = sn;
+        g = gn;
+        if (q < top) {
+            const uint32_t w = stk[(q + 1) * stride];
+            sn = site_of(w);
+            gn = gval_of(w);
+        }
+    }
+    // out[z * ostride] = eval(z) for z = z0 .. z1 - 1 (the envelope non-empty),
+    // taking the same choices as eval without re-evaluating both parabolas
+    // at every z: with f the current and f' the next parabola, f'(z) - f(z)
+    // falls by 2 (sn - s) per step, so the next site takes over when that
+    // running difference is no longer positive; f itself advances by
+    // 2 (z - s) + 1.
+    __device__ __forceinline__ void fill(int z0, int z1, int32_t *out, long long ostride)
+    {
+        if (z0 >= z1)
+            return;
+        int z = z0;
+        while (next_wins(z))
+            advance();
+        int fc = parab(z, s, g), inc = 2 * (z - s) + 1;
+        int delta = q < top ? parab(z, sn, gn) - fc : INT32_MAX, dd = q < top ? 2 * (sn - s) : 0;
+        int32_t *p = out + (long long)z * ostride;
+        for (; z < z1; ++z) {
+            if (delta <= 0) {
+                advance();
+                while (next_wins(z))
+                    advance();
+                fc = parab(z, s, g);
+                inc = 2 * (z - s) + 1;
+                delta = q < top ? parab(z, sn, gn) - fc : INT32_MAX;
+                dd = q < top ? 2 * (sn - s) : 0;
+            }
+            *p = fc;
+            p += ostride;
+            fc += inc;
+            inc += 2;
+            delta -= dd;
+        }
+    }
 };
 
 // Push site (e, g) onto a stack kept in shared memory (entry q at
