@@ -336,7 +336,9 @@ int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, vo
  * CTA per 128-row tile issues tcgen05.mma (BF16 operands in shared memory,
  * FP32 accumulator in tensor memory), reads each layer back with tcgen05.ld
  * for the bias, ReLU and BF16 rounding, and evaluates the head from tensor
- * memory.  Same arithmetic up to the order of the FP32 sums (outputs within
+ * memory.  The hidden weights stream through an 8-stage ring of bulk copies
+ * from a packed copy in the state that pcdf_mlp_init and pcdf_mlp_adam keep
+ * current (the state is only read here).  Same arithmetic up to the order of the FP32 sums (outputs within
  * FP32 rounding of pcdf_mlp_infer, not bit-identical).  A tile whose
  * bounded wait on the tensor cores expires (about a second) gets NaN. */
 int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);

@@ -43,8 +43,10 @@ static_assert(kP == PCDF_MLP_PARAMS, "parameter count");
 static_assert(kH == PCDF_MLP_BF16_WEIGHTS, "bf16 weight count");
 
 // state layout (bytes): master, adam m, adam v, grad (FP32 [kPpad] each), bf16 weights
+// then the hidden BF16 weights again, packed for the tensor-core kernel
 constexpr size_t sMaster = 0, sM = 4 * kPpad, sV = 8 * kPpad, sGrad = 12 * kPpad, sHalf = 16 * kPpad,
-                 kStateBytes = sHalf + 2 * kH;
+                 sPack = (sHalf + 2 * kH + 255) / 256 * 256, kPackElems = 2LL * kW * kW,
+                 kStateBytes = sPack + 2 * kPackElems;
 
 using bf16 = __nv_bfloat16;
 
@@ -369,14 +371,20 @@ __global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ w
 // ---------------------------------------------------------------------------
 // fused inference on the 5th-generation tensor cores (tcgen05 + TMEM)
 // ---------------------------------------------------------------------------
-// One CTA of 128 threads per 128-row tile.  Each layer is D[128 x 256] =
-// A[128 x K] B[256 x K]^T with D in tensor memory (256 fp32 columns, row r in
-// lane r): one thread issues tcgen05.mma (kind::f16, BF16 operands, FP32
-// accumulate) on operands in shared memory and commits to an mbarrier; the
-// four warps then read their 32 lanes back with tcgen05.ld, add the bias,
-// apply ReLU and store the BF16 activations as the next layer's A operand.
-// W2 and W3 pass through shared memory in 64-column chunks (cp.async).  The
+// One CTA of 128 threads per SM-resident 128-row tile.  Each layer is
+// D[128 x 256] = A[128 x K] B[256 x K]^T with D in tensor memory (256 fp32
+// columns, row r in lane r): one thread issues tcgen05.mma (kind::f16, BF16
+// operands in shared memory, FP32 accumulate) and commits to mbarriers; the
+// four warps read their 32 lanes back with tcgen05.ld, add the bias, apply
+// ReLU and store the BF16 activations as the next layer's A operand.  The
 // head reads the last layer straight from tensor memory.
+//
+// W2 and W3 are pre-packed (k_pack_hidden) into 16 chunks of 32 columns, each
+// laid out exactly as the B operand in shared memory, so one bulk copy moves
+// a chunk.  An 8-stage ring keeps the copies ahead of the products: the issuing
+// thread refills the stage of chunk c - 1 with chunk c + 7 as soon as the
+// products of chunk c - 1 have committed, so up to eight chunks are in flight
+// while the tensor cores work.
 //
 // Operand tiles use the canonical K-major layout without swizzling: 8 x 16
 // byte core matrices (8 rows of 8 BF16); element (r, k) of a tile with Kt
@@ -384,15 +392,17 @@ __global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ w
 // (k % 8) * 2, so K-adjacent core matrices are 128 bytes apart (leading byte
 // offset) and 8-row groups Kt * 16 bytes apart (stride byte offset).
 //
-// Waits on the mbarrier give up after about a second: the CTA then writes NaN
-// for its rows, and it frees its tensor memory on every path.
+// Every mbarrier wait gives up after about a second: the CTA then writes NaN
+// for its rows, gives the operations it issued a second bounded wait, and
+// frees its tensor memory on every path.
 namespace tc {
 
-constexpr int kM = 128, kThreads = 128, kKC = 64;
+constexpr int kM = 128, kThreads = 128, kKC = 32, kStages = 8, kChunks = 2 * (kW / kKC);
 constexpr uint32_t kCols = 256;
-constexpr uint32_t kBytesA = kM * kW * 2, kBytesB = kW * kKC * 2, kBytesX = kM * kIn * 2, kBytesW1 = kW * kIn * 2;
-constexpr size_t kSmem = 1024 + (size_t)kBytesA + kBytesB + kBytesX + kBytesW1;
+constexpr uint32_t kBytesA = kM * kW * 2, kBytesChunk = kW * kKC * 2, kBytesX = kM * kIn * 2, kBytesW1 = kW * kIn * 2;
+constexpr size_t kSmem = 1024 + (size_t)kBytesA + (size_t)kStages * kBytesChunk + kBytesX + kBytesW1;
 constexpr uint64_t kWaitNs = 1000000000ull;
+static_assert(kChunks == 2 * kStages, "the ring refills each stage once");
 
 __device__ __forceinline__ uint32_t kmaj(int r, int k, int Kt)
 {
@@ -455,7 +465,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 __device__ __forceinline__ void mbar_init(uint64_t *bar)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// one arrival expecting `bytes` of copy completions, then the bulk copy
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
 {
@@ -504,25 +524,56 @@ __device__ __forceinline__ void epilogue(uint32_t tmem_row, const float *__restr
 
 }  // namespace tc
 
+// W2 and W3 into the chunked B-operand layout: chunk j (layer j / 8, columns
+// 32 (j % 8) ..) holds element (n, k) at tc::kmaj(n, k, 32) / 2
+__global__ void k_pack_hidden(const bf16 *__restrict__ wh, bf16 *__restrict__ packed)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte piece
+    if (v >= 2 * kW * (kW / 8))
+        return;
+    const int l = v / (kW * (kW / 8)), rem = v % (kW * (kW / 8));
+    const int n = rem / (kW / 8), kq = rem % (kW / 8);
+    const bf16 *W = wh + (l == 0 ? hW2 : hW3);
+    const int k = kq * 8, chunk = l * (kW / tc::kKC) + k / tc::kKC;
+    bf16 *dst = packed + (long long)chunk * (kW * tc::kKC) + tc::kmaj(n, k % tc::kKC, tc::kKC) / 2;
+    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(W + n * kW + k);
+}
+
 __global__ void __launch_bounds__(tc::kThreads, 1)
-    k_mlp_infer_tc(const bf16 *__restrict__ wh, const float *__restrict__ p, const bf16 *__restrict__ x, long long M,
-                   float *__restrict__ y)
+    k_mlp_infer_tc(const bf16 *__restrict__ wh, const float *__restrict__ p, const bf16 *__restrict__ packed,
+                   const bf16 *__restrict__ x, long long M, float *__restrict__ y)
 {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t bar;
+    __shared__ uint64_t full[tc::kStages], done[tc::kStages], l1bar;
     __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned operand area
-    unsigned char *sA = base, *sB = sA + tc::kBytesA, *sX = sB + tc::kBytesB, *sW1 = sX + tc::kBytesX;
-    const uint32_t aA = smem_u32(sA), aB = smem_u32(sB), aX = smem_u32(sX), aW1 = smem_u32(sW1);
+    unsigned char *sA = base, *sRing = sA + tc::kBytesA, *sX = sRing + tc::kStages * tc::kBytesChunk,
+                  *sW1 = sX + tc::kBytesX;
+    const uint32_t aA = smem_u32(sA), aRing = smem_u32(sRing), aX = smem_u32(sX), aW1 = smem_u32(sW1);
     const int tid = threadIdx.x, warp = tid >> 5;
     const long long m0 = (long long)blockIdx.x * tc::kM;
-    const bf16 *W1 = wh + hW1, *W2 = wh + hW2, *W3 = wh + hW3;
+    auto issue = [&](int c) {  // chunk c into stage c % kStages
+        const int st = c % tc::kStages;
+        tc::bulk_load(sRing + st * tc::kBytesChunk, packed + (long long)c * (kW * tc::kKC), tc::kBytesChunk,
+                      &full[st]);
+    };
+    int copies = 0;  // chunks issued (thread 0)
 
     if (warp == 0)
         tc::tmem_alloc(&s_tmem);
-    if (tid == 0)
-        tc::mbar_init(&bar);
+    if (tid == 0) {
+        for (int s2 = 0; s2 < tc::kStages; ++s2) {
+            tc::mbar_init(&full[s2]);
+            tc::mbar_init(&done[s2]);
+        }
+        tc::mbar_init(&l1bar);
+        tc::fence_mbar_init();
+        s_fail = 0;
+        for (; copies < tc::kStages; ++copies)
+            issue(copies);
+    }
     // x tile (rows past M read as zeros) and W1, 16-byte pieces
     for (int v = tid; v < tc::kM * 2; v += tc::kThreads) {
         const int r = v >> 1, h = (v & 1) * 8;
@@ -531,7 +582,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     }
     for (int v = tid; v < kW * 2; v += tc::kThreads) {
         const int n = v >> 1, h = (v & 1) * 8;
-        cp16(sW1 + tc::kmaj(n, h, kIn), W1 + n * kIn + h, 16);
+        cp16(sW1 + tc::kmaj(n, h, kIn), wh + hW1 + n * kIn + h, 16);
     }
     cp_commit();
     cp_wait_all();
@@ -542,65 +593,72 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     const uint32_t tmem = s_tmem;
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
     const int r = tid;                                                  // row of the tile = TMEM lane
-    uint32_t phase = 0;
-    bool ok = true;
+    int mma_chunks = 0;                                                 // chunks whose products were issued (thread 0)
 
-    // layer 1: K = 16, one MMA
+    // layer 1: K = 16, one product
     if (tid == 0) {
         tc::mma(tmem, tc::sdesc(aX, 128, kIn * 16), tc::sdesc(aW1, 128, kIn * 16), 0u);
-        tc::commit(&bar);
+        tc::commit(&l1bar);
     }
-    ok = __syncthreads_and(tc::mbar_wait(&bar, phase));  // the same verdict in every thread
-    phase ^= 1u;
+    bool ok = __syncthreads_and(tc::mbar_wait(&l1bar, 0));
     tc::fence_after();
     if (ok)
         tc::epilogue(tmem_row, p + oB1, sA, r);
 
-    for (int layer = 2; layer <= 3 && ok; ++layer) {
-        const bf16 *W = layer == 2 ? W2 : W3;
+    for (int layer = 0; layer < 2 && ok; ++layer) {
         // the A tile is written and every lane of D has been read
         tc::fence_proxy_async();
         tc::fence_before();
         __syncthreads();
-        for (int c = 0; c < kW / tc::kKC && ok; ++c) {
-            for (int v = tid; v < kW * (tc::kKC / 8); v += tc::kThreads) {
-                const int n = v / (tc::kKC / 8), q = (v % (tc::kKC / 8)) * 8;
-                cp16(sB + tc::kmaj(n, q, tc::kKC), W + n * kW + c * tc::kKC + q, 16);
-            }
-            cp_commit();
-            cp_wait_all();
-            tc::fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after();
+        const int c0 = layer * tc::kStages, c1 = c0 + tc::kStages;
+        if (tid == 0) {
+            tc::fence_after();
+            for (int c = c0; c < c1; ++c) {
+                const int st = c % tc::kStages;
+                if (!tc::mbar_wait(&full[st], (uint32_t)(c / tc::kStages) & 1u)) {
+                    s_fail = 1;
+                    break;
+                }
 #pragma unroll
                 for (int kk = 0; kk < tc::kKC / 16; ++kk) {
-                    const int k0 = c * tc::kKC + kk * 16;
+                    const int k0 = (c % tc::kStages) * tc::kKC + kk * 16;
                     tc::mma(tmem, tc::sdesc(aA + (uint32_t)(k0 / 8) * 128u, 128, kW * 16),
-                            tc::sdesc(aB + (uint32_t)(kk * 2) * 128u, 128, tc::kKC * 16), (c | kk) != 0);
+                            tc::sdesc(aRing + (uint32_t)(st * tc::kBytesChunk + kk * 256), 128, tc::kKC * 16),
+                            (c % tc::kStages) != 0 || kk != 0);
                 }
-                tc::commit(&bar);
+                tc::commit(&done[st]);
+                mma_chunks = c + 1;
+                // the products of chunk c - 1 are done with its stage: refill it
+                const int cp = c - 1;
+                if (cp >= 0 && cp + tc::kStages < tc::kChunks) {
+                    if (!tc::mbar_wait(&done[cp % tc::kStages], (uint32_t)(cp / tc::kStages) & 1u)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    issue(copies++);
+                }
             }
-            ok = tc::mbar_wait(&bar, phase);  // this chunk's products are done: sB may be refilled
-            phase ^= 1u;
-            ok = __syncthreads_and(ok);
         }
+        // every thread waits for the layer's last products
+        const int last = c1 - 1;
+        bool w = tc::mbar_wait(&done[last % tc::kStages], (uint32_t)(last / tc::kStages) & 1u);
+        ok = __syncthreads_and(w) && !s_fail;
         tc::fence_after();
         if (!ok)
             break;
-        if (layer == 2) {
+        if (layer == 0) {
             tc::epilogue(tmem_row, p + oB2, sA, r);
         } else {
             // head: relu(D + b3) rounded to BF16 (as stored between layers), then . w4 + b4
             float acc = 0.f;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kW; c0 += 32) {
+            for (int c = 0; c < kW; c += 32) {
                 float v[32];
-                tc::tmem_ld32(tmem_row + (uint32_t)c0, v);
+                tc::tmem_ld32(tmem_row + (uint32_t)c, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float hv = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + __ldg(p + oB3 + c0 + j), 0.f)));
-                    acc = fmaf(hv, __bfloat162float(wh[hW4 + c0 + j]), acc);
+                    const float hv = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + __ldg(p + oB3 + c + j), 0.f)));
+                    acc = fmaf(hv, __bfloat162float(wh[hW4 + c + j]), acc);
                 }
             }
             if (m0 + r < M)
@@ -608,9 +666,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         }
     }
     if (!ok) {
-        // a wait expired: give the products in flight another bounded wait
-        // before the tensor memory is freed; this tile has no answer
-        (void)tc::mbar_wait(&bar, phase ^ 1u);
+        // a wait expired: give what was issued a second bounded wait before the
+        // tensor memory is freed (the last copies and the last commit; products
+        // complete in order); this tile has no answer
+        if (tid == 0) {
+            (void)tc::mbar_wait(&l1bar, 0);
+            for (int c = copies - tc::kStages > 0 ? copies - tc::kStages : 0; c < copies; ++c)
+                (void)tc::mbar_wait(&full[c % tc::kStages], (uint32_t)(c / tc::kStages) & 1u);
+            if (mma_chunks > 0)
+                (void)tc::mbar_wait(&done[(mma_chunks - 1) % tc::kStages], (uint32_t)((mma_chunks - 1) / tc::kStages) & 1u);
+        }
         if (m0 + r < M)
             y[m0 + r] = __int_as_float(0x7fc00000);
     }
@@ -787,7 +852,7 @@ __global__ void k_init(float *__restrict__ p, float *__restrict__ mo, float *__r
 // ---------------------------------------------------------------------------
 struct State {
     float *p, *m, *v, *g;
-    bf16 *h;
+    bf16 *h, *pk;  // BF16 weights; W2 and W3 packed for the tensor-core kernel
     explicit State(void *s)
     {
         char *b = (char *)s;
@@ -796,8 +861,17 @@ struct State {
         v = (float *)(b + sV);
         g = (float *)(b + sGrad);
         h = (bf16 *)(b + sHalf);
+        pk = (bf16 *)(b + sPack);
     }
 };
+
+// refreshes the packed copy of W2 and W3 after the BF16 weights change
+__global__ void k_pack_hidden(const bf16 *__restrict__ wh, bf16 *__restrict__ packed);
+cudaError_t launch_pack(const State &S, cudaStream_t st)
+{
+    k_pack_hidden<<<(2 * kW * (kW / 8) + 255) / 256, 256, 0, st>>>(S.h, S.pk);
+    return cudaGetLastError();
+}
 
 struct Acts {
     bf16 *H1, *H2, *H3, *dA, *dB;
@@ -923,6 +997,8 @@ int pcdf_mlp_init(void *state, uint64_t seed, void *stream)
         k_init<<<(unsigned)((kP + 255) / 256), 256, 0, st>>>(S.p, S.m, S.v, S.h, (unsigned long long)seed);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess)
+        e = launch_pack(S, st);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp init");
 }
 
@@ -984,8 +1060,8 @@ int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y,
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmem);
     if (e == cudaSuccess) {
-        k_mlp_infer_tc<<<(unsigned)((M + tc::kM - 1) / tc::kM), tc::kThreads, tc::kSmem, st>>>(S.h, S.p,
-                                                                                               (const bf16 *)x, M, y);
+        k_mlp_infer_tc<<<(unsigned)((M + tc::kM - 1) / tc::kM), tc::kThreads, tc::kSmem, st>>>(
+            S.h, S.p, S.pk, (const bf16 *)x, M, y);
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp inference (tcgen05)");
@@ -1051,6 +1127,8 @@ int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, in
     cudaStream_t st = (cudaStream_t)stream;
     k_adam<<<(unsigned)((kP + 255) / 256), 256, 0, st>>>(S.p, S.m, S.v, S.g, S.h, lr, beta1, beta2, eps, c1, c2);
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_pack(S, st);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp adam");
 }
 

@@ -84,6 +84,14 @@ def test_adam_step():
     # the BF16 copy follows the master copy
     half = net._bf16()
     assert torch.equal(half[4096:4096 + 65536], p1[4352:4352 + 65536].to(torch.bfloat16))
+    # the tensor-core kernel reads the packed copy of W2 and W3, which the
+    # step refreshed: it still agrees with the fused kernel after training
+    for _ in range(3):
+        net.backward(x, t)
+        net.adam(1e-2)
+    y = net.infer(x)
+    y_tc = net.infer_tc(x)
+    assert torch.allclose(y_tc, y, rtol=0, atol=1e-5 * max(1.0, float(y.abs().max())))
 
 
 def scene_set(seeds, grid_only=False):
