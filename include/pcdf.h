@@ -332,15 +332,18 @@ int pcdf_mlp_forward(const void *state, const uint16_t *x, int64_t M, float *y, 
  * device fp32 [M]. */
 int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);
 
-/* pcdf_mlp_infer_tc  the same network on the 5th-generation tensor cores: one
- * CTA per 128-row tile issues tcgen05.mma (BF16 operands in shared memory,
- * FP32 accumulator in tensor memory), reads each layer back with tcgen05.ld
- * for the bias, ReLU and BF16 rounding, and evaluates the head from tensor
- * memory.  The hidden weights stream through an 8-stage ring of bulk copies
- * from a packed copy in the state that pcdf_mlp_init and pcdf_mlp_adam keep
- * current (the state is only read here).  Same arithmetic up to the order of the FP32 sums (outputs within
- * FP32 rounding of pcdf_mlp_infer, not bit-identical).  A tile whose
- * bounded wait on the tensor cores expires (about a second) gets NaN. */
+/* pcdf_mlp_infer_tc  the same network on the 5th-generation tensor cores: a
+ * persistent kernel (one CTA per SM) walks 128-row tiles; one thread issues
+ * tcgen05.mma (BF16 operands in shared memory, FP32 accumulators in tensor
+ * memory), a producer warp streams the x tiles and the hidden weights (bulk
+ * copies from a packed copy in the state that pcdf_mlp_init and
+ * pcdf_mlp_adam keep current; the state is only read here), and eight
+ * epilogue warps read each layer back with tcgen05.ld for the bias, ReLU and
+ * BF16 rounding, overlapping the next layer's products.  Same arithmetic up
+ * to the order of the FP32 sums (outputs within FP32 rounding of
+ * pcdf_mlp_infer, not bit-identical).  A tile whose bounded wait on the
+ * tensor cores expires (about a second) gets NaN, as do the CTA's later
+ * tiles. */
 int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);
 int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64_t M, float *y, float *loss,
                       void *workspace, size_t workspace_bytes, void *stream);

@@ -371,20 +371,16 @@ __global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ w
 // ---------------------------------------------------------------------------
 // fused inference on the 5th-generation tensor cores (tcgen05 + TMEM)
 // ---------------------------------------------------------------------------
-// One CTA of 128 threads per SM-resident 128-row tile.  Each layer is
-// D[128 x 256] = A[128 x K] B[256 x K]^T with D in tensor memory (256 fp32
-// columns, row r in lane r): one thread issues tcgen05.mma (kind::f16, BF16
-// operands in shared memory, FP32 accumulate) and commits to mbarriers; the
-// four warps read their 32 lanes back with tcgen05.ld, add the bias, apply
-// ReLU and store the BF16 activations as the next layer's A operand.  The
-// head reads the last layer straight from tensor memory.
+// Each layer of a 128-row tile is D[128 x 256] = A[128 x K] B[256 x K]^T with
+// D in tensor memory (256 fp32 columns, row r in lane r): one thread issues
+// tcgen05.mma (kind::f16, BF16 operands in shared memory, FP32 accumulate)
+// and commits to mbarriers; the epilogue warps read the accumulator back with
+// tcgen05.ld, add the bias, apply ReLU and store the BF16 activations as the
+// next layer's A operand.  The head reads the last layer from tensor memory.
 //
 // W2 and W3 are pre-packed (k_pack_hidden) into 16 chunks of 32 columns, each
 // laid out exactly as the B operand in shared memory, so one bulk copy moves
-// a chunk.  An 8-stage ring keeps the copies ahead of the products: the issuing
-// thread refills the stage of chunk c - 1 with chunk c + 7 as soon as the
-// products of chunk c - 1 have committed, so up to eight chunks are in flight
-// while the tensor cores work.
+// a chunk.
 //
 // Operand tiles use the canonical K-major layout without swizzling: 8 x 16
 // byte core matrices (8 rows of 8 BF16); element (r, k) of a tile with Kt
@@ -393,16 +389,12 @@ __global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ w
 // offset) and 8-row groups Kt * 16 bytes apart (stride byte offset).
 //
 // Every mbarrier wait gives up after about a second: the CTA then writes NaN
-// for its rows, gives the operations it issued a second bounded wait, and
-// frees its tensor memory on every path.
+// for its remaining rows, gives the operations it issued a second bounded
+// wait, and frees its tensor memory on every path.
 namespace tc {
 
-constexpr int kM = 128, kThreads = 128, kKC = 32, kStages = 8, kChunks = 2 * (kW / kKC);
-constexpr uint32_t kCols = 256;
-constexpr uint32_t kBytesA = kM * kW * 2, kBytesChunk = kW * kKC * 2, kBytesX = kM * kIn * 2, kBytesW1 = kW * kIn * 2;
-constexpr size_t kSmem = 1024 + (size_t)kBytesA + (size_t)kStages * kBytesChunk + kBytesX + kBytesW1;
+constexpr int kM = 128, kKC = 32;  // tile rows; K columns of a packed weight chunk
 constexpr uint64_t kWaitNs = 1000000000ull;
-static_assert(kChunks == 2 * kStages, "the ring refills each stage once");
 
 __device__ __forceinline__ uint32_t kmaj(int r, int k, int Kt)
 {
@@ -438,15 +430,15 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst)
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t cols)
 {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(kCols)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr)
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols)
 {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
 }
 
 // 32 consecutive fp32 columns of the calling thread's lane
@@ -462,9 +454,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
         v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar)
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count = 1)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 // one arrival expecting `bytes` of copy completions, then the bulk copy
@@ -504,24 +500,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return true;
 }
 
-// relu(D + bias) of the thread's row as BF16 into the A operand tile
-__device__ __forceinline__ void epilogue(uint32_t tmem_row, const float *__restrict__ bias, unsigned char *sA, int r)
-{
-#pragma unroll 1
-    for (int c0 = 0; c0 < kW; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem_row + (uint32_t)c0, v);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            __align__(16) bf16 h[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                h[j] = __float2bfloat16_rn(fmaxf(v[8 * g + j] + __ldg(bias + c0 + 8 * g + j), 0.f));
-            *reinterpret_cast<uint4 *>(sA + kmaj(r, c0 + 8 * g, kW)) = *reinterpret_cast<const uint4 *>(h);
-        }
-    }
-}
-
 }  // namespace tc
 
 // W2 and W3 into the chunked B-operand layout: chunk j (layer j / 8, columns
@@ -539,50 +517,106 @@ __global__ void k_pack_hidden(const bf16 *__restrict__ wh, bf16 *__restrict__ pa
     *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(W + n * kW + k);
 }
 
-__global__ void __launch_bounds__(tc::kThreads, 1)
-    k_mlp_infer_tc(const bf16 *__restrict__ wh, const float *__restrict__ p, const bf16 *__restrict__ packed,
-                   const bf16 *__restrict__ x, long long M, float *__restrict__ y)
+// ---------------------------------------------------------------------------
+// The kernel is persistent and warp-specialised: one CTA per SM walks its
+// 128-row tiles with three roles working concurrently on mbarriers
+//   warp 0 (one thread)  issues the products and commits;
+//   warp 1               producer: the x tiles (double-buffered) and the
+//                        packed W2/W3 chunks through the 8-stage ring;
+//   warps 2..9           epilogue: warp w reads TMEM lanes 32 (w % 4) .. and,
+//                        in group (w - 2) / 4, every second 32-column chunk.
+// Tensor memory holds two 256-column accumulators; the layers of the CTA's
+// tiles (q = 3 * tile + layer) alternate between them, so the epilogue of
+// layer q overlaps the products of layer q + 1: chunk j of layer q + 1 is
+// issued as soon as the epilogue has written chunk j of its A operand
+// (barrier aready[j]), and an accumulator is overwritten only after every
+// epilogue thread has read it (accempty).  The head sums each group's
+// columns and the groups are added in a fixed order.
+// ---------------------------------------------------------------------------
+namespace ws {
+constexpr int kStages = 8, kEpiWarps = 8, kGroups = kEpiWarps / 4, kThreads = 32 * (2 + kEpiWarps);
+constexpr uint32_t kCols = 512;
+constexpr uint32_t kBytesA = 128 * kW * 2, kBytesChunk = kW * 32 * 2, kBytesX = 128 * kIn * 2, kBytesW1 = kW * kIn * 2;
+constexpr uint32_t oA = 0, oRing = oA + kBytesA, oX = oRing + kStages * kBytesChunk, oW1 = oX + 2 * kBytesX,
+                   oBias = oW1 + kBytesW1, oW4 = oBias + 3 * kW * 4, oPart = oW4 + kW * 4,
+                   kEnd = oPart + 2 * kGroups * 128 * 4;
+constexpr size_t kSmem = 1024 + (size_t)kEnd;
+static_assert(kSmem <= 227 * 1024, "shared memory");
+static_assert(kEpiWarps % 4 == 0 && (8 % kGroups) == 0, "epilogue warps cover the four lane quarters");
+
+// lane 0's value for every lane of the (converged) warp, through the warp's
+// own shared slot, so that the warp takes every branch as a whole
+__device__ __forceinline__ int warp_uniform(int v, volatile int *slot, int lane)
+{
+    if (lane == 0)
+        *slot = v;
+    __syncwarp();
+    const int u = *slot;
+    __syncwarp();
+    return u;
+}
+// a bounded wait taken by lane 0 on behalf of the warp
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *slot, int lane)
+{
+    return warp_uniform(lane == 0 ? (int)tc::mbar_wait(bar, parity) : 0, slot, lane) != 0;
+}
+}  // namespace ws
+
+// two floats rounded to BF16 (nearest even), low half first
+__device__ __forceinline__ uint32_t bf2_bits(float lo, float hi)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__global__ void __launch_bounds__(ws::kThreads, 1)
+    k_mlp_infer_ws(const bf16 *__restrict__ wh, const float *__restrict__ p, const bf16 *__restrict__ packed,
+                   const bf16 *__restrict__ x, long long M, long long ntiles, float *__restrict__ y)
 {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t full[tc::kStages], done[tc::kStages], l1bar;
+    __shared__ uint64_t full[ws::kStages], empty[ws::kStages], xfull[2], xempty[2], accfull[2], accempty[2],
+        aready[8], partfull[2], drain;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_fail;
+    __shared__ volatile int s_fail;
+    __shared__ volatile int s_slot[2 + ws::kEpiWarps];
     const uint32_t raw = smem_u32(smem_raw);
-    unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned operand area
-    unsigned char *sA = base, *sRing = sA + tc::kBytesA, *sX = sRing + tc::kStages * tc::kBytesChunk,
-                  *sW1 = sX + tc::kBytesX;
+    unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    unsigned char *sA = base + ws::oA, *sRing = base + ws::oRing, *sX = base + ws::oX, *sW1 = base + ws::oW1;
+    float *sBias = reinterpret_cast<float *>(base + ws::oBias), *sW4 = reinterpret_cast<float *>(base + ws::oW4),
+          *sPart = reinterpret_cast<float *>(base + ws::oPart);
     const uint32_t aA = smem_u32(sA), aRing = smem_u32(sRing), aX = smem_u32(sX), aW1 = smem_u32(sW1);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const long long m0 = (long long)blockIdx.x * tc::kM;
-    auto issue = [&](int c) {  // chunk c into stage c % kStages
-        const int st = c % tc::kStages;
-        tc::bulk_load(sRing + st * tc::kBytesChunk, packed + (long long)c * (kW * tc::kKC), tc::kBytesChunk,
-                      &full[st]);
-    };
-    int copies = 0;  // chunks issued (thread 0)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0)
-        tc::tmem_alloc(&s_tmem);
+        tc::tmem_alloc(&s_tmem, ws::kCols);
     if (tid == 0) {
-        for (int s2 = 0; s2 < tc::kStages; ++s2) {
-            tc::mbar_init(&full[s2]);
-            tc::mbar_init(&done[s2]);
+        for (int i = 0; i < ws::kStages; ++i) {
+            tc::mbar_init(&full[i]);
+            tc::mbar_init(&empty[i]);
         }
-        tc::mbar_init(&l1bar);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&xfull[i], 32);
+            tc::mbar_init(&xempty[i]);
+            tc::mbar_init(&accfull[i]);
+            tc::mbar_init(&accempty[i], ws::kEpiWarps * 32);
+            tc::mbar_init(&partfull[i], ws::kEpiWarps * 32);
+        }
+        for (int j = 0; j < 8; ++j)
+            tc::mbar_init(&aready[j], 128);
+        tc::mbar_init(&drain);
         tc::fence_mbar_init();
         s_fail = 0;
-        for (; copies < tc::kStages; ++copies)
-            issue(copies);
     }
-    // x tile (rows past M read as zeros) and W1, 16-byte pieces
-    for (int v = tid; v < tc::kM * 2; v += tc::kThreads) {
-        const int r = v >> 1, h = (v & 1) * 8;
-        const bool in = m0 + r < M;
-        cp16(sX + tc::kmaj(r, h, kIn), x + (in ? (m0 + r) * kIn + h : 0), in ? 16 : 0);
-    }
-    for (int v = tid; v < kW * 2; v += tc::kThreads) {
+    // W1, the biases and the head weights
+    for (int v = tid; v < kW * 2; v += ws::kThreads) {
         const int n = v >> 1, h = (v & 1) * 8;
         cp16(sW1 + tc::kmaj(n, h, kIn), wh + hW1 + n * kIn + h, 16);
+    }
+    for (int i = tid; i < kW; i += ws::kThreads) {
+        sBias[i] = p[oB1 + i];
+        sBias[kW + i] = p[oB2 + i];
+        sBias[2 * kW + i] = p[oB3 + i];
+        sW4[i] = __bfloat162float(wh[hW4 + i]);
     }
     cp_commit();
     cp_wait_all();
@@ -591,99 +625,198 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
-    const int r = tid;                                                  // row of the tile = TMEM lane
-    int mma_chunks = 0;                                                 // chunks whose products were issued (thread 0)
+    const float b4 = p[oB4];
 
-    // layer 1: K = 16, one product
-    if (tid == 0) {
-        tc::mma(tmem, tc::sdesc(aX, 128, kIn * 16), tc::sdesc(aW1, 128, kIn * 16), 0u);
-        tc::commit(&l1bar);
-    }
-    bool ok = __syncthreads_and(tc::mbar_wait(&l1bar, 0));
-    tc::fence_after();
-    if (ok)
-        tc::epilogue(tmem_row, p + oB1, sA, r);
-
-    for (int layer = 0; layer < 2 && ok; ++layer) {
-        // the A tile is written and every lane of D has been read
-        tc::fence_proxy_async();
-        tc::fence_before();
-        __syncthreads();
-        const int c0 = layer * tc::kStages, c1 = c0 + tc::kStages;
-        if (tid == 0) {
-            tc::fence_after();
-            for (int c = c0; c < c1; ++c) {
-                const int st = c % tc::kStages;
-                if (!tc::mbar_wait(&full[st], (uint32_t)(c / tc::kStages) & 1u)) {
-                    s_fail = 1;
+    if (warp == 0) {
+        // ---- products -----------------------------------------------------
+        if (lane == 0) {
+            long long g = 0;  // chunks consumed
+            bool ok = true;
+            int it = 0;
+            for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+                const int b = it & 1;
+                const long long q1 = 3LL * it;
+                ok = tc::mbar_wait(&xfull[b], (uint32_t)(it >> 1) & 1u) &&
+                     (q1 < 2 || tc::mbar_wait(&accempty[q1 & 1], (uint32_t)((q1 - 2) >> 1) & 1u));
+                if (!ok)
                     break;
-                }
+                tc::fence_after();
+                tc::mma(tmem + (uint32_t)(q1 & 1) * 256u, tc::sdesc(aX + b * ws::kBytesX, 128, kIn * 16),
+                        tc::sdesc(aW1, 128, kIn * 16), 0u);
+                tc::commit(&xempty[b]);
+                tc::commit(&accfull[q1 & 1]);
+                for (int L = 1; L <= 2 && ok; ++L) {
+                    const long long q = q1 + L;
+                    const uint32_t dcol = tmem + (uint32_t)(q & 1) * 256u;
+                    if (q >= 2 && !tc::mbar_wait(&accempty[q & 1], (uint32_t)((q - 2) >> 1) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t aph = (uint32_t)(2 * it + L - 1) & 1u;
+                    for (int j = 0; j < 8; ++j, ++g) {
+                        const int st = (int)(g % ws::kStages);
+                        if (!tc::mbar_wait(&full[st], (uint32_t)(g / ws::kStages) & 1u) ||
+                            !tc::mbar_wait(&aready[j], aph)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after();
 #pragma unroll
-                for (int kk = 0; kk < tc::kKC / 16; ++kk) {
-                    const int k0 = (c % tc::kStages) * tc::kKC + kk * 16;
-                    tc::mma(tmem, tc::sdesc(aA + (uint32_t)(k0 / 8) * 128u, 128, kW * 16),
-                            tc::sdesc(aRing + (uint32_t)(st * tc::kBytesChunk + kk * 256), 128, tc::kKC * 16),
-                            (c % tc::kStages) != 0 || kk != 0);
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const int k0 = 32 * j + 16 * kk;
+                            tc::mma(dcol, tc::sdesc(aA + (uint32_t)(k0 / 8) * 128u, 128, kW * 16),
+                                    tc::sdesc(aRing + (uint32_t)(st * ws::kBytesChunk + kk * 256), 128, 32 * 16),
+                                    (uint32_t)(j | kk));
+                        }
+                        tc::commit(&empty[st]);
+                    }
+                    if (ok)
+                        tc::commit(&accfull[q & 1]);
                 }
-                tc::commit(&done[st]);
-                mma_chunks = c + 1;
-                // the products of chunk c - 1 are done with its stage: refill it
-                const int cp = c - 1;
-                if (cp >= 0 && cp + tc::kStages < tc::kChunks) {
-                    if (!tc::mbar_wait(&done[cp % tc::kStages], (uint32_t)(cp / tc::kStages) & 1u)) {
+                if (s_fail)
+                    ok = false;
+            }
+            if (!ok)
+                s_fail = 1;
+            // every product issued has finished before the tensor memory is freed
+            tc::commit(&drain);
+            (void)tc::mbar_wait(&drain, 0);
+        }
+    } else if (warp == 1) {
+        // ---- producer -----------------------------------------------------
+        volatile int *slot = s_slot + 1;
+        long long g = 0;  // chunks issued (lane 0)
+        int it = 0;
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int b = it & 1;
+            int stop = 0;
+            if (lane == 0) {
+                stop = s_fail;
+                if (!stop && it >= 2 && !tc::mbar_wait(&xempty[b], (uint32_t)((it >> 1) - 1) & 1u))
+                    stop = s_fail = 1;
+            }
+            if (ws::warp_uniform(stop, slot, lane))
+                break;
+            const long long m0 = tile * 128;
+            unsigned char *xb = sX + b * ws::kBytesX;
+#pragma unroll
+            for (int v = lane; v < 256; v += 32) {
+                const int r = v >> 1, h = (v & 1) * 8;
+                uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                if (m0 + r < M)
+                    val = __ldg(reinterpret_cast<const uint4 *>(x + (m0 + r) * kIn + h));
+                *reinterpret_cast<uint4 *>(xb + tc::kmaj(r, h, kIn)) = val;
+            }
+            tc::fence_proxy_async();
+            tc::mbar_arrive(&xfull[b]);
+            if (lane == 0) {
+                for (int c = 0; c < 16; ++c, ++g) {
+                    const int st = (int)(g % ws::kStages);
+                    if (g >= ws::kStages && !tc::mbar_wait(&empty[st], (uint32_t)(g / ws::kStages - 1) & 1u)) {
                         s_fail = 1;
                         break;
                     }
-                    issue(copies++);
+                    tc::bulk_load(sRing + st * ws::kBytesChunk, packed + (long long)c * (kW * 32), ws::kBytesChunk,
+                                  &full[st]);
                 }
             }
         }
-        // every thread waits for the layer's last products
-        const int last = c1 - 1;
-        bool w = tc::mbar_wait(&done[last % tc::kStages], (uint32_t)(last / tc::kStages) & 1u);
-        ok = __syncthreads_and(w) && !s_fail;
-        tc::fence_after();
-        if (!ok)
-            break;
-        if (layer == 0) {
-            tc::epilogue(tmem_row, p + oB2, sA, r);
-        } else {
-            // head: relu(D + b3) rounded to BF16 (as stored between layers), then . w4 + b4
-            float acc = 0.f;
-#pragma unroll 1
-            for (int c = 0; c < kW; c += 32) {
-                float v[32];
-                tc::tmem_ld32(tmem_row + (uint32_t)c, v);
+        if (lane == 0) {
+            // copies still in flight are among the last kStages issued
+            for (long long c = g > ws::kStages ? g - ws::kStages : 0; c < g; ++c)
+                (void)tc::mbar_wait(&full[c % ws::kStages], (uint32_t)(c / ws::kStages) & 1u);
+        }
+    } else {
+        // ---- epilogue -----------------------------------------------------
+        const int quarter = warp & 3, group = (warp - 2) >> 2;
+        const int r = quarter * 32 + lane;
+        volatile int *slot = s_slot + warp;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        int it = 0;
+        long long tile = blockIdx.x;
+        bool ok = true;
+        for (; tile < ntiles; tile += gridDim.x, ++it) {
+            const long long m0 = tile * 128;
+            for (int L = 0; L < 3 && ok; ++L) {
+                const long long q = 3LL * it + L;
+                const int a = (int)(q & 1);
+                if (!ws::warp_wait(&accfull[a], (uint32_t)(q >> 1) & 1u, slot, lane)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t tb = tmem + (uint32_t)a * 256u + lane_off;
+                if (L < 2) {
+                    const float *bias = sBias + L * kW;
+                    for (int j = group; j < 8; j += ws::kGroups) {
+                        float v[32];
+                        tc::tmem_ld32(tb + (uint32_t)(32 * j), v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float hv = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + __ldg(p + oB3 + c + j), 0.f)));
-                    acc = fmaf(hv, __bfloat162float(wh[hW4 + c + j]), acc);
+                        for (int gq = 0; gq < 4; ++gq) {
+                            const float4 b0 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq);
+                            const float4 b1 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq + 4);
+                            const float *u = v + 8 * gq;
+                            uint4 pk;
+                            pk.x = bf2_bits(fmaxf(u[0] + b0.x, 0.f), fmaxf(u[1] + b0.y, 0.f));
+                            pk.y = bf2_bits(fmaxf(u[2] + b0.z, 0.f), fmaxf(u[3] + b0.w, 0.f));
+                            pk.z = bf2_bits(fmaxf(u[4] + b1.x, 0.f), fmaxf(u[5] + b1.y, 0.f));
+                            pk.w = bf2_bits(fmaxf(u[6] + b1.z, 0.f), fmaxf(u[7] + b1.w, 0.f));
+                            *reinterpret_cast<uint4 *>(sA + tc::kmaj(r, 32 * j + 8 * gq, kW)) = pk;
+                        }
+                        tc::fence_proxy_async();
+                        tc::fence_before();
+                        tc::mbar_arrive(&aready[j]);
+                    }
+                    tc::mbar_arrive(&accempty[a]);
+                } else {
+                    // head: relu(D + b3) rounded to BF16 (as stored between layers), . w4
+                    float acc = 0.f;
+                    for (int j = group; j < 8; j += ws::kGroups) {
+                        float v[32];
+                        tc::tmem_ld32(tb + (uint32_t)(32 * j), v);
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int c = 32 * j + e;
+                            const float hv = __bfloat162float(__float2bfloat16_rn(fmaxf(v[e] + sBias[2 * kW + c], 0.f)));
+                            acc = fmaf(hv, sW4[c], acc);
+                        }
+                    }
+                    tc::fence_before();
+                    tc::mbar_arrive(&accempty[a]);
+                    float *part = sPart + (it & 1) * (ws::kGroups * 128);
+                    part[group * 128 + r] = acc;
+                    tc::mbar_arrive(&partfull[it & 1]);
+                    if (group == 0) {
+                        if (!ws::warp_wait(&partfull[it & 1], (uint32_t)(it >> 1) & 1u, slot, lane)) {
+                            ok = false;
+                            break;
+                        }
+                        float sum = 0.f;
+#pragma unroll
+                        for (int g2 = 0; g2 < ws::kGroups; ++g2)
+                            sum += part[g2 * 128 + r];
+                        if (m0 + r < M)
+                            y[m0 + r] = sum + b4;
+                    }
                 }
             }
-            if (m0 + r < M)
-                y[m0 + r] = acc + p[oB4];
+            if (!ok || ws::warp_uniform(s_fail, slot, lane))
+                break;
         }
-    }
-    if (!ok) {
-        // a wait expired: give what was issued a second bounded wait before the
-        // tensor memory is freed (the last copies and the last commit; products
-        // complete in order); this tile has no answer
-        if (tid == 0) {
-            (void)tc::mbar_wait(&l1bar, 0);
-            for (int c = copies - tc::kStages > 0 ? copies - tc::kStages : 0; c < copies; ++c)
-                (void)tc::mbar_wait(&full[c % tc::kStages], (uint32_t)(c / tc::kStages) & 1u);
-            if (mma_chunks > 0)
-                (void)tc::mbar_wait(&done[(mma_chunks - 1) % tc::kStages], (uint32_t)((mma_chunks - 1) / tc::kStages) & 1u);
+        if (!ok || ws::warp_uniform(s_fail, slot, lane)) {
+            s_fail = 1;
+            // this tile and the CTA's later ones have no answer
+            if (group == 0)
+                for (; tile < ntiles; tile += gridDim.x)
+                    if (tile * 128 + r < M)
+                        y[tile * 128 + r] = __int_as_float(0x7fc00000);
         }
-        if (m0 + r < M)
-            y[m0 + r] = __int_as_float(0x7fc00000);
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
         tc::fence_after();
-        tc::tmem_dealloc(tmem);
+        tc::tmem_dealloc(tmem, ws::kCols);
     }
 }
 
@@ -1058,10 +1191,17 @@ int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y,
         return fail(PCDF_EINVAL, "x must be 16-byte aligned, state %zu-byte aligned", kAlign);
     State S(const_cast<void *>(state));
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmem);
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp_infer_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws::kSmem);
     if (e == cudaSuccess) {
-        k_mlp_infer_tc<<<(unsigned)((M + tc::kM - 1) / tc::kM), tc::kThreads, tc::kSmem, st>>>(
-            S.h, S.p, S.pk, (const bf16 *)x, M, y);
+        // persistent: one CTA per SM (or per tile, if fewer)
+        const long long ntiles = (M + 127) / 128;
+        k_mlp_infer_ws<<<(unsigned)(ntiles < nsm ? ntiles : nsm), ws::kThreads, ws::kSmem, st>>>(
+            S.h, S.p, S.pk, (const bf16 *)x, M, ntiles, y);
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp inference (tcgen05)");
