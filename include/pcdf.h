@@ -345,6 +345,12 @@ int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, vo
  * tensor cores expires (about a second) gets NaN, as do the CTA's later
  * tiles. */
 int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);
+/* pcdf_mlp_infer_tc_count  pcdf_mlp_infer_tc over the first *count rows of x
+ * (count: device int32, read by the kernel, clamped to [0, M_max]), so that
+ * a row count produced on the device (pcdf_surrogate_select) needs no host
+ * round trip; x and y hold M_max rows, y past the count is left unwritten. */
+int pcdf_mlp_infer_tc_count(const void *state, const uint16_t *x, int64_t M_max, const int32_t *count, float *y,
+                            void *stream);
 int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64_t M, float *y, float *loss,
                       void *workspace, size_t workspace_bytes, void *stream);
 int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, int32_t step, void *stream);

@@ -40,7 +40,7 @@ EXPORTS = (
     "pcdf_batch_create", "pcdf_batch_destroy", "pcdf_batch_workspace_bytes", "pcdf_batch_tiles_used",
     "pcdf_batch_upload", "pcdf_batch_run", "pcdf_batch_error", "pcdf_batch_autotune_workspace_bytes",
     "pcdf_batch_autotune",
-    "pcdf_mlp_state_bytes", "pcdf_mlp_workspace_bytes", "pcdf_mlp_init", "pcdf_mlp_forward", "pcdf_mlp_infer", "pcdf_mlp_infer_tc",
+    "pcdf_mlp_state_bytes", "pcdf_mlp_workspace_bytes", "pcdf_mlp_init", "pcdf_mlp_forward", "pcdf_mlp_infer", "pcdf_mlp_infer_tc", "pcdf_mlp_infer_tc_count",
     "pcdf_mlp_backward",
     "pcdf_mlp_adam", "pcdf_surrogate_samples", "pcdf_surrogate_features", "pcdf_surrogate_finish_workspace_bytes",
     "pcdf_surrogate_finish", "pcdf_surrogate_finish_slab", "pcdf_surrogate_select",
@@ -92,6 +92,7 @@ def _declare(lib):
         "pcdf_mlp_forward": [P, P, I64, P, P, SZ, P],
         "pcdf_mlp_infer": [P, P, I64, P, P],
         "pcdf_mlp_infer_tc": [P, P, I64, P, P],
+        "pcdf_mlp_infer_tc_count": [P, P, I64, P, P, P],
         "pcdf_mlp_backward": [P, P, P, I64, P, P, P, SZ, P],
         "pcdf_mlp_adam": [P, F32, F32, F32, F32, I32, P],
         "pcdf_surrogate_samples": [G, P, P, P, I32, I32, I64, U64, F32, P, P, P],

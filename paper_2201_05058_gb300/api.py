@@ -619,14 +619,22 @@ class SurrogateMLP:
                                             ctypes.c_void_p(_stream(self.device))), "pcdf_mlp_infer")
         return y
 
-    def infer_tc(self, x: torch.Tensor) -> torch.Tensor:
+    def infer_tc(self, x: torch.Tensor, count: torch.Tensor = None) -> torch.Tensor:
         """forward on the tcgen05 tensor cores (FP32 accumulator in tensor
-        memory): y within FP32 rounding of forward.  x: CUDA bfloat16 [M, 16]."""
+        memory): y within FP32 rounding of forward.  x: CUDA bfloat16 [M, 16].
+        count: optional CUDA int32 [1]; then only the first count rows are
+        computed (read on the device, no host synchronisation) and y past
+        them is left unwritten."""
         _need(x, "x", torch.bfloat16)
         M = x.shape[0]
         y = torch.empty(M, dtype=torch.float32, device=self.device)
-        _lib.check(self._lib.pcdf_mlp_infer_tc(_ptr(self.state), _ptr(x), M, _ptr(y),
-                                               ctypes.c_void_p(_stream(self.device))), "pcdf_mlp_infer_tc")
+        st = ctypes.c_void_p(_stream(self.device))
+        if count is None:
+            _lib.check(self._lib.pcdf_mlp_infer_tc(_ptr(self.state), _ptr(x), M, _ptr(y), st), "pcdf_mlp_infer_tc")
+        else:
+            _need(count, "count", torch.int32)
+            _lib.check(self._lib.pcdf_mlp_infer_tc_count(_ptr(self.state), _ptr(x), M, _ptr(count), _ptr(y), st),
+                       "pcdf_mlp_infer_tc_count")
         return y
 
     def backward(self, x: torch.Tensor, target: torch.Tensor):
@@ -721,9 +729,11 @@ def surrogate_features(grid, spheres, tidx, T, caps_dev):
     return x
 
 
-def surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev):
+def surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev, sync=True):
     """Rows the network must answer (the others cannot beat the static field
-    in their cell).  Returns (x BF16 [kept rows][16], y_index int32 [N * H])."""
+    in their cell).  Returns (x BF16 [kept rows][16], y_index int32 [N * H]);
+    with sync=False no host synchronisation: (x BF16 [N * H][16] whose first
+    count rows are the kept ones, y_index, count int32 [1] on the device)."""
     N = spheres.numel() // 4
     H = int(caps_dev.shape[1])
     dev = spheres.device
@@ -736,6 +746,8 @@ def surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev):
     _lib.check(_lib.load().pcdf_surrogate_select(ctypes.byref(g), _ptr(static_sdf), _ptr(spheres), _ptr(tidx), N,
                                                  int(T), H, _ptr(caps_dev), _ptr(x), _ptr(yi), _ptr(cnt),
                                                  ctypes.c_void_p(_stream(dev))), "pcdf_surrogate_select")
+    if not sync:
+        return x, yi, cnt
     return x[: int(cnt.item())], yi
 
 
@@ -785,7 +797,8 @@ def surrogate_query(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps
     if caps_dev is None:
         caps_dev = torch.from_numpy(caps).to(spheres.device)
     T = int(caps.shape[0])
-    x, yi = surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev)
-    y = model.infer_tc(x) if x.shape[0] else torch.empty(1, dtype=torch.float32, device=spheres.device)
+    # select -> network -> finish with the kept-row count on the device
+    x, yi, cnt = surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev, sync=False)
+    y = model.infer_tc(x, count=cnt) if x.shape[0] else torch.empty(1, dtype=torch.float32, device=spheres.device)
     return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound,
                             comp_workspace, y_index=yi)

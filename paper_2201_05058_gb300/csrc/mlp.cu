@@ -571,8 +571,14 @@ __device__ __forceinline__ uint32_t bf2_bits(float lo, float hi)
 
 __global__ void __launch_bounds__(ws::kThreads, 1)
     k_mlp_infer_ws(const bf16 *__restrict__ wh, const float *__restrict__ p, const bf16 *__restrict__ packed,
-                   const bf16 *__restrict__ x, long long M, long long ntiles, float *__restrict__ y)
+                   const bf16 *__restrict__ x, long long M, const int32_t *__restrict__ count, float *__restrict__ y)
 {
+    // rows: M, or the first *count of them when a device count is given
+    if (count) {
+        const long long c = *count;
+        M = c < 0 ? 0 : (c < M ? c : M);
+    }
+    const long long ntiles = (M + 127) / 128;
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full[ws::kStages], empty[ws::kStages], xfull[2], xempty[2], accfull[2], accempty[2],
         aready[8], partfull[2], drain;
@@ -1101,6 +1107,40 @@ cudaError_t back_weight(const bf16 *dZ, const bf16 *X, int Kin, float *gW, long 
 
 using namespace pcdf::mlp;
 
+namespace pcdf {
+namespace mlp {
+namespace {
+int infer_tc(const void *state, const uint16_t *x, int64_t M, const int32_t *count, float *y, void *stream)
+{
+    if (!state || (M > 0 && (!x || !y)))
+        return fail(PCDF_EINVAL, "state, x and y must be non-NULL");
+    if (M < 0 || M > (1LL << 31) - 1)
+        return fail(PCDF_EINVAL, "M out of range");
+    if (M == 0)
+        return PCDF_OK;
+    if (!aligned(x, 16) || !aligned(state, kAlign))
+        return fail(PCDF_EINVAL, "x must be 16-byte aligned, state %zu-byte aligned", kAlign);
+    State S(const_cast<void *>(state));
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp_infer_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws::kSmem);
+    if (e == cudaSuccess) {
+        // persistent: one CTA per SM (or per tile of the M rows, if fewer)
+        const long long ntiles = (M + 127) / 128;
+        k_mlp_infer_ws<<<(unsigned)(ntiles < nsm ? ntiles : nsm), ws::kThreads, ws::kSmem, st>>>(
+            S.h, S.p, S.pk, (const bf16 *)x, M, count, y);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp inference (tcgen05)");
+}
+}  // namespace
+}  // namespace mlp
+}  // namespace pcdf
+
 extern "C" {
 
 int pcdf_mlp_state_bytes(size_t *bytes)
@@ -1179,32 +1219,18 @@ int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, vo
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp inference");
 }
 
+
 int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y, void *stream)
 {
-    if (!state || (M > 0 && (!x || !y)))
-        return fail(PCDF_EINVAL, "state, x and y must be non-NULL");
-    if (M < 0 || M > (1LL << 31) - 1)
-        return fail(PCDF_EINVAL, "M out of range");
-    if (M == 0)
-        return PCDF_OK;
-    if (!aligned(x, 16) || !aligned(state, kAlign))
-        return fail(PCDF_EINVAL, "x must be 16-byte aligned, state %zu-byte aligned", kAlign);
-    State S(const_cast<void *>(state));
-    cudaStream_t st = (cudaStream_t)stream;
-    int dev = 0, nsm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mlp_infer_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws::kSmem);
-    if (e == cudaSuccess) {
-        // persistent: one CTA per SM (or per tile, if fewer)
-        const long long ntiles = (M + 127) / 128;
-        k_mlp_infer_ws<<<(unsigned)(ntiles < nsm ? ntiles : nsm), ws::kThreads, ws::kSmem, st>>>(
-            S.h, S.p, S.pk, (const bf16 *)x, M, ntiles, y);
-        e = cudaGetLastError();
-    }
-    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp inference (tcgen05)");
+    return pcdf::mlp::infer_tc(state, x, M, nullptr, y, stream);
+}
+
+int pcdf_mlp_infer_tc_count(const void *state, const uint16_t *x, int64_t M_max, const int32_t *count, float *y,
+                            void *stream)
+{
+    if (!count)
+        return fail(PCDF_EINVAL, "count must be non-NULL");
+    return pcdf::mlp::infer_tc(state, x, M_max, count, y, stream);
 }
 
 int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64_t M, float *y, float *loss,

@@ -62,6 +62,12 @@ def test_mlp_forward_and_gradients_match_oracle(M):
     assert np.max(np.abs(y_tc.cpu().double().numpy() - want_y)) <= 2e-2 * max(1.0, np.max(np.abs(want_y)))
     y_tc2 = net.infer_tc(x[: M - 7])
     assert torch.allclose(y_tc2, y[: M - 7], rtol=0, atol=1e-5 * max(1.0, float(y.abs().max())))
+    # a row count on the device: the first count rows, the rest untouched
+    for c in (M - 7, 0, M + 5, -3):
+        cnt = torch.tensor([c], dtype=torch.int32, device=d)
+        y_c = net.infer_tc(x, count=cnt)
+        k = max(0, min(c, M))
+        assert torch.equal(y_c[:k], y_tc[:k])
 
 
 def test_adam_step():
