@@ -545,87 +545,118 @@ __global__ void k_sur_fallback(QueryGrid g, const int32_t *__restrict__ static_s
 // The same exact answers from the 2-D partial field of the capsule slab that
 // pcdf_composite_prepare leaves in its workspace (dyn_mid[t][e][y][x] for the
 // slab slices zlo + e, e < S).  The dynamic value at a corner voxel is the
-// lower envelope of its column evaluated by brute force: outside the humans
-// min over slab slices z' of (z - z')^2 + g(z') (g the partial at a free
-// voxel, 0 at an occupied one); inside, minus min over the column of
-// (z - z')^2 + g(z') with g = 0 at free voxels (the slab's and the first
-// ones beyond it) and minus the partial at occupied ones.  The minima are
-// the ones the composite z pass takes, so the values are the same integers.
-// Warp per query; lanes over the slab slices of each of the cell's four
-// columns, both corner heights at once.
+// lower envelope of its column evaluated directly: outside the humans min
+// over slab slices z' of (z - z')^2 + g(z') (g the partial at a free voxel,
+// 0 at an occupied one); inside, minus min over the column of (z - z')^2 +
+// g(z') with g = 0 at free voxels (the slab's and the first ones beyond it)
+// and minus the partial at occupied ones.  The minima are the ones the
+// composite z pass takes, so the values are the same integers.
+// Four lanes per query, one per column of the cell (x bit 0, y bit 1), both
+// corner heights z0 and z1 = z0 (+ 1) at once.  Every term is at least
+// (z - z')^2, so each lane visits the slices in order of distance from the
+// corner pair (z0 - k below, z0 + 1 + k above) and stops once (k + 1)^2
+// reaches both minima; the quad's eight corner values meet in its first lane
+// for the interpolation.
 __global__ void k_sur_fallback_slab(QueryGrid g, const int32_t *__restrict__ static_sq,
                                     const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
                                     const int32_t *__restrict__ tidx, int T, const int32_t *__restrict__ dyn_mid,
                                     int zlo, int S, float eps, const int *__restrict__ list,
                                     const int *__restrict__ count, float *__restrict__ h, float *__restrict__ d_out)
 {
-    const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31, col = lane & 3;
+    const long long gq = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 2;  // this quad's first query
+    const long long nq = ((long long)gridDim.x * blockDim.x) >> 2;
     const long long V2 = (long long)g.n[0] * g.n[1];
     const int nz = g.n[2];
     const int n = *count;
-    for (long long w = warp; w < n; w += nwarps) {
-        const long long q = list[w];
+    for (long long w = gq;; w += nq) {
+        // the loop ends for the whole warp at once (shuffles below)
+        if (w - (lane >> 2) >= n)
+            break;
+        const bool valid = w < n;
+        const long long q = list[valid ? w : w - (lane >> 2)];
         const float4 s = spheres[q];
         const int t = min(max(tidx[q], 0), T - 1);
         const Cell cl = locate(g, s);
-        int dyn[8];
+        const int x = (col & 1) ? cl.i1[0] : cl.i0[0], y = (col & 2) ? cl.i1[1] : cl.i0[1];
+        const int32_t *pc = dyn_mid + (long long)t * S * V2 + (long long)y * g.n[0] + x;  // slice e at pc[e * V2]
+        const int zc[2] = {cl.i0[2], cl.i1[2]};
+        bool inside[2];
+        int best[2];
 #pragma unroll
-        for (int col = 0; col < 4; ++col) {
-            const int x = (col & 1) ? cl.i1[0] : cl.i0[0], y = (col & 2) ? cl.i1[1] : cl.i0[1];
-            const int32_t *pc = dyn_mid + (long long)t * S * V2 + (long long)y * g.n[0] + x;  // slice e at pc[e * V2]
-            int zc[2] = {cl.i0[2], cl.i1[2]};
-            bool inside[2];
-            int best[2] = {kInf32, kInf32};
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int e = zc[u] - zlo;
-                inside[u] = e >= 0 && e < S && __ldg(pc + (long long)e * V2) < 0;
-            }
-            for (int e = lane; e < S; e += 32) {
-                const int32_t P = __ldg(pc + (long long)e * V2);
-                const int zz = zlo + e;
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int dz2 = (zc[u] - zz) * (zc[u] - zz);
-                    if (inside[u]) {
-                        if (P >= 0)
-                            best[u] = min(best[u], dz2);  // a free voxel
-                        else if (P != -kInf32)
-                            best[u] = min(best[u], dz2 - P);
-                    } else {
-                        if (P < 0)
-                            best[u] = min(best[u], dz2);  // an occupied voxel
-                        else if (P != kInf32)
-                            best[u] = min(best[u], dz2 + P);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                int b = warp_min(best[u]);
-                if (inside[u]) {
-                    // the free voxels next to the slab
-                    if (zlo - 1 >= 0)
-                        b = min(b, (zc[u] - (zlo - 1)) * (zc[u] - (zlo - 1)));
-                    if (zlo + S < nz)
-                        b = min(b, (zlo + S - zc[u]) * (zlo + S - zc[u]));
-                    b = b == kInf32 ? -kInf32 : -b;
-                }
-                dyn[col + 4 * u] = b;  // corner index: x bit 0, y bit 1, z bit 2
+        for (int u = 0; u < 2; ++u) {
+            const int e = zc[u] - zlo;
+            inside[u] = e >= 0 && e < S && __ldg(pc + (long long)e * V2) < 0;
+            best[u] = kInf32;
+            if (inside[u]) {
+                // the free voxels next to the slab
+                if (zlo - 1 >= 0)
+                    best[u] = min(best[u], (zc[u] - (zlo - 1)) * (zc[u] - (zlo - 1)));
+                if (zlo + S < nz)
+                    best[u] = min(best[u], (zlo + S - zc[u]) * (zlo + S - zc[u]));
             }
         }
-        if (lane == 0) {
-            float c[2][2][2];
-            for (int k = 0; k < 8; ++k) {
-                const int vx = (k & 1) ? cl.i1[0] : cl.i0[0], vy = (k & 2) ? cl.i1[1] : cl.i0[1],
-                          vz = (k & 4) ? cl.i1[2] : cl.i0[2];
-                const long long o = ((long long)vz * g.n[1] + vy) * g.n[0] + vx;
-                const int32_t sv = static_sq[o];
-                c[(k >> 2) & 1][(k >> 1) & 1][k & 1] =
-                    sv <= dyn[k] ? static_sdf[o] : sq_to_sdf_fast(min(sv, dyn[k]), g.vox);
+        auto visit = [&](int e, int32_t P) {
+            const int zz = zlo + e;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int dz2 = (zc[u] - zz) * (zc[u] - zz);
+                if (inside[u]) {
+                    if (P >= 0)
+                        best[u] = min(best[u], dz2);  // a free voxel
+                    else if (P != -kInf32)
+                        best[u] = min(best[u], dz2 - P);
+                } else {
+                    if (P < 0)
+                        best[u] = min(best[u], dz2);  // an occupied voxel
+                    else if (P != kInf32)
+                        best[u] = min(best[u], dz2 + P);
+                }
             }
+        };
+        const int ec = zc[0] - zlo;
+        // k runs until both sides have left the slab; four steps (eight
+        // slices) are loaded before they are folded in
+        const int kmax = max(ec + 1, S - ec);
+        for (int k0 = 0; k0 < kmax; k0 += 4) {
+            const long long bound = (long long)k0 * k0;  // every slice not yet visited is >= k0 away
+            if (bound >= (long long)max(best[0], best[1]))
+                break;
+            int32_t P[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int ea = ec - k0 - i, eb = ec + 1 + k0 + i;
+                P[2 * i] = (ea >= 0 && ea < S) ? __ldg(pc + (long long)ea * V2) : kInf32;
+                P[2 * i + 1] = (eb >= 0 && eb < S) ? __ldg(pc + (long long)eb * V2) : kInf32;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int ea = ec - k0 - i, eb = ec + 1 + k0 + i;
+                if (ea >= 0 && ea < S)
+                    visit(ea, P[2 * i]);
+                if (eb >= 0 && eb < S)
+                    visit(eb, P[2 * i + 1]);
+            }
+        }
+        // this lane's two corners (x, y of its column; z0 and z1)
+        float cv[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            int b = best[u];
+            if (inside[u])
+                b = b == kInf32 ? -kInf32 : -b;
+            const long long o = ((long long)zc[u] * g.n[1] + y) * g.n[0] + x;
+            const int32_t sv = __ldg(static_sq + o);
+            cv[u] = sv <= b ? __ldg(static_sdf + o) : sq_to_sdf_fast(min(sv, b), g.vox);
+        }
+        float c[2][2][2];
+        const int base = lane & ~3;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            c[0][k >> 1][k & 1] = __shfl_sync(0xffffffffu, cv[0], base + k);
+            c[1][k >> 1][k & 1] = __shfl_sync(0xffffffffu, cv[1], base + k);
+        }
+        if (valid && col == 0) {
             const Sample r = interpolate(cl, c, false);
             const float hv = (eps + s.w) - r.d;
             h[q] = hv > 0.f ? hv : 0.f;
