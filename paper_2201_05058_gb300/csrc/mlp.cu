@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ w
 // tcgen05.ld, add the bias, apply ReLU and store the BF16 activations as the
 // next layer's A operand.  The head reads the last layer from tensor memory.
 //
-// W2 and W3 are pre-packed (k_pack_hidden) into 16 chunks of 32 columns, each
+// W2 and W3 are pre-packed (k_pack_hidden) into 8 chunks of 64 columns, each
 // laid out exactly as the B operand in shared memory, so one bulk copy moves
 // a chunk.
 //
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ w
 // wait, and frees its tensor memory on every path.
 namespace tc {
 
-constexpr int kM = 128, kKC = 32;  // tile rows; K columns of a packed weight chunk
+constexpr int kM = 128, kKC = 64;  // tile rows; K columns of a packed weight chunk
 constexpr uint64_t kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t kmaj(int r, int k, int Kt)
@@ -502,8 +502,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 
 }  // namespace tc
 
-// W2 and W3 into the chunked B-operand layout: chunk j (layer j / 8, columns
-// 32 (j % 8) ..) holds element (n, k) at tc::kmaj(n, k, 32) / 2
+// W2 and W3 into the chunked B-operand layout: chunk j (layer j / 4, columns
+// 64 (j % 4) ..) holds element (n, k) at tc::kmaj(n, k, 64) / 2
 __global__ void k_pack_hidden(const bf16 *__restrict__ wh, bf16 *__restrict__ packed)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte piece
@@ -522,27 +522,29 @@ __global__ void k_pack_hidden(const bf16 *__restrict__ wh, bf16 *__restrict__ pa
 // 128-row tiles with three roles working concurrently on mbarriers
 //   warp 0 (one thread)  issues the products and commits;
 //   warp 1               producer: the x tiles (double-buffered) and the
-//                        packed W2/W3 chunks through the 8-stage ring;
+//                        packed W2/W3 chunks through the 4-stage ring;
 //   warps 2..9           epilogue: warp w reads TMEM lanes 32 (w % 4) .. and,
-//                        in group (w - 2) / 4, every second 32-column chunk.
+//                        in group (w - 2) / 4, every second 32-column slice.
 // Tensor memory holds two 256-column accumulators; the layers of the CTA's
 // tiles (q = 3 * tile + layer) alternate between them, so the epilogue of
-// layer q overlaps the products of layer q + 1: chunk j of layer q + 1 is
-// issued as soon as the epilogue has written chunk j of its A operand
-// (barrier aready[j]), and an accumulator is overwritten only after every
-// epilogue thread has read it (accempty).  The head sums each group's
+// layer q overlaps the products of layer q + 1: the four products of chunk c
+// (64 columns) of layer q + 1 are issued as soon as both groups have written
+// those columns of its A operand (barrier aready[c]), and an accumulator is
+// overwritten only after every epilogue thread has read it (accempty).  The head sums each group's
 // columns and the groups are added in a fixed order.
 // ---------------------------------------------------------------------------
 namespace ws {
-constexpr int kStages = 8, kEpiWarps = 8, kGroups = kEpiWarps / 4, kThreads = 32 * (2 + kEpiWarps);
+constexpr int kStages = 4, kEpiWarps = 8, kGroups = kEpiWarps / 4, kThreads = 32 * (2 + kEpiWarps);
+constexpr int kChunks = kW / tc::kKC;  // chunks of a hidden layer
 constexpr uint32_t kCols = 512;
-constexpr uint32_t kBytesA = 128 * kW * 2, kBytesChunk = kW * 32 * 2, kBytesX = 128 * kIn * 2, kBytesW1 = kW * kIn * 2;
+constexpr uint32_t kBytesA = 128 * kW * 2, kBytesChunk = kW * tc::kKC * 2, kBytesX = 128 * kIn * 2,
+                   kBytesW1 = kW * kIn * 2;
 constexpr uint32_t oA = 0, oRing = oA + kBytesA, oX = oRing + kStages * kBytesChunk, oW1 = oX + 2 * kBytesX,
                    oBias = oW1 + kBytesW1, oW4 = oBias + 3 * kW * 4, oPart = oW4 + kW * 4,
                    kEnd = oPart + 2 * kGroups * 128 * 4;
 constexpr size_t kSmem = 1024 + (size_t)kEnd;
 static_assert(kSmem <= 227 * 1024, "shared memory");
-static_assert(kEpiWarps % 4 == 0 && (8 % kGroups) == 0, "epilogue warps cover the four lane quarters");
+static_assert(kEpiWarps == 8 && kGroups == 2, "two groups of four warps: each 64-column chunk is two 32-column slices");
 
 // lane 0's value for every lane of the (converged) warp, through the warp's
 // own shared slot, so that the warp takes every branch as a whole
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     const long long ntiles = (M + 127) / 128;
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full[ws::kStages], empty[ws::kStages], xfull[2], xempty[2], accfull[2], accempty[2],
-        aready[8], partfull[2], drain;
+        aready[ws::kChunks], partfull[2], drain;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_fail;
     __shared__ volatile int s_slot[2 + ws::kEpiWarps];
@@ -607,8 +609,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             tc::mbar_init(&accempty[i], ws::kEpiWarps * 32);
             tc::mbar_init(&partfull[i], ws::kEpiWarps * 32);
         }
-        for (int j = 0; j < 8; ++j)
-            tc::mbar_init(&aready[j], 128);
+        for (int j = 0; j < ws::kChunks; ++j)
+            tc::mbar_init(&aready[j], ws::kEpiWarps * 32);
         tc::mbar_init(&drain);
         tc::fence_mbar_init();
         s_fail = 0;
@@ -659,20 +661,20 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                         break;
                     }
                     const uint32_t aph = (uint32_t)(2 * it + L - 1) & 1u;
-                    for (int j = 0; j < 8; ++j, ++g) {
+                    for (int c = 0; c < ws::kChunks; ++c, ++g) {
                         const int st = (int)(g % ws::kStages);
                         if (!tc::mbar_wait(&full[st], (uint32_t)(g / ws::kStages) & 1u) ||
-                            !tc::mbar_wait(&aready[j], aph)) {
+                            !tc::mbar_wait(&aready[c], aph)) {
                             ok = false;
                             break;
                         }
                         tc::fence_after();
 #pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            const int k0 = 32 * j + 16 * kk;
+                        for (int kk = 0; kk < tc::kKC / 16; ++kk) {
+                            const int k0 = tc::kKC * c + 16 * kk;
                             tc::mma(dcol, tc::sdesc(aA + (uint32_t)(k0 / 8) * 128u, 128, kW * 16),
-                                    tc::sdesc(aRing + (uint32_t)(st * ws::kBytesChunk + kk * 256), 128, 32 * 16),
-                                    (uint32_t)(j | kk));
+                                    tc::sdesc(aRing + (uint32_t)(st * ws::kBytesChunk + kk * 256), 128, tc::kKC * 16),
+                                    (uint32_t)(c | kk));
                         }
                         tc::commit(&empty[st]);
                     }
@@ -716,14 +718,14 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             tc::fence_proxy_async();
             tc::mbar_arrive(&xfull[b]);
             if (lane == 0) {
-                for (int c = 0; c < 16; ++c, ++g) {
+                for (int c = 0; c < 2 * ws::kChunks; ++c, ++g) {
                     const int st = (int)(g % ws::kStages);
                     if (g >= ws::kStages && !tc::mbar_wait(&empty[st], (uint32_t)(g / ws::kStages - 1) & 1u)) {
                         s_fail = 1;
                         break;
                     }
-                    tc::bulk_load(sRing + st * ws::kBytesChunk, packed + (long long)c * (kW * 32), ws::kBytesChunk,
-                                  &full[st]);
+                    tc::bulk_load(sRing + st * ws::kBytesChunk, packed + (long long)c * (kW * tc::kKC),
+                                  ws::kBytesChunk, &full[st]);
                 }
             }
         }
@@ -771,7 +773,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                         }
                         tc::fence_proxy_async();
                         tc::fence_before();
-                        tc::mbar_arrive(&aready[j]);
+                        tc::mbar_arrive(&aready[j >> 1]);
                     }
                     tc::mbar_arrive(&accempty[a]);
                 } else {
