@@ -454,6 +454,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
         v[i] = __uint_as_float(r[i]);
 }
 
+// the same load without its wait: r may be read only after tmem_wait_ld(r),
+// which takes the registers as in-out operands so that no use moves above it
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count = 1)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -756,39 +772,64 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                 const uint32_t tb = tmem + (uint32_t)a * 256u + lane_off;
                 if (L < 2) {
                     const float *bias = sBias + L * kW;
-                    for (int j = group; j < 8; j += ws::kGroups) {
-                        float v[32];
-                        tc::tmem_ld32(tb + (uint32_t)(32 * j), v);
+                    // slice j (32 columns): bias, ReLU, BF16 into the A operand, then
+                    // its chunk's barrier; the next slice's load is in flight meanwhile
+                    auto slice = [&](const uint32_t(&v)[32], int j) {
 #pragma unroll
                         for (int gq = 0; gq < 4; ++gq) {
                             const float4 b0 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq);
                             const float4 b1 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq + 4);
-                            const float *u = v + 8 * gq;
+                            const uint32_t *u = v + 8 * gq;
                             uint4 pk;
-                            pk.x = bf2_bits(fmaxf(u[0] + b0.x, 0.f), fmaxf(u[1] + b0.y, 0.f));
-                            pk.y = bf2_bits(fmaxf(u[2] + b0.z, 0.f), fmaxf(u[3] + b0.w, 0.f));
-                            pk.z = bf2_bits(fmaxf(u[4] + b1.x, 0.f), fmaxf(u[5] + b1.y, 0.f));
-                            pk.w = bf2_bits(fmaxf(u[6] + b1.z, 0.f), fmaxf(u[7] + b1.w, 0.f));
+                            pk.x = bf2_bits(fmaxf(__uint_as_float(u[0]) + b0.x, 0.f), fmaxf(__uint_as_float(u[1]) + b0.y, 0.f));
+                            pk.y = bf2_bits(fmaxf(__uint_as_float(u[2]) + b0.z, 0.f), fmaxf(__uint_as_float(u[3]) + b0.w, 0.f));
+                            pk.z = bf2_bits(fmaxf(__uint_as_float(u[4]) + b1.x, 0.f), fmaxf(__uint_as_float(u[5]) + b1.y, 0.f));
+                            pk.w = bf2_bits(fmaxf(__uint_as_float(u[6]) + b1.z, 0.f), fmaxf(__uint_as_float(u[7]) + b1.w, 0.f));
                             *reinterpret_cast<uint4 *>(sA + tc::kmaj(r, 32 * j + 8 * gq, kW)) = pk;
                         }
                         tc::fence_proxy_async();
                         tc::fence_before();
                         tc::mbar_arrive(&aready[j >> 1]);
-                    }
+                    };
+                    uint32_t va[32], vb[32];
+                    tc::tmem_ld32_async(tb + (uint32_t)(32 * group), va);
+                    tc::tmem_wait_ld(va);
+                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 2)), vb);
+                    slice(va, group);
+                    tc::tmem_wait_ld(vb);
+                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 4)), va);
+                    slice(vb, group + 2);
+                    tc::tmem_wait_ld(va);
+                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 6)), vb);
+                    slice(va, group + 4);
+                    tc::tmem_wait_ld(vb);
+                    slice(vb, group + 6);
                     tc::mbar_arrive(&accempty[a]);
                 } else {
                     // head: relu(D + b3) rounded to BF16 (as stored between layers), . w4
                     float acc = 0.f;
-                    for (int j = group; j < 8; j += ws::kGroups) {
-                        float v[32];
-                        tc::tmem_ld32(tb + (uint32_t)(32 * j), v);
+                    auto slice = [&](const uint32_t(&v)[32], int j) {
 #pragma unroll
                         for (int e = 0; e < 32; ++e) {
                             const int c = 32 * j + e;
-                            const float hv = __bfloat162float(__float2bfloat16_rn(fmaxf(v[e] + sBias[2 * kW + c], 0.f)));
+                            const float hv = __bfloat162float(
+                                __float2bfloat16_rn(fmaxf(__uint_as_float(v[e]) + sBias[2 * kW + c], 0.f)));
                             acc = fmaf(hv, sW4[c], acc);
                         }
-                    }
+                    };
+                    uint32_t va[32], vb[32];
+                    tc::tmem_ld32_async(tb + (uint32_t)(32 * group), va);
+                    tc::tmem_wait_ld(va);
+                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 2)), vb);
+                    slice(va, group);
+                    tc::tmem_wait_ld(vb);
+                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 4)), va);
+                    slice(vb, group + 2);
+                    tc::tmem_wait_ld(va);
+                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 6)), vb);
+                    slice(va, group + 4);
+                    tc::tmem_wait_ld(vb);
+                    slice(vb, group + 6);
                     tc::fence_before();
                     tc::mbar_arrive(&accempty[a]);
                     float *part = sPart + (it & 1) * (ws::kGroups * 128);
