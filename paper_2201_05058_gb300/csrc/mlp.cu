@@ -755,12 +755,26 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         const int quarter = warp & 3, group = (warp - 2) >> 2;
         const int r = quarter * 32 + lane;
         volatile int *slot = s_slot + warp;
+        long long pend = -1;  // tile whose head sums wait to be added (group 0)
+        int pend_it = 0;
+        auto flush_pending = [&]() -> bool {
+            if (!ws::warp_wait(&partfull[pend_it & 1], (uint32_t)(pend_it >> 1) & 1u, slot, lane))
+                return false;
+            const float *part = sPart + (pend_it & 1) * (ws::kGroups * 128);
+            float sum = 0.f;
+#pragma unroll
+            for (int g2 = 0; g2 < ws::kGroups; ++g2)
+                sum += part[g2 * 128 + r];
+            if (pend * 128 + r < M)
+                y[pend * 128 + r] = sum + b4;
+            pend = -1;
+            return true;
+        };
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         int it = 0;
         long long tile = blockIdx.x;
         bool ok = true;
         for (; tile < ntiles; tile += gridDim.x, ++it) {
-            const long long m0 = tile * 128;
             for (int L = 0; L < 3 && ok; ++L) {
                 const long long q = 3LL * it + L;
                 const int a = (int)(q & 1);
@@ -806,15 +820,23 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                     slice(vb, group + 6);
                     tc::mbar_arrive(&accempty[a]);
                 } else {
-                    // head: relu(D + b3) rounded to BF16 (as stored between layers), . w4
-                    float acc = 0.f;
+                    // head: relu(D + b3) rounded to BF16 (as stored between layers), . w4,
+                    // in four partial sums
+                    float acc4[4] = {0.f, 0.f, 0.f, 0.f};
                     auto slice = [&](const uint32_t(&v)[32], int j) {
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const int c = 32 * j + e;
-                            const float hv = __bfloat162float(
-                                __float2bfloat16_rn(fmaxf(__uint_as_float(v[e]) + sBias[2 * kW + c], 0.f)));
-                            acc = fmaf(hv, sW4[c], acc);
+                        for (int gq = 0; gq < 8; ++gq) {
+                            const float4 b = *reinterpret_cast<const float4 *>(sBias + 2 * kW + 32 * j + 4 * gq);
+                            const float4 w = *reinterpret_cast<const float4 *>(sW4 + 32 * j + 4 * gq);
+                            const uint32_t *u = v + 4 * gq;
+                            const uint32_t p0 = bf2_bits(fmaxf(__uint_as_float(u[0]) + b.x, 0.f),
+                                                         fmaxf(__uint_as_float(u[1]) + b.y, 0.f));
+                            const uint32_t p1 = bf2_bits(fmaxf(__uint_as_float(u[2]) + b.z, 0.f),
+                                                         fmaxf(__uint_as_float(u[3]) + b.w, 0.f));
+                            acc4[0] = fmaf(__uint_as_float(p0 << 16), w.x, acc4[0]);
+                            acc4[1] = fmaf(__uint_as_float(p0 & 0xffff0000u), w.y, acc4[1]);
+                            acc4[2] = fmaf(__uint_as_float(p1 << 16), w.z, acc4[2]);
+                            acc4[3] = fmaf(__uint_as_float(p1 & 0xffff0000u), w.w, acc4[3]);
                         }
                     };
                     uint32_t va[32], vb[32];
@@ -832,33 +854,34 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                     slice(vb, group + 6);
                     tc::fence_before();
                     tc::mbar_arrive(&accempty[a]);
-                    float *part = sPart + (it & 1) * (ws::kGroups * 128);
-                    part[group * 128 + r] = acc;
+                    sPart[(it & 1) * (ws::kGroups * 128) + group * 128 + r] = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
                     tc::mbar_arrive(&partfull[it & 1]);
-                    if (group == 0) {
-                        if (!ws::warp_wait(&partfull[it & 1], (uint32_t)(it >> 1) & 1u, slot, lane)) {
-                            ok = false;
-                            break;
-                        }
-                        float sum = 0.f;
-#pragma unroll
-                        for (int g2 = 0; g2 < ws::kGroups; ++g2)
-                            sum += part[g2 * 128 + r];
-                        if (m0 + r < M)
-                            y[m0 + r] = sum + b4;
-                    }
+                    // group 0 adds the groups' sums once it has written the next
+                    // tile's first-layer activations (off the critical path)
+                    pend = tile;
+                    pend_it = it;
+                }
+                if (L == 0 && group == 0 && pend >= 0 && !flush_pending()) {
+                    ok = false;
+                    break;
                 }
             }
             if (!ok || ws::warp_uniform(s_fail, slot, lane))
                 break;
         }
-        if (!ok || ws::warp_uniform(s_fail, slot, lane)) {
+        bool failed = !ok || ws::warp_uniform(s_fail, slot, lane);
+        if (!failed && group == 0 && pend >= 0 && !flush_pending())
+            failed = true;
+        if (failed) {
             s_fail = 1;
-            // this tile and the CTA's later ones have no answer
-            if (group == 0)
+            // the pending tile, this tile and the CTA's later ones have no answer
+            if (group == 0) {
+                if (pend >= 0 && pend * 128 + r < M)
+                    y[pend * 128 + r] = __int_as_float(0x7fc00000);
                 for (; tile < ntiles; tile += gridDim.x)
                     if (tile * 128 + r < M)
                         y[tile * 128 + r] = __int_as_float(0x7fc00000);
+            }
         }
     }
     tc::fence_before();
