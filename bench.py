@@ -406,6 +406,21 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
                              err_bound=err_bound, comp_workspace=cws)
 
     t_sur = ev_time(surrogate_path)
+    # the same plan step replayed from a CUDA graph (no host work between
+    # its kernels; the inputs are the captured buffers)
+    try:
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            surrogate_path()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            surrogate_path()
+        t_sur_graph = ev_time(graph.replay)
+    except RuntimeError as exc:  # capture unsupported here: report the eager number only
+        print(f"surrogate graph capture failed: {exc}", file=sys.stderr)
+        t_sur_graph = None
     t_sur_local = ev_time(lambda: pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2,
                                                        band=band, caps_dev=caps_dev, err_bound=err_bound))
     x_q = pcdf.surrogate_features(grid, sph, tidx, T, caps_dev)
@@ -436,7 +451,7 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
             "at_band_0_05_m": {"fallback_frac": float(np.mean([x[5] for x in stats])),
                                "wrong_decisions": int(sum(x[6] for x in stats)),
                                "queries": int(sph.numel() // 4 * len(stats))},
-            "surrogate_ms": t_sur, "surrogate_local_search_ms": t_sur_local, "features_ms": t_feat,
+            "surrogate_ms": t_sur, "surrogate_graph_ms": t_sur_graph, "surrogate_local_search_ms": t_sur_local, "features_ms": t_feat,
             "rows_to_network_frac": x_sel.shape[0] / (sph.numel() // 4), "mlp_forward_selected_ms": t_mlp_sel,
             "mlp_infer_ms": t_inf, "mlp_infer_selected_ms": t_inf_sel,
             "mlp_infer_tflops": 2 * 136193 * sph.numel() / 4 / (t_inf * 1e-3) / 1e12,
@@ -444,7 +459,8 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
             "mlp_infer_tcgen05_tflops": 2 * 136193 * sph.numel() / 4 / (t_tc * 1e-3) / 1e12,
             "mlp_forward_ms": t_mlp,
             "mlp_tflops": 2 * 136193 * sph.numel() / 4 / (t_mlp * 1e-3) / 1e12, "exact_composite_ms": t_comp, "exact_scratch_ms": t_scr,
-            "speedup_vs_scratch": t_scr / t_sur, "speedup_vs_composite": t_comp / t_sur}
+            "speedup_vs_scratch": t_scr / t_sur, "speedup_vs_composite": t_comp / t_sur,
+            "graph_speedup_vs_scratch": t_scr / t_sur_graph if t_sur_graph else None}
 
 
 def run_native(args):
