@@ -169,6 +169,47 @@ def test_fallback_exact_with_several_humans():
     assert np.max(np.abs(h.cpu().numpy() - want)) <= 1e-5
 
 
+def test_surrogate_step_replays_from_a_cuda_graph():
+    """The plan step (capsule-slab partials, selection, network, exact
+    fallback) has no host round trip, so it captures into a CUDA graph; a
+    replay on new query contents gives the eager answers bit for bit."""
+    d = dev()
+    sc = scenes.scene_small_walking(seed=81, T=20, H=1)
+    grid = sc["grid"]
+    rng = np.random.default_rng(9)
+    sph_np, tidx_np = scenes.spheres_along_paths(grid, 64, 40, 8, rng, T=20)
+    sph = torch.from_numpy(sph_np).to(d)
+    tidx = torch.from_numpy(tidx_np).to(d)
+    occ = torch.from_numpy(sc["occ"]).to(d)
+    static_sq, static_sdf = pcdf.build_static_sdf(occ, grid)
+    caps_dev = torch.from_numpy(np.ascontiguousarray(sc["caps"])).to(d)
+    net = pcdf.SurrogateMLP(d, seed=8)
+    ws = pcdf.composite_workspace(grid, sc["caps"], d)
+
+    def step():
+        pcdf.composite_prepare(grid, sc["caps"], ws)
+        return pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=0.3,
+                                    err_bound=0.5, caps_dev=caps_dev, comp_workspace=ws)
+
+    side = torch.cuda.Stream(d)
+    side.wait_stream(torch.cuda.current_stream(d))
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream(d).wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        h_g, d_g, n_g = step()
+    # new query contents in the captured buffers
+    sph2_np, tidx2_np = scenes.spheres_along_paths(grid, 64, 40, 8, np.random.default_rng(10), T=20)
+    sph.copy_(torch.from_numpy(sph2_np).to(d))
+    tidx.copy_(torch.from_numpy(tidx2_np).to(d))
+    graph.replay()
+    torch.cuda.synchronize()
+    h_e, d_e, n_e = step()
+    assert torch.equal(h_g, h_e) and torch.equal(d_g, d_e)
+    assert int(n_g.item()) == int(n_e.item()) > 0
+
+
 def test_row_selection_skips_only_static_cells():
     """The selection keeps a row wherever the exact capsule field beats the
     static field at some corner of the query's cell (the skip rule is a
