@@ -58,7 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
-    ap.add_argument("--profile-case", choices=["composite", "static", "scratch", "query"], default=None,
+    ap.add_argument("--profile-case", choices=["composite", "static", "scratch", "query", "mlp", "surrogate"],
+                    default=None,
                     help="run one small untimed case of the named stage (for ncu captures) and exit")
     ap.add_argument("--profile-T", type=int, default=4, help="horizon of the --profile-case composite")
     return ap.parse_args(argv)
@@ -688,6 +689,45 @@ def run_native(args):
     return 0
 
 
+def run_profile_surrogate(dev):
+    """The surrogate plan step (1,024,000 queries, 20 fields of 64^3) with a
+    network trained briefly (200 scenes, 300 steps), twice inside the NVTX
+    range "plan_step" after three warm-up steps."""
+    import torch
+
+    import paper_2201_05058_gb300 as pcdf
+    from paper_2201_05058_gb300 import surrogate as sg
+    T = 20
+    train_sc = [scenes.scene_small_walking(seed=1000 + i, T=T, H=1) for i in range(200)]
+    grid = train_sc[0]["grid"]
+    fields, caps, tf = sg.exact_dynamic_fields(grid, [sc["caps"] for sc in train_sc], dev)
+    net = pcdf.SurrogateMLP(dev, seed=17)
+    sg.train(net, grid, fields, caps, tf, T, steps=300, batch=65536, lr=2e-3, log_every=100)
+    del fields
+    sc = scenes.scene_small_walking(seed=6001, T=T, H=1)
+    sph, tidx = scenes.spheres_along_paths(grid, 1024, 40, 25, np.random.default_rng(6001), T=T)
+    sph, tidx = torch.from_numpy(sph).to(dev), torch.from_numpy(tidx).to(dev)
+    st_sq, st_sdf = pcdf.build_static_sdf(torch.from_numpy(sc["occ"]).to(dev), grid)
+    caps_dev = torch.from_numpy(np.ascontiguousarray(sc["caps"])).to(dev)
+    cws = pcdf.composite_workspace(grid, sc["caps"], dev)
+
+    def step():
+        pcdf.composite_prepare(grid, sc["caps"], cws)
+        return pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.135,
+                                    caps_dev=caps_dev, err_bound=0.156, comp_workspace=cws)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("plan_step")
+    for _ in range(2):
+        _, _, nfb = step()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(f"profile case surrogate done: {int(nfb.item())} fallback queries")
+    return 0
+
+
 def run_profile_case(args):
     """One small untimed case for an ncu capture: the 256^3 scene with a short
     horizon (outputs still far larger than L2), run twice so a capture can skip
@@ -696,6 +736,20 @@ def run_profile_case(args):
 
     import paper_2201_05058_gb300 as pcdf
     dev = torch.device("cuda", 0)
+    if args.profile_case == "mlp":
+        # tcgen05 inference on 362,000 rows (the kept rows of a 1,024,000-query plan step)
+        net = pcdf.SurrogateMLP(dev, seed=3)
+        g = torch.Generator(device="cpu").manual_seed(1)
+        x = torch.randn(362000, 16, generator=g).to(torch.bfloat16)
+        x[:, 13:] = 0
+        x = x.to(dev)
+        for _ in range(2):
+            net.infer_tc(x)
+        torch.cuda.synchronize()
+        print("profile case mlp done")
+        return 0
+    if args.profile_case == "surrogate":
+        return run_profile_surrogate(dev)
     sc = scenes.scene_composite(seed=args.seed, T=args.profile_T, H=H_HUMANS)
     grid, caps = sc["grid"], sc["caps"]
     occ = torch.from_numpy(sc["occ"]).to(dev)

@@ -416,7 +416,12 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
  * stream; comp_workspace_bytes >= pcdf_composite_workspace_bytes): each
  * corner's dynamic value is the minimum over its column's slab sites, the
  * integers the composite z pass produces, at a few loads per corner instead
- * of a search over the capsules' voxels. */
+ * of a search over the capsules' voxels.
+ * Both finish calls, pcdf_surrogate_select and pcdf_mlp_infer_tc_count make
+ * no host synchronisation and copy nothing from host memory (the capsules
+ * reach the device as kernel parameters), so a plan step of
+ * pcdf_composite_prepare, select, inference and finish can be captured in a
+ * CUDA graph and replayed on new sphere contents. */
 int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                                const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
                                const int32_t *caps_host, const void *comp_workspace, size_t comp_workspace_bytes,

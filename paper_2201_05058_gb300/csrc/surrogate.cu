@@ -760,6 +760,15 @@ int pcdf_surrogate_finish_workspace_bytes(int32_t T, int32_t H, int64_t N, size_
 
 namespace {
 
+// capsules into the workspace from a kernel parameter: the values are copied
+// at launch (and captured by value in a CUDA graph), so the host array may go
+// as soon as the call returns
+__global__ void k_put_caps(const __grid_constant__ pcdf::CapBatch b, pcdf::CapInfo *__restrict__ dst)
+{
+    for (int i = threadIdx.x; i < b.count; i += blockDim.x)
+        dst[i] = b.caps[i];
+}
+
 // combine, then the exact answers: from the capsule slab's 2-D partials when
 // dyn_mid is given, else by local search over the capsules' voxels
 int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, const float *spheres,
@@ -790,8 +799,14 @@ int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const floa
     pcdf::CapInfo *dcaps = (pcdf::CapInfo *)(ws + align_up(sizeof(int)) + align_up((size_t)N * sizeof(int)));
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dcaps, ci.data(), ci.size() * sizeof(pcdf::CapInfo), cudaMemcpyHostToDevice, st);
+    for (size_t i0 = 0; e == cudaSuccess && i0 < ci.size(); i0 += pcdf::kMaxCapsPerLaunch) {
+        static thread_local pcdf::CapBatch batch;  // 24 KB: kept off the stack
+        const size_t n = std::min(ci.size() - i0, (size_t)pcdf::kMaxCapsPerLaunch);
+        batch.count = (int32_t)n;
+        std::copy(ci.begin() + i0, ci.begin() + i0 + n, batch.caps);
+        k_put_caps<<<1, 128, 0, st>>>(batch, dcaps + i0);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess)
         return cuda_fail(e, "surrogate setup");
     const FeatGrid G = feat_grid(grid);
