@@ -70,6 +70,32 @@ def test_mlp_forward_and_gradients_match_oracle(M):
         assert torch.equal(y_c[:k], y_tc[:k])
 
 
+def test_tensor_core_inference_over_many_tiles_per_cta():
+    """The persistent kernel at several 128-row tiles per CTA (every SM busy,
+    a ragged last tile): accumulators alternate across tiles, barrier phases
+    wrap, and each tile's head sums are added one tile later.  All rows
+    against the bit-exact mma.sync kernel, sampled rows against the oracle."""
+    d = dev()
+    sms = torch.cuda.get_device_properties(d).multi_processor_count
+    M = sms * 128 * 5 + 77
+    rng = np.random.default_rng(12)
+    net = pcdf.SurrogateMLP(d, seed=9)
+    x = rand_x(M, rng, d)
+    y_ref = net.infer(x)
+    y_tc = net.infer_tc(x)
+    torch.cuda.synchronize()
+    assert not torch.isnan(y_tc).any()
+    scale = max(1.0, float(y_ref.abs().max()))
+    assert float((y_tc - y_ref).abs().max()) <= 1e-5 * scale
+    rows = np.concatenate([rng.choice(M, 500, replace=False), np.arange(M - 77, M)])
+    want, _ = omlp.forward(net.params(), x[rows].float().cpu().double().numpy(), rounding=True)
+    got = y_tc[rows].cpu().double().numpy()
+    assert np.max(np.abs(got - want)) <= 2e-2 * max(1.0, np.max(np.abs(want)))
+    # the same rows through a device row count
+    cnt = torch.tensor([M - 77], dtype=torch.int32, device=d)
+    assert torch.equal(net.infer_tc(x, count=cnt)[: M - 77], y_tc[: M - 77])
+
+
 def test_adam_step():
     d = dev()
     rng = np.random.default_rng(1)
