@@ -540,17 +540,20 @@ __global__ void k_pack_hidden(const bf16 *__restrict__ wh, bf16 *__restrict__ pa
 //   warp 1               producer: the x tiles (double-buffered) and the
 //                        packed W2/W3 chunks through the 4-stage ring;
 //   warps 2..9           epilogue: warp w reads TMEM lanes 32 (w % 4) .. and,
-//                        in group (w - 2) / 4, every second 32-column slice.
+//                        in group g = (w - 2) / 4, the 32-column slices
+//                        g, g + 2, g + 4, g + 6 of every layer.
 // Tensor memory holds two 256-column accumulators; the layers of the CTA's
 // tiles (q = 3 * tile + layer) alternate between them, so the epilogue of
 // layer q overlaps the products of layer q + 1: the four products of chunk c
-// (64 columns) of layer q + 1 are issued as soon as both groups have written
-// those columns of its A operand (barrier aready[c]), and an accumulator is
-// overwritten only after every epilogue thread has read it (accempty).  The head sums each group's
+// (64 columns) of layer q + 1 are issued as soon as the two groups holding its
+// slices have written those columns of its A operand (barrier aready[c]), and
+// an accumulator is overwritten only after every epilogue thread has read it
+// (accempty).  The head sums each group's
 // columns and the groups are added in a fixed order.
 // ---------------------------------------------------------------------------
 namespace ws {
 constexpr int kStages = 4, kEpiWarps = 8, kGroups = kEpiWarps / 4, kThreads = 32 * (2 + kEpiWarps);
+constexpr int kSlices = 8 / kGroups;  // 32-column slices of a layer per epilogue warp
 constexpr int kChunks = kW / tc::kKC;  // chunks of a hidden layer
 constexpr uint32_t kCols = 512;
 constexpr uint32_t kBytesA = 128 * kW * 2, kBytesChunk = kW * tc::kKC * 2, kBytesX = 128 * kIn * 2,
@@ -560,7 +563,8 @@ constexpr uint32_t oA = 0, oRing = oA + kBytesA, oX = oRing + kStages * kBytesCh
                    kEnd = oPart + 2 * kGroups * 128 * 4;
 constexpr size_t kSmem = 1024 + (size_t)kEnd;
 static_assert(kSmem <= 227 * 1024, "shared memory");
-static_assert(kEpiWarps == 8 && kGroups == 2, "two groups of four warps: each 64-column chunk is two 32-column slices");
+static_assert(kEpiWarps % 4 == 0 && 8 % kGroups == 0 && kGroups % 2 == 0,
+              "groups of four warps; the two slices of a 64-column chunk belong to two groups");
 
 // lane 0's value for every lane of the (converged) warp, through the warp's
 // own shared slot, so that the warp takes every branch as a whole
@@ -626,7 +630,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             tc::mbar_init(&partfull[i], ws::kEpiWarps * 32);
         }
         for (int j = 0; j < ws::kChunks; ++j)
-            tc::mbar_init(&aready[j], ws::kEpiWarps * 32);
+            tc::mbar_init(&aready[j], 2 * 4 * 32);  // two slices, each written by the four warps of its group
         tc::mbar_init(&drain);
         tc::fence_mbar_init();
         s_fail = 0;
@@ -771,6 +775,24 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             return true;
         };
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        // this warp's slices group, group + kGroups, ... of the accumulator at
+        // tb; the next slice's load is in flight while f converts the current
+        auto each_slice = [&](uint32_t tb, auto &&f) {
+            uint32_t va[32], vb[32];
+            tc::tmem_ld32_async(tb + (uint32_t)(32 * group), va);
+            tc::tmem_wait_ld(va);
+#pragma unroll
+            for (int k = 0; k < ws::kSlices; ++k) {
+                const int j = group + k * ws::kGroups;
+                uint32_t(&cur)[32] = (k & 1) ? vb : va;
+                uint32_t(&nxt)[32] = (k & 1) ? va : vb;
+                if (k + 1 < ws::kSlices)
+                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (j + ws::kGroups)), nxt);
+                f(cur, j);
+                if (k + 1 < ws::kSlices)
+                    tc::tmem_wait_ld(nxt);
+            }
+        };
         int it = 0;
         long long tile = blockIdx.x;
         bool ok = true;
@@ -805,19 +827,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                         tc::fence_before();
                         tc::mbar_arrive(&aready[j >> 1]);
                     };
-                    uint32_t va[32], vb[32];
-                    tc::tmem_ld32_async(tb + (uint32_t)(32 * group), va);
-                    tc::tmem_wait_ld(va);
-                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 2)), vb);
-                    slice(va, group);
-                    tc::tmem_wait_ld(vb);
-                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 4)), va);
-                    slice(vb, group + 2);
-                    tc::tmem_wait_ld(va);
-                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 6)), vb);
-                    slice(va, group + 4);
-                    tc::tmem_wait_ld(vb);
-                    slice(vb, group + 6);
+                    each_slice(tb, slice);
                     tc::mbar_arrive(&accempty[a]);
                 } else {
                     // head: relu(D + b3) rounded to BF16 (as stored between layers), . w4,
@@ -839,19 +849,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                             acc4[3] = fmaf(__uint_as_float(p1 & 0xffff0000u), w.w, acc4[3]);
                         }
                     };
-                    uint32_t va[32], vb[32];
-                    tc::tmem_ld32_async(tb + (uint32_t)(32 * group), va);
-                    tc::tmem_wait_ld(va);
-                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 2)), vb);
-                    slice(va, group);
-                    tc::tmem_wait_ld(vb);
-                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 4)), va);
-                    slice(vb, group + 2);
-                    tc::tmem_wait_ld(va);
-                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (group + 6)), vb);
-                    slice(va, group + 4);
-                    tc::tmem_wait_ld(vb);
-                    slice(vb, group + 6);
+                    each_slice(tb, slice);
                     tc::fence_before();
                     tc::mbar_arrive(&accempty[a]);
                     sPart[(it & 1) * (ws::kGroups * 128) + group * 128 + r] = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
