@@ -38,7 +38,7 @@ EXPORTS = (
     "pcdf_scratch_workspace_bytes", "pcdf_build_from_scratch",
     "pcdf_query_cost", "pcdf_query_cost_backward",
     "pcdf_batch_create", "pcdf_batch_destroy", "pcdf_batch_workspace_bytes", "pcdf_batch_tiles_used",
-    "pcdf_batch_upload", "pcdf_batch_run", "pcdf_batch_error", "pcdf_batch_autotune_workspace_bytes",
+    "pcdf_batch_upload", "pcdf_batch_run", "pcdf_batch_error", "pcdf_batch_block_stage", "pcdf_batch_autotune_workspace_bytes",
     "pcdf_batch_autotune",
     "pcdf_mlp_state_bytes", "pcdf_mlp_workspace_bytes", "pcdf_mlp_init", "pcdf_mlp_forward", "pcdf_mlp_infer", "pcdf_mlp_infer_tc", "pcdf_mlp_infer_tc_count",
     "pcdf_mlp_backward",
@@ -81,6 +81,7 @@ def _declare(lib):
         "pcdf_batch_upload": [P, P, SZ, P],
         "pcdf_batch_run": [P, P, P],
         "pcdf_batch_error": [P, P, P, ctypes.POINTER(I32)],
+        "pcdf_batch_block_stage": [P, I32, I32],
         "pcdf_batch_autotune_workspace_bytes": [E, I32, SZP],
         "pcdf_batch_autotune": [E, I32, P, SZ, P, I32, TL, ctypes.POINTER(ctypes.c_float)],
     })

@@ -520,6 +520,14 @@ class Batch:
                                               ctypes.byref(code)), "pcdf_batch_error")
         return code.value
 
+    def block_stage(self, env: int, stage: int):
+        """Testing aid for the failure path (pcdf_batch_block_stage): the
+        items waiting on stage `stage` of environment `env` can only time out;
+        the next run() then reports PCDF_ETIMEOUT through error()."""
+        _lib.check(self._lib.pcdf_batch_block_stage(self._h, int(env), int(stage)), "pcdf_batch_block_stage")
+        _lib.check(self._lib.pcdf_batch_upload(self._h, _ptr(self.workspace), self.workspace.numel(),
+                                               ctypes.c_void_p(_stream(self.device))), "pcdf_batch_upload")
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.pcdf_batch_destroy(self._h)

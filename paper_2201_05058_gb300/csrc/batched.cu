@@ -347,6 +347,14 @@ int pcdf_batch_tiles_used(const pcdf_batch *b, pcdf_batch_tiles *tiles)
     return PCDF_OK;
 }
 
+int pcdf_batch_block_stage(pcdf_batch *b, int32_t env, int32_t stage)
+{
+    if (!b || env < 0 || env >= b->n_env || stage < 0 || stage > 3)
+        return fail(PCDF_EINVAL, "batch, environment %d or stage %d out of range", env, stage);
+    b->desc[env].need[stage] = 1 << 30;  // above any item count: the waits on it can only expire
+    return PCDF_OK;
+}
+
 int pcdf_batch_upload(pcdf_batch *b, void *workspace, size_t workspace_bytes, void *stream)
 {
     using namespace pcdf;

@@ -67,6 +67,25 @@ def test_batched_matches_oracle_and_single_calls(batch_case):
     b.close()
 
 
+def test_an_expired_wait_reports_timeout_and_the_context_stays_usable(batch_case):
+    """The failure path without a GPU fault: environment 0's capsule stage is
+    given a target no run reaches, so its composite items wait until their
+    bound (about a second) expires and are skipped; error() reports
+    PCDF_ETIMEOUT.  A fresh batch on the same context is then exact again."""
+    envs, dev_envs, want = batch_case
+    b = pcdf.Batch(dev_envs)
+    b.block_stage(0, 3)
+    b.run()
+    assert b.error() == -4  # PCDF_ETIMEOUT
+    b.close()
+    b2 = pcdf.Batch(dev_envs)
+    b2.run()
+    assert b2.error() == 0
+    for e in range(len(dev_envs)):
+        assert np.array_equal(b2.comp_sq[e].cpu().numpy(), want[e]), e
+    b2.close()
+
+
 @pytest.mark.parametrize("tiles", [(8, 1, 1), (32, 4, 1), (128, 1, 4), (8, 4, 4), (128, 4, 1), (32, 1, 4)])
 def test_every_tile_shape_gives_identical_bits(batch_case, tiles):
     envs, dev_envs, want = batch_case
