@@ -12,6 +12,7 @@ from .api import (  # noqa: F401
     surrogate_features,
     surrogate_finish,
     surrogate_query,
+    surrogate_step,
     surrogate_select,
     surrogate_samples,
     Batch,

@@ -795,6 +795,32 @@ def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps
     return h, d, nfb
 
 
+def surrogate_step(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps, band, comp_workspace,
+                   caps_dev=None, err_bound=None):
+    """One plan step of the surrogate: the capsule-slab partials of the
+    composite's first stage (composite_prepare into comp_workspace) run on a
+    side stream while the rows are selected on the current stream; the
+    network waits for both (its persistent grid wants every SM), then the
+    exact fallback reads the partials.  No host synchronisation: capturable
+    in a CUDA graph.  Returns (h, d, n_fallback[1]) as surrogate_query."""
+    caps = _caps_host(caps)
+    dev = spheres.device
+    if caps_dev is None:
+        caps_dev = torch.from_numpy(caps).to(dev)
+    T = int(caps.shape[0])
+    main = torch.cuda.current_stream(dev)
+    side = _side_stream(dev)
+    side.wait_stream(main)
+    with torch.cuda.stream(side):
+        composite_prepare(grid, caps, comp_workspace)
+    comp_workspace.record_stream(side)
+    x, yi, cnt = surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev, sync=False)
+    main.wait_stream(side)
+    y = model.infer_tc(x, count=cnt) if x.shape[0] else torch.empty(1, dtype=torch.float32, device=dev)
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound,
+                            comp_workspace, y_index=yi)
+
+
 def surrogate_query(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps, band, caps_dev=None,
                     err_bound=None, comp_workspace=None):
     """Hinge cost of every sphere through the network, exact within `band`

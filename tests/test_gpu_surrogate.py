@@ -217,6 +217,10 @@ def test_surrogate_step_replays_from_a_cuda_graph():
         return pcdf.surrogate_query(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, band=0.3,
                                     err_bound=0.5, caps_dev=caps_dev, comp_workspace=ws)
 
+    def step_overlapped():
+        return pcdf.surrogate_step(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, 0.3, ws,
+                                   caps_dev=caps_dev, err_bound=0.5)
+
     side = torch.cuda.Stream(d)
     side.wait_stream(torch.cuda.current_stream(d))
     with torch.cuda.stream(side):
@@ -234,6 +238,20 @@ def test_surrogate_step_replays_from_a_cuda_graph():
     h_e, d_e, n_e = step()
     assert torch.equal(h_g, h_e) and torch.equal(d_g, d_e)
     assert int(n_g.item()) == int(n_e.item()) > 0
+    # the overlapped plan step (capsule slab on a side stream), eager and as a graph
+    h_o, d_o, n_o = step_overlapped()
+    assert torch.equal(h_o, h_e) and torch.equal(d_o, d_e) and int(n_o.item()) == int(n_e.item())
+    side = torch.cuda.Stream(d)
+    side.wait_stream(torch.cuda.current_stream(d))
+    with torch.cuda.stream(side):
+        step_overlapped()
+    torch.cuda.current_stream(d).wait_stream(side)
+    graph2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph2):
+        h_g2, d_g2, _ = step_overlapped()
+    graph2.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(h_g2, h_e) and torch.equal(d_g2, d_e)
 
 
 def test_row_selection_skips_only_static_cells():
