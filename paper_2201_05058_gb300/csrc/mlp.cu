@@ -584,11 +584,13 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
 }
 }  // namespace ws
 
-// two floats rounded to BF16 (nearest even), low half first
-__device__ __forceinline__ uint32_t bf2_bits(float lo, float hi)
+// relu of two floats rounded to BF16 (nearest even), low half first, in one
+// conversion (rounding keeps the sign, so relu before or after it agree)
+__device__ __forceinline__ uint32_t bf2_relu_bits(float lo, float hi)
 {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&h);
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
 __global__ void __launch_bounds__(ws::kThreads, 1)
@@ -817,10 +819,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                             const float4 b1 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq + 4);
                             const uint32_t *u = v + 8 * gq;
                             uint4 pk;
-                            pk.x = bf2_bits(fmaxf(__uint_as_float(u[0]) + b0.x, 0.f), fmaxf(__uint_as_float(u[1]) + b0.y, 0.f));
-                            pk.y = bf2_bits(fmaxf(__uint_as_float(u[2]) + b0.z, 0.f), fmaxf(__uint_as_float(u[3]) + b0.w, 0.f));
-                            pk.z = bf2_bits(fmaxf(__uint_as_float(u[4]) + b1.x, 0.f), fmaxf(__uint_as_float(u[5]) + b1.y, 0.f));
-                            pk.w = bf2_bits(fmaxf(__uint_as_float(u[6]) + b1.z, 0.f), fmaxf(__uint_as_float(u[7]) + b1.w, 0.f));
+                            pk.x = bf2_relu_bits(__uint_as_float(u[0]) + b0.x, __uint_as_float(u[1]) + b0.y);
+                            pk.y = bf2_relu_bits(__uint_as_float(u[2]) + b0.z, __uint_as_float(u[3]) + b0.w);
+                            pk.z = bf2_relu_bits(__uint_as_float(u[4]) + b1.x, __uint_as_float(u[5]) + b1.y);
+                            pk.w = bf2_relu_bits(__uint_as_float(u[6]) + b1.z, __uint_as_float(u[7]) + b1.w);
                             *reinterpret_cast<uint4 *>(sA + tc::kmaj(r, 32 * j + 8 * gq, kW)) = pk;
                         }
                         tc::fence_proxy_async();
@@ -839,10 +841,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                             const float4 b = *reinterpret_cast<const float4 *>(sBias + 2 * kW + 32 * j + 4 * gq);
                             const float4 w = *reinterpret_cast<const float4 *>(sW4 + 32 * j + 4 * gq);
                             const uint32_t *u = v + 4 * gq;
-                            const uint32_t p0 = bf2_bits(fmaxf(__uint_as_float(u[0]) + b.x, 0.f),
-                                                         fmaxf(__uint_as_float(u[1]) + b.y, 0.f));
-                            const uint32_t p1 = bf2_bits(fmaxf(__uint_as_float(u[2]) + b.z, 0.f),
-                                                         fmaxf(__uint_as_float(u[3]) + b.w, 0.f));
+                            const uint32_t p0 = bf2_relu_bits(__uint_as_float(u[0]) + b.x, __uint_as_float(u[1]) + b.y);
+                            const uint32_t p1 = bf2_relu_bits(__uint_as_float(u[2]) + b.z, __uint_as_float(u[3]) + b.w);
                             acc4[0] = fmaf(__uint_as_float(p0 << 16), w.x, acc4[0]);
                             acc4[1] = fmaf(__uint_as_float(p0 & 0xffff0000u), w.y, acc4[1]);
                             acc4[2] = fmaf(__uint_as_float(p1 << 16), w.z, acc4[2]);
