@@ -169,6 +169,30 @@ def test_fallback_everywhere_is_bit_exact():
     assert torch.equal(h2, h_ex)
 
 
+def test_full_size_plan_step_exact_path_is_bit_exact():
+    """The bench's plan step at full size: 1,024,000 spheres (1024
+    trajectories x 40 states x 25 spheres) on 20 fields of 64^3, through
+    surrogate_step (capsule slab on a side stream, device row count, slab
+    fallback).  Untrained network and an unbounded band: every answer comes
+    from the exact path or from a cell the static field provably wins, so h
+    equals the exact composite query bit for bit."""
+    d = dev()
+    sc = scenes.scene_small_walking(seed=6001, T=20, H=1)
+    grid = sc["grid"]
+    rng = np.random.default_rng(6001)
+    sph_np, tidx_np = scenes.spheres_along_paths(grid, 1024, 40, 25, rng, T=20)
+    sph = torch.from_numpy(sph_np).to(d)
+    tidx = torch.from_numpy(tidx_np).to(d)
+    assert sph.numel() // 4 == 1024000
+    static_sq, static_sdf, h_ex, _ = exact_query(sc, d, sph, tidx, 0.2)
+    net = pcdf.SurrogateMLP(d, seed=21)
+    ws = pcdf.composite_workspace(grid, sc["caps"], d)
+    h, _, nfb = pcdf.surrogate_step(net, grid, static_sq, static_sdf, sph, tidx, sc["caps"], 0.2, 1.0e9, ws)
+    torch.cuda.synchronize()
+    assert 0 < int(nfb.item()) <= 1024000
+    assert torch.equal(h, h_ex)
+
+
 def test_fallback_exact_with_several_humans():
     d = dev()
     sc = scenes.scene_small_walking(seed=78, T=6, H=3)
