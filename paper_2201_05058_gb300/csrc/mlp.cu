@@ -592,6 +592,27 @@ __device__ __forceinline__ uint32_t bf2_relu_bits(float lo, float hi)
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
     return d;
 }
+// relu(v + b) of a pair rounded to BF16 as above, the two additions in one
+// paired FP32 instruction (each lane an IEEE round-to-nearest add)
+__device__ __forceinline__ uint32_t bf2_bias_relu_bits(float v0, float v1, float b0, float b1)
+{
+    uint32_t d;
+    asm("{\n\t.reg .b64 a, b, s;\n\t.reg .f32 lo, hi;\n\t"
+        "mov.b64 a, {%1, %2};\n\tmov.b64 b, {%3, %4};\n\tadd.rn.f32x2 s, a, b;\n\t"
+        "mov.b64 {lo, hi}, s;\n\tcvt.rn.relu.bf16x2.f32 %0, hi, lo;\n\t}"
+        : "=r"(d)
+        : "f"(v0), "f"(v1), "f"(b0), "f"(b1));
+    return d;
+}
+// (a0, a1) += (x0, x1) * (y0, y1), each lane an IEEE fused multiply-add
+__device__ __forceinline__ void fma2(float &a0, float &a1, float x0, float x1, float y0, float y1)
+{
+    asm("{\n\t.reg .b64 a, x, y;\n\t"
+        "mov.b64 a, {%0, %1};\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "fma.rn.f32x2 a, x, y, a;\n\tmov.b64 {%0, %1}, a;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(x0), "f"(x1), "f"(y0), "f"(y1));
+}
 
 __global__ void __launch_bounds__(ws::kThreads, 1)
     k_mlp_infer_ws(const bf16 *__restrict__ wh, const float *__restrict__ p, const bf16 *__restrict__ packed,
@@ -819,10 +840,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                             const float4 b1 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq + 4);
                             const uint32_t *u = v + 8 * gq;
                             uint4 pk;
-                            pk.x = bf2_relu_bits(__uint_as_float(u[0]) + b0.x, __uint_as_float(u[1]) + b0.y);
-                            pk.y = bf2_relu_bits(__uint_as_float(u[2]) + b0.z, __uint_as_float(u[3]) + b0.w);
-                            pk.z = bf2_relu_bits(__uint_as_float(u[4]) + b1.x, __uint_as_float(u[5]) + b1.y);
-                            pk.w = bf2_relu_bits(__uint_as_float(u[6]) + b1.z, __uint_as_float(u[7]) + b1.w);
+                            pk.x = bf2_bias_relu_bits(__uint_as_float(u[0]), __uint_as_float(u[1]), b0.x, b0.y);
+                            pk.y = bf2_bias_relu_bits(__uint_as_float(u[2]), __uint_as_float(u[3]), b0.z, b0.w);
+                            pk.z = bf2_bias_relu_bits(__uint_as_float(u[4]), __uint_as_float(u[5]), b1.x, b1.y);
+                            pk.w = bf2_bias_relu_bits(__uint_as_float(u[6]), __uint_as_float(u[7]), b1.z, b1.w);
                             *reinterpret_cast<uint4 *>(sA + tc::kmaj(r, 32 * j + 8 * gq, kW)) = pk;
                         }
                         tc::fence_proxy_async();
@@ -841,12 +862,12 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                             const float4 b = *reinterpret_cast<const float4 *>(sBias + 2 * kW + 32 * j + 4 * gq);
                             const float4 w = *reinterpret_cast<const float4 *>(sW4 + 32 * j + 4 * gq);
                             const uint32_t *u = v + 4 * gq;
-                            const uint32_t p0 = bf2_relu_bits(__uint_as_float(u[0]) + b.x, __uint_as_float(u[1]) + b.y);
-                            const uint32_t p1 = bf2_relu_bits(__uint_as_float(u[2]) + b.z, __uint_as_float(u[3]) + b.w);
-                            acc4[0] = fmaf(__uint_as_float(p0 << 16), w.x, acc4[0]);
-                            acc4[1] = fmaf(__uint_as_float(p0 & 0xffff0000u), w.y, acc4[1]);
-                            acc4[2] = fmaf(__uint_as_float(p1 << 16), w.z, acc4[2]);
-                            acc4[3] = fmaf(__uint_as_float(p1 & 0xffff0000u), w.w, acc4[3]);
+                            const uint32_t p0 = bf2_bias_relu_bits(__uint_as_float(u[0]), __uint_as_float(u[1]), b.x, b.y);
+                            const uint32_t p1 = bf2_bias_relu_bits(__uint_as_float(u[2]), __uint_as_float(u[3]), b.z, b.w);
+                            fma2(acc4[0], acc4[1], __uint_as_float(p0 << 16), __uint_as_float(p0 & 0xffff0000u), w.x,
+                                 w.y);
+                            fma2(acc4[2], acc4[3], __uint_as_float(p1 << 16), __uint_as_float(p1 & 0xffff0000u), w.z,
+                                 w.w);
                         }
                     };
                     each_slice(tb, slice);
