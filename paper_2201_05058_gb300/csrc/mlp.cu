@@ -658,10 +658,25 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         tc::fence_mbar_init();
         s_fail = 0;
     }
-    // W1, the biases and the head weights
+    // W1, the biases and the head weights.  The first layer's bias rides in
+    // the product: the x tiles carry 1 in their three padding columns (13,
+    // 14, 15) and W1 gets b1 there, split into three BF16 parts whose sum is
+    // b1 to FP32 rounding (high part, then the high parts of the remainders).
+    static_assert(kIn == 16 && PCDF_MLP_IN == 13, "three padding columns carry the first bias");
     for (int v = tid; v < kW * 2; v += ws::kThreads) {
         const int n = v >> 1, h = (v & 1) * 8;
-        cp16(sW1 + tc::kmaj(n, h, kIn), wh + hW1 + n * kIn + h, 16);
+        uint4 w = __ldg(reinterpret_cast<const uint4 *>(wh + hW1 + n * kIn + h));
+        if (h == 8) {
+            const float b = p[oB1 + n];
+            const __nv_bfloat16 bh = __float2bfloat16_rn(b);
+            const float r1 = b - __bfloat162float(bh);
+            const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 bl = __float2bfloat16_rn(r1 - __bfloat162float(bm));
+            // elements 8..15 of the row: k = 13 is the high half of .z, 14 and 15 are .w
+            w.z = (w.z & 0xFFFFu) | ((uint32_t)__bfloat16_as_ushort(bh) << 16);
+            w.w = (uint32_t)__bfloat16_as_ushort(bm) | ((uint32_t)__bfloat16_as_ushort(bl) << 16);
+        }
+        *reinterpret_cast<uint4 *>(sW1 + tc::kmaj(n, h, kIn)) = w;
     }
     for (int i = tid; i < kW; i += ws::kThreads) {
         sBias[i] = p[oB1 + i];
@@ -756,6 +771,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                 uint4 val = make_uint4(0u, 0u, 0u, 0u);
                 if (m0 + r < M)
                     val = __ldg(reinterpret_cast<const uint4 *>(x + (m0 + r) * kIn + h));
+                if (h == 8) {  // the padding columns 13, 14, 15 carry 1 (the first bias, above)
+                    val.z = (val.z & 0xFFFFu) | (0x3F80u << 16);
+                    val.w = 0x3F803F80u;
+                }
                 *reinterpret_cast<uint4 *>(xb + tc::kmaj(r, h, kIn)) = val;
             }
             tc::fence_proxy_async();
@@ -831,19 +850,27 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                 const uint32_t tb = tmem + (uint32_t)a * 256u + lane_off;
                 if (L < 2) {
                     const float *bias = sBias + L * kW;
+                    const bool with_bias = L == 1;  // the first layer's bias came with its product
                     // slice j (32 columns): bias, ReLU, BF16 into the A operand, then
                     // its chunk's barrier; the next slice's load is in flight meanwhile
                     auto slice = [&](const uint32_t(&v)[32], int j) {
 #pragma unroll
                         for (int gq = 0; gq < 4; ++gq) {
-                            const float4 b0 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq);
-                            const float4 b1 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq + 4);
                             const uint32_t *u = v + 8 * gq;
                             uint4 pk;
-                            pk.x = bf2_bias_relu_bits(__uint_as_float(u[0]), __uint_as_float(u[1]), b0.x, b0.y);
-                            pk.y = bf2_bias_relu_bits(__uint_as_float(u[2]), __uint_as_float(u[3]), b0.z, b0.w);
-                            pk.z = bf2_bias_relu_bits(__uint_as_float(u[4]), __uint_as_float(u[5]), b1.x, b1.y);
-                            pk.w = bf2_bias_relu_bits(__uint_as_float(u[6]), __uint_as_float(u[7]), b1.z, b1.w);
+                            if (with_bias) {
+                                const float4 b0 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq);
+                                const float4 b1 = *reinterpret_cast<const float4 *>(bias + 32 * j + 8 * gq + 4);
+                                pk.x = bf2_bias_relu_bits(__uint_as_float(u[0]), __uint_as_float(u[1]), b0.x, b0.y);
+                                pk.y = bf2_bias_relu_bits(__uint_as_float(u[2]), __uint_as_float(u[3]), b0.z, b0.w);
+                                pk.z = bf2_bias_relu_bits(__uint_as_float(u[4]), __uint_as_float(u[5]), b1.x, b1.y);
+                                pk.w = bf2_bias_relu_bits(__uint_as_float(u[6]), __uint_as_float(u[7]), b1.z, b1.w);
+                            } else {
+                                pk.x = bf2_relu_bits(__uint_as_float(u[0]), __uint_as_float(u[1]));
+                                pk.y = bf2_relu_bits(__uint_as_float(u[2]), __uint_as_float(u[3]));
+                                pk.z = bf2_relu_bits(__uint_as_float(u[4]), __uint_as_float(u[5]));
+                                pk.w = bf2_relu_bits(__uint_as_float(u[6]), __uint_as_float(u[7]));
+                            }
                             *reinterpret_cast<uint4 *>(sA + tc::kmaj(r, 32 * j + 8 * gq, kW)) = pk;
                         }
                         tc::fence_proxy_async();
