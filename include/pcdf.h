@@ -351,9 +351,11 @@ int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, vo
  * epilogue warps read each layer back with tcgen05.ld for the bias, ReLU and
  * BF16 rounding, overlapping the next layer's products.  Same arithmetic up
  * to the order of the FP32 sums (outputs within FP32 rounding of
- * pcdf_mlp_infer, not bit-identical).  A tile whose bounded wait on the
- * tensor cores expires (about a second) gets NaN, as do the CTA's later
- * tiles. */
+ * pcdf_mlp_infer, not bit-identical).  The three padding columns of x
+ * (after the PCDF_MLP_IN features) are ignored: the kernel puts 1 there and
+ * the first layer's bias in the matching columns of W1.  A tile whose
+ * bounded wait on the tensor cores expires (about a second) gets NaN, as do
+ * the CTA's later tiles. */
 int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);
 /* pcdf_mlp_infer_tc_count  pcdf_mlp_infer_tc over the first *count rows of x
  * (count: device int32, read by the kernel, clamped to [0, M_max]), so that
