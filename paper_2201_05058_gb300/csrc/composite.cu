@@ -8,9 +8,12 @@ namespace pcdf {
 namespace {
 
 __global__ void __launch_bounds__(128)
-    k_dyn_xy(const __grid_constant__ CapBatch caps, int H, int nx, int ny, int zlo, int S, int t0, int cap,
-             int32_t *__restrict__ dyn_mid)
+    k_dyn_xy(const __grid_constant__ CapBatch caps, const __grid_constant__ SlabMap map, int H, int nx, int ny,
+             int zlo, int S, int t0, int cap, int32_t *__restrict__ dyn_mid)
 {
+    // a slice whose cross-sections equal an earlier slice's is read from that one
+    if (map.on && map.rep[(t0 + (int)blockIdx.y) * S + (int)blockIdx.x] != (int)blockIdx.x)
+        return;
     extern __shared__ __align__(16) int32_t sm[];
     comp::dyn_xy_slice(caps.caps + blockIdx.y * H, H, nx, ny, zlo, S, t0 + (int)blockIdx.y, (int)blockIdx.x, cap,
                        dyn_mid, sm);
@@ -21,13 +24,14 @@ __global__ void __launch_bounds__(128)
 template <bool kSq, bool kSdfOut, bool kStaticSdf>
 __global__ void __launch_bounds__(128, 8)
     k_composite_z(const int32_t *__restrict__ static_sq, const float *__restrict__ static_sdf,
-                  const int32_t *__restrict__ colmax, const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz,
-                  int zlo, int S, int t0, int nt, int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox,
-                  int vec)
+                  const int32_t *__restrict__ colmax, const int32_t *__restrict__ dyn_mid,
+                  const __grid_constant__ SlabMap map, int nx, int ny, int nz, int zlo, int S, int t0, int nt,
+                  int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf, float vox, int vec)
 {
     extern __shared__ uint32_t smem[];
-    comp::composite_block_short<kSq, kSdfOut, kStaticSdf>(static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S,
-                                                          t0 + (int)(blockIdx.x % nt),
+    const int t = t0 + (int)(blockIdx.x % nt);
+    comp::composite_block_short<kSq, kSdfOut, kStaticSdf>(static_sq, static_sdf, colmax, dyn_mid,
+                                                          map.on ? map.rep + t * S : nullptr, nx, ny, nz, zlo, S, t,
                                                           (long long)(blockIdx.x / nt) * blockDim.x, comp_sq, comp_sdf,
                                                           vox, vec != 0, smem);
 }
@@ -62,8 +66,8 @@ size_t dyn_xy_smem(int ny, int H, int cap) { return ((size_t)ny * (H + 1) + (siz
 
 bool dyn_xy_fits(int ny, int H, int cap) { return dyn_xy_smem(ny, H, cap) <= 200 * 1024; }
 
-cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, int S, int t0, int n_t, int cap,
-                          int32_t *dyn_mid, cudaStream_t stream)
+cudaError_t launch_dyn_xy(const CapBatch *caps, const SlabMap *map, int H, int nx, int ny, int zlo, int S, int t0,
+                          int n_t, int cap, int32_t *dyn_mid, cudaStream_t stream)
 {
     if (S <= 0 || n_t <= 0)
         return cudaSuccess;
@@ -71,8 +75,8 @@ cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, 
     cudaError_t e = cudaFuncSetAttribute(k_dyn_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_dyn_xy<<<dim3((unsigned)S, (unsigned)n_t), kDynThreads, smem, stream>>>(*caps, H, nx, ny, zlo, S, t0, cap,
-                                                                               dyn_mid);
+    k_dyn_xy<<<dim3((unsigned)S, (unsigned)n_t), kDynThreads, smem, stream>>>(*caps, *map, H, nx, ny, zlo, S, t0,
+                                                                               cap, dyn_mid);
     return cudaGetLastError();
 }
 
@@ -80,15 +84,16 @@ namespace {
 
 template <bool kSq, bool kSdfOut, bool kStaticSdf>
 cudaError_t launch_cz(int nblk, int nthr, size_t smem, const int32_t *static_sq, const float *static_sdf,
-                      const int32_t *colmax, const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int t0,
-                      int nt, int32_t *comp_sq, float *comp_sdf, float vox, int vec, cudaStream_t stream)
+                      const int32_t *colmax, const int32_t *dyn_mid, const SlabMap *map, int nx, int ny, int nz,
+                      int zlo, int S, int t0, int nt, int32_t *comp_sq, float *comp_sdf, float vox, int vec,
+                      cudaStream_t stream)
 {
     auto kern = k_composite_z<kSq, kSdfOut, kStaticSdf>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    kern<<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S, t0,
-                                                 nt, comp_sq, comp_sdf, vox, vec);
+    kern<<<(unsigned)nblk, nthr, smem, stream>>>(static_sq, static_sdf, colmax, dyn_mid, *map, nx, ny, nz, zlo, S,
+                                                 t0, nt, comp_sq, comp_sdf, vox, vec);
     return cudaGetLastError();
 }
 
@@ -104,8 +109,8 @@ cudaError_t launch_colmax(const int32_t *sq, int nx, int ny, int nz, int32_t *co
 }
 
 cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf, const int32_t *colmax,
-                               const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int t0, int nt,
-                               int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream)
+                               const int32_t *dyn_mid, const SlabMap *map, int nx, int ny, int nz, int zlo, int S,
+                               int t0, int nt, int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream)
 {
     const long long V2 = (long long)nx * ny;
     const int words = S + 2 + (S + 31) / 32;
@@ -120,8 +125,8 @@ cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf
     const int vec = V2 % 4 == 0 && aligned16(static_sq) && (!st || aligned16(static_sdf)) &&
                     (!sq || aligned16(comp_sq)) && (!sd || aligned16(comp_sdf));
 #define PCDF_CZ(a, b, c)                                                                                            \
-    return launch_cz<a, b, c>(nblk, nthr, smem, static_sq, static_sdf, colmax, dyn_mid, nx, ny, nz, zlo, S, t0, nt, \
-                              comp_sq, comp_sdf, vox, vec, stream)
+    return launch_cz<a, b, c>(nblk, nthr, smem, static_sq, static_sdf, colmax, dyn_mid, map, nx, ny, nz, zlo, S, t0, \
+                              nt, comp_sq, comp_sdf, vox, vec, stream)
     if (sq && sd && st)
         PCDF_CZ(true, true, true);
     if (sq && sd)

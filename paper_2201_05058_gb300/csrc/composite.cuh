@@ -415,7 +415,7 @@ __device__ __forceinline__ void copy_static_block(const int32_t *__restrict__ st
 template <bool kCoherent, class O_t>
 __device__ __forceinline__ int build_sets(uint32_t *tile, uint32_t *mk, bool occ, int nthr, int S, int nz, int zlo,
                                           const int32_t *scol, const float *sfcol, const int32_t *dcol, long long V2,
-                                          const O_t &out, int &za, int &zb)
+                                          const O_t &out, int &za, int &zb, const uint8_t *rep = nullptr)
 {
     constexpr bool kStaticSdf = O_t::kHaveStatic;
     const int nw = (S + 31) >> 5;
@@ -471,7 +471,7 @@ __device__ __forceinline__ int build_sets(uint32_t *tile, uint32_t *mk, bool occ
         // restore the staged column for set O
 #pragma unroll 8
         for (int e = 0; e < S; ++e)
-            tile[(e + 1) * nthr] = (uint32_t)ldx<kCoherent>(dcol + (long long)e * V2);
+            tile[(e + 1) * nthr] = (uint32_t)ldx<kCoherent>(dcol + (long long)(rep ? rep[e] : e) * V2);
     }
 
     // set O over the slab: sites are the free slab voxels with a finite
@@ -536,8 +536,10 @@ __device__ __forceinline__ void composite_block(const int32_t *__restrict__ stat
 
 // The CTA of k_composite_z: columns [col0, col0 + blockDim.x) of time t with
 // the static shortcuts.  colmax: the largest static value of every column;
-// vec: the CTA may copy with 16-byte accesses.  Block-wide barriers: every
-// thread of the CTA calls.
+// rep (nullable: the identity): slab element e of time t is stored in slice
+// rep[e] (slices of equal capsule cross-sections computed once); vec: the
+// CTA may copy with 16-byte accesses.  Block-wide barriers: every thread of
+// the CTA calls.
 //  * every column static (colmax <= gmin): the CTA copies the static block;
 //  * else each column with dynamic influence has a window [w0, w1) (the slab
 //    and every z less than R slices from it, R the least integer with
@@ -549,7 +551,8 @@ template <bool kSq, bool kSdfOut, bool kStaticSdf>
 __device__ __forceinline__ void composite_block_short(const int32_t *__restrict__ static_sq,
                                                       const float *__restrict__ static_sdf,
                                                       const int32_t *__restrict__ colmax,
-                                                      const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz,
+                                                      const int32_t *__restrict__ dyn_mid,
+                                                      const uint8_t *__restrict__ rep, int nx, int ny, int nz,
                                                       int zlo, int S, int t, long long col0,
                                                       int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf,
                                                       float vox, bool vec, uint32_t *smem)
@@ -574,7 +577,7 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
     const int32_t cmax = live ? __ldg(colmax + c) : kInf32;
     if (live) {
         for (int e = 0; e < S; ++e)
-            cp_async4(tile + (e + 1) * nthr, dcol + (long long)e * V2);
+            cp_async4(tile + (e + 1) * nthr, dcol + (long long)(rep ? rep[e] : e) * V2);
         cp_async_wait_all();
 #pragma unroll 8
         for (int e = 0; e < S; ++e)
@@ -629,7 +632,7 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
     int top = -1;  // set O stack top (-1: no site, or a static column)
     if (dyn) {
         int za, zb;
-        top = build_sets<false>(tile, mk, occ, nthr, S, nz, zlo, scol, sfcol, dcol, V2, out, za, zb);
+        top = build_sets<false>(tile, mk, occ, nthr, S, nz, zlo, scol, sfcol, dcol, V2, out, za, zb, rep);
     }
     EnvCursor O(tile + nthr, nthr, top);
     const bool useO = top >= 0;

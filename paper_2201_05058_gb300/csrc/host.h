@@ -38,7 +38,11 @@ struct CompositePlan {
     int cap = 0;         // its per-thread stack capacity
     size_t need = 0;     // workspace bytes
     size_t colmax_off = 0;  // workspace offset of the static column maxima
+    std::vector<uint8_t> rep;  // [T][S] first slab slice with the same capsule cross-sections (empty: identity)
 };
+
+// the slab map of a plan as a kernel parameter (identity when the plan has none)
+void slab_map(const CompositePlan &p, SlabMap &m);
 
 int plan_composite(const pcdf_grid *grid, int T, int H, const int32_t *caps, CompositePlan &p);
 int32_t *plan_mid(const CompositePlan &p, void *workspace);

@@ -37,6 +37,19 @@ struct CapBatch {
     CapInfo caps[kMaxCapsPerLaunch];
 };
 
+// Slab slices of equal capsule cross-sections: rep[t * S + e] is the first
+// slab slice of time t whose voxel set in every capsule equals slice e's
+// (upright capsules: every slice between the caps; cap slices at the same
+// distance from their cap centres).  Only those slices are computed, and
+// every reader of the slab partials goes through the map.  A kernel
+// parameter like CapBatch; on = 0: the identity.
+constexpr int kSlabMapMax = 4096;
+struct SlabMap {
+    int32_t on;
+    int32_t S;
+    uint8_t rep[kSlabMapMax];
+};
+
 // Columns handled by one CTA of the lower-envelope pass (the CTA has two
 // threads per column, one per site set).
 constexpr int kEnvCols = 32;
@@ -66,7 +79,8 @@ cudaError_t launch_envelope_i32(const int32_t *in, int32_t *out, float *sdf, flo
 // output dyn_mid[t][s][y][x], signed 2-D partial squared distances.  `cap` is
 // the per-thread stack capacity; dyn_xy_fits tells whether it fits on chip.
 bool dyn_xy_fits(int ny, int H, int cap);
-cudaError_t launch_dyn_xy(const CapBatch *caps, int H, int nx, int ny, int zlo, int S, int t0, int n_t, int cap,
+cudaError_t launch_dyn_xy(const CapBatch *caps, const SlabMap *map, int H, int nx, int ny, int zlo, int S, int t0,
+                          int n_t, int cap,
                           int32_t *dyn_mid, cudaStream_t stream);
 
 // colmax[y][x] = largest value of the column (x, y) of sq [nz][ny][nx].
@@ -80,8 +94,8 @@ cudaError_t launch_colmax(const int32_t *sq, int nx, int ny, int nz, int32_t *co
 // column maxima of static_sq (launch_colmax): columns and z ranges where the
 // static field provably wins skip the envelope.
 cudaError_t launch_composite_z(const int32_t *static_sq, const float *static_sdf, const int32_t *colmax,
-                               const int32_t *dyn_mid, int nx, int ny, int nz, int zlo, int S, int t0, int nt,
-                               int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream);
+                               const int32_t *dyn_mid, const SlabMap *map, int nx, int ny, int nz, int zlo, int S,
+                               int t0, int nt, int32_t *comp_sq, float *comp_sdf, float vox, cudaStream_t stream);
 
 // Copies static_sq into t = t0 .. t0 + nt - 1 of comp (and its float field)
 // when no capsule touches the grid.

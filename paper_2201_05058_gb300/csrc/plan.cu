@@ -150,6 +150,65 @@ size_t full_edt_ws(const pcdf_grid *g)
 
 
 
+namespace {
+
+// The z-dependence of a capsule's voxel set in slice k, as a key: two slices
+// with equal keys hold the same voxels of it.  For a capsule whose axis is
+// upright (a and b share x and y) the exact predicate at a voxel centre p
+// (16k + 8 along z) reduces to: below the segment |p - a|^2 <= r^2, above it
+// |p - b|^2 <= r^2, which depend on z only through |p_z - a_z| or |p_z - b_z|
+// (one key per distance, the same for both caps), and between them
+// (p_x - a_x)^2 + (p_y - a_y)^2 <= r^2, the same in every slice; a cylinder
+// holds that disk between its end planes and nothing elsewhere.  Any other
+// capsule gets a key of its own in every slice.
+constexpr long long kKeyEmpty = -1, kKeyMid = -2;
+long long slice_key(const CapInfo &c, int k)
+{
+    if (c.lo[0] > c.hi[0])
+        return kKeyEmpty;  // no voxel of the grid
+    if (c.a[0] != c.b[0] || c.a[1] != c.b[1])
+        return (1LL << 40) + k;
+    const long long pz = 16LL * k + 8, za = std::min(c.a[2], c.b[2]), zb = std::max(c.a[2], c.b[2]);
+    if (c.cyl)
+        return pz >= za && pz <= zb ? kKeyMid : kKeyEmpty;
+    if (pz > za && pz < zb)
+        return kKeyMid;
+    const long long dz = pz <= za ? za - pz : pz - zb;
+    return dz > c.r ? kKeyEmpty : dz;
+}
+
+void plan_slab_map(int T, int H, CompositePlan &p)
+{
+    p.rep.clear();
+    if (p.S <= 0 || p.S > 255 || (long long)T * p.S > kSlabMapMax)
+        return;
+    p.rep.resize((size_t)T * p.S);
+    std::vector<long long> keys((size_t)p.S * std::max(H, 1));
+    for (int t = 0; t < T; ++t) {
+        for (int e = 0; e < p.S; ++e)
+            for (int h = 0; h < H; ++h)
+                keys[(size_t)e * H + h] = slice_key(p.ci[(size_t)t * H + h], p.zlo + e);
+        for (int e = 0; e < p.S; ++e) {
+            int r = e;
+            for (int f = 0; f < e && r == e; ++f)
+                if (std::equal(keys.begin() + (size_t)f * H, keys.begin() + (size_t)(f + 1) * H,
+                               keys.begin() + (size_t)e * H))
+                    r = f;
+            p.rep[(size_t)t * p.S + e] = (uint8_t)r;
+        }
+    }
+}
+
+}  // namespace
+
+void slab_map(const CompositePlan &p, SlabMap &m)
+{
+    m.on = p.rep.empty() ? 0 : 1;
+    m.S = p.S;
+    if (m.on)
+        std::memcpy(m.rep, p.rep.data(), p.rep.size());
+}
+
 int plan_composite(const pcdf_grid *grid, int T, int H, const int32_t *caps, CompositePlan &p)
 {
     if (int rc = check_grid(grid))
@@ -175,6 +234,7 @@ int plan_composite(const pcdf_grid *grid, int T, int H, const int32_t *caps, Com
     }
     p.cap = std::min(ext_max + 2 * H + 2, grid->ny + 2);
     p.fused = H <= pcdf::kMaxCapsPerLaunch && pcdf::dyn_xy_fits(grid->ny, H, p.cap);
+    plan_slab_map(T, H, p);
     if (p.S == 0)
         p.need = 0;
     else if (p.fused)
@@ -216,11 +276,14 @@ int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &
     const int t_chunk = std::max(1, pcdf::kMaxCapsPerLaunch / std::max(H, 1));
     static thread_local pcdf::CapBatch batch;
     if (p.fused) {
+        static thread_local pcdf::SlabMap map;
+        slab_map(p, map);
         for (int t0 = 0; t0 < T; t0 += t_chunk) {
             const int nt = std::min(t_chunk, T - t0);
             batch.count = nt * H;
             std::memcpy(batch.caps, p.ci.data() + (size_t)t0 * H, sizeof(pcdf::CapInfo) * nt * H);
-            cudaError_t e = pcdf::launch_dyn_xy(&batch, H, grid->nx, grid->ny, p.zlo, p.S, t0, nt, p.cap, mid, st);
+            cudaError_t e =
+                pcdf::launch_dyn_xy(&batch, &map, H, grid->nx, grid->ny, p.zlo, p.S, t0, nt, p.cap, mid, st);
             if (e != cudaSuccess)
                 return cuda_fail(e, "dynamic x+y pass");
         }
@@ -254,8 +317,10 @@ int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const floa
     e = pcdf::launch_colmax(static_sq, grid->nx, grid->ny, grid->nz, colmax, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "static column maxima");
-    e = pcdf::launch_composite_z(static_sq, static_sdf, colmax, mid, grid->nx, grid->ny, grid->nz, p.zlo, p.S, t0,
-                                 nt, comp_sq, comp_sdf, grid->vox, st);
+    static thread_local pcdf::SlabMap map;
+    slab_map(p, map);
+    e = pcdf::launch_composite_z(static_sq, static_sdf, colmax, mid, &map, grid->nx, grid->ny, grid->nz, p.zlo, p.S,
+                                 t0, nt, comp_sq, comp_sdf, grid->vox, st);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "composite z pass");
 }
 

@@ -560,8 +560,9 @@ __global__ void k_sur_fallback(QueryGrid g, const int32_t *__restrict__ static_s
 __global__ void k_sur_fallback_slab(QueryGrid g, const int32_t *__restrict__ static_sq,
                                     const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
                                     const int32_t *__restrict__ tidx, int T, const int32_t *__restrict__ dyn_mid,
-                                    int zlo, int S, float eps, const int *__restrict__ list,
-                                    const int *__restrict__ count, float *__restrict__ h, float *__restrict__ d_out)
+                                    const __grid_constant__ pcdf::SlabMap map, int zlo, int S, float eps,
+                                    const int *__restrict__ list, const int *__restrict__ count,
+                                    float *__restrict__ h, float *__restrict__ d_out)
 {
     const int lane = threadIdx.x & 31, col = lane & 3;
     const long long gq = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 2;  // this quad's first query
@@ -580,13 +581,15 @@ __global__ void k_sur_fallback_slab(QueryGrid g, const int32_t *__restrict__ sta
         const Cell cl = locate(g, s);
         const int x = (col & 1) ? cl.i1[0] : cl.i0[0], y = (col & 2) ? cl.i1[1] : cl.i0[1];
         const int32_t *pc = dyn_mid + (long long)t * S * V2 + (long long)y * g.n[0] + x;  // slice e at pc[e * V2]
+        const uint8_t *rp = map.on ? map.rep + t * S : nullptr;  // slab element e is stored in slice rp[e]
+        auto slab = [&](int e) { return __ldg(pc + (long long)(rp ? rp[e] : e) * V2); };
         const int zc[2] = {cl.i0[2], cl.i1[2]};
         bool inside[2];
         int best[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int e = zc[u] - zlo;
-            inside[u] = e >= 0 && e < S && __ldg(pc + (long long)e * V2) < 0;
+            inside[u] = e >= 0 && e < S && slab(e) < 0;
             best[u] = kInf32;
             if (inside[u]) {
                 // the free voxels next to the slab
@@ -626,8 +629,8 @@ __global__ void k_sur_fallback_slab(QueryGrid g, const int32_t *__restrict__ sta
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int ea = ec - k0 - i, eb = ec + 1 + k0 + i;
-                P[2 * i] = (ea >= 0 && ea < S) ? __ldg(pc + (long long)ea * V2) : kInf32;
-                P[2 * i + 1] = (eb >= 0 && eb < S) ? __ldg(pc + (long long)eb * V2) : kInf32;
+                P[2 * i] = (ea >= 0 && ea < S) ? slab(ea) : kInf32;
+                P[2 * i + 1] = (eb >= 0 && eb < S) ? slab(eb) : kInf32;
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -773,7 +776,8 @@ __global__ void k_put_caps(const __grid_constant__ pcdf::CapBatch b, pcdf::CapIn
 // dyn_mid is given, else by local search over the capsules' voxels
 int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, const float *spheres,
                      const int32_t *tidx, int64_t N, int32_t T, int32_t H, const int32_t *caps_host,
-                     const int32_t *dyn_mid, int zlo_slab, int S_slab, const float *y, const int32_t *y_index,
+                     const int32_t *dyn_mid, const pcdf::SlabMap *map, int zlo_slab, int S_slab, const float *y,
+                     const int32_t *y_index,
                      float eps, float band,
                      float err_bound, float *h, float *d_out, int32_t *n_fallback, void *workspace,
                      size_t workspace_bytes, void *stream)
@@ -818,7 +822,7 @@ int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const floa
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (dyn_mid)
         k_sur_fallback_slab<<<sms * 8, 256, 0, st>>>(G.g, static_sq, static_sdf, (const float4 *)spheres, tidx, T,
-                                                    dyn_mid, zlo_slab, S_slab, eps, list, count, h, d_out);
+                                                    dyn_mid, *map, zlo_slab, S_slab, eps, list, count, h, d_out);
     else
         k_sur_fallback<<<sms * 8, 256, 0, st>>>(G.g, static_sq, static_sdf, (const float4 *)spheres, tidx, T, H,
                                                dcaps, eps, list, count, h, d_out);
@@ -845,8 +849,8 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
         return fail(PCDF_EINVAL, "bad surrogate arguments");
     if (N == 0)
         return PCDF_OK;
-    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, nullptr, 0, 0, y, y_index,
-                            eps, band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes, stream);
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, nullptr, nullptr, 0, 0, y,
+                            y_index, eps, band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes, stream);
 }
 
 int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
@@ -870,9 +874,12 @@ int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, 
     const int32_t *mid = p.S > 0 ? plan_mid(p, const_cast<void *>(comp_workspace)) : nullptr;
     // no capsule in the grid: the dynamic field is +INF everywhere (an empty slab)
     static const int32_t none = 0;
-    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, mid ? mid : &none, p.zlo,
-                            p.S, y, y_index, eps, band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes,
-                            stream);
+    // the slices of equal capsule cross-sections that the prepare stage computed once
+    static thread_local pcdf::SlabMap map;
+    slab_map(p, map);
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, mid ? mid : &none, &map,
+                            p.zlo, p.S, y, y_index, eps, band, err_bound, h, d_out, n_fallback, workspace,
+                            workspace_bytes, stream);
 }
 
 }  // extern "C"
