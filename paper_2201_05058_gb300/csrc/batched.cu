@@ -52,6 +52,7 @@ struct BatchEnv {
     int32_t *mid;
     int32_t *static_sq;
     int32_t *dyn;
+    const uint8_t *rep;   // [T][S] slab slice map (slices of equal capsule cross-sections); NULL: identity
     const CapInfo *caps;  // [T][H]
 };
 
@@ -148,6 +149,8 @@ __global__ void __launch_bounds__(kThreads)
                 break;
             case kDyn:
                 for (int s = I.b; s < min(I.b + dyn_slices, E.S); ++s) {
+                    if (E.rep && E.rep[I.a * E.S + s] != s)
+                        continue;  // read from the earlier slice of equal cross-sections
                     comp::dyn_xy_slice(E.caps + (long long)I.a * E.H, E.H, E.nx, E.ny, E.zlo, E.S, I.a, s, E.cap,
                                        E.dyn, reinterpret_cast<int32_t *>(smem));
                     __syncthreads();
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(kThreads)
                 for (int t = I.a; t < min(I.a + comp_t, E.T); ++t)
                     comp::composite_block<true, false, false, true>(E.static_sq, nullptr, E.dyn, E.nx, E.ny, E.nz,
                                                                     E.zlo, E.S, t, (long long)I.b, E.comp_sq, nullptr,
-                                                                    E.vox, smem);
+                                                                    E.vox, smem, E.rep ? E.rep + t * E.S : nullptr);
                 break;
             }
         }
@@ -189,7 +192,7 @@ struct pcdf_batch {
     std::vector<pcdf_env> user;
     std::vector<pcdf::host::CompositePlan> plans;
     std::vector<pcdf::BatchEnv> desc;   // device pointers filled at upload
-    std::vector<size_t> off_g16, off_mid, off_static, off_dyn, off_caps;
+    std::vector<size_t> off_g16, off_mid, off_static, off_dyn, off_caps, off_rep;
     std::vector<pcdf::BatchItem> items;
     size_t off_desc = 0, off_items = 0, off_state = 0, bytes = 0;
     size_t smem = 0;
@@ -226,6 +229,7 @@ int build_plan(const pcdf_env *envs, int n_env, const pcdf_batch_tiles *tiles, p
     B.off_static.resize(n_env);
     B.off_dyn.resize(n_env);
     B.off_caps.resize(n_env);
+    B.off_rep.resize(n_env);
     size_t off = 0, words = 0;
     std::vector<BatchItem> rows, dyn, ys, zs, comps;
     for (int e = 0; e < n_env; ++e) {
@@ -250,6 +254,8 @@ int build_plan(const pcdf_env *envs, int n_env, const pcdf_batch_tiles *tiles, p
         off += align_up((size_t)p.slab * 4);
         B.off_caps[e] = off;
         off += align_up(p.ci.size() * sizeof(CapInfo));
+        B.off_rep[e] = off;
+        off += align_up(p.rep.size());
         words = std::max(words, smem_words_env(p, g, U.H));
 
         BatchEnv &D = B.desc[e];
@@ -375,6 +381,13 @@ int pcdf_batch_upload(pcdf_batch *b, void *workspace, size_t workspace_bytes, vo
         D.static_sq = (int32_t *)(ws + b->off_static[e]);
         D.dyn = (int32_t *)(ws + b->off_dyn[e]);
         D.caps = (const CapInfo *)(ws + b->off_caps[e]);
+        const std::vector<uint8_t> &rp = b->plans[e].rep;
+        D.rep = rp.empty() ? nullptr : (const uint8_t *)(ws + b->off_rep[e]);
+        if (!rp.empty()) {
+            cudaError_t err = cudaMemcpyAsync(ws + b->off_rep[e], rp.data(), rp.size(), cudaMemcpyHostToDevice, st);
+            if (err != cudaSuccess)
+                return cuda_fail(err, "batch upload");
+        }
         const std::vector<CapInfo> &ci = b->plans[e].ci;
         if (!ci.empty()) {
             cudaError_t err = cudaMemcpyAsync(ws + b->off_caps[e], ci.data(), ci.size() * sizeof(CapInfo),

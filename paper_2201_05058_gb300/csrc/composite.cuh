@@ -506,7 +506,8 @@ __device__ __forceinline__ void composite_block(const int32_t *__restrict__ stat
                                                 const float *__restrict__ static_sdf,
                                                 const int32_t *__restrict__ dyn_mid, int nx, int ny, int nz, int zlo,
                                                 int S, int t, long long col0, int32_t *__restrict__ comp_sq,
-                                                float *__restrict__ comp_sdf, float vox, uint32_t *smem)
+                                                float *__restrict__ comp_sdf, float vox, uint32_t *smem,
+                                                const uint8_t *__restrict__ rep = nullptr)
 {
     const int nthr = blockDim.x, tid = threadIdx.x;
     const long long V2 = (long long)nx * ny;
@@ -518,8 +519,10 @@ __device__ __forceinline__ void composite_block(const int32_t *__restrict__ stat
     const int32_t *dcol = dyn_mid + (long long)t * S * V2 + c;
 
 #pragma unroll 8
-    for (int e = 0; e < S; ++e)
-        tile[(e + 1) * nthr] = (uint32_t)(kCoherent ? __ldcg(dcol + (long long)e * V2) : __ldcs(dcol + (long long)e * V2));
+    for (int e = 0; e < S; ++e) {
+        const int32_t *src = dcol + (long long)(rep ? rep[e] : e) * V2;
+        tile[(e + 1) * nthr] = (uint32_t)(kCoherent ? __ldcg(src) : __ldcs(src));
+    }
 
     const long long V = V2 * nz;
     const int32_t *scol = static_sq + c;
@@ -529,7 +532,7 @@ __device__ __forceinline__ void composite_block(const int32_t *__restrict__ stat
     out.fcol = kSdfOut ? comp_sdf + (long long)t * V + c : nullptr;
     out.vox = vox;
     int za, zb;
-    const int top = build_sets<kCoherent>(tile, mk, true, nthr, S, nz, zlo, scol, sfcol, dcol, V2, out, za, zb);
+    const int top = build_sets<kCoherent>(tile, mk, true, nthr, S, nz, zlo, scol, sfcol, dcol, V2, out, za, zb, rep);
     EnvCursor O(tile + nthr, nthr, top);
     emit_all<kCoherent>(za, zb, nz, top < 0, O, mk, zlo, nthr, scol, sfcol, (int)V2, out);
 }
