@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "host.h"
@@ -183,18 +184,15 @@ void plan_slab_map(int T, int H, CompositePlan &p)
     if (p.S <= 0 || p.S > 255 || (long long)T * p.S > kSlabMapMax)
         return;
     p.rep.resize((size_t)T * p.S);
-    std::vector<long long> keys((size_t)p.S * std::max(H, 1));
+    std::map<std::vector<long long>, int> first;  // key vector -> first slice of this t holding it
+    std::vector<long long> key(std::max(H, 0));
     for (int t = 0; t < T; ++t) {
-        for (int e = 0; e < p.S; ++e)
-            for (int h = 0; h < H; ++h)
-                keys[(size_t)e * H + h] = slice_key(p.ci[(size_t)t * H + h], p.zlo + e);
+        first.clear();
         for (int e = 0; e < p.S; ++e) {
-            int r = e;
-            for (int f = 0; f < e && r == e; ++f)
-                if (std::equal(keys.begin() + (size_t)f * H, keys.begin() + (size_t)(f + 1) * H,
-                               keys.begin() + (size_t)e * H))
-                    r = f;
-            p.rep[(size_t)t * p.S + e] = (uint8_t)r;
+            for (int h = 0; h < H; ++h)
+                key[h] = slice_key(p.ci[(size_t)t * H + h], p.zlo + e);
+            const auto it = first.emplace(key, e).first;
+            p.rep[(size_t)t * p.S + e] = (uint8_t)it->second;
         }
     }
 }
