@@ -139,6 +139,36 @@ def test_composite_ragged_grid_and_edge_capsules():
     check_composite(occ, caps, grid)
 
 
+def test_composite_slab_map_dedup_and_its_limits():
+    """Slab slices of equal capsule cross-sections are computed once and read
+    through a map.  Upright capsules and a cylinder (deduplicated) mixed with
+    a slanted capsule (a key of its own in every slice it touches), then the
+    two limits where the map falls back to the identity: more than 255 slab
+    slices, and more than 4096 (t, slice) entries."""
+    grid = scenes.Grid(20, 18, 80, 0.05)
+    rng = np.random.default_rng(21)
+    occ, _ = scenes.boxes_occupancy(grid, 4, rng)
+    T = 3
+    caps = np.zeros((T, 3, 7), np.int32)
+    for t in range(T):
+        caps[t, 0] = [40 + 16 * t, 150, 90, 40 + 16 * t, 150, 900, 60]            # upright capsule
+        caps[t, 1] = [200, 60 + 8 * t, 200, 200, 60 + 8 * t, 700, 50 | pcdf.CYLINDER]  # upright cylinder
+        caps[t, 2] = [100, 100, 300 + 20 * t, 260, 220, 600, 40]                   # slanted
+    check_composite(occ, caps, grid)
+    # a slab of more than 255 slices: 8 x 8 x 300 voxels, one capsule over the whole height
+    tall = scenes.Grid(8, 8, 300, 0.05)
+    occ_t = np.zeros(tall.shape, np.uint8)
+    occ_t[10:20, 2:4, 1:3] = 1
+    caps_t = np.array([[[56, 56, 40, 56, 56, 4700, 30]], [[72, 56, 40, 72, 56, 4700, 30]]], np.int32)
+    check_composite(occ_t, caps_t, tall)
+    # more than 4096 (t, slice) entries: T = 24 over a 180-slice slab
+    mid = scenes.Grid(8, 8, 200, 0.05)
+    occ_m = np.zeros(mid.shape, np.uint8)
+    occ_m[5:9, 1:3, 4:6] = 1
+    caps_m = np.array([[[40 + (t % 4) * 8, 64, 100, 40 + (t % 4) * 8, 64, 2900, 40]] for t in range(24)], np.int32)
+    check_composite(occ_m, caps_m, mid)
+
+
 def test_composite_odd_slice_size():
     # nx * ny not a multiple of 4: all-static column blocks are copied one
     # column per thread instead of with 16-byte accesses
