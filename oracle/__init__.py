@@ -17,6 +17,9 @@ Paper passages followed (Finean et al., arXiv 2201.05058):
   * Sec. 7, hinge-loss obstacle factor (GPMP2 form): cost ``eps - d`` when the
     distance ``d`` is within ``eps``, else 0; the sphere radius is added to eps.
   * Sec. 8: obstacle factor i reads composite field ``min(i, n)``.
+  * Sec. 6, the primitive's field computed once: ``template_field`` is the
+    signed EDT of one primitive on a box around it, ``translated_composite``
+    places copies of it at integer voxel offsets and takes the same ``min``.
 """
 from __future__ import annotations
 
@@ -176,6 +179,74 @@ def from_scratch(occ, caps) -> np.ndarray:
     for t in range(T):
         u = capsule_occupancy(occ.shape, caps[t]) | (np.asarray(occ) != 0).astype(np.uint8)
         out[t] = edt(u)
+    return out
+
+
+# --------------------------------------------------------------------------
+# translated primitive field (Sec. 6: the field of the human primitive is
+# computed once and composited at each predicted position)
+# --------------------------------------------------------------------------
+
+CYLINDER = 1 << 30
+
+
+def template_box(cap, R: int):
+    """(lo, dims), both (x, y, z) voxel indices: the box of voxels whose centres
+    16*i + 8 can lie in the primitive, i.e. within [min(a, b) - r, max(a, b) + r]
+    on each axis, widened by R voxels on every side.  Not clipped to any grid.
+    Raises ValueError when no voxel centre lies in that range on some axis."""
+    cap = [int(v) for v in np.asarray(cap).reshape(7)]
+    r = cap[6] & ~CYLINDER
+    lo, dims = [], []
+    for a in range(3):
+        mn = min(cap[a], cap[3 + a]) - r
+        mx = max(cap[a], cap[3 + a]) + r
+        first = -((8 - mn) // 16)  # ceil((mn - 8) / 16)
+        last = (mx - 8) // 16      # floor((mx - 8) / 16)
+        if last < first:
+            raise ValueError("no voxel centre within the primitive's range on axis %d" % a)
+        lo.append(first - R)
+        dims.append(last - first + 1 + 2 * R)
+    return lo, dims
+
+
+def template_field(cap, R: int):
+    """(tmpl, lo): the signed squared EDT of the primitive's voxels on its
+    template box (int32 [dz][dy][dx]), and the map index of the box's voxel 0.
+    Template voxel (i, j, k) is map voxel lo + (i, j, k); the primitive is moved
+    into the box's frame by subtracting 16*lo from a and b."""
+    lo, dims = template_box(cap, R)
+    c = np.asarray(cap, np.int64).reshape(7).copy()
+    for a in range(3):
+        c[a] -= 16 * lo[a]
+        c[3 + a] -= 16 * lo[a]
+    occ = capsule_occupancy((dims[2], dims[1], dims[0]), c.astype(np.int32))
+    return edt(occ), lo
+
+
+def translated_composite(S_static, tmpl, lo) -> np.ndarray:
+    """comp[t] = min(S_static, min_h P_th) where P_th(v) = tmpl[v - lo[t][h]]
+    inside the template box placed at lo[t][h] ((x, y, z) map index of its
+    voxel 0) and +INF outside it.  lo: int [T][H][3]."""
+    S_static = np.asarray(S_static, np.int32)
+    tmpl = np.asarray(tmpl, np.int32)
+    lo = np.asarray(lo, np.int64)
+    T, H = lo.shape[0], lo.shape[1]
+    nz, ny, nx = S_static.shape
+    dz, dy, dx = tmpl.shape
+    out = np.empty((T, nz, ny, nx), np.int32)
+    for t in range(T):
+        dyn = np.full(S_static.shape, INF32, np.int32)
+        for h in range(H):
+            x0, y0, z0 = (int(v) for v in lo[t, h])
+            xa, xb = max(x0, 0), min(x0 + dx, nx)
+            ya, yb = max(y0, 0), min(y0 + dy, ny)
+            za, zb = max(z0, 0), min(z0 + dz, nz)
+            if xa >= xb or ya >= yb or za >= zb:
+                continue
+            sub = tmpl[za - z0:zb - z0, ya - y0:yb - y0, xa - x0:xb - x0]
+            dyn[za:zb, ya:yb, xa:xb] = np.minimum(dyn[za:zb, ya:yb, xa:xb], sub)
+        out[t] = composite(S_static, dyn)
     return out
 
 

@@ -581,3 +581,137 @@ def test_cylinder_field_sandwich():
         axial = max(40 - p[2], p[2] - 200, 0.0)
         cont = np.hypot(radial, axial) / 16.0
         assert np.sqrt(S[k, j, i]) >= cont - 1e-9
+
+
+# ---------------------------------------------------------------------------
+# translated primitive field (Sec. 6: one primitive field, moved to each
+# predicted position)
+# ---------------------------------------------------------------------------
+
+def inside_voxels_map(cap, lo, dims):
+    """occupancy [dz,dy,dx] of the box at map index lo, tested voxel by voxel
+    with the primitive in map coordinates (no shift of the primitive)."""
+    dx, dy, dz = dims
+    occ = np.zeros((dz, dy, dx), np.uint8)
+    for k in range(dz):
+        for j in range(dy):
+            for i in range(dx):
+                p = (16 * (lo[0] + i) + 8, 16 * (lo[1] + j) + 8, 16 * (lo[2] + k) + 8)
+                occ[k, j, i] = oracle.capsule_inside(p, cap)
+    return occ
+
+
+def test_template_box_is_the_tight_box_of_an_upright_capsule():
+    """An upright capsule whose axis passes through voxel centres: the inner box
+    (without R) is exactly the bounding box of its voxels."""
+    for (i, j, k0, k1, rv) in [(5, 7, 3, 9, 2), (0, 0, 0, 0, 1), (-4, 11, -2, 6, 3)]:
+        r = 16 * rv + 5
+        cap = np.array([16 * i + 8, 16 * j + 8, 16 * k0 + 8, 16 * i + 8, 16 * j + 8, 16 * k1 + 8, r], np.int32)
+        for R in (0, 2):
+            lo, dims = oracle.template_box(cap, R)
+            assert lo == [i - rv - R, j - rv - R, k0 - rv - R]
+            assert dims == [2 * rv + 1 + 2 * R, 2 * rv + 1 + 2 * R, k1 - k0 + 2 * rv + 1 + 2 * R]
+
+
+def test_template_box_holds_every_voxel_of_the_primitive():
+    rng = np.random.default_rng(40)
+    for n in range(12):
+        a = rng.integers(-200, 300, 3)
+        b = a + rng.integers(-120, 120, 3)
+        r = int(rng.integers(10, 60))
+        if n % 3 == 2 and not np.array_equal(a, b):
+            r |= oracle.CYLINDER
+        cap = np.array([*a, *b, r], np.int32)
+        lo, dims = oracle.template_box(cap, 0)
+        # scan a wider box: nothing inside the primitive lies outside the template box
+        wide_lo = [lo[q] - 2 for q in range(3)]
+        wide = inside_voxels_map(cap, wide_lo, [dims[q] + 4 for q in range(3)])
+        inner = np.zeros_like(wide)
+        inner[2:-2, 2:-2, 2:-2] = 1
+        assert not np.any(wide & (1 - inner))
+
+
+def test_template_box_rejects_a_primitive_between_centres():
+    cap = np.array([20, 20, 20, 20, 20, 20, 3], np.int32)  # radius 3/16 voxel, 4/16 from any centre
+    with pytest.raises(ValueError):
+        oracle.template_box(cap, 4)
+
+
+def test_template_field_brute_force():
+    """Template values against the squared distance to the primitive's voxels,
+    found in map coordinates with no shift, and against the distance to the
+    free voxels inside it."""
+    for cap in (np.array([40, 56, 30, 40, 56, 90, 20], np.int32),
+                np.array([10, 30, 20, 70, 50, 60, 17], np.int32),
+                np.array([40, 40, 10, 40, 40, 70, 18 | oracle.CYLINDER], np.int32)):
+        R = 2
+        tmpl, lo = oracle.template_field(cap, R)
+        dz, dy, dx = tmpl.shape
+        occ = inside_voxels_map(cap, lo, (dx, dy, dz))
+        assert occ.any()
+        pts_in = [tuple(p) for p in np.argwhere(occ == 1)]
+        pts_out = [tuple(p) for p in np.argwhere(occ == 0)]
+        d_in = sq_dist_to_set(tmpl.shape, pts_in)
+        d_out = sq_dist_to_set(tmpl.shape, pts_out)
+        want = np.where(occ == 1, -d_out, d_in)
+        assert np.array_equal(tmpl, want)
+
+
+def _static_and_R(shape, seed, n_boxes=4):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    occ = np.zeros(shape, np.uint8)
+    for _ in range(n_boxes):
+        lo = [int(rng.integers(0, n - 3)) for n in shape]
+        hi = [min(lo[q] + int(rng.integers(1, 4)), shape[q]) for q in range(3)]
+        occ[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] = 1
+    S = oracle.edt(occ)
+    R = int(np.ceil(np.sqrt(float(S.max()))))
+    return S, R
+
+
+def test_translated_composite_equals_the_exact_composite():
+    """Integer moves of a primitive well inside the grid, template box widened
+    to R with R^2 >= every static value: the translated template gives the
+    exact composite of the moved primitives (two humans kept apart)."""
+    shape = (20, 18, 22)
+    S, R = _static_and_R(shape, 3)
+    ref = np.array([16 * 5 + 8, 16 * 5 + 3, 16 * 4 + 8, 16 * 5 + 8, 16 * 5 + 3, 16 * 9 + 8, 26], np.int32)
+    tmpl, lo0 = oracle.template_field(ref, R)
+    moves = [[(0, 0, 0), (9, 6, 1)], [(1, 2, 0), (10, 8, 2)], [(3, 1, 1), (8, 3, 3)]]
+    T, H = len(moves), 2
+    caps = np.zeros((T, H, 7), np.int32)
+    lo = np.zeros((T, H, 3), np.int64)
+    for t in range(T):
+        for h in range(H):
+            m = np.array(moves[t][h])
+            caps[t, h, :3] = ref[:3] + 16 * m
+            caps[t, h, 3:6] = ref[3:6] + 16 * m
+            caps[t, h, 6] = ref[6]
+            lo[t, h] = np.array(lo0) + m
+    want = oracle.predicted_composite(S, caps)
+    got = oracle.translated_composite(S, tmpl, lo)
+    assert np.array_equal(got, want)
+    # a box cut too tight (R = 0) misses voxels where the human is nearer than the static field
+    tight, lo_t = oracle.template_field(ref, 0)
+    lo_tight = lo - np.array(lo0) + np.array(lo_t)
+    assert not np.array_equal(oracle.translated_composite(S, tight, lo_tight), want)
+
+
+def test_translated_composite_clips_boxes_at_the_grid_edges():
+    """Boxes partly or wholly outside the grid, by explicit loops over voxels."""
+    rng = np.random.default_rng(41)
+    S = rng.integers(-30, 60, (5, 6, 7)).astype(np.int32)
+    tmpl = rng.integers(-9, 50, (3, 4, 5)).astype(np.int32)
+    lo = np.array([[[-2, -1, 3], [4, 3, -1]], [[6, 5, 4], [-7, 0, 0]], [[1, 1, 1], [0, -3, 2]]], np.int64)
+    got = oracle.translated_composite(S, tmpl, lo)
+    for t in range(3):
+        for k in range(5):
+            for j in range(6):
+                for i in range(7):
+                    best = int(S[k, j, i])
+                    for h in range(2):
+                        u = (i - lo[t, h, 0], j - lo[t, h, 1], k - lo[t, h, 2])
+                        if 0 <= u[0] < 5 and 0 <= u[1] < 4 and 0 <= u[2] < 3:
+                            best = min(best, int(tmpl[u[2], u[1], u[0]]))
+                    assert got[t, k, j, i] == best
