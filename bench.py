@@ -58,7 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
-    ap.add_argument("--profile-case", choices=["composite", "static", "scratch", "query", "mlp", "surrogate"],
+    ap.add_argument("--profile-case", choices=["composite", "static", "scratch", "query", "mlp", "surrogate",
+                                               "translated"],
                     default=None,
                     help="run one small untimed case of the named stage (for ncu captures) and exit")
     ap.add_argument("--profile-T", type=int, default=4, help="horizon of the --profile-case composite")
@@ -503,6 +504,55 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
             "graph_speedup_vs_scratch": t_scr / t_sur_graph if t_sur_graph else None}
 
 
+def bench_translated(pcdf, dev, grid, caps, static_sq, static_sdf, comp_sq, comp_sdf, timed, k):
+    """The paper's own primitive handling (Sec. 6): one field of the human
+    primitive computed once and moved to each predicted position.  It is exact
+    on lattice moves only, so every human is laid on the lattice relative to
+    human 0 at t = 0; the exact composite path runs on the same lattice
+    capsules for comparison."""
+    import torch
+
+    T = caps.shape[0]
+    V = grid.nvox
+    tr_caps = scenes.lattice_moves(caps, caps[0, 0])
+    ref = tr_caps[0, 0]
+    R = pcdf.template_radius(static_sq)
+    tmpl, lo0 = pcdf.build_template(ref, R, dev)
+    stream = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    tmpl, lo0 = pcdf.build_template(ref, R, dev)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    tmpl_ms = a.elapsed_time(b)
+    lo = pcdf.lattice_placements(tr_caps, ref, lo0)
+    ws_tr = pcdf.composite_workspace(grid, tr_caps, dev)
+
+    def tr_step(_=None):
+        pcdf.composite_translated(static_sq, grid, tmpl, lo, R, static_sdf=static_sdf, comp_sq=comp_sq,
+                                  comp_sdf=comp_sdf)
+
+    def exact_step(_=None):
+        pcdf.composite_prepare(grid, tr_caps, ws_tr)
+        pcdf.composite_finish(static_sq, grid, tr_caps, ws_tr, comp_sq, comp_sdf, static_sdf=static_sdf)
+
+    tr_step()
+    tr_ms, _ = timed(tr_step, k)
+    exact_step()
+    ex_ms, _ = timed(exact_step, k)
+    tr_avg, ex_avg = float(np.mean(tr_ms)), float(np.mean(ex_ms))
+    # bytes: the static pair read once, T int32 + fp32 fields written, the template read once
+    tr_bytes = 8 * V + 8 * T * V + 4 * tmpl.numel()
+    peak, peak_kind = measured_peaks()
+    gbs = tr_bytes / (tr_avg * 1e-3) / 1e9
+    return {"ms": tr_avg, "gvox_s": T * V / (tr_avg * 1e-3) / 1e9, "template_build_ms": tmpl_ms, "R": R,
+            "template_box": list(tmpl.shape[::-1]), "exact_composite_same_caps_ms": ex_avg,
+            "speedup_vs_exact_composite": ex_avg / tr_avg, "algorithmic_bytes": tr_bytes, "achieved_gbs": gbs,
+            "frac_of_hbm": gbs / peak, "peak_source": peak_kind,
+            "what": "k_composite_translated: T fields from one template moved by whole voxels (humans on the "
+                    "lattice relative to human 0 at t = 0); exact composite path timed on the same capsules"}
+
+
 def run_native(args):
     import torch
 
@@ -602,6 +652,7 @@ def run_native(args):
     scr_ms, _ = timed(scratch, k_side)
     comp_avg = float(np.mean(comp_ms))
     scr_avg = float(np.mean(scr_ms))
+    translated = bench_translated(pcdf, dev, grid, caps, static_sq, static_sdf, comp_sq, comp_sdf, timed, k_side)
 
     # roofline of the dominant stage, timed by the events around
     # composite_finish: k_colmax (reads static_sq, writes one int32 per
@@ -717,7 +768,7 @@ def run_native(args):
             "composite_only": {"ms": comp_avg, "gvox_s": T * V / (comp_avg * 1e-3) / 1e9},
             "from_scratch": {"ms": scr_avg, "gvox_s": T * V / (scr_avg * 1e-3) / 1e9,
                              "composite_speedup": scr_avg / comp_avg},
-            "query": query, "mapping": mapping, "batched": batched, "surrogate": surrogate, "roofline": roofline,
+            "translated": translated, "query": query, "mapping": mapping, "batched": batched, "surrogate": surrogate, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "e2e_planner": e2e_planner,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
         }
@@ -792,6 +843,17 @@ def run_profile_case(args):
     sc = scenes.scene_composite(seed=args.seed, T=args.profile_T, H=H_HUMANS)
     grid, caps = sc["grid"], sc["caps"]
     occ = torch.from_numpy(sc["occ"]).to(dev)
+    if args.profile_case == "translated":
+        static_sq, static_sdf = pcdf.build_static_sdf(occ, grid)
+        tr_caps = scenes.lattice_moves(caps, caps[0, 0])
+        R = pcdf.template_radius(static_sq)
+        tmpl, lo0 = pcdf.build_template(tr_caps[0, 0], R, dev)
+        lo = pcdf.lattice_placements(tr_caps, tr_caps[0, 0], lo0)
+        for _ in range(2):
+            pcdf.composite_translated(static_sq, grid, tmpl, lo, R, static_sdf=static_sdf)
+        torch.cuda.synchronize()
+        print("profile case translated done")
+        return 0
     for _ in range(2):
         if args.profile_case in ("static", "composite"):
             static_sq, static_sdf = pcdf.build_static_sdf(occ, grid)

@@ -207,6 +207,61 @@ int pcdf_build_from_scratch(const pcdf_grid *grid, const uint8_t *occ, int32_t T
                             int32_t *sq, float *sdf, void *workspace, size_t workspace_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Translated primitive field (Sec. 6: the field of the human primitive is
+ * computed once and composited at each tracked or predicted position).
+ *
+ * The template of a primitive cap (HOST int32 [7], fixed point as above,
+ * capsule or cylinder) is the signed squared EDT of its voxels on a box: on
+ * each axis the voxels whose centres 16 i + 8 lie in
+ * [min(a, b) - r, max(a, b) + r], widened by R >= 0 voxels on every side.
+ * Box voxel (i, j, k) is map voxel lo + (i, j, k) for the primitive where cap
+ * puts it.
+ *
+ * pcdf_template_box: lo[3] and dims[3] (x, y, z) of that box (HOST outputs).
+ *   PCDF_EINVAL if some axis holds no voxel centre of the primitive's range,
+ *   a coordinate or radius is out of range, or a side exceeds PCDF_MAX_DIM.
+ * pcdf_build_template: tmpl = device int32 [dz][dy][dx], the signed squared
+ *   EDT of the primitive's voxels inside the box (interior voxels negative,
+ *   +/-PCDF_INF where the opposite set is empty).  workspace: device,
+ *   256-byte aligned, >= pcdf_template_workspace_bytes(cap, R).
+ *
+ * pcdf_composite_translated: for t = 0..T-1,
+ *   comp[t](v) = min(static_sq(v), min_h P(v - lo[t][h]))
+ * where P is the template inside its box and +INF outside, and lo is HOST
+ * int32 [T][H][3], the map index (x, y, z) of the box's voxel 0 for primitive
+ * h at t (the template's own lo plus an integer voxel move; each entry within
+ * [-PCDF_MAX_DIM, PCDF_MAX_DIM]).  dims: HOST int32 [3], the template's box;
+ * R: the widening the template was built with (0 <= 2 R < every side).  The
+ * primitive's voxels lie in the box less R per side, so a voxel whose static
+ * value is at most its squared gap to that inner box skips the template read
+ * (same result: the template is at least that gap there).
+ * static_sq, static_sdf, comp_sq and comp_sdf as for the composite above
+ * (H = 0: every output is the static field).  No workspace.
+ *
+ * Exactness.  The output equals pcdf_build_predicted_composite of the moved
+ * primitives wherever (1) the static value is at most R^2 or the voxel lies
+ * inside every placed box (outside its box a primitive is more than R voxels
+ * away), (2) each moved primitive and the free voxels next to it lie inside
+ * the grid (the composite path counts in-grid voxels only), and (3) the
+ * primitives of one t share no voxel and touch no face (otherwise their
+ * interior values are the min over the primitives, not those of the union).
+ * The translation is exact only for integer voxel moves; a primitive at a
+ * sub-voxel position needs its own template.
+ * ------------------------------------------------------------------------- */
+/* pcdf_field_max: *out (device int32) = the largest value v of sq[0..n) with
+ * 0 < v < PCDF_INF, or 0 if there is none; with R the least integer whose
+ * square is at least that value, condition (1) below holds wherever the
+ * static field is finite.  sq: device int32 [n]. */
+int pcdf_field_max(const int32_t *sq, int64_t n, int32_t *out, void *stream);
+int pcdf_template_box(const int32_t *cap, int32_t R, int32_t *lo, int32_t *dims);
+int pcdf_template_workspace_bytes(const int32_t *cap, int32_t R, size_t *bytes);
+int pcdf_build_template(const int32_t *cap, int32_t R, int32_t *tmpl, void *workspace, size_t workspace_bytes,
+                        void *stream);
+int pcdf_composite_translated(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int32_t T,
+                              int32_t H, const int32_t *tmpl, const int32_t *dims, int32_t R, const int32_t *lo,
+                              int32_t *comp_sq, float *comp_sdf, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Hinge obstacle cost at body spheres (Sec. 7 hinge form, GPMP2 obstacle
  * factor; Sec. 8 field assignment).
  *

@@ -20,6 +20,11 @@ from .api import (  # noqa: F401
     Grid,
     HingeCost,
     build_from_scratch,
+    build_template,
+    composite_translated,
+    lattice_placements,
+    template_box,
+    template_radius,
     build_predicted_composite,
     build_static_sdf,
     CYLINDER,

@@ -8,6 +8,7 @@ error.  No step of the computation runs in Python or PyTorch.
 from __future__ import annotations
 
 import ctypes
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -372,6 +373,104 @@ def build_from_scratch(occ: torch.Tensor, grid, caps, want_sdf: bool = True, out
     _lib.check(lib.pcdf_build_from_scratch(ctypes.byref(g), _ptr(occ), T, H, cp, _ptr(sq), _ptr(sdf), _ptr(ws),
                                            ws.numel(), ctypes.c_void_p(_stream(dev))), "pcdf_build_from_scratch")
     return sq, sdf
+
+
+# ---------------------------------------------------------------------------
+# translated primitive field (Sec. 6: the primitive's field computed once)
+# ---------------------------------------------------------------------------
+
+def _cap7(cap) -> np.ndarray:
+    c = np.asarray(cap.detach().cpu().numpy() if isinstance(cap, torch.Tensor) else cap, dtype=np.int64)
+    if c.size != 7:
+        raise ValueError(f"a primitive is 7 int32 values, got {c.shape}")
+    return np.ascontiguousarray(c.reshape(7), dtype=np.int32)
+
+
+def template_box(cap, R: int):
+    """(lo, dims), each [x, y, z]: the template box of primitive cap (the voxels
+    whose centres can lie in it, widened by R voxels) in map voxel indices."""
+    c = _cap7(cap)
+    lo = (ctypes.c_int32 * 3)()
+    dims = (ctypes.c_int32 * 3)()
+    _lib.check(_lib.load().pcdf_template_box(c.ctypes.data_as(ctypes.c_void_p), int(R), lo, dims),
+               "pcdf_template_box")
+    return list(lo), list(dims)
+
+
+def build_template(cap, R: int, device):
+    """(tmpl, lo): the signed squared EDT of primitive cap on its template box,
+    int32 [dz][dy][dx] on `device`, and the box's map index [x, y, z]."""
+    c = _cap7(cap)
+    lo, dims = template_box(c, R)
+    dev = torch.device(device)
+    lib = _lib.load()
+    nbytes = ctypes.c_size_t(0)
+    cp = c.ctypes.data_as(ctypes.c_void_p)
+    _lib.check(lib.pcdf_template_workspace_bytes(cp, int(R), ctypes.byref(nbytes)), "template workspace")
+    tmpl = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.int32, device=dev)
+    ws = _workspace(nbytes.value, dev)
+    _lib.check(lib.pcdf_build_template(cp, int(R), _ptr(tmpl), _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(dev))),
+               "pcdf_build_template")
+    return tmpl, lo
+
+
+def template_radius(static_sq: torch.Tensor) -> int:
+    """Least R with R * R at least every finite positive static value: with a box
+    widened by R, the translated composite is exact wherever the static field
+    is finite (one device-to-host read)."""
+    _need(static_sq, "static_sq", torch.int32)
+    out = torch.empty(1, dtype=torch.int32, device=static_sq.device)
+    _lib.check(_lib.load().pcdf_field_max(_ptr(static_sq), static_sq.numel(), _ptr(out),
+                                          ctypes.c_void_p(_stream(static_sq.device))), "pcdf_field_max")
+    m = int(out.item())
+    R = math.isqrt(m)
+    return R if R * R >= m else R + 1
+
+
+def lattice_placements(caps, ref_cap, ref_lo) -> np.ndarray:
+    """Box placements int32 [T][H][3] for primitives that are ref_cap moved by
+    whole voxels (the template built from ref_cap has its box at ref_lo).
+    Raises ValueError for a primitive of another shape or a sub-voxel move."""
+    c = _caps_host(caps).astype(np.int64)
+    ref = _cap7(ref_cap).astype(np.int64)
+    d = c[..., 0:3] - ref[0:3]
+    if np.any(c[..., 3:6] - ref[3:6] != d) or np.any(c[..., 6] != ref[6]) or np.any(d % 16 != 0):
+        raise ValueError("every primitive must be ref_cap moved by whole voxels")
+    return np.ascontiguousarray(np.asarray(ref_lo, np.int64) + d // 16, dtype=np.int32)
+
+
+def composite_translated(static_sq: torch.Tensor, grid, tmpl: torch.Tensor, lo, R: int, static_sdf=None,
+                         want_sq: bool = True, want_sdf: bool = True, comp_sq=None, comp_sdf=None):
+    """comp[t] = min(static, min_h template placed at lo[t][h]) for lo int [T][H][3];
+    R is the widening the template was built with (see
+    pcdf_composite_translated for when this equals the exact composite)."""
+    shp = _shape(grid)
+    _need(static_sq, "static_sq", torch.int32, shp)
+    if static_sdf is not None:
+        _need(static_sdf, "static_sdf", torch.float32, shp)
+    _need(tmpl, "tmpl", torch.int32)
+    if tmpl.dim() != 3:
+        raise ValueError("tmpl must be [dz][dy][dx]")
+    lo = np.ascontiguousarray(np.asarray(lo, dtype=np.int64), dtype=np.int32)
+    if lo.ndim != 3 or lo.shape[2] != 3:
+        raise ValueError(f"lo must be [T][H][3], got {lo.shape}")
+    T, H = int(lo.shape[0]), int(lo.shape[1])
+    dev = static_sq.device
+    if want_sq and comp_sq is None:
+        comp_sq = torch.empty((T,) + shp, dtype=torch.int32, device=dev)
+    if want_sdf and comp_sdf is None:
+        comp_sdf = torch.empty((T,) + shp, dtype=torch.float32, device=dev)
+    if comp_sq is not None:
+        _need(comp_sq, "comp_sq", torch.int32, (T,) + shp)
+    if comp_sdf is not None:
+        _need(comp_sdf, "comp_sdf", torch.float32, (T,) + shp)
+    dims = (ctypes.c_int32 * 3)(int(tmpl.shape[2]), int(tmpl.shape[1]), int(tmpl.shape[0]))
+    g = _cgrid(grid)
+    _lib.check(_lib.load().pcdf_composite_translated(
+        ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), T, H, _ptr(tmpl), dims, int(R),
+        lo.ctypes.data_as(ctypes.c_void_p) if H > 0 else None, _ptr(comp_sq), _ptr(comp_sdf),
+        ctypes.c_void_p(_stream(dev))), "pcdf_composite_translated")
+    return comp_sq, comp_sdf
 
 
 # ---------------------------------------------------------------------------

@@ -200,3 +200,19 @@ def scene_batch(seed=0, n_env=64, vox=0.04, dims=((64, 320), (64, 320), (64, 128
 def random_occupancy(shape_zyx, density, rng):
     """uint8 occupancy with i.i.d. voxels (density in [0, 1])."""
     return (rng.uniform(0.0, 1.0, size=shape_zyx) < density).astype(np.uint8)
+
+
+def lattice_moves(caps, ref):
+    """caps [T][H][7] laid on the voxel lattice relative to the primitive ref:
+    each primitive becomes ref moved by the whole-voxel step nearest to its own
+    displacement from ref (same shape and sub-voxel phase as ref).  The input
+    of the translated-primitive variant, where a predicted position is an
+    integer voxel move of one template."""
+    caps = np.asarray(caps, np.int64)
+    ref = np.asarray(ref, np.int64).reshape(7)
+    move = np.rint((caps[..., 0:3] - ref[0:3]) / 16.0).astype(np.int64)
+    out = np.empty(caps.shape, np.int64)
+    out[..., 0:3] = ref[0:3] + 16 * move
+    out[..., 3:6] = ref[3:6] + 16 * move
+    out[..., 6] = ref[6]
+    return out.astype(np.int32)

@@ -100,3 +100,60 @@ def test_query_rejects_unaligned_spheres():
     assert rc == -1 and "aligned" in err()
     assert lib.pcdf_query_cost(ctypes.byref(g), fake, 0, fake, fake, 10, 0.2, fake, None, None) == -1
     assert lib.pcdf_query_cost(ctypes.byref(g), fake, 1, fake, fake, -1, 0.2, fake, None, None) == -1
+
+
+def test_template_box_matches_the_oracle_and_rejects_bad_primitives():
+    """The host-side template box of the translated primitive field against the
+    oracle's, and its argument checks (no device work)."""
+    import numpy as np
+
+    import oracle
+    import paper_2201_05058_gb300 as pcdf
+
+    rng = np.random.default_rng(7)
+    for n in range(200):
+        a = rng.integers(-1500, 4000, 3)
+        b = a + rng.integers(-300, 300, 3)
+        r = int(rng.integers(0, 200))
+        if n % 4 == 3 and not np.array_equal(a, b):
+            r |= oracle.CYLINDER
+        cap = np.array([*a, *b, r], np.int32)
+        R = int(rng.integers(0, 40))
+        try:
+            want = oracle.template_box(cap, R)
+        except ValueError:
+            with pytest.raises(RuntimeError):
+                pcdf.template_box(cap, R)
+            continue
+        if max(want[1]) > 512:
+            with pytest.raises(RuntimeError):
+                pcdf.template_box(cap, R)
+            continue
+        assert pcdf.template_box(cap, R) == (list(want[0]), list(want[1]))
+    lib = _lib.load()
+    lo = (ctypes.c_int32 * 3)()
+    dims = (ctypes.c_int32 * 3)()
+    ok = np.array([40, 40, 40, 40, 40, 200, 30], np.int32)
+    p = ok.ctypes.data_as(ctypes.c_void_p)
+    assert lib.pcdf_template_box(p, 4, lo, dims) == 0
+    assert lib.pcdf_template_box(p, -1, lo, dims) == -1          # R < 0
+    assert lib.pcdf_template_box(p, 600, lo, dims) == -1         # side > PCDF_MAX_DIM
+    assert lib.pcdf_template_box(None, 4, lo, dims) == -1
+    zero_cyl = np.array([40, 40, 40, 40, 40, 40, 30 | oracle.CYLINDER], np.int32)
+    assert lib.pcdf_template_box(zero_cyl.ctypes.data_as(ctypes.c_void_p), 4, lo, dims) == -1
+    g = grid()
+    placements = np.zeros((1, 1, 3), np.int32)
+    placements[0, 0, 0] = 900                                    # outside [-512, 512]
+    d3 = (ctypes.c_int32 * 3)(8, 8, 8)
+    small = (ctypes.c_int32 * 3)(4, 4, 4)   # with R = 2: 2 R >= side
+    fake = ctypes.c_void_p(256)                                  # never dereferenced: rejected first
+    assert lib.pcdf_composite_translated(ctypes.byref(g), fake, None, 1, 1, fake, d3, 2,
+                                         placements.ctypes.data_as(ctypes.c_void_p), fake, None, None) == -1
+    assert lib.pcdf_composite_translated(ctypes.byref(g), fake, None, 1, 1, None, d3, 2,
+                                         placements.ctypes.data_as(ctypes.c_void_p), fake, None, None) == -1
+    placements[0, 0, 0] = 0
+    assert lib.pcdf_composite_translated(ctypes.byref(g), fake, None, 1, 1, fake, small, 2,
+                                         placements.ctypes.data_as(ctypes.c_void_p), fake, None, None) == -1  # 2 R >= side
+    bad_dims = (ctypes.c_int32 * 3)(4, 0, 4)
+    assert lib.pcdf_composite_translated(ctypes.byref(g), fake, None, 1, 1, fake, bad_dims, 2,
+                                         placements.ctypes.data_as(ctypes.c_void_p), fake, None, None) == -1
