@@ -50,18 +50,30 @@ __device__ __forceinline__ void template_min(int x, int y, int z, const int32_t 
                                              const int32_t *__restrict__ tmpl, int dx, int dy, int dz, int R,
                                              const int4 *pl, int H, int32_t *d)
 {
+    int32_t smax = sv[0];
+#pragma unroll
+    for (int i = 1; i < W; ++i)
+        smax = max(smax, sv[i]);
     for (int h = 0; h < H; ++h) {
         const int4 p = pl[h];
         const int j = y - p.y, k = z - p.z;
         if ((unsigned)j >= (unsigned)dy || (unsigned)k >= (unsigned)dz)
             continue;
+        const int u0 = x - p.x;
+        if (u0 + W <= 0 || u0 >= dx)
+            continue;  // the group lies beside the box
         const int gy = max(0, max(R - j, j - (dy - 1 - R)));
         const int gz = max(0, max(R - k, k - (dz - 1 - R)));
         const int gyz = gy * gy + gz * gz;
+        // the group's least gap (its voxel nearest the inner box) bounds all W
+        const int gx0 = max(0, max(R - (u0 + W - 1), u0 - (dx - 1 - R)));
+        const int lb0 = gx0 * gx0 + gyz;
+        if (lb0 > 0 && smax <= lb0)
+            continue;
         const int32_t *trow = tmpl + ((long long)k * dy + j) * dx;
 #pragma unroll
         for (int i = 0; i < W; ++i) {
-            const int u = x + i - p.x;
+            const int u = u0 + i;
             if ((unsigned)u >= (unsigned)dx)
                 continue;
             const int gx = max(0, max(R - u, u - (dx - 1 - R)));
@@ -88,10 +100,20 @@ __device__ __forceinline__ void translated_finish(int x, int y, int z, int off, 
     template_min<W>(x, y, z, sv, tmpl, dx, dy, dz, R, pl, H, d);
     int32_t cv[W];
     float f[W];
+    bool any = false;  // some voxel of the group where the template is nearer
 #pragma unroll
     for (int i = 0; i < W; ++i) {
         cv[i] = min(sv[i], d[i]);
-        f[i] = (kStaticSdf && sv[i] <= d[i]) ? sf[i] : sq_to_sdf_fast(cv[i], vox);
+        any |= d[i] < sv[i];
+    }
+    if (kStaticSdf && !any) {
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+            f[i] = sf[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+            f[i] = (kStaticSdf && sv[i] <= d[i]) ? sf[i] : sq_to_sdf_fast(cv[i], vox);
     }
     if (W == 4) {
         if (kSq)
