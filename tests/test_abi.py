@@ -157,3 +157,46 @@ def test_template_box_matches_the_oracle_and_rejects_bad_primitives():
     bad_dims = (ctypes.c_int32 * 3)(4, 0, 4)
     assert lib.pcdf_composite_translated(ctypes.byref(g), fake, None, 1, 1, fake, bad_dims, 2,
                                          placements.ctypes.data_as(ctypes.c_void_p), fake, None, None) == -1
+
+
+def test_lattice_placements_follow_the_moved_boxes():
+    """Placements of whole-voxel moves are the moved primitives' own template
+    boxes (oracle), and anything that is not such a move is refused."""
+    import numpy as np
+
+    import oracle
+    import paper_2201_05058_gb300 as pcdf
+    import scenes
+
+    rng = np.random.default_rng(21)
+    ref = np.array([300, 410, 100, 300, 410, 620, 100], np.int32)
+    lo0, _ = oracle.template_box(ref, 7)
+    moves = rng.integers(-20, 20, (4, 3, 3))
+    caps = np.empty((4, 3, 7), np.int32)
+    caps[..., 0:3] = ref[0:3] + 16 * moves
+    caps[..., 3:6] = ref[3:6] + 16 * moves
+    caps[..., 6] = ref[6]
+    lo = pcdf.lattice_placements(caps, ref, lo0)
+    for t in range(4):
+        for h in range(3):
+            assert list(lo[t, h]) == list(oracle.template_box(caps[t, h], 7)[0])
+    # the scene helper lays sub-voxel positions on that lattice, keeping the shape
+    sc = scenes.scene_composite(seed=1, n=64, n_boxes=4, T=5)
+    lat = scenes.lattice_moves(sc["caps"], sc["caps"][0, 0])
+    step = lat[..., 0:3].astype(np.int64) - sc["caps"][0, 0, 0:3]
+    assert np.all(step % 16 == 0)
+    assert np.all(np.abs(lat[..., 0:3].astype(np.int64) - sc["caps"][..., 0:3]) <= 8)
+    pcdf.lattice_placements(lat, lat[0, 0], lo0)
+    bad = caps.copy()
+    bad[1, 2, 0] += 3                       # a sub-voxel move
+    bad[1, 2, 3] += 3
+    with pytest.raises(ValueError):
+        pcdf.lattice_placements(bad, ref, lo0)
+    bad = caps.copy()
+    bad[0, 1, 6] += 1                       # another radius
+    with pytest.raises(ValueError):
+        pcdf.lattice_placements(bad, ref, lo0)
+    bad = caps.copy()
+    bad[2, 0, 5] += 16                      # another length
+    with pytest.raises(ValueError):
+        pcdf.lattice_placements(bad, ref, lo0)
