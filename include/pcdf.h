@@ -250,7 +250,7 @@ int pcdf_build_from_scratch(const pcdf_grid *grid, const uint8_t *occ, int32_t T
  * ------------------------------------------------------------------------- */
 /* pcdf_field_max: *out (device int32) = the largest value v of sq[0..n) with
  * 0 < v < PCDF_INF, or 0 if there is none; with R the least integer whose
- * square is at least that value, condition (1) below holds wherever the
+ * square is at least that value, condition (1) above holds wherever the
  * static field is finite.  sq: device int32 [n]. */
 int pcdf_field_max(const int32_t *sq, int64_t n, int32_t *out, void *stream);
 int pcdf_template_box(const int32_t *cap, int32_t R, int32_t *lo, int32_t *dims);
