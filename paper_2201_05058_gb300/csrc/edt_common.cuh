@@ -13,17 +13,21 @@ namespace pcdf {
 
 constexpr uint32_t kG22 = (1u << 22) - 1;
 
-__device__ __forceinline__ uint32_t pack_site(int s, int g) { return ((uint32_t)s << 22) | (uint32_t)g; }
-__device__ __forceinline__ int site_of(uint32_t w) { return (int)(w >> 22); }
-__device__ __forceinline__ int gval_of(uint32_t w) { return (int)(w & kG22); }
-__device__ __forceinline__ int parab(int x, int s, int g) { return (x - s) * (x - s) + g; }
+// Also callable from host code, so that the envelope code can be exercised on
+// the CPU.
+#define PCDF_HD __host__ __device__ __forceinline__
+
+PCDF_HD uint32_t pack_site(int s, int g) { return ((uint32_t)s << 22) | (uint32_t)g; }
+PCDF_HD int site_of(uint32_t w) { return (int)(w >> 22); }
+PCDF_HD int gval_of(uint32_t w) { return (int)(w & kG22); }
+PCDF_HD int parab(int x, int s, int g) { return (x - s) * (x - s) + g; }
 
 // With sites s0 < s1 < s2, s1 is nowhere strictly below both neighbours iff
 // the parabola of s2 overtakes s1 no later than s1 overtakes s0.  The two
 // abscissae are the fractions (f1 - f0) / 2(s1 - s0) and (f2 - f1) / 2(s2 - s1)
 // with f = s^2 + g; they are compared by cross-multiplication (positive
 // denominators), so the test is exact.
-__device__ __forceinline__ bool dominated(int s0, int g0, int s1, int g1, int s2, int g2)
+PCDF_HD bool dominated(int s0, int g0, int s1, int g1, int s2, int g2)
 {
     const int f0 = s0 * s0 + g0, f1 = s1 * s1 + g1, f2 = s2 * s2 + g2;
     return (f2 - f1) * (s1 - s0) <= (f1 - f0) * (s2 - s1);

@@ -46,12 +46,4 @@ cudaError_t launch_envelope_i16(const int16_t *in, int32_t *out, int n, int nx, 
     return launch_banded<int16_t, false>(in, out, nullptr, 0.f, n, nx, ncols, outer_stride, stride, stream);
 }
 
-cudaError_t launch_envelope_i32(const int32_t *in, int32_t *out, float *sdf, float vox, int n, int nx,
-                                long long ncols, long long outer_stride, long long stride, cudaStream_t stream)
-{
-    if (sdf)
-        return launch_banded<int32_t, true>(in, out, sdf, vox, n, nx, ncols, outer_stride, stride, stream);
-    return launch_banded<int32_t, false>(in, out, nullptr, vox, n, nx, ncols, outer_stride, stride, stream);
-}
-
 }  // namespace pcdf

@@ -67,12 +67,19 @@ constexpr int kEnvCols = 32;
 cudaError_t launch_pass_x(int mode, const uint8_t *occ, const CapBatch *caps, int H, int nx, int ny, int z0,
                           int nslices, int n_t, int16_t *g16, cudaStream_t stream);
 
+// Exact signed EDT of a whole grid (edt_full.cu): row bits of the occupancy
+// (mode 0), of the occupancy OR the capsules caps->caps[0 .. H) (mode 1) or of
+// the capsules alone (mode 2), then the fused x+y pass and the z pass; sq and
+// (nullable) sdf are [nz][ny][nx].  ws holds full_edt_scratch() bytes
+// (256-byte aligned): row words, their carries and the 2-D partial field.
+size_t full_edt_scratch(int nx, int ny, int nz, size_t *bits_off, size_t *carry_off, size_t *mid_off);
+cudaError_t launch_full_edt(int mode, const uint8_t *occ, const CapBatch *caps, int H, int nx, int ny, int nz,
+                            int32_t *sq, float *sdf, float vox, void *ws, cudaStream_t stream);
+
 // Lower-envelope pass over ncols columns: element e of column c lives at
 // (c / nx) * outer_stride + (c % nx) + e * stride, e in [0, n).
 cudaError_t launch_envelope_i16(const int16_t *in, int32_t *out, int n, int nx, long long ncols,
                                 long long outer_stride, long long stride, cudaStream_t stream);
-cudaError_t launch_envelope_i32(const int32_t *in, int32_t *out, float *sdf, float vox, int n, int nx,
-                                long long ncols, long long outer_stride, long long stride, cudaStream_t stream);
 
 // Analytic x+y passes of the capsule field over the slab slices zlo .. zlo+S-1
 // for t = t0 .. t0 + n_t - 1 (capsules of local t at caps->caps[t * H ...]);

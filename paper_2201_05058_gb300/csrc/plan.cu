@@ -122,31 +122,20 @@ int check_caps_args(int T, int H, const int32_t *caps)
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-// Static (or union) signed EDT of one grid: row pass (mode 0 or 1 with the
-// capsules of one t), y envelope, z envelope with optional float epilogue.
+// Static (or union) signed EDT of one grid: row bits (mode 0 occupancy, 1
+// occupancy OR the capsules of one t, 2 the capsules alone), fused x+y pass,
+// z pass with optional float epilogue.
 int run_full_edt(const pcdf_grid *g, int mode, const uint8_t *occ, const pcdf::CapBatch *caps, int H, int32_t *sq,
                  float *sdf, void *ws, cudaStream_t st)
 {
-    const long long V = nvox(g);
-    int16_t *g16 = (int16_t *)ws;
-    int32_t *mid = (int32_t *)((char *)ws + align_up((size_t)V * sizeof(int16_t)));
-    cudaError_t e = pcdf::launch_pass_x(mode, occ, caps, H, g->nx, g->ny, 0, g->nz, 1, g16, st);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "row pass");
-    const long long slice = (long long)g->nx * g->ny;
-    e = pcdf::launch_envelope_i16(g16, mid, g->ny, g->nx, (long long)g->nx * g->nz, slice, g->nx, st);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "y pass");
-    e = pcdf::launch_envelope_i32(mid, sq, sdf, g->vox, g->nz, g->nx, slice, g->nx, slice, st);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "z pass");
-    return PCDF_OK;
+    cudaError_t e = pcdf::launch_full_edt(mode, occ, caps, H, g->nx, g->ny, g->nz, sq, sdf, g->vox, ws, st);
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "full EDT");
 }
 
 size_t full_edt_ws(const pcdf_grid *g)
 {
-    const long long V = nvox(g);
-    return align_up((size_t)V * sizeof(int16_t)) + align_up((size_t)V * sizeof(int32_t));
+    size_t bo, co, mo;
+    return pcdf::full_edt_scratch(g->nx, g->ny, g->nz, &bo, &co, &mo);
 }
 
 
