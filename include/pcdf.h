@@ -113,9 +113,16 @@ int pcdf_build_static_sdf(const pcdf_grid *grid, const uint8_t *occ, int32_t *st
  * scratch is a fixed array inside the library (about 12 MB on every device
  * that loads it, held until exit), so grids are limited to
  * PCDF_NOALLOC_MAX_VOXELS voxels (larger grids fail with PCDF_EINVAL and
- * nothing is enqueued).  Allocates nothing.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * nothing is enqueued).  Allocates nothing itself.  CUDA loads the library's
+ * modules lazily, so the driver allocates the array when the first call on a
+ * device loads it: that call can fail with PCDF_ECUDA (out of memory), and a
+ * caller that must not fail later makes its first call at start-up.  Every
+ * call whose stream is not being captured looks up the array's device address
+ * (cudaGetSymbolAddress, with the call's device current), so a device reset
+ * between calls is harmless.  A call made while its stream is being captured
+ * does not look the address up: it reuses the last one found on the device,
+ * and fails with PCDF_EINVAL if there is none, so the first call on a device
+ * should come before any stream capture.  All calls share
  * the array: calls that overlap on the GPU race on it and must be serialised
  * by the caller.  No part of the array needs to start at zero. */
 #define PCDF_NOALLOC_MAX_VOXELS 2097152
@@ -253,6 +260,20 @@ int pcdf_build_from_scratch(const pcdf_grid *grid, const uint8_t *occ, int32_t T
  * square is at least that value, condition (1) above holds wherever the
  * static field is finite.  sq: device int32 [n]. */
 int pcdf_field_max(const int32_t *sq, int64_t n, int32_t *out, void *stream);
+/* pcdf_template_radius: *R (HOST) = the least integer R >= 0 with R * R >=
+ * max_value, for max_value (>= 0) as pcdf_field_max returns it; with that R
+ * the template covers every voxel whose static value is finite (condition (1)
+ * above).  PCDF_EINVAL for a negative max_value or a NULL R. */
+int pcdf_template_radius(int32_t max_value, int32_t *R);
+/* pcdf_lattice_placements: the box placements lo (HOST int32 [T][H][3]) of
+ * primitives caps (HOST int32 [T][H][7]) that are all ref_cap (HOST int32 [7],
+ * whose template box starts at ref_lo, HOST int32 [3]) moved by whole voxels:
+ * lo[t][h] = ref_lo + (a[t][h] - a_ref) / 16 per axis.  PCDF_EINVAL (nothing
+ * written) if some primitive has another radius or axis, a move that is not a
+ * multiple of 16 (one voxel), or a placement outside [-PCDF_MAX_DIM,
+ * PCDF_MAX_DIM]. */
+int pcdf_lattice_placements(const int32_t *caps, int32_t T, int32_t H, const int32_t *ref_cap, const int32_t *ref_lo,
+                            int32_t *lo);
 int pcdf_template_box(const int32_t *cap, int32_t R, int32_t *lo, int32_t *dims);
 int pcdf_template_workspace_bytes(const int32_t *cap, int32_t R, size_t *bytes);
 int pcdf_build_template(const int32_t *cap, int32_t R, int32_t *tmpl, void *workspace, size_t workspace_bytes,

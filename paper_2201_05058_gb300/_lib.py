@@ -36,7 +36,7 @@ EXPORTS = (
     "pcdf_composite_prepare", "pcdf_composite_finish", "pcdf_composite_finish_range", "pcdf_composite_slab",
     "pcdf_filter_voxels", "pcdf_collapse_2d",
     "pcdf_scratch_workspace_bytes", "pcdf_build_from_scratch",
-    "pcdf_field_max", "pcdf_template_box", "pcdf_template_workspace_bytes", "pcdf_build_template", "pcdf_composite_translated",
+    "pcdf_field_max", "pcdf_template_radius", "pcdf_lattice_placements", "pcdf_template_box", "pcdf_template_workspace_bytes", "pcdf_build_template", "pcdf_composite_translated",
     "pcdf_query_cost", "pcdf_query_cost_backward",
     "pcdf_batch_create", "pcdf_batch_destroy", "pcdf_batch_workspace_bytes", "pcdf_batch_tiles_used",
     "pcdf_batch_upload", "pcdf_batch_run", "pcdf_batch_error", "pcdf_batch_block_stage", "pcdf_batch_autotune_workspace_bytes",
@@ -70,6 +70,8 @@ def _declare(lib):
         "pcdf_scratch_workspace_bytes": [G, I32, I32, SZP],
         "pcdf_build_from_scratch": [G, P, I32, I32, P, P, P, P, SZ, P],
         "pcdf_field_max": [P, I64, P, P],
+        "pcdf_template_radius": [I32, P],
+        "pcdf_lattice_placements": [P, I32, I32, P, P, P],
         "pcdf_template_box": [P, I32, P, P],
         "pcdf_template_workspace_bytes": [P, I32, SZP],
         "pcdf_build_template": [P, I32, P, P, SZ, P],

@@ -8,7 +8,6 @@ error.  No step of the computation runs in Python or PyTorch.
 from __future__ import annotations
 
 import ctypes
-import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -422,21 +421,26 @@ def template_radius(static_sq: torch.Tensor) -> int:
     out = torch.empty(1, dtype=torch.int32, device=static_sq.device)
     _lib.check(_lib.load().pcdf_field_max(_ptr(static_sq), static_sq.numel(), _ptr(out),
                                           ctypes.c_void_p(_stream(static_sq.device))), "pcdf_field_max")
-    m = int(out.item())
-    R = math.isqrt(m)
-    return R if R * R >= m else R + 1
+    R = ctypes.c_int32(0)
+    _lib.check(_lib.load().pcdf_template_radius(int(out.item()), ctypes.byref(R)), "pcdf_template_radius")
+    return int(R.value)
 
 
 def lattice_placements(caps, ref_cap, ref_lo) -> np.ndarray:
     """Box placements int32 [T][H][3] for primitives that are ref_cap moved by
     whole voxels (the template built from ref_cap has its box at ref_lo).
     Raises ValueError for a primitive of another shape or a sub-voxel move."""
-    c = _caps_host(caps).astype(np.int64)
-    ref = _cap7(ref_cap).astype(np.int64)
-    d = c[..., 0:3] - ref[0:3]
-    if np.any(c[..., 3:6] - ref[3:6] != d) or np.any(c[..., 6] != ref[6]) or np.any(d % 16 != 0):
-        raise ValueError("every primitive must be ref_cap moved by whole voxels")
-    return np.ascontiguousarray(np.asarray(ref_lo, np.int64) + d // 16, dtype=np.int32)
+    c = _caps_host(caps)
+    ref = _cap7(ref_cap)
+    rlo = np.ascontiguousarray(np.asarray(ref_lo, np.int64), dtype=np.int32)
+    T, H = int(c.shape[0]), int(c.shape[1])
+    lo = np.empty((T, H, 3), np.int32)
+    rc = _lib.load().pcdf_lattice_placements(c.ctypes.data_as(ctypes.c_void_p), T, H,
+                                             ref.ctypes.data_as(ctypes.c_void_p),
+                                             rlo.ctypes.data_as(ctypes.c_void_p), lo.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError(_lib.load().pcdf_last_error().decode())
+    return lo
 
 
 def composite_translated(static_sq: torch.Tensor, grid, tmpl: torch.Tensor, lo, R: int, static_sdf=None,

@@ -20,6 +20,8 @@
 // the static row.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -326,6 +328,52 @@ int pcdf_field_max(const int32_t *sq, int64_t n, int32_t *out, void *stream)
         }
     }
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "field max");
+}
+
+int pcdf_template_radius(int32_t max_value, int32_t *R)
+{
+    if (!R)
+        return fail(PCDF_EINVAL, "R is NULL");
+    if (max_value < 0)
+        return fail(PCDF_EINVAL, "max_value = %d < 0", max_value);
+    // integer square root, rounded up: the least r with r * r >= max_value
+    long long r = (long long)std::sqrt((double)max_value);
+    while (r * r < max_value)
+        ++r;
+    while (r > 0 && (r - 1) * (r - 1) >= max_value)
+        --r;
+    *R = (int32_t)r;
+    return PCDF_OK;
+}
+
+int pcdf_lattice_placements(const int32_t *caps, int32_t T, int32_t H, const int32_t *ref_cap, const int32_t *ref_lo,
+                            int32_t *lo)
+{
+    if (T < 1 || T > PCDF_MAX_T || H < 0 || H > PCDF_MAX_H)
+        return fail(PCDF_EINVAL, "T = %d or H = %d out of range", T, H);
+    if (!ref_cap || !ref_lo || (H > 0 && (!caps || !lo)))
+        return fail(PCDF_EINVAL, "caps, ref_cap, ref_lo and lo must be non-NULL");
+    // check everything before writing anything
+    for (long long q = 0; q < (long long)T * H; ++q) {
+        const int32_t *c = caps + 7 * q;
+        if (c[6] != ref_cap[6])
+            return fail(PCDF_EINVAL, "primitive %lld has another radius or kind than the reference", q);
+        for (int a = 0; a < 3; ++a) {
+            const long long d = (long long)c[a] - ref_cap[a];
+            if ((long long)c[3 + a] - ref_cap[3 + a] != d)
+                return fail(PCDF_EINVAL, "primitive %lld has another axis than the reference", q);
+            if (d % 16 != 0)
+                return fail(PCDF_EINVAL, "primitive %lld is not a whole-voxel move of the reference", q);
+            const long long p = (long long)ref_lo[a] + d / 16;
+            if (p < -PCDF_MAX_DIM || p > PCDF_MAX_DIM)
+                return fail(PCDF_EINVAL, "placement of primitive %lld outside [%d, %d]", q, -PCDF_MAX_DIM,
+                            PCDF_MAX_DIM);
+        }
+    }
+    for (long long q = 0; q < (long long)T * H; ++q)
+        for (int a = 0; a < 3; ++a)
+            lo[3 * q + a] = ref_lo[a] + (caps[7 * q + a] - ref_cap[a]) / 16;
+    return PCDF_OK;
 }
 
 int pcdf_template_workspace_bytes(const int32_t *cap, int32_t R, size_t *bytes)

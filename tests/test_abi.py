@@ -201,3 +201,18 @@ def test_lattice_placements_follow_the_moved_boxes():
     bad[2, 0, 5] += 16                      # another length
     with pytest.raises(ValueError):
         pcdf.lattice_placements(bad, ref, lo0)
+
+
+def test_template_radius_is_the_ceiling_square_root():
+    """pcdf_template_radius against the integer square root (rounded up) and
+    its argument checks."""
+    import math
+
+    lib = _lib.load()
+    R = ctypes.c_int32(-1)
+    for m in [0, 1, 2, 3, 4, 5, 8, 9, 10, 11880, 11881, 11882, 3 * 511 * 511, 2 ** 31 - 2, 2 ** 31 - 1]:
+        assert lib.pcdf_template_radius(m, ctypes.byref(R)) == 0
+        r = math.isqrt(m)
+        assert R.value == (r if r * r >= m else r + 1), m
+    assert lib.pcdf_template_radius(-1, ctypes.byref(R)) == -1
+    assert lib.pcdf_template_radius(4, None) == -1

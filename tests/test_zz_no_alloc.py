@@ -5,7 +5,9 @@ It is for callers that cannot allocate device memory when they need a field
 memory belongs to another runtime).  Called through the C ABI, it must give
 the same fields as pcdf_build_static_sdf (bit for bit, as all integer and
 float fields of this library) on two calls in a row, whatever the shared
-scratch array holds from the call before.  This file is collected last.
+scratch array holds from the call before, and a call after the first on a
+device must leave the device's free memory and PyTorch's allocation count
+unchanged.  This file is collected last.
 """
 import ctypes
 
@@ -21,15 +23,12 @@ pcdf = pytest.importorskip("paper_2201_05058_gb300")
 from paper_2201_05058_gb300 import _lib  # noqa: E402
 
 
-def noalloc(occ, grid):
+def noalloc_into(occ, grid, sq, sdf):
     lib = _lib.load()
-    sq = torch.empty(occ.shape, dtype=torch.int32, device=occ.device)
-    sdf = torch.empty(occ.shape, dtype=torch.float32, device=occ.device)
     g = _lib.PcdfGrid(grid.nx, grid.ny, grid.nz, grid.vox, (ctypes.c_float * 3)(*grid.origin))
-    rc = lib.pcdf_build_static_sdf_noalloc(ctypes.byref(g), ctypes.c_void_p(occ.data_ptr()),
-                                           ctypes.c_void_p(sq.data_ptr()), ctypes.c_void_p(sdf.data_ptr()),
-                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    return rc, sq, sdf
+    return lib.pcdf_build_static_sdf_noalloc(ctypes.byref(g), ctypes.c_void_p(occ.data_ptr()),
+                                             ctypes.c_void_p(sq.data_ptr()), ctypes.c_void_p(sdf.data_ptr()),
+                                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
 def test_noalloc_matches_workspace_build_on_two_calls():
@@ -42,10 +41,19 @@ def test_noalloc_matches_workspace_build_on_two_calls():
     for grid, occ_np in zip(cases, occs):
         occ = torch.from_numpy(occ_np).to(d)
         want_sq, want_sdf = pcdf.build_static_sdf(occ, grid)
-        for _ in range(2):  # two calls in a row share the scratch array
-            rc, sq, sdf = noalloc(occ, grid)
+        sq = torch.empty(occ.shape, dtype=torch.int32, device=d)
+        sdf = torch.empty(occ.shape, dtype=torch.float32, device=d)
+        for k in range(2):  # two calls in a row share the scratch array
+            sq.fill_(7)
+            sdf.fill_(7.0)
+            torch.cuda.synchronize()
+            free0, alloc0 = torch.cuda.mem_get_info(d)[0], torch.cuda.memory_allocated(d)
+            rc = noalloc_into(occ, grid, sq, sdf)
             assert rc == 0, _lib.load().pcdf_last_error().decode()
             torch.cuda.synchronize()
+            if k == 1:  # the first call on the device may load the library's module; later calls allocate nothing
+                assert torch.cuda.mem_get_info(d)[0] == free0
+                assert torch.cuda.memory_allocated(d) == alloc0
             assert torch.equal(sq, want_sq)
             assert torch.equal(sdf.view(torch.int32), want_sdf.view(torch.int32))
 
