@@ -395,6 +395,14 @@ int pcdf_batch_autotune(const pcdf_env *envs, int32_t n_env, void *workspace, si
  * Workspace: pcdf_mlp_workspace_bytes(M), 256-byte aligned.
  * pcdf_mlp_backward runs the forward pass (y), the loss mean((y - t)^2)
  * (added to *loss if non-NULL, after zeroing it) and overwrites the gradient.
+ * On return the workspace holds what the passes stored, in sections of
+ * A = M * 512 bytes rounded up to a multiple of 256, in this order: H1, H2,
+ * H3 (BF16 [M][256]: the hidden activations relu(Z_l)) and D3, D2, D1 (BF16
+ * [M][256]: the loss gradient with respect to Z_3, Z_2, Z_1, zero where the
+ * activation is zero).  pcdf_mlp_forward leaves H1, H2, H3
+ * the same way.  With dy = 2 (y - t) / M (FP32), D3 = dy * w4 (FP32 product
+ * rounded to BF16), D_l = D_{l+1} W_{l+1} (FP32 sum rounded to BF16) and
+ * grad W_l = D_l^T H_{l-1} (H_0 = x), grad b_l = the column sums of D_l.
  * pcdf_mlp_adam applies one Adam step (bias-corrected, step >= 1) to the FP32
  * parameters and refreshes the BF16 copies.
  * ------------------------------------------------------------------------- */

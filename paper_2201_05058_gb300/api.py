@@ -761,6 +761,17 @@ class SurrogateMLP:
                    "pcdf_mlp_backward")
         return y, loss
 
+    def stored(self, M: int):
+        """Views of what the last forward or backward pass of M rows stored in
+        the workspace (layout in include/pcdf.h): H1, H2, H3, D3, D2, D1
+        (bfloat16 [M, 256])."""
+        a = -(-M * 512 // 256) * 256
+        ws = self._ws
+        out = {}
+        for i, k in enumerate(("H1", "H2", "H3", "D3", "D2", "D1")):
+            out[k] = ws[i * a:i * a + M * 512].view(torch.bfloat16).view(M, 256)
+        return out
+
     def adam(self, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
         self.step += 1
         _lib.check(self._lib.pcdf_mlp_adam(_ptr(self.state), float(lr), float(beta1), float(beta2), float(eps),

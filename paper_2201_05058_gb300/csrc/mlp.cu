@@ -1124,12 +1124,14 @@ cudaError_t launch_pack(const State &S, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Workspace sections (each 256-byte aligned, in this order): the stored
+// activations H1, H2, H3 and the stored pre-activation gradients D3, D2, D1
+// (BF16 [M][256] each); see pcdf_mlp_backward.
 struct Acts {
-    bf16 *H1, *H2, *H3, *dA, *dB;
-    float *y;
+    bf16 *H1, *H2, *H3, *D3, *D2, *D1;
 };
 
-size_t ws_bytes(long long M) { return 5 * align_up((size_t)M * kW * 2) + align_up((size_t)M * 4); }
+size_t ws_bytes(long long M) { return 6 * align_up((size_t)M * kW * 2); }
 
 Acts carve(void *ws, long long M)
 {
@@ -1139,9 +1141,9 @@ Acts carve(void *ws, long long M)
     r.H1 = (bf16 *)b;
     r.H2 = (bf16 *)(b + a);
     r.H3 = (bf16 *)(b + 2 * a);
-    r.dA = (bf16 *)(b + 3 * a);
-    r.dB = (bf16 *)(b + 4 * a);
-    r.y = (float *)(b + 5 * a);
+    r.D3 = (bf16 *)(b + 3 * a);
+    r.D2 = (bf16 *)(b + 4 * a);
+    r.D1 = (bf16 *)(b + 5 * a);
     return r;
 }
 
@@ -1368,28 +1370,28 @@ int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64
     if (int rc = forward(S, X, M, A, st))
         return rc;
     k_head<<<(unsigned)((M + kHeadRows - 1) / kHeadRows), 256, 0, st>>>(A.H3, S.h + hW4, S.p + oB4, M, y, target,
-                                                                        A.dA, S.g + oW4, S.g + oB4, loss,
+                                                                        A.D3, S.g + oW4, S.g + oB4, loss,
                                                                         1.f / (float)M);
     e = cudaGetLastError();
     const unsigned cs = (unsigned)((M + 255) / 256);
     // layer 3: Z3 = H2 W3^T + b3
     if (e == cudaSuccess) {
-        k_colsum<<<cs, kW, 0, st>>>(A.dA, M, S.g + oB3);
-        e = back_weight(A.dA, A.H2, kW, S.g + oW3, M, st);
+        k_colsum<<<cs, kW, 0, st>>>(A.D3, M, S.g + oB3);
+        e = back_weight(A.D3, A.H2, kW, S.g + oW3, M, st);
     }
     if (e == cudaSuccess)
-        e = back_input(A.dA, S.h + hW3, kW, A.H2, A.dB, M, st);
+        e = back_input(A.D3, S.h + hW3, kW, A.H2, A.D2, M, st);
     // layer 2
     if (e == cudaSuccess) {
-        k_colsum<<<cs, kW, 0, st>>>(A.dB, M, S.g + oB2);
-        e = back_weight(A.dB, A.H1, kW, S.g + oW2, M, st);
+        k_colsum<<<cs, kW, 0, st>>>(A.D2, M, S.g + oB2);
+        e = back_weight(A.D2, A.H1, kW, S.g + oW2, M, st);
     }
     if (e == cudaSuccess)
-        e = back_input(A.dB, S.h + hW2, kW, A.H1, A.dA, M, st);
+        e = back_input(A.D2, S.h + hW2, kW, A.H1, A.D1, M, st);
     // layer 1 (the input needs no gradient)
     if (e == cudaSuccess) {
-        k_colsum<<<cs, kW, 0, st>>>(A.dA, M, S.g + oB1);
-        e = back_weight(A.dA, X, kIn, S.g + oW1, M, st);
+        k_colsum<<<cs, kW, 0, st>>>(A.D1, M, S.g + oB1);
+        e = back_weight(A.D1, X, kIn, S.g + oW1, M, st);
     }
     if (e == cudaSuccess)
         e = cudaGetLastError();

@@ -7,6 +7,7 @@ import torch
 import oracle
 import scenes
 from oracle import mlp as omlp
+from tests import mlp_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -28,6 +29,14 @@ def rand_x(M, rng, d):
 
 @pytest.mark.parametrize("M", [300, 4096])
 def test_mlp_forward_and_gradients_match_oracle(M):
+    """Every stored value of a backward pass, element by element, against the
+    network's definition evaluated on the GPU's own inputs to that step
+    (tests/mlp_parity.py): each BF16 activation and pre-activation gradient
+    equals the rounding of its exact value unless that value lies within the
+    FP32 accumulation bound of a rounding midpoint (then either neighbour);
+    the layer-3 gradient matches the head's FP32 arithmetic bit for bit; every
+    weight and bias gradient entry, the outputs and the loss lie within the
+    FP32 accumulation bound of their exact sums."""
     d = dev()
     rng = np.random.default_rng(M)
     net = pcdf.SurrogateMLP(d, seed=3)
@@ -36,19 +45,14 @@ def test_mlp_forward_and_gradients_match_oracle(M):
     y, loss = net.backward(x, t)
     torch.cuda.synchronize()
     P = net.params()
+    st = {k: v.float().cpu().double().numpy() for k, v in net.stored(M).items()}
+    st["y"] = y.cpu().double().numpy()
     xo = x.float().cpu().double().numpy()
-    want_loss, G, want_y = omlp.loss_and_grad(P, xo, t.cpu().double().numpy(), rounding=True)
-    yg = y.cpu().double().numpy()
-    assert np.max(np.abs(yg - want_y)) <= 2e-2 * max(1.0, np.max(np.abs(want_y)))
-    assert abs(float(loss.item()) - want_loss) <= 1e-2 * want_loss
-    got = net.grads()
-    for k in G:
-        a = np.asarray(G[k], np.float64).ravel()
-        b = np.asarray(got[k], np.float64).ravel()
-        if k == "W1":  # the three zero input columns have zero gradient
-            b = b.reshape(256, 16)[:, :13].ravel()
-            a = a.reshape(256, 16)[:, :13].ravel()
-        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(a) + 1e-9, k
+    amb = mlp_parity.check_passes(P, xo, t.cpu().double().numpy(), st, net.grads(), float(loss.item()))
+    assert all(v < 0.5 for v in amb.values()), amb
+    # and the FP64 oracle with its own activations agrees on the loss
+    want_loss, _, _ = omlp.loss_and_grad(P, xo, t.cpu().double().numpy(), rounding=True)
+    assert abs(float(loss.item()) - want_loss) <= 1e-3 * want_loss
     # the forward pass alone gives the same outputs, and so does the fused
     # inference kernel (tail tiles included)
     y2 = net.forward(x)
@@ -59,7 +63,6 @@ def test_mlp_forward_and_gradients_match_oracle(M):
     y_tc = net.infer_tc(x)
     assert not torch.isnan(y_tc).any()
     assert torch.allclose(y_tc, y, rtol=0, atol=1e-5 * max(1.0, float(y.abs().max())))
-    assert np.max(np.abs(y_tc.cpu().double().numpy() - want_y)) <= 2e-2 * max(1.0, np.max(np.abs(want_y)))
     y_tc2 = net.infer_tc(x[: M - 7])
     assert torch.allclose(y_tc2, y[: M - 7], rtol=0, atol=1e-5 * max(1.0, float(y.abs().max())))
     # a row count on the device: the first count rows, the rest untouched
