@@ -395,117 +395,173 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
         return sc, torch.from_numpy(sph).to(dev), torch.from_numpy(tidx).to(dev)
 
     def exact(sc, sph, tidx):
+        sgrid = sc["grid"]
         occ = torch.from_numpy(sc["occ"]).to(dev)
-        st_sq, st_sdf = pcdf.build_static_sdf(occ, grid)
-        _, comp = pcdf.build_predicted_composite(st_sq, grid, sc["caps"], want_sq=False, static_sdf=st_sdf)
+        st_sq, st_sdf = pcdf.build_static_sdf(occ, sgrid)
+        _, comp = pcdf.build_predicted_composite(st_sq, sgrid, sc["caps"], want_sq=False, static_sdf=st_sdf)
         big = 16.0
-        d = (big + sph[..., 3]) - pcdf.query_cost(comp, grid, sph, tidx, big)
+        d = (big + sph[..., 3]) - pcdf.query_cost(comp, sgrid, sph, tidx, big)
         return occ, st_sq, st_sdf, comp, d
 
-    # bands from validation scenes: the decision band (every wrong predicted
-    # decision falls inside it) and the error bound (largest error)
-    dps, des, thrs = [], [], []
-    for s in range(seed + 5000, seed + 5002):
-        sc, sph, tidx = queries(s)
-        _, st_sq, st_sdf, _, d_ex = exact(sc, sph, tidx)
-        _, d_pr, _ = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.0)
-        dps.append(d_pr.reshape(-1))
-        des.append(d_ex.reshape(-1))
-        thrs.append((0.2 + sph[..., 3]).reshape(-1))
-    dps, des, thrs = torch.cat(dps), torch.cat(des), torch.cat(thrs)
-    band = sg.band_from_decisions(dps, des, thrs)
-    err_bound = sg.band_from_errors(dps, des)
-    # held-out test scenes
-    stats = []
-    for s in range(seed + 6000, seed + 6002):
-        sc, sph, tidx = queries(s)
-        occ, st_sq, st_sdf, comp, d_ex = exact(sc, sph, tidx)
-        h_ex = pcdf.query_cost(comp, grid, sph, tidx, 0.2)
-        _, d_pr, _ = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.0)
-        cws = pcdf.composite_workspace(grid, sc["caps"], dev)
-        pcdf.composite_prepare(grid, sc["caps"], cws)
-        h, _, nfb = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band,
-                                         err_bound=err_bound, comp_workspace=cws)
-        # the fallback band stated for this workload, 0.05 m
-        h05, _, nfb05 = pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.05,
-                                             err_bound=err_bound, comp_workspace=cws)
-        e = (d_pr - d_ex).abs()
-        stats.append((float(e.max()), float(e.mean()), int(nfb.item()) / sph.numel() * 4,
-                      bool(torch.equal(h > 0, h_ex > 0)), int((h > 0).sum()),
-                      int(nfb05.item()) / sph.numel() * 4, int(((h05 > 0) != (h_ex > 0)).sum())))
-    # timing on the last test scene: one plan step of 1M queries
-    caps_dev = torch.from_numpy(np.ascontiguousarray(sc["caps"])).to(dev)
+    # The stated fallback band: |d - (eps + r)| < 0.05 m.  Certified: the
+    # certificate of every query sends the uncertain ones to the exact path
+    # too, so decisions are the exact path's by construction.
+    BAND = 0.05
 
-    def surrogate_path():
-        # exact answers from the capsule-slab partials (the composite's first
-        # stage, run for this plan step's capsules), one stream: the least
-        # host work per call
-        pcdf.composite_prepare(grid, sc["caps"], cws)
-        pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=band, caps_dev=caps_dev,
-                             err_bound=err_bound, comp_workspace=cws)
-
-    def surrogate_path_overlapped():
-        # the capsule slab on a side stream while the rows are selected (pays
-        # off once the host work is gone, i.e. replayed from a graph)
-        pcdf.surrogate_step(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band, cws, caps_dev=caps_dev,
-                            err_bound=err_bound)
-
-    t_sur = ev_time(surrogate_path)
-    # the same plan step replayed from a CUDA graph (no host work between
-    # its kernels; the inputs are the captured buffers)
-    try:
+    def graph_ms(fn):
         side = torch.cuda.Stream(dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):
-            surrogate_path_overlapped()
+            fn()
         torch.cuda.current_stream(dev).wait_stream(side)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            surrogate_path_overlapped()
-        t_sur_graph = ev_time(graph.replay)
-    except RuntimeError as exc:  # capture unsupported here: report the eager number only
-        print(f"surrogate graph capture failed: {exc}", file=sys.stderr)
-        t_sur_graph = None
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return ev_time(g.replay)
+
+    def evaluate(sc, sph, tidx, timing):
+        sgrid = sc["grid"]
+        occ, st_sq, st_sdf, comp, d_ex = exact(sc, sph, tidx)
+        h_ex = pcdf.query_cost(comp, sgrid, sph, tidx, 0.2)
+        cws = pcdf.composite_workspace(sgrid, sc["caps"], dev)
+        pcdf.composite_prepare(sgrid, sc["caps"], cws)
+        caps_dev = torch.from_numpy(np.ascontiguousarray(sc["caps"])).to(dev)
+        # the network's own distances (every row where the humans can matter, no exact answers)
+        _, d_pr, _ = pcdf.surrogate_query(net, sgrid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.0,
+                                          certified=False)
+        # the plain band rule without the certificate
+        h_u, _, nfb_u = pcdf.surrogate_query(net, sgrid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=BAND,
+                                             comp_workspace=cws, certified=False)
+        # the certified plan step, and the same step without the network (zero residual: the
+        # continuous capsule distance clamped to the certified interval)
+        x, yi, cnt, bnd = pcdf.surrogate_select(sgrid, st_sdf, sph, tidx, T, caps_dev, 0.2, sync=False)
+        y = net.infer_tc(x, count=cnt)
+        h, _, nfb = pcdf.surrogate_finish(sgrid, st_sq, st_sdf, sph, tidx, T, sc["caps"], y, 0.2, BAND,
+                                          comp_workspace=cws, y_index=yi, bounds=bnd)
+        h0, _, nfb0 = pcdf.surrogate_finish(sgrid, st_sq, st_sdf, sph, tidx, T, sc["caps"], torch.zeros_like(y),
+                                            0.2, BAND, comp_workspace=cws, y_index=yi, bounds=bnd)
+        e = (d_pr - d_ex).abs()
+        e = e[torch.isfinite(e)]
+        nq = sph.numel() // 4
+        r = {"max_err": float(e.max()), "mean_err": float(e.mean()),
+             "fallback": int(nfb.item()) / nq, "wrong": int(((h > 0) != (h_ex > 0)).sum()),
+             "rows": int(cnt.item()) / nq, "active": int((h_ex > 0).sum()) / nq,
+             "h_err": float((h - h_ex).abs().mean()), "h_err0": float((h0 - h_ex).abs().mean()),
+             "h_err_max": float((h - h_ex).abs().max()), "h_err0_max": float((h0 - h_ex).abs().max()),
+             "wrong0": int(((h0 > 0) != (h_ex > 0)).sum()), "fallback0": int(nfb0.item()) / nq,
+             "u_fallback": int(nfb_u.item()) / nq, "u_wrong": int(((h_u > 0) != (h_ex > 0)).sum()), "nq": nq}
+        if not timing:
+            return r
+
+        def surrogate_path():
+            # exact answers from the capsule-slab partials (the composite's
+            # first stage, run for this plan step's capsules), one stream
+            pcdf.composite_prepare(sgrid, sc["caps"], cws)
+            pcdf.surrogate_query(net, sgrid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=BAND,
+                                 caps_dev=caps_dev, comp_workspace=cws)
+
+        def surrogate_path_overlapped():
+            # the capsule slab on a side stream while the certificate and the rows are computed
+            pcdf.surrogate_step(net, sgrid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, BAND, cws,
+                                caps_dev=caps_dev)
+
+        comp_out = torch.empty((T,) + sgrid.shape, dtype=torch.float32, device=dev)
+
+        def exact_composite():
+            # the T composite fields (kept on the device) and the query on them
+            pcdf.composite_prepare(sgrid, sc["caps"], cws)
+            pcdf.composite_finish(st_sq, sgrid, sc["caps"], cws, None, comp_out, static_sdf=st_sdf)
+            pcdf.query_cost(comp_out, sgrid, sph, tidx, 0.2)
+
+        def exact_scratch():
+            _, fs = pcdf.build_from_scratch(occ, sgrid, sc["caps"])
+            pcdf.query_cost(fs, sgrid, sph, tidx, 0.2)
+
+        r["surrogate_ms"] = ev_time(surrogate_path)
+        r["exact_composite_ms"] = ev_time(exact_composite)
+        r["exact_scratch_ms"] = ev_time(exact_scratch)
+        try:
+            r["surrogate_graph_ms"] = graph_ms(surrogate_path_overlapped)
+            r["exact_composite_graph_ms"] = graph_ms(exact_composite)
+        except RuntimeError as exc:  # capture unsupported here: eager numbers only
+            print(f"graph capture failed: {exc}", file=sys.stderr)
+            r["surrogate_graph_ms"] = r["exact_composite_graph_ms"] = None
+        return r, (sc, sph, tidx, st_sq, st_sdf, caps_dev, cws)
+
+    stats = []
+    for s in range(seed + 6000, seed + 6002):
+        sc, sph, tidx = queries(s)
+        res = evaluate(sc, sph, tidx, timing=(s == seed + 6001))
+        if isinstance(res, tuple):
+            res, keep = res
+        stats.append(res)
+    timing = stats[-1]
+    sc, sph, tidx, st_sq, st_sdf, caps_dev, cws = keep
+    # a larger workload of the same voxel size: the 12.8 x 12.8 x 3.2 m room
+    # (256 x 256 x 64 voxels of 5 cm, 160 boxes, 3 walking humans), where
+    # keeping all T fields costs 16 times as much and the queries do not grow
+    room = scenes.scene_room(seed=seed + 7000, T=T, H=3)
+    rsph, rtidx = scenes.spheres_along_paths(room["grid"], 1024, 40, 25, np.random.default_rng(seed + 7000), T=T)
+    room_r, _ = evaluate(room, torch.from_numpy(rsph).to(dev), torch.from_numpy(rtidx).to(dev), timing=True)
     t_sur_local = ev_time(lambda: pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2,
-                                                       band=band, caps_dev=caps_dev, err_bound=err_bound))
+                                                       band=BAND, caps_dev=caps_dev))
     x_q = pcdf.surrogate_features(grid, sph, tidx, T, caps_dev)
     t_feat = ev_time(lambda: pcdf.surrogate_features(grid, sph, tidx, T, caps_dev))
     t_mlp = ev_time(lambda: net.forward(x_q))
-    x_sel, _ = pcdf.surrogate_select(grid, st_sdf, sph, tidx, T, caps_dev)
+    x_sel, _, _ = pcdf.surrogate_select(grid, st_sdf, sph, tidx, T, caps_dev, 0.2, certified=False)
     t_mlp_sel = ev_time(lambda: net.forward(x_sel))
     t_inf = ev_time(lambda: net.infer(x_q))
     t_inf_sel = ev_time(lambda: net.infer(x_sel))
     t_tc = ev_time(lambda: net.infer_tc(x_q))
     t_tc_sel = ev_time(lambda: net.infer_tc(x_sel))
 
-    def exact_composite():
-        _, cs = pcdf.build_predicted_composite(st_sq, grid, sc["caps"], want_sq=False, static_sdf=st_sdf)
-        pcdf.query_cost(cs, grid, sph, tidx, 0.2)
+    def speeds(r):
+        out = {"surrogate_ms": r["surrogate_ms"], "surrogate_graph_ms": r["surrogate_graph_ms"],
+               "exact_composite_ms": r["exact_composite_ms"], "exact_composite_graph_ms": r["exact_composite_graph_ms"],
+               "exact_scratch_ms": r["exact_scratch_ms"],
+               "speedup_vs_composite": r["exact_composite_ms"] / r["surrogate_ms"],
+               "speedup_vs_scratch": r["exact_scratch_ms"] / r["surrogate_ms"]}
+        if r["surrogate_graph_ms"] and r["exact_composite_graph_ms"]:
+            out["graph_speedup_vs_composite"] = r["exact_composite_graph_ms"] / r["surrogate_graph_ms"]
+            out["graph_speedup_vs_scratch"] = r["exact_scratch_ms"] / r["surrogate_graph_ms"]
+        return out
 
-    def exact_scratch():
-        _, fs = pcdf.build_from_scratch(occ, grid, sc["caps"])
-        pcdf.query_cost(fs, grid, sph, tidx, 0.2)
-
-    t_comp = ev_time(exact_composite)
-    t_scr = ev_time(exact_scratch)
     return {"workload": f"MLP 16-256-256-256-1 bf16/fp32, trained on {n_train_scenes} 64^3 scenes x T=20 "
                         f"({steps * batch} samples); 1,024,000 sphere queries per plan step on held-out scenes",
             "train_s": t_train, "fields_s": t_fields, "loss_first": hist[0][1], "loss_last": hist[-1][1],
-            "band_m": band, "err_bound_m": err_bound, "max_err_m": max(x[0] for x in stats), "mean_err_m": float(np.mean([x[1] for x in stats])),
-            "fallback_frac": float(np.mean([x[2] for x in stats])), "decisions_identical": all(x[3] for x in stats),
-            "at_band_0_05_m": {"fallback_frac": float(np.mean([x[5] for x in stats])),
-                               "wrong_decisions": int(sum(x[6] for x in stats)),
-                               "queries": int(sph.numel() // 4 * len(stats))},
-            "surrogate_ms": t_sur, "surrogate_graph_ms": t_sur_graph, "surrogate_local_search_ms": t_sur_local, "features_ms": t_feat,
+            "band_m": BAND, "certified": True,
+            "max_err_m": max(x["max_err"] for x in stats), "mean_err_m": float(np.mean([x["mean_err"] for x in stats])),
+            "fallback_frac": float(np.mean([x["fallback"] for x in stats])),
+            "wrong_decisions": int(sum(x["wrong"] for x in stats)), "queries": int(sum(x["nq"] for x in stats)),
+            "decisions_identical": all(x["wrong"] == 0 for x in stats),
+            "network_rows_frac": float(np.mean([x["rows"] for x in stats])),
+            "active_frac": float(np.mean([x["active"] for x in stats])),
+            "h_mean_abs_err_m": float(np.mean([x["h_err"] for x in stats])),
+            "h_max_abs_err_m": max(x["h_err_max"] for x in stats),
+            "without_network": {"h_mean_abs_err_m": float(np.mean([x["h_err0"] for x in stats])),
+                                "h_max_abs_err_m": max(x["h_err0_max"] for x in stats),
+                                "wrong_decisions": int(sum(x["wrong0"] for x in stats)),
+                                "fallback_frac": float(np.mean([x["fallback0"] for x in stats])),
+                                "what": "zero residual: the continuous capsule distance clamped to the certified "
+                                        "interval, same certificate and band"},
+            "uncertified_at_band_0_05_m": {"fallback_frac": float(np.mean([x["u_fallback"] for x in stats])),
+                                           "wrong_decisions": int(sum(x["u_wrong"] for x in stats))},
+            **speeds(timing),
+            "room": {"workload": "12.8 x 12.8 x 3.2 m room, 256 x 256 x 64 voxels of 5 cm, 160 boxes, 3 walking "
+                                 "humans, T = 20; 1,024,000 sphere queries; the same network",
+                     "max_err_m": room_r["max_err"], "mean_err_m": room_r["mean_err"],
+                     "fallback_frac": room_r["fallback"], "wrong_decisions": room_r["wrong"],
+                     "queries": room_r["nq"], "network_rows_frac": room_r["rows"],
+                     "h_mean_abs_err_m": room_r["h_err"], "without_network_h_mean_abs_err_m": room_r["h_err0"],
+                     **speeds(room_r)},
+            "surrogate_local_search_ms": t_sur_local, "features_ms": t_feat,
             "rows_to_network_frac": x_sel.shape[0] / (sph.numel() // 4), "mlp_forward_selected_ms": t_mlp_sel,
             "mlp_infer_ms": t_inf, "mlp_infer_selected_ms": t_inf_sel,
             "mlp_infer_tflops": 2 * 136193 * sph.numel() / 4 / (t_inf * 1e-3) / 1e12,
             "mlp_infer_tcgen05_ms": t_tc, "mlp_infer_tcgen05_selected_ms": t_tc_sel,
             "mlp_infer_tcgen05_tflops": 2 * 136193 * sph.numel() / 4 / (t_tc * 1e-3) / 1e12,
             "mlp_forward_ms": t_mlp,
-            "mlp_tflops": 2 * 136193 * sph.numel() / 4 / (t_mlp * 1e-3) / 1e12, "exact_composite_ms": t_comp, "exact_scratch_ms": t_scr,
-            "speedup_vs_scratch": t_scr / t_sur, "speedup_vs_composite": t_comp / t_sur,
-            "graph_speedup_vs_scratch": t_scr / t_sur_graph if t_sur_graph else None}
+            "mlp_tflops": 2 * 136193 * sph.numel() / 4 / (t_mlp * 1e-3) / 1e12}
 
 
 def bench_translated(pcdf, dev, grid, caps, static_sq, static_sdf, comp_sq, comp_sdf, timed, k):
@@ -811,8 +867,8 @@ def run_profile_surrogate(dev):
 
     def step():
         pcdf.composite_prepare(grid, sc["caps"], cws)
-        return pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.135,
-                                    caps_dev=caps_dev, err_bound=0.156, comp_workspace=cws)
+        return pcdf.surrogate_query(net, grid, st_sq, st_sdf, sph, tidx, sc["caps"], 0.2, band=0.05,
+                                    caps_dev=caps_dev, comp_workspace=cws)
 
     for _ in range(3):
         step()

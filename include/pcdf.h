@@ -455,13 +455,14 @@ int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, in
  * Surrogate queries (an extension beyond the paper).
  *
  * Features of a point p (metres) at time index t of a horizon T for one
- * capsule (a, b, r): p - grid centre scaled by 2 / largest grid extent;
- * 2 t / (T - 1) - 1 (0 if T == 1); p - a and p - b in units of 2 m; r in units
- * of 2 m; the continuous signed distance |p - n| - r from p to the capsule
- * (n the nearest axis point) in units of 2 m; the axis parameter of n scaled
- * to [-1, 1]; three zeros.  (The capsule enters relative to the point; the
- * network learns the exact voxel field's departure from the continuous
- * distance.)
+ * capsule (a, b, r): two zeros; the height of p above the grid floor in
+ * units of 2 m; 2 t / (T - 1) - 1 (0 if T == 1); p - a and p - b in units of
+ * 2 m; r in units of 2 m; the continuous signed distance |p - n| - r from p to
+ * the capsule (n the nearest axis point) in units of 2 m; the axis parameter
+ * of n scaled to [-1, 1]; three zeros.  (The capsule enters relative to the
+ * point and only the floor fixes a position, so a network trained in one
+ * grid serves any grid of the same voxel size; the network learns the exact
+ * voxel field's departure from the continuous distance.)
  *
  * pcdf_surrogate_samples  M training rows from exact dynamic fields
  *     fields  device fp32 [n_fields][nz][ny][nx] (float fields of one capsule
@@ -481,14 +482,17 @@ int pcdf_mlp_adam(void *state, float lr, float beta1, float beta2, float eps, in
  *     d = trilinear over the query's cell of min(static corner value,
  *     min_h (D_h + u_h . (corner - p))), u_h the unit vector from
  *     capsule h's nearest axis point to p (the dynamic value extrapolated to
- *     the corners along its distance gradient); where
- *     |d - (eps + r)| < band and the humans can matter in the query's cell
- *     (min_h D_h - err_bound - 2 sqrt(3) vox does not exceed every static
- *     corner value; err_bound must bound the network's error) the query is
- *     answered
- *     exactly (corner voxels of
- *     its cell from static_sq and an exact local search over the capsules'
- *     voxels, interpolated like pcdf_query_cost: same bits as the exact
+ *     the corners along its distance gradient); rows with y_index -1 count as
+ *     +INF.  With bounds (device fp32 [N][2] from pcdf_surrogate_select,
+ *     8-byte aligned): d is clamped to [d_lo, d_hi], and a query is answered
+ *     exactly when its decision is not certain (d_lo < eps + r <= d_hi) or
+ *     when it is certainly active (d_hi < eps + r), has a network row and
+ *     |d - (eps + r)| < band; every other decision (h > 0 or not) is the
+ *     exact path's by construction.  With bounds NULL (to measure the
+ *     network): a query with a network row is answered exactly when
+ *     |d - (eps + r)| < band.  Exact answers take the corner voxels of the
+ *     cell from static_sq and an exact local search over the capsules'
+ *     voxels, interpolated like pcdf_query_cost (same bits as the exact
  *     composite path); h[q] = max(0, eps + r - d) (device fp32 [N]), d_out
  *     (nullable) the distance used; n_fallback (device int32, nullable) the
  *     number of exact answers.  caps_host: HOST int32 [T][H][7].  Workspace:
@@ -502,8 +506,8 @@ int pcdf_surrogate_features(const pcdf_grid *grid, const float *spheres, const i
 int pcdf_surrogate_finish_workspace_bytes(int32_t T, int32_t H, int64_t N, size_t *bytes);
 int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                           const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
-                          const int32_t *caps_host, const float *y, const int32_t *y_index, float eps, float band,
-                          float err_bound, float *h, float *d_out, int32_t *n_fallback, void *workspace,
+                          const int32_t *caps_host, const float *y, const int32_t *y_index, const float *bounds,
+                          float eps, float band, float *h, float *d_out, int32_t *n_fallback, void *workspace,
                           size_t workspace_bytes, void *stream);
 
 /* pcdf_surrogate_finish_slab  the same, with the exact answers taken from the
@@ -521,26 +525,38 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
 int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                                const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
                                const int32_t *caps_host, const void *comp_workspace, size_t comp_workspace_bytes,
-                               const float *y, const int32_t *y_index, float eps, float band, float err_bound,
+                               const float *y, const int32_t *y_index, const float *bounds, float eps, float band,
                                float *h, float *d_out, int32_t *n_fallback, void *workspace, size_t workspace_bytes,
                                void *stream);
 
-/* pcdf_surrogate_select  the rows the network must answer.  Row i = q * H + h
- * (sphere q, capsule h of time clamp(tidx[q], 0, T - 1); caps DEVICE int32
- * [T][H][7]) is skipped when its capsule cannot be nearer than the static
- * field at any corner of the query's cell: the continuous distance from the
- * sphere centre to the capsule, less the largest centre-to-corner distance of
- * the cell and 1e-4 m, exceeds zero and every static corner value of
- * static_sdf (the exact distance to a capsule's voxels is never below the
- * continuous distance to the capsule).  Kept rows get their features in x
- * (BF16 bits [<= N * H][16]) at slot y_index[i] (device int32 [N * H]; -1
- * for a skipped row), slots taken in an unspecified order; *count (device
- * int32) receives the number kept.  The network runs on x[0 .. *count) and
- * pcdf_surrogate_finish(_slab) reads its output through y_index (a NULL
- * y_index there means y holds every row in order). */
+/* pcdf_surrogate_select  the certificate of every query and the rows the
+ * network must answer.  Query q: sphere (p, r) at time t = clamp(tidx[q], 0,
+ * T - 1), capsules caps DEVICE int32 [T][H][7] (H <= 64).  bounds[q] (device
+ * fp32 [N][2], 8-byte aligned, out) = (d_lo, d_hi) with d_lo <= d <= d_hi
+ * for the exact composite path's distance d, from:
+ *   - the exact static corner values of the query's cell (static_sdf);
+ *   - at a corner outside capsule h (continuous signed distance D > 0 from
+ *     the voxel centre), the exact field of the capsule's voxels lies in
+ *     [D, D + sqrt(3) vox] (the lower end always; the upper end when
+ *     r >= 14/16 voxel and the capsule lies inside the grid, else +inf);
+ *     inside it (D <= 0) it is at most D (no lower end);
+ *   - the humans' field is the min over the capsules outside them and at
+ *     most that min inside them; the composite is min(static, humans) and
+ *     the trilinear weights are non-negative;
+ *   - a margin of 1e-4 m on each side for FP32 rounding.
+ * Row i = q * H + h needs the network if capsule h can lie below the static
+ * field at some corner (its lower end is below the static value there) and,
+ * with mode 0, if the query is certainly active (d_hi < eps + r), the only
+ * queries whose cost uses the network's value; mode 1 keeps every row where
+ * the capsule can matter (to measure the network).  Kept rows get their
+ * features in x (BF16 bits [<= N * H][16]) at slot y_index[i] (device int32
+ * [N * H]; -1 for a skipped row), slots taken in an unspecified order;
+ * *count (device int32) receives the number kept.  The network runs on
+ * x[0 .. *count) and pcdf_surrogate_finish(_slab) reads its output through
+ * y_index (a NULL y_index there means y holds every row in order). */
 int pcdf_surrogate_select(const pcdf_grid *grid, const float *static_sdf, const float *spheres, const int32_t *tidx,
-                          int64_t N, int32_t T, int32_t H, const int32_t *caps, uint16_t *x, int32_t *y_index,
-                          int32_t *count, void *stream);
+                          int64_t N, int32_t T, int32_t H, const int32_t *caps, float eps, int32_t mode, uint16_t *x,
+                          int32_t *y_index, int32_t *count, float *bounds, void *stream);
 
 #ifdef __cplusplus
 }

@@ -107,10 +107,10 @@ def _declare(lib):
         "pcdf_surrogate_samples": [G, P, P, P, I32, I32, I64, U64, F32, P, P, P],
         "pcdf_surrogate_features": [G, P, P, I64, I32, I32, P, P, P],
         "pcdf_surrogate_finish_workspace_bytes": [I32, I32, I64, SZP],
-        "pcdf_surrogate_finish": [G, P, P, P, P, I64, I32, I32, P, P, P, F32, F32, F32, P, P, P, P, SZ, P],
-        "pcdf_surrogate_finish_slab": [G, P, P, P, P, I64, I32, I32, P, P, SZ, P, P, F32, F32, F32, P, P, P, P, SZ,
+        "pcdf_surrogate_finish": [G, P, P, P, P, I64, I32, I32, P, P, P, P, F32, F32, P, P, P, P, SZ, P],
+        "pcdf_surrogate_finish_slab": [G, P, P, P, P, I64, I32, I32, P, P, SZ, P, P, P, F32, F32, P, P, P, P, SZ,
                                        P],
-        "pcdf_surrogate_select": [G, P, P, P, I64, I32, I32, P, P, P, P, P],
+        "pcdf_surrogate_select": [G, P, P, P, I64, I32, I32, P, F32, I32, P, P, P, P, P],
     })
     lib.pcdf_batch_destroy.argtypes = [P]
     lib.pcdf_batch_destroy.restype = None

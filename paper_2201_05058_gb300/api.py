@@ -851,36 +851,42 @@ def surrogate_features(grid, spheres, tidx, T, caps_dev):
     return x
 
 
-def surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev, sync=True):
-    """Rows the network must answer (the others cannot beat the static field
-    in their cell).  Returns (x BF16 [kept rows][16], y_index int32 [N * H]);
-    with sync=False no host synchronisation: (x BF16 [N * H][16] whose first
-    count rows are the kept ones, y_index, count int32 [1] on the device)."""
+def surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev, eps, certified=True, sync=True):
+    """The certificate of every query (bounds float32 [N, 2]: d_lo <= d <= d_hi
+    for the exact path's distance d) and the rows the network must answer:
+    with certified=True only rows of queries that are certainly in collision
+    (the only ones whose cost uses the network), else every row whose human
+    can matter in the query's cell (to measure the network).  Returns (x BF16
+    [kept rows][16], y_index int32 [N * H], bounds); with sync=False no host
+    synchronisation: (x BF16 [N * H][16] whose first count rows are the kept
+    ones, y_index, count int32 [1] on the device, bounds)."""
     N = spheres.numel() // 4
     H = int(caps_dev.shape[1])
     dev = spheres.device
-    x = torch.empty((N * H, 16), dtype=torch.bfloat16, device=dev)
-    yi = torch.empty(N * H, dtype=torch.int32, device=dev)
+    x = torch.empty((max(N * H, 1), MLP_IN_PAD), dtype=torch.bfloat16, device=dev)
+    yi = torch.empty(max(N * H, 1), dtype=torch.int32, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
-    _need(static_sdf, "static_sdf", torch.float32, _shape(grid))
-    _need(caps_dev, "caps", torch.int32)
+    bounds = torch.empty((max(N, 1), 2), dtype=torch.float32, device=dev)
     g = _cgrid(grid)
     _lib.check(_lib.load().pcdf_surrogate_select(ctypes.byref(g), _ptr(static_sdf), _ptr(spheres), _ptr(tidx), N,
-                                                 int(T), H, _ptr(caps_dev), _ptr(x), _ptr(yi), _ptr(cnt),
+                                                 int(T), H, _ptr(caps_dev), float(eps), 0 if certified else 1,
+                                                 _ptr(x), _ptr(yi), _ptr(cnt), _ptr(bounds),
                                                  ctypes.c_void_p(_stream(dev))), "pcdf_surrogate_select")
     if not sync:
-        return x, yi, cnt
-    return x[: int(cnt.item())], yi
+        return x, yi, cnt, bounds
+    return x[: int(cnt.item())], yi, bounds
 
 
-def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound=None,
-                     comp_workspace=None, y_index=None):
-    """Hinge cost from the network outputs with exact answers near the
-    threshold (err_bound: bound on the network error, default band).  With
-    comp_workspace (after composite_prepare on the same grid and caps) the
-    exact answers come from its capsule-slab partials, else from a local
+def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, comp_workspace=None,
+                     y_index=None, bounds=None):
+    """Hinge cost from the network outputs.  With bounds (the certificate of
+    surrogate_select) every collision decision is the exact path's: the
+    prediction is clamped to the certified interval, and queries whose
+    decision is not certain, or whose prediction lies within `band` of the
+    threshold, are answered exactly.  Without bounds the band alone decides.
+    With comp_workspace (after composite_prepare on the same grid and caps)
+    the exact answers come from its capsule-slab partials, else from a local
     search over the capsules' voxels.  Returns (h, d, n_fallback[1])."""
-    err_bound = band if err_bound is None else err_bound
     caps = _caps_host(caps)
     H = int(caps.shape[1])
     N = spheres.numel() // 4
@@ -894,29 +900,29 @@ def surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps
     ws = _workspace(n.value, dev)
     g = _cgrid(grid)
     cp = caps.ctypes.data_as(ctypes.c_void_p)
-    tail = (float(eps), float(band), float(err_bound), _ptr(h), _ptr(d), _ptr(nfb), _ptr(ws), ws.numel(),
-            ctypes.c_void_p(_stream(dev)))
+    tail = (float(eps), float(band), _ptr(h), _ptr(d), _ptr(nfb), _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(dev)))
     if comp_workspace is None:
         _lib.check(lib.pcdf_surrogate_finish(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), _ptr(spheres),
-                                             _ptr(tidx), N, int(T), H, cp, _ptr(y), _ptr(y_index), *tail),
-                   "pcdf_surrogate_finish")
+                                             _ptr(tidx), N, int(T), H, cp, _ptr(y), _ptr(y_index), _ptr(bounds),
+                                             *tail), "pcdf_surrogate_finish")
     else:
         _need(comp_workspace, "comp_workspace", torch.uint8)
         _lib.check(lib.pcdf_surrogate_finish_slab(ctypes.byref(g), _ptr(static_sq), _ptr(static_sdf), _ptr(spheres),
                                                   _ptr(tidx), N, int(T), H, cp, _ptr(comp_workspace),
-                                                  comp_workspace.numel(), _ptr(y), _ptr(y_index), *tail),
-                   "pcdf_surrogate_finish_slab")
+                                                  comp_workspace.numel(), _ptr(y), _ptr(y_index), _ptr(bounds),
+                                                  *tail), "pcdf_surrogate_finish_slab")
     return h, d, nfb
 
 
 def surrogate_step(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps, band, comp_workspace,
-                   caps_dev=None, err_bound=None):
-    """One plan step of the surrogate: the capsule-slab partials of the
-    composite's first stage (composite_prepare into comp_workspace) run on a
-    side stream while the rows are selected on the current stream; the
-    network waits for both (its persistent grid wants every SM), then the
-    exact fallback reads the partials.  No host synchronisation: capturable
-    in a CUDA graph.  Returns (h, d, n_fallback[1]) as surrogate_query."""
+                   caps_dev=None):
+    """One certified plan step of the surrogate: the capsule-slab partials of
+    the composite's first stage (composite_prepare into comp_workspace) run on
+    a side stream while the certificate and the rows are computed on the
+    current stream; the network waits for both (its persistent grid wants
+    every SM), then the exact answers read the partials.  Every collision
+    decision is the exact path's.  No host synchronisation: capturable in a
+    CUDA graph.  Returns (h, d, n_fallback[1]) as surrogate_query."""
     caps = _caps_host(caps)
     dev = spheres.device
     if caps_dev is None:
@@ -928,25 +934,29 @@ def surrogate_step(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps,
     with torch.cuda.stream(side):
         composite_prepare(grid, caps, comp_workspace)
     comp_workspace.record_stream(side)
-    x, yi, cnt = surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev, sync=False)
+    x, yi, cnt, bounds = surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev, eps, sync=False)
     main.wait_stream(side)
     y = model.infer_tc(x, count=cnt) if x.shape[0] else torch.empty(1, dtype=torch.float32, device=dev)
-    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound,
-                            comp_workspace, y_index=yi)
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, comp_workspace,
+                            y_index=yi, bounds=bounds)
 
 
 def surrogate_query(model, grid, static_sq, static_sdf, spheres, tidx, caps, eps, band, caps_dev=None,
-                    err_bound=None, comp_workspace=None):
-    """Hinge cost of every sphere through the network, exact within `band`
-    of the threshold where the humans can matter (from the capsule-slab
-    partials in comp_workspace when given, after composite_prepare).
+                    comp_workspace=None, certified=True):
+    """Hinge cost of every sphere through the network, exact where needed (from
+    the capsule-slab partials in comp_workspace when given, after
+    composite_prepare).  certified=True: every collision decision is the
+    exact path's (see surrogate_finish); certified=False: the network's own
+    prediction for every query where the humans can matter, exact only within
+    `band` of the threshold (band 0: the network alone).
     Returns (h, d, n_fallback[1])."""
     caps = _caps_host(caps)
     if caps_dev is None:
         caps_dev = torch.from_numpy(caps).to(spheres.device)
     T = int(caps.shape[0])
     # select -> network -> finish with the kept-row count on the device
-    x, yi, cnt = surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev, sync=False)
+    x, yi, cnt, bounds = surrogate_select(grid, static_sdf, spheres, tidx, T, caps_dev, eps, certified=certified,
+                                          sync=False)
     y = model.infer_tc(x, count=cnt) if x.shape[0] else torch.empty(1, dtype=torch.float32, device=spheres.device)
-    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, err_bound,
-                            comp_workspace, y_index=yi)
+    return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, T, caps, y, eps, band, comp_workspace,
+                            y_index=yi, bounds=bounds if certified else None)

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "edt_common.cuh"
@@ -36,8 +37,6 @@ constexpr float kLen = 2.0f;  // metres: scale of the point-to-endpoint features
 
 struct FeatGrid {
     QueryGrid g;
-    float centre[3];
-    float scale;  // 2 / largest grid extent
 };
 
 __device__ __forceinline__ float fixed_to_m(int32_t v, float origin, float vox)
@@ -81,19 +80,21 @@ __device__ __forceinline__ CapGeo capsule_geo(const QueryGrid &g, const float (&
     return r;
 }
 
-// Features of point p at time index t (horizon T) for one capsule:
-// p scaled to [-1, 1] by the grid, t scaled to [-1, 1], p - a and p - b in
-// units of kLen, the radius in units of kLen, the continuous signed distance
-// to the capsule in units of kLen and the axis parameter of its nearest point
-// scaled to [-1, 1], then zeros.  The network's output is the exact field's
-// departure from that continuous distance (its target in training).
+// Features of point p at time index t (horizon T) for one capsule: two
+// zeros, the height of p above the grid floor in units of kLen, t scaled to
+// [-1, 1], p - a and p - b in units of kLen, the radius in units of kLen, the
+// continuous signed distance to the capsule in units of kLen and the axis
+// parameter of its nearest point scaled to [-1, 1], then zeros.  Nothing but
+// the floor fixes a position, so a network trained in one grid applies to
+// any grid of the same voxel size.  The network's output is the exact
+// field's departure from the continuous distance (its target in training).
 __device__ __forceinline__ void features(const FeatGrid &G, const float (&p)[3], int t, int T, const int32_t *cap,
                                          const CapGeo &geo, bf16 *out)
 {
     float f[16];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        f[a] = (p[a] - G.centre[a]) * G.scale;
+    f[0] = 0.f;
+    f[1] = 0.f;
+    f[2] = (p[2] - G.g.origin[2]) * (1.f / kLen);
     f[3] = T > 1 ? 2.f * (float)t / (float)(T - 1) - 1.f : 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -182,65 +183,201 @@ __global__ void k_sur_features(FeatGrid G, const float4 *__restrict__ spheres, c
     features(G, p, t, T, cap, capsule_geo(G.g, p, cap), x + i * 16);
 }
 
-// Rows (sphere q, capsule h) that need the network.  The exact dynamic value
-// at a voxel outside the humans is at least the continuous distance from its
-// centre to the capsule (the nearest voxel centre inside lies in the solid),
-// and the continuous distance changes by at most |corner - p| between p and a
-// corner.  So when that distance at p, less the largest |corner - p| of the
-// query's cell and a rounding margin, exceeds every static corner value (and
-// zero), the static field is the min at all eight corners whatever the
-// network says: the row is skipped (y_index -1) and its capsule counts as
-// +INF.  The other rows get their features at slots taken in warp order.
+// Continuous signed distance |p - n| - r from point p (metres) to a capsule.
+__device__ __forceinline__ float capsule_dist(const QueryGrid &g, const float (&p)[3], const int32_t *cap)
+{
+    float w[3], ab[3], L = 0.f, sd = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float am = fixed_to_m(cap[a], g.origin[a], g.vox);
+        w[a] = p[a] - am;
+        ab[a] = fixed_to_m(cap[3 + a], g.origin[a], g.vox) - am;
+        L += ab[a] * ab[a];
+        sd += w[a] * ab[a];
+    }
+    const float sp = L > 0.f ? fminf(fmaxf(sd / L, 0.f), 1.f) : 0.f;
+    float nn = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float u = w[a] - sp * ab[a];
+        nn += u * u;
+    }
+    return sqrtf(nn) - (float)cap[6] * (g.vox / 16.f);
+}
+
+constexpr float kCertMargin = 1e-4f;  // metres: covers the FP32 rounding of distances and interpolation
+constexpr float kSqrt3 = 1.7320508f;
+
+// Can the exact field of capsule cap (fixed point, 1/16 voxel from the grid
+// corner) exceed the continuous distance at an exterior voxel centre by more
+// than sqrt(3) voxels?  Not when the radius is at least sqrt(3)/2 voxels
+// (some voxel centre lies within sqrt(3)/2 voxels of any point at that depth
+// inside it) and the capsule lies inside the grid (that centre is a voxel of
+// the grid).
+__device__ __forceinline__ bool capsule_regular(const QueryGrid &g, const int32_t *cap)
+{
+    if (cap[6] < 14)  // 14/16 voxel > sqrt(3)/2 voxel
+        return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long mn = (long long)min(cap[a], cap[3 + a]) - cap[6];
+        const long long mx = (long long)max(cap[a], cap[3 + a]) + cap[6];
+        if (mn < 0 || mx > 16LL * g.n[a])
+            return false;
+    }
+    return true;
+}
+
+// The certificate of a query: exact bounds [d_lo, d_hi] on the exact path's
+// distance d, from the exact static corners and bounds on the humans' exact
+// field at the corners, plus which humans can lower the field at some corner.
+//  * At a voxel centre c outside capsule k (continuous distance D > 0) the
+//    exact field of the capsule's voxels is at least D (the nearest voxel
+//    centre inside lies in the solid) and, for a regular capsule, at most
+//    D + sqrt(3) vox (from the nearest surface point go sqrt(3)/2 vox inward:
+//    the voxel holding that point has its centre inside the capsule).  The
+//    humans' field outside them is the min over the capsules.
+//  * At a centre inside (D <= 0) it is at most D (every free voxel centre lies
+//    outside the solid, at least |D| away); no lower bound is used.
+//  * The composite corner is min(static, humans) and the trilinear weights
+//    are non-negative, so interpolating the corner bounds bounds d.
+// A margin of kCertMargin on each side covers FP32 rounding.
+struct Cert {
+    float dlo, dhi;
+    unsigned long long matters;  // bit k: capsule k can be below the static field at some corner
+};
+
+__device__ __forceinline__ Cert certify(const QueryGrid &g, const float *__restrict__ static_sdf, const Cell &cl,
+                                        const float (&p)[3], const int32_t *caps_t, int H)
+{
+    const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+    float sc[2][2][2], lo[2][2][2], hi[2][2][2], smax = __int_as_float(0xff800000);
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                sc[dz][dy][dx] = __ldg(static_sdf + (dz ? cl.i1[2] : cl.i0[2]) * sz + (dy ? cl.i1[1] : cl.i0[1]) * sy +
+                                       (dx ? cl.i1[0] : cl.i0[0]));
+                smax = fmaxf(smax, sc[dz][dy][dx]);
+                lo[dz][dy][dx] = hi[dz][dy][dx] = __int_as_float(0x7f800000);
+            }
+    // the largest distance from p to a corner of its cell
+    float md2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float c0 = g.origin[a] + ((float)cl.i0[a] + 0.5f) * g.vox;
+        const float c1 = g.origin[a] + ((float)cl.i1[a] + 0.5f) * g.vox;
+        const float m = fmaxf(fabsf(p[a] - c0), fabsf(p[a] - c1));
+        md2 += m * m;
+    }
+    const float reach = sqrtf(md2) + 2.f * kCertMargin;
+    Cert r;
+    r.matters = 0;
+    const float ninf = __int_as_float(0xff800000), pinf = __int_as_float(0x7f800000);
+    for (int k = 0; k < H; ++k) {
+        const int32_t *cap = caps_t + 7 * k;
+        // the continuous distance is 1-Lipschitz: if at p it exceeds zero and
+        // every static corner value by the reach, every corner lies outside
+        // the capsule with its lower end above the static value there, and
+        // the capsule changes neither bound
+        if (capsule_dist(g, p, cap) - reach > fmaxf(smax, 2.f * kCertMargin))
+            continue;
+        const bool reg = capsule_regular(g, cap);
+        bool m = false;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const float c[3] = {g.origin[0] + ((float)(dx ? cl.i1[0] : cl.i0[0]) + 0.5f) * g.vox,
+                                        g.origin[1] + ((float)(dy ? cl.i1[1] : cl.i0[1]) + 0.5f) * g.vox,
+                                        g.origin[2] + ((float)(dz ? cl.i1[2] : cl.i0[2]) + 0.5f) * g.vox};
+                    const float D = capsule_dist(g, c, cap);
+                    const float l = D > kCertMargin ? D - kCertMargin : ninf;
+                    const float u = reg ? D + kSqrt3 * g.vox + kCertMargin : (D < -kCertMargin ? D + kCertMargin : pinf);
+                    lo[dz][dy][dx] = fminf(lo[dz][dy][dx], l);
+                    hi[dz][dy][dx] = fminf(hi[dz][dy][dx], u);
+                    m |= l < sc[dz][dy][dx];
+                }
+        if (m)
+            r.matters |= 1ull << k;
+    }
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                lo[dz][dy][dx] = fminf(sc[dz][dy][dx], lo[dz][dy][dx]);
+                hi[dz][dy][dx] = fminf(sc[dz][dy][dx], hi[dz][dy][dx]);
+            }
+    r.dlo = interpolate(cl, lo, false).d - kCertMargin;
+    r.dhi = interpolate(cl, hi, false).d + kCertMargin;
+    return r;
+}
+
+// Rows (sphere q, capsule k) that need the network, from the certificate of
+// query q: capsules that cannot be below the static field at any corner of
+// the cell never need it (the row is skipped, y_index -1, and the capsule
+// counts as +INF).  mode 0 (the certified query): rows only of queries whose
+// decision is certainly active (d_hi < eps + r), the only ones whose cost uses
+// the network's value; mode 1: every row where the capsule can matter (to
+// measure the network).  Rows get their features at slots taken in warp
+// order; bounds[q] = (d_lo, d_hi).
 __global__ void k_sur_select(FeatGrid G, const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
                              const int32_t *__restrict__ tidx, long long N, int T, int H,
-                             const int32_t *__restrict__ caps, bf16 *__restrict__ x, int32_t *__restrict__ y_index,
-                             int *__restrict__ count)
+                             const int32_t *__restrict__ caps, float eps, int mode, bf16 *__restrict__ x,
+                             int32_t *__restrict__ y_index, int *__restrict__ count, float2 *__restrict__ bounds)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool need = false;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long need = 0;
     float p[3] = {0.f, 0.f, 0.f};
     int t = 0;
-    const int32_t *cap = caps;
-    CapGeo geo{};
-    if (i < N * H) {
-        const long long q = i / H;
-        const int h = (int)(i % H);
+    if (q < N) {
         const float4 s = spheres[q];
         t = min(max(tidx[q], 0), T - 1);
         p[0] = s.x;
         p[1] = s.y;
         p[2] = s.z;
-        cap = caps + 7 * ((long long)t * H + h);
-        geo = capsule_geo(G.g, p, cap);
         const Cell cl = locate(G.g, s);
-        const long long sy = G.g.n[0], sz = (long long)G.g.n[0] * G.g.n[1];
-        float smax = 0.f, md2 = 0.f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            smax = fmaxf(smax, __ldg(static_sdf + ((k & 4) ? cl.i1[2] : cl.i0[2]) * sz +
-                                     ((k & 2) ? cl.i1[1] : cl.i0[1]) * sy + ((k & 1) ? cl.i1[0] : cl.i0[0])));
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float c0 = G.g.origin[a] + ((float)cl.i0[a] + 0.5f) * G.g.vox;
-            const float c1 = G.g.origin[a] + ((float)cl.i1[a] + 0.5f) * G.g.vox;
-            const float m = fmaxf(fabsf(p[a] - c0), fabsf(p[a] - c1));
-            md2 += m * m;
-        }
-        need = !(geo.dist - sqrtf(md2) - 1e-4f > smax);
+        const Cert c = certify(G.g, static_sdf, cl, p, caps + 7LL * t * H, H);
+        bounds[q] = make_float2(c.dlo, c.dhi);
+        need = c.matters;
+        if (mode == 0 && !(c.dhi < eps + s.w))
+            need = 0;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, need);
+    // slots: one atomic per warp, rows in lane order
     const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (m) {
-        if (lane == __ffs(m) - 1)
-            base = atomicAdd(count, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    const int cnt = __popcll(need);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += v;
     }
-    if (i < N * H) {
-        const int slot = base + __popc(m & ((1u << lane) - 1u));
-        y_index[i] = need ? slot : -1;
-        if (need)
-            features(G, p, t, T, cap, geo, x + (long long)slot * 16);
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int base = 0;
+    if (total) {
+        if (lane == 31)
+            base = atomicAdd(count, total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+    }
+    if (q < N) {
+        int slot = base + incl - cnt;
+        for (int k = 0; k < H; ++k) {
+            const int32_t *cap = caps + 7 * ((long long)t * H + k);
+            if ((need >> k) & 1ull) {
+                y_index[q * H + k] = slot;
+                features(G, p, t, T, cap, capsule_geo(G.g, p, cap), x + (long long)slot * 16);
+                ++slot;
+            } else {
+                y_index[q * H + k] = -1;
+            }
+        }
     }
 }
 
@@ -250,18 +387,20 @@ __global__ void k_sur_select(FeatGrid G, const float *__restrict__ static_sdf, c
 // continuous distance plus the network's output (the learned departure of the
 // exact voxel field from it); at a corner it is extrapolated along the
 // capsule's distance gradient (the unit vector from the nearest axis point),
-// then the min over humans.
+// then the min over humans.  Capsules without a row count as +INF.
 //
-// A query needs the exact answer only if the prediction is within `band` of
-// the threshold and the humans can matter in its cell.  They cannot when the
-// predicted dynamic distance, less `err` (a bound on the network's error) and
-// less 2 sqrt(3) voxels (how far the signed voxel field can change across a
-// cell), still exceeds every static corner value: then the static field is
-// the min at all eight corners and its interpolation is the exact distance.
+// With the certificate (bounds, from k_sur_select): the prediction is clamped
+// to [d_lo, d_hi]; a query whose threshold eps + r lies inside the interval
+// (the decision is not certain) is answered exactly, and so is a certainly
+// active query whose prediction lies within `band` of the threshold.  Every
+// other decision is the exact one by construction.  Without it (bounds NULL,
+// to measure the network): a query with some row is answered exactly when
+// the prediction lies within `band` of the threshold; a query without rows
+// has the static field as its exact distance.
 __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf, const float4 *__restrict__ spheres,
                               const int32_t *__restrict__ tidx, int T, const CapInfo *__restrict__ caps, long long N,
-                              int H, const float *__restrict__ y, const int32_t *__restrict__ y_index, float eps,
-                              float band, float err,
+                              int H, const float *__restrict__ y, const int32_t *__restrict__ y_index,
+                              const float2 *__restrict__ bounds, float eps, float band,
                               float *__restrict__ h, float *__restrict__ d_out, int *__restrict__ list,
                               int *__restrict__ count)
 {
@@ -272,30 +411,28 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
         const int t = min(max(tidx[q], 0), T - 1);
         const Cell cl = locate(g, s);
         const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
-        float c[2][2][2], dync[2][2][2], smax = __int_as_float(0xff800000);
+        float c[2][2][2], dync[2][2][2];
 #pragma unroll
         for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
-                    const float v = __ldg(static_sdf + (dz ? cl.i1[2] : cl.i0[2]) * sz + (dy ? cl.i1[1] : cl.i0[1]) * sy +
+                    c[dz][dy][dx] = __ldg(static_sdf + (dz ? cl.i1[2] : cl.i0[2]) * sz + (dy ? cl.i1[1] : cl.i0[1]) * sy +
                                           (dx ? cl.i1[0] : cl.i0[0]));
-                    c[dz][dy][dx] = v;
-                    smax = fmaxf(smax, v);
                     dync[dz][dy][dx] = __int_as_float(0x7f800000);
                 }
         const float p[3] = {s.x, s.y, s.z};
-        float dyn = __int_as_float(0x7f800000);
+        bool rows = false;
         for (int k = 0; k < H; ++k) {
-            const CapInfo &C = caps[(long long)t * H + k];
-            const int32_t cp[7] = {C.a[0], C.a[1], C.a[2], C.b[0], C.b[1], C.b[2], C.r};
-            const CapGeo geo = capsule_geo(g, p, cp);
             const long long yi = y_index ? (long long)y_index[q * H + k] : q * H + k;
             if (yi < 0)
                 continue;  // the static field wins in the cell whatever this capsule
+            rows = true;
+            const CapInfo &C = caps[(long long)t * H + k];
+            const int32_t cp[7] = {C.a[0], C.a[1], C.a[2], C.b[0], C.b[1], C.b[2], C.r};
+            const CapGeo geo = capsule_geo(g, p, cp);
             const float yk = y[yi] + geo.dist;  // residual + continuous distance
-            dyn = fminf(dyn, yk);
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
@@ -317,11 +454,16 @@ __global__ void k_sur_combine(QueryGrid g, const float *__restrict__ static_sdf,
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx)
                     c[dz][dy][dx] = fminf(c[dz][dy][dx], dync[dz][dy][dx]);
-        const float d = interpolate(cl, c, false).d;
+        float d = interpolate(cl, c, false).d;
         const float thr = eps + s.w;
-        const float lip = 2.f * 1.7320508f * g.vox;
-        const bool static_certain = dyn - err - lip > smax;
-        fb = fabsf(d - thr) < band && !static_certain;
+        if (bounds) {
+            const float2 b = bounds[q];
+            d = fminf(fmaxf(d, b.x), b.y);
+            const bool inactive = thr <= b.x, active = b.y < thr;
+            fb = !(inactive || active) || (active && rows && fabsf(d - thr) < band);
+        } else {
+            fb = rows && fabsf(d - thr) < band;
+        }
         const float hv = thr - d;
         h[q] = hv > 0.f ? hv : 0.f;
         if (d_out)
@@ -678,10 +820,6 @@ FeatGrid feat_grid(const pcdf_grid *grid)
     for (int a = 0; a < 3; ++a)
         G.g.origin[a] = grid->origin[a];
     G.g.vox = grid->vox;
-    const float ext[3] = {grid->nx * grid->vox, grid->ny * grid->vox, grid->nz * grid->vox};
-    for (int a = 0; a < 3; ++a)
-        G.centre[a] = grid->origin[a] + 0.5f * ext[a];
-    G.scale = 2.f / std::max(ext[0], std::max(ext[1], ext[2]));
     return G;
 }
 
@@ -729,24 +867,29 @@ int pcdf_surrogate_features(const pcdf_grid *grid, const float *spheres, const i
 }
 
 int pcdf_surrogate_select(const pcdf_grid *grid, const float *static_sdf, const float *spheres, const int32_t *tidx,
-                          int64_t N, int32_t T, int32_t H, const int32_t *caps, uint16_t *x, int32_t *y_index,
-                          int32_t *count, void *stream)
+                          int64_t N, int32_t T, int32_t H, const int32_t *caps, float eps, int32_t mode, uint16_t *x,
+                          int32_t *y_index, int32_t *count, float *bounds, void *stream)
 {
     if (int rc = check_grid(grid))
         return rc;
-    if (N < 0 || T < 1 || H < 1 || !count || (N > 0 && (!static_sdf || !spheres || !tidx || !caps || !x || !y_index)))
+    if (N < 0 || T < 1 || H < 1 || H > 64 || !count || (mode != 0 && mode != 1) ||
+        (N > 0 && (!static_sdf || !spheres || !tidx || !caps || !x || !y_index || !bounds)))
         return fail(PCDF_EINVAL, "bad surrogate selection arguments");
+    if (!std::isfinite(eps))
+        return fail(PCDF_EINVAL, "eps must be finite");
+    if (N > 0 && !aligned(bounds, 8))
+        return fail(PCDF_EINVAL, "bounds must be 8-byte aligned");
     if (!aligned(spheres, 16) || !aligned(x, 16))
         return fail(PCDF_EINVAL, "spheres and x must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess)
         return cuda_fail(e, "surrogate selection");
-    const long long R = N * H;
-    if (R == 0)
+    if (N == 0)
         return PCDF_OK;
-    k_sur_select<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(feat_grid(grid), static_sdf, (const float4 *)spheres, tidx,
-                                                             N, T, H, caps, (bf16 *)x, y_index, count);
+    k_sur_select<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(feat_grid(grid), static_sdf, (const float4 *)spheres, tidx,
+                                                             N, T, H, caps, eps, mode, (bf16 *)x, y_index, count,
+                                                             (float2 *)bounds);
     e = cudaGetLastError();
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "surrogate selection");
 }
@@ -777,13 +920,13 @@ __global__ void k_put_caps(const __grid_constant__ pcdf::CapBatch b, pcdf::CapIn
 int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, const float *spheres,
                      const int32_t *tidx, int64_t N, int32_t T, int32_t H, const int32_t *caps_host,
                      const int32_t *dyn_mid, const pcdf::SlabMap *map, int zlo_slab, int S_slab, const float *y,
-                     const int32_t *y_index,
-                     float eps, float band,
-                     float err_bound, float *h, float *d_out, int32_t *n_fallback, void *workspace,
-                     size_t workspace_bytes, void *stream)
+                     const int32_t *y_index, const float *bounds, float eps, float band, float *h, float *d_out,
+                     int32_t *n_fallback, void *workspace, size_t workspace_bytes, void *stream)
 {
     if (!static_sq || !static_sdf || !spheres || !tidx || !y || !h || !workspace)
         return fail(PCDF_EINVAL, "required pointer is NULL");
+    if (bounds && !aligned(bounds, 8))
+        return fail(PCDF_EINVAL, "bounds must be 8-byte aligned");
     if (!aligned(spheres, 16) || !aligned(workspace, kAlign))
         return fail(PCDF_EINVAL, "spheres must be 16-byte aligned, workspace %zu-byte aligned", kAlign);
     size_t need = 0;
@@ -815,8 +958,8 @@ int surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const floa
         return cuda_fail(e, "surrogate setup");
     const FeatGrid G = feat_grid(grid);
     k_sur_combine<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(G.g, static_sdf, (const float4 *)spheres, tidx, T,
-                                                              dcaps, N, H, y, y_index, eps, band, err_bound, h, d_out,
-                                                              list, count);
+                                                              dcaps, N, H, y, y_index, (const float2 *)bounds, eps, band,
+                                                              h, d_out, list, count);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -839,8 +982,8 @@ extern "C" {
 
 int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                           const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
-                          const int32_t *caps_host, const float *y, const int32_t *y_index, float eps, float band,
-                          float err_bound, float *h, float *d_out, int32_t *n_fallback, void *workspace,
+                          const int32_t *caps_host, const float *y, const int32_t *y_index, const float *bounds,
+                          float eps, float band, float *h, float *d_out, int32_t *n_fallback, void *workspace,
                           size_t workspace_bytes, void *stream)
 {
     if (int rc = check_grid(grid))
@@ -850,13 +993,13 @@ int pcdf_surrogate_finish(const pcdf_grid *grid, const int32_t *static_sq, const
     if (N == 0)
         return PCDF_OK;
     return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, nullptr, nullptr, 0, 0, y,
-                            y_index, eps, band, err_bound, h, d_out, n_fallback, workspace, workspace_bytes, stream);
+                            y_index, bounds, eps, band, h, d_out, n_fallback, workspace, workspace_bytes, stream);
 }
 
 int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf,
                                const float *spheres, const int32_t *tidx, int64_t N, int32_t T, int32_t H,
                                const int32_t *caps_host, const void *comp_workspace, size_t comp_workspace_bytes,
-                               const float *y, const int32_t *y_index, float eps, float band, float err_bound,
+                               const float *y, const int32_t *y_index, const float *bounds, float eps, float band,
                                float *h, float *d_out, int32_t *n_fallback, void *workspace, size_t workspace_bytes,
                                void *stream)
 {
@@ -878,7 +1021,7 @@ int pcdf_surrogate_finish_slab(const pcdf_grid *grid, const int32_t *static_sq, 
     static thread_local pcdf::SlabMap map;
     slab_map(p, map);
     return surrogate_finish(grid, static_sq, static_sdf, spheres, tidx, N, T, H, caps_host, mid ? mid : &none, &map,
-                            p.zlo, p.S, y, y_index, eps, band, err_bound, h, d_out, n_fallback, workspace,
+                            p.zlo, p.S, y, y_index, bounds, eps, band, h, d_out, n_fallback, workspace,
                             workspace_bytes, stream);
 }
 

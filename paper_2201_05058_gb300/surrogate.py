@@ -48,22 +48,3 @@ def train(model, grid, fields, caps, tf, T, steps, batch, lr=2e-3, lr_min=5e-5, 
         if log_every and (k % log_every == 0 or k == steps - 1):
             hist.append((k, float(loss.item())))
     return hist
-
-
-def band_from_errors(d_pred, d_exact, margin=1.5, floor=0.05):
-    """A fallback band that covers the observed surrogate error with a margin."""
-    err = (d_pred - d_exact).abs()
-    err = err[torch.isfinite(err)]
-    m = float(err.max().item()) if err.numel() else 0.0
-    return max(floor, margin * m)
-
-
-def band_from_decisions(d_pred, d_exact, thr, margin=1.5, floor=0.05):
-    """The smallest band that would have sent to the exact path every
-    validation query whose predicted decision (d < thr) was wrong, with a
-    margin: max |d_pred - thr| over those queries."""
-    wrong = (d_pred < thr) != (d_exact < thr)
-    gap = (d_pred - thr).abs()[wrong]
-    gap = gap[torch.isfinite(gap)]
-    m = float(gap.max().item()) if gap.numel() else 0.0
-    return max(floor, margin * m)

@@ -168,6 +168,16 @@ def scene_small_walking(seed=0, T=20, H=1):
     return dict(grid=grid, occ=occ, caps=caps, eps=0.2)
 
 
+def scene_room(seed=0, T=20, H=3, nx=256, ny=256, nz=64, vox=0.05, n_boxes=160):
+    """A room of 12.8 x 12.8 x 3.2 m in 5 cm voxels (the 64^3 scenes' voxel
+    size and box density: 10 boxes per 64^3), H humans walking over T steps."""
+    rng = np.random.default_rng(seed)
+    grid = Grid(nx, ny, nz, vox)
+    occ, _ = boxes_occupancy(grid, n_boxes, rng)
+    caps = walking_capsules(grid, H, T, rng)
+    return dict(grid=grid, occ=occ, caps=caps, eps=0.2)
+
+
 def scene_composite(seed=0, n=256, vox=0.04, n_boxes=60, H=3, T=20):
     """256^3 grid of 4 cm voxels, 60 boxes, 3 walking humans over T = 20 steps."""
     rng = np.random.default_rng(seed)
