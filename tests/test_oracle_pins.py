@@ -236,6 +236,44 @@ def test_capsule_field_sandwich():
     assert np.array_equal(Sf < 0, dc <= 1e-12)
 
 
+def test_capsule_field_bounds_of_the_certificate():
+    """The two inequalities that the surrogate's certificate rests on, on
+    random slanted capsules (radius >= 14/16 voxel, inside the grid, some
+    touching the floor) and on unions of two: outside every capsule the exact
+    field lies in [min_k d_k, min_k d_k + sqrt(3)] (voxel units, d_k the
+    continuous distance to capsule k); inside the union it is at most
+    min_k d_k (no lower bound is claimed there)."""
+    rng = np.random.default_rng(31)
+    grid = scenes.Grid(24, 22, 26, 0.05)
+    nz, ny, nx = grid.shape
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    P = np.stack([16 * i + 8, 16 * j + 8, 16 * k + 8], -1).reshape(-1, 3).astype(np.float64)
+    checked = 0
+    for trial in range(12):
+        caps = []
+        for h in range(1 + trial % 2):
+            r = int(rng.integers(14, 70))
+            lo = np.array([r, r, r]) + 1
+            hi = 16 * np.array([nx, ny, nz]) - r - 1
+            a = rng.integers(lo, hi)
+            b = rng.integers(lo, hi)
+            if trial % 3 == 0:  # standing on the floor
+                a[2] = r
+                b[:2] = a[:2]
+            caps.append([*a, *b, r])
+        caps = np.array(caps, np.int32)
+        S = oracle.edt(oracle.capsule_occupancy(grid.shape, caps)).reshape(-1).astype(np.float64)
+        dmin = np.min([(np.array([seg_dist(q, c[:3], c[3:6]) for q in P]) - c[6]) / 16.0 for c in caps], axis=0)
+        ext = S > 0
+        root = np.sqrt(S[ext])
+        assert np.all(dmin[ext] <= root + 1e-9)
+        assert np.all(root <= dmin[ext] + np.sqrt(3.0) + 1e-9)
+        inside = (S < 0) & (S != -oracle.INF32)
+        assert np.all(-np.sqrt(-S[inside]) <= dmin[inside] + 1e-9)
+        checked += int(ext.sum() + inside.sum())
+    assert checked > 50000
+
+
 def test_capsule_occupancy_matches_predicate_loop():
     grid = scenes.Grid(12, 10, 14, 0.05)
     caps = np.array([[40, 50, 30, 150, 60, 180, 45], [10, 10, 10, 10, 10, 10, 60]], np.int32)
