@@ -365,14 +365,16 @@ int pcdf_batch_upload(pcdf_batch *batch, void *workspace, size_t workspace_bytes
 int pcdf_batch_run(const pcdf_batch *batch, void *workspace, void *stream);
 int pcdf_batch_error(const pcdf_batch *batch, const void *workspace, void *stream, int32_t *code);
 /* pcdf_batch_block_stage  testing aid for the failure path: raises the
- * completion target of one stage (0 rows, 1 y pass, 2 z pass, 3 capsule
- * field) of environment `env` above any item count, so that the items that
- * wait on it can only give up when their bounded wait (about a second)
- * expires.  Those items are skipped, pcdf_batch_error then reports
- * PCDF_ETIMEOUT, and the outputs of the run are not valid.  Nothing is
- * computed from unfinished inputs when the blocked stage is the capsule
- * field (stage 3): only the composite items of `env` wait on it.  Takes
- * effect at the next pcdf_batch_upload; a new batch starts unblocked. */
+ * completion target of one stage (0 rows, 1 y pass, 2 z pass) of environment
+ * `env` above any item count, so that the items that wait on it (the y, z
+ * and first-launch items after it) can only give up when their bounded wait
+ * (about a second) expires.  After the first expiry every later wait gives
+ * up at once, so no item reads unfinished inputs: the waiting items are
+ * skipped, the second launch (the composite items) skips everything,
+ * pcdf_batch_error then reports PCDF_ETIMEOUT, and the outputs of the run
+ * are not valid.  The capsule stage (3) has no waiter in the first launch and
+ * is refused (PCDF_EINVAL).  Takes effect at the next pcdf_batch_upload; a
+ * new batch starts unblocked. */
 int pcdf_batch_block_stage(pcdf_batch *batch, int32_t env, int32_t stage);
 int pcdf_batch_autotune_workspace_bytes(const pcdf_env *envs, int32_t n_env, size_t *bytes);
 int pcdf_batch_autotune(const pcdf_env *envs, int32_t n_env, void *workspace, size_t workspace_bytes, void *stream,

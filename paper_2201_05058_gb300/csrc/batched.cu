@@ -1,12 +1,18 @@
 // Many environments of uneven size, horizon and human count in one
 // persistent launch (sm_103a).
 //
-// Every environment needs the static field (row pass, y pass, z pass) and its
-// T composite fields (capsule x+y pass over the slab, fused z pass).  The host
-// cuts all of that into work items (environment, stage, tile) and orders them
-// stage by stage: all row-pass items, all capsule items, all y items, all z
-// items, all composite items.  Persistent CTAs take items from a global queue
-// in that order.  An item whose inputs come from an earlier stage of the same
+// Every environment needs the static field (row words, the fused x+y pass and
+// the z pass of edt_full.cuh, the last also recording each column's largest
+// value) and its T composite fields
+// (capsule x+y pass over the slab, fused z pass).  The host cuts all of that
+// into work items (environment, stage, tile).  The first persistent launch
+// takes the row-pass, capsule, y and z items from a global queue in that
+// order; the second takes the composite items (column block, time steps),
+// which run the single-environment kernel's shortcuts: columns whose static
+// maximum no human can undercut are copies, blocks of such columns are copied
+// with 16-byte accesses, and the envelope is evaluated only in the z window
+// around the slab.  Two launches let each have its own register and shared
+// memory budget.  An item whose inputs come from an earlier stage of the same
 // environment waits (one thread, bounded spin, acquire loads) until the
 // completion counter of that stage reaches the stage's item count; finished
 // items publish with a release increment.  Because an item only ever waits for
@@ -24,9 +30,8 @@
 #include <vector>
 
 #include "composite.cuh"
-#include "envelope.cuh"
+#include "edt_full.cuh"
 #include "host.h"
-#include "rows.cuh"
 
 using namespace pcdf::host;
 
@@ -34,6 +39,7 @@ namespace pcdf {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kBands = kThreads / lean::kCols;  // envelope threads per column
 constexpr long long kSpinLimit = 1LL << 22;  // x 256 ns sleep: about one second
 
 enum ItemType : int { kRow = 0, kY = 1, kZ = 2, kDyn = 3, kComp = 4 };
@@ -43,14 +49,17 @@ struct BatchItem {
 };
 
 struct BatchEnv {
-    int nx, ny, nz, T, H, zlo, S, cap, segs;
+    int nx, ny, nz, T, H, zlo, S, cap, W;
     float vox;
     int need[4];  // items of the row, y, z and capsule stages
+    int vec;      // 16-byte copies of all-static column blocks allowed
     const uint8_t *occ;
     int32_t *comp_sq;
-    int16_t *g16;
+    uint32_t *bits;   // row words, [nz][ny][W]
+    uint2 *carry;     // their carries, [nz][ny][W]
     int32_t *mid;
     int32_t *static_sq;
+    int32_t *colmax;  // [ny][nx] largest static value of each column
     int32_t *dyn;
     const uint8_t *rep;   // [T][S] slab slice map (slices of equal capsule cross-sections); NULL: identity
     const CapInfo *caps;  // [T][H]
@@ -84,27 +93,17 @@ __device__ bool wait_ge(const int *p, int target, int *err)
     return false;
 }
 
-template <int C>
-__device__ __forceinline__ void rows_c(const BatchEnv &E, int r0, int r1)
+__device__ __forceinline__ void run_rows(const BatchEnv &E, int r0, int r1)
 {
     const int lane = threadIdx.x & 31;
     for (int r = r0 + (threadIdx.x >> 5); r < r1; r += kThreads / 32)
-        row_pass_row<C, 0>(E.occ, nullptr, 0, E.nx, E.ny, r % E.ny, r / E.ny, E.g16 + (long long)r * E.nx, lane);
+        full::row_bits_row<0>(E.occ, nullptr, 0, E.nx, E.ny, r, E.W, E.bits, E.carry, lane);
 }
 
-__device__ __forceinline__ void run_rows(const BatchEnv &E, int r0, int r1)
-{
-    switch (E.segs) {
-    case 1: rows_c<1>(E, r0, r1); break;
-    case 2: rows_c<2>(E, r0, r1); break;
-    case 4: rows_c<4>(E, r0, r1); break;
-    case 8: rows_c<8>(E, r0, r1); break;
-    case 12: rows_c<12>(E, r0, r1); break;
-    default: rows_c<16>(E, r0, r1); break;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads)
+// 5 CTAs per SM: the envelope stages' shared memory (up to 42 KB at 320-voxel
+// axes) allows no more, and the register budget that follows keeps spills
+// to a few words
+__global__ void __launch_bounds__(kThreads, 5)
     k_batched(const BatchEnv *__restrict__ envs, const BatchItem *__restrict__ items, int n_items, int *state,
               int row_rows, int dyn_slices, int comp_t)
 {
@@ -127,8 +126,6 @@ __global__ void __launch_bounds__(kThreads)
                 ok = wait_ge(ce + kRow, E.need[kRow], err);
             else if (I.type == kZ)
                 ok = wait_ge(ce + kY, E.need[kY], err);
-            else if (I.type == kComp)
-                ok = wait_ge(ce + kZ, E.need[kZ], err) && wait_ge(ce + kDyn, E.need[kDyn], err);
             s_ok = ok;
         }
         __syncthreads();
@@ -137,15 +134,12 @@ __global__ void __launch_bounds__(kThreads)
             case kRow:
                 run_rows(E, I.a, min(I.a + row_rows, E.ny * E.nz));
                 break;
-            case kY:
-                env::envelope_tile<int16_t, false, true>(E.g16, E.mid, nullptr, 0.f, E.ny, E.nx,
-                                                         (long long)E.nx * E.nz, (long long)E.nx * E.ny, E.nx,
-                                                         (long long)I.a, smem);
+            case kY:  // slice I.a, row word I.b
+                full::edt_xy_block<kBands, true>(E.bits, E.carry, E.nx, E.ny, E.W, I.b, I.a, E.mid, smem);
                 break;
             case kZ:
-                env::envelope_tile<int32_t, false, true>(E.mid, E.static_sq, nullptr, 0.f, E.nz, E.nx,
-                                                         (long long)E.nx * E.ny, E.nx, E.nx * E.ny, (long long)I.a,
-                                                         smem);
+                full::edt_z_block<kBands, false, true>(E.mid, E.static_sq, nullptr, 0.f, E.nz,
+                                                       (long long)E.nx * E.ny, (long long)I.a, smem, E.colmax);
                 break;
             case kDyn:
                 for (int s = I.b; s < min(I.b + dyn_slices, E.S); ++s) {
@@ -157,31 +151,58 @@ __global__ void __launch_bounds__(kThreads)
                 }
                 break;
             default:
-                for (int t = I.a; t < min(I.a + comp_t, E.T); ++t)
-                    comp::composite_block<true, false, false, true>(E.static_sq, nullptr, E.dyn, E.nx, E.ny, E.nz,
-                                                                    E.zlo, E.S, t, (long long)I.b, E.comp_sq, nullptr,
-                                                                    E.vox, smem, E.rep ? E.rep + t * E.S : nullptr);
                 break;
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0 && I.type != kComp) {
+        if (threadIdx.x == 0) {
             __threadfence();
             add_release(ce + I.type, 1);
         }
     }
 }
 
+// The composite items, after every static and capsule item has finished (the
+// previous launch on the stream): item (env, t, column block) computes time
+// steps t .. t + comp_t - 1 of 128 consecutive columns.  Nothing to wait for;
+// if a dependency wait of the first launch expired, the items are skipped.
+__global__ void __launch_bounds__(kThreads)
+    k_batched_comp(const BatchEnv *__restrict__ envs, const BatchItem *__restrict__ items, int n_items,
+                   const int *__restrict__ err, int *head, int comp_t)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_item;
+    if (*err != 0)
+        return;  // uniform: every thread reads the same word
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(head, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items)
+            break;
+        const BatchItem I = items[it];
+        const BatchEnv &E = envs[I.env];
+        for (int t = I.a; t < min(I.a + comp_t, E.T); ++t) {
+            comp::composite_block_short<true, false, false>(E.static_sq, nullptr, E.colmax, E.dyn,
+                                                            E.rep ? E.rep + t * E.S : nullptr, E.nx, E.ny, E.nz,
+                                                            E.zlo, E.S, t, (long long)I.b, E.comp_sq, nullptr,
+                                                            E.vox, E.vec != 0, smem);
+            __syncthreads();
+        }
+    }
+}
+
+// shared memory words of the first launch's stages, and of a composite item
 size_t smem_words_env(const CompositePlan &p, const pcdf_grid &g, int H)
 {
-    auto col = [](int n) { return (size_t)env::kCols * (n + (n + 31) / 32); };
+    auto col = [](int n) { return (size_t)lean::kCols * (n + (n + 31) / 32); };
     size_t w = std::max(col(g.ny), col(g.nz));
-    if (p.S > 0) {
+    if (p.S > 0)
         w = std::max(w, (size_t)g.ny * (H + 1) + (size_t)p.cap * kThreads);
-        w = std::max(w, (size_t)kThreads * (p.S + 2 + (p.S + 31) / 32));
-    }
     return w;
 }
+size_t smem_words_comp(const CompositePlan &p) { return (size_t)kThreads * (p.S + 2 + (p.S + 31) / 32); }
 
 }  // namespace
 }  // namespace pcdf
@@ -192,11 +213,12 @@ struct pcdf_batch {
     std::vector<pcdf_env> user;
     std::vector<pcdf::host::CompositePlan> plans;
     std::vector<pcdf::BatchEnv> desc;   // device pointers filled at upload
-    std::vector<size_t> off_g16, off_mid, off_static, off_dyn, off_caps, off_rep;
-    std::vector<pcdf::BatchItem> items;
+    std::vector<size_t> off_bits, off_carry, off_mid, off_static, off_colmax, off_dyn, off_caps, off_rep;
+    std::vector<pcdf::BatchItem> items;  // the first launch's items, then the composite items
+    int n_first = 0;                     // items of the first launch
     size_t off_desc = 0, off_items = 0, off_state = 0, bytes = 0;
-    size_t smem = 0;
-    int blocks = 0;
+    size_t smem = 0, smem_comp = 0;
+    int blocks = 0, blocks_comp = 0;
 };
 
 namespace {
@@ -224,13 +246,15 @@ int build_plan(const pcdf_env *envs, int n_env, const pcdf_batch_tiles *tiles, p
     B.user.assign(envs, envs + n_env);
     B.plans.resize(n_env);
     B.desc.resize(n_env);
-    B.off_g16.resize(n_env);
+    B.off_bits.resize(n_env);
+    B.off_carry.resize(n_env);
     B.off_mid.resize(n_env);
     B.off_static.resize(n_env);
+    B.off_colmax.resize(n_env);
     B.off_dyn.resize(n_env);
     B.off_caps.resize(n_env);
     B.off_rep.resize(n_env);
-    size_t off = 0, words = 0;
+    size_t off = 0, words = 0, words_comp = 0;
     std::vector<BatchItem> rows, dyn, ys, zs, comps;
     for (int e = 0; e < n_env; ++e) {
         const pcdf_env &U = envs[e];
@@ -244,12 +268,17 @@ int build_plan(const pcdf_env *envs, int n_env, const pcdf_batch_tiles *tiles, p
                         p.cap);
         const pcdf_grid &g = U.grid;
         const long long V = (long long)g.nx * g.ny * g.nz;
-        B.off_g16[e] = off;
-        off += align_up((size_t)V * 2);
+        const size_t nw = (size_t)g.nz * g.ny * ((g.nx + 31) / 32);
+        B.off_bits[e] = off;
+        off += align_up(nw * sizeof(uint32_t));
+        B.off_carry[e] = off;
+        off += align_up(nw * sizeof(uint2));
         B.off_mid[e] = off;
         off += align_up((size_t)V * 4);
         B.off_static[e] = off;
         off += align_up((size_t)V * 4);
+        B.off_colmax[e] = off;
+        off += align_up((size_t)g.nx * g.ny * 4);
         B.off_dyn[e] = off;
         off += align_up((size_t)p.slab * 4);
         B.off_caps[e] = off;
@@ -257,6 +286,7 @@ int build_plan(const pcdf_env *envs, int n_env, const pcdf_batch_tiles *tiles, p
         B.off_rep[e] = off;
         off += align_up(p.rep.size());
         words = std::max(words, smem_words_env(p, g, U.H));
+        words_comp = std::max(words_comp, smem_words_comp(p));
 
         BatchEnv &D = B.desc[e];
         std::memset(&D, 0, sizeof(D));
@@ -268,7 +298,7 @@ int build_plan(const pcdf_env *envs, int n_env, const pcdf_batch_tiles *tiles, p
         D.zlo = p.zlo;
         D.S = p.S;
         D.cap = p.cap;
-        D.segs = row_segments(g.nx);
+        D.W = (g.nx + 31) / 32;
         D.vox = g.vox;
         const int nrows = g.ny * g.nz;
         for (int r = 0; r < nrows; r += B.tiles.row_rows)
@@ -278,13 +308,14 @@ int build_plan(const pcdf_env *envs, int n_env, const pcdf_batch_tiles *tiles, p
             for (int s = 0; s < p.S; s += B.tiles.dyn_slices)
                 dyn.push_back({kDyn, e, t, s});
         D.need[kDyn] = U.T * ((p.S + B.tiles.dyn_slices - 1) / B.tiles.dyn_slices);
-        const long long ycols = (long long)g.nx * g.nz, zcols = (long long)g.nx * g.ny;
-        for (long long c = 0; c < ycols; c += env::kCols)
-            ys.push_back({kY, e, (int)c, 0});
-        D.need[kY] = (int)((ycols + env::kCols - 1) / env::kCols);
-        for (long long c = 0; c < zcols; c += env::kCols)
+        const long long zcols = (long long)g.nx * g.ny;
+        for (int z = 0; z < g.nz; ++z)
+            for (int w = 0; w < D.W; ++w)
+                ys.push_back({kY, e, z, w});
+        D.need[kY] = g.nz * D.W;
+        for (long long c = 0; c < zcols; c += lean::kCols)
             zs.push_back({kZ, e, (int)c, 0});
-        D.need[kZ] = (int)((zcols + env::kCols - 1) / env::kCols);
+        D.need[kZ] = (int)((zcols + lean::kCols - 1) / lean::kCols);
         // composite items t-fastest within a column block: the blocks of one
         // column range run together and share the static column in L2
         for (long long c = 0; c < zcols; c += kThreads)
@@ -292,28 +323,37 @@ int build_plan(const pcdf_env *envs, int n_env, const pcdf_batch_tiles *tiles, p
                 comps.push_back({kComp, e, t, (int)c});
     }
     B.items.clear();
-    for (auto *v : {&rows, &dyn, &ys, &zs, &comps})
+    for (auto *v : {&rows, &dyn, &ys, &zs})
         B.items.insert(B.items.end(), v->begin(), v->end());
+    B.n_first = (int)B.items.size();
+    B.items.insert(B.items.end(), comps.begin(), comps.end());
     B.off_desc = off;
     off += align_up(sizeof(BatchEnv) * n_env);
     B.off_items = off;
     off += align_up(sizeof(BatchItem) * B.items.size());
     B.off_state = off;
-    off += align_up(sizeof(int) * (2 + 4 * (size_t)n_env));
+    off += align_up(sizeof(int) * (3 + 4 * (size_t)n_env));
     B.bytes = off;
     B.smem = words * 4;
-    if (B.smem > 227 * 1024)
-        return fail(PCDF_EINVAL, "an environment needs %zu bytes of shared memory (limit 227 KB)", B.smem);
+    B.smem_comp = std::max<size_t>(words_comp * 4, 16);
+    if (B.smem > 227 * 1024 || B.smem_comp > 227 * 1024)
+        return fail(PCDF_EINVAL, "an environment needs %zu bytes of shared memory (limit 227 KB)",
+                    std::max(B.smem, B.smem_comp));
     cudaError_t e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batched_comp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem_comp);
     if (e != cudaSuccess)
         return cuda_fail(e, "batched kernel attributes");
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0, per_sm = 0, per_sm_comp = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, kThreads, B.smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_comp, k_batched_comp, kThreads, B.smem_comp);
     if (e != cudaSuccess)
         return cuda_fail(e, "batched kernel occupancy");
     B.blocks = std::max(1, sms * std::max(per_sm, 1));
+    B.blocks_comp = std::max(1, sms * std::max(per_sm_comp, 1));
     return PCDF_OK;
 }
 
@@ -355,8 +395,9 @@ int pcdf_batch_tiles_used(const pcdf_batch *b, pcdf_batch_tiles *tiles)
 
 int pcdf_batch_block_stage(pcdf_batch *b, int32_t env, int32_t stage)
 {
-    if (!b || env < 0 || env >= b->n_env || stage < 0 || stage > 3)
-        return fail(PCDF_EINVAL, "batch, environment %d or stage %d out of range", env, stage);
+    if (!b || env < 0 || env >= b->n_env || stage < 0 || stage > 2)
+        return fail(PCDF_EINVAL, "batch, environment %d or stage %d out of range (stages 0 to 2 have waiters)", env,
+                    stage);
     b->desc[env].need[stage] = 1 << 30;  // above any item count: the waits on it can only expire
     return PCDF_OK;
 }
@@ -376,9 +417,13 @@ int pcdf_batch_upload(pcdf_batch *b, void *workspace, size_t workspace_bytes, vo
         BatchEnv &D = b->desc[e];
         D.occ = b->user[e].occ;
         D.comp_sq = b->user[e].comp_sq;
-        D.g16 = (int16_t *)(ws + b->off_g16[e]);
+        D.bits = (uint32_t *)(ws + b->off_bits[e]);
+        D.carry = (uint2 *)(ws + b->off_carry[e]);
         D.mid = (int32_t *)(ws + b->off_mid[e]);
         D.static_sq = (int32_t *)(ws + b->off_static[e]);
+        D.colmax = (int32_t *)(ws + b->off_colmax[e]);
+        D.vec = ((long long)D.nx * D.ny) % 4 == 0 && ((uintptr_t)D.comp_sq & 15u) == 0 &&
+                ((uintptr_t)D.static_sq & 15u) == 0;
         D.dyn = (int32_t *)(ws + b->off_dyn[e]);
         D.caps = (const CapInfo *)(ws + b->off_caps[e]);
         const std::vector<uint8_t> &rp = b->plans[e].rep;
@@ -414,14 +459,21 @@ int pcdf_batch_run(const pcdf_batch *b, void *workspace, void *stream)
     char *ws = (char *)workspace;
     cudaStream_t st = (cudaStream_t)stream;
     int *state = (int *)(ws + b->off_state);
-    cudaError_t err = cudaMemsetAsync(state, 0, sizeof(int) * (2 + 4 * (size_t)b->n_env), st);
+    cudaError_t err = cudaMemsetAsync(state, 0, sizeof(int) * (3 + 4 * (size_t)b->n_env), st);
     if (err != cudaSuccess)
         return cuda_fail(err, "batch counter reset");
-    k_batched<<<b->blocks, kThreads, b->smem, st>>>((const BatchEnv *)(ws + b->off_desc),
-                                                   (const BatchItem *)(ws + b->off_items), (int)b->items.size(),
-                                                   state, b->tiles.row_rows, b->tiles.dyn_slices, b->tiles.comp_t);
+    const BatchEnv *desc = (const BatchEnv *)(ws + b->off_desc);
+    const BatchItem *items = (const BatchItem *)(ws + b->off_items);
+    k_batched<<<b->blocks, kThreads, b->smem, st>>>(desc, items, b->n_first, state, b->tiles.row_rows,
+                                                   b->tiles.dyn_slices, b->tiles.comp_t);
     err = cudaGetLastError();
-    return err == cudaSuccess ? PCDF_OK : cuda_fail(err, "batched launch");
+    if (err != cudaSuccess)
+        return cuda_fail(err, "batched launch");
+    const int n_comp = (int)b->items.size() - b->n_first;
+    k_batched_comp<<<b->blocks_comp, kThreads, b->smem_comp, st>>>(desc, items + b->n_first, n_comp, state + 1,
+                                                                   state + 2 + 4 * b->n_env, b->tiles.comp_t);
+    err = cudaGetLastError();
+    return err == cudaSuccess ? PCDF_OK : cuda_fail(err, "batched composite launch");
 }
 
 int pcdf_batch_error(const pcdf_batch *b, const void *workspace, void *stream, int32_t *code)

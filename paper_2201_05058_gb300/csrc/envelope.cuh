@@ -77,13 +77,17 @@ struct Merged {
 static_assert(kBands == 4, "Merged assumes four bands");
 
 // The CTA (kCols * kBands threads) computes columns [col0, col0 + kCols);
-// smem holds kCols * (n + ceil(n / 32)) words.
+// smem holds kCols * (n + ceil(n / 32)) words.  colmax (non-NULL: every
+// column's largest output value, indexed by column) is written at the end.
 template <typename TIn, bool kSdf, bool kCoherent>
 __device__ __forceinline__ void envelope_tile(const TIn *__restrict__ in, int32_t *__restrict__ out,
                                               float *__restrict__ sdf, float vox, int n, int nx, long long ncols,
-                                              long long outer_stride, int stride, long long col0, uint32_t *smem)
+                                              long long outer_stride, int stride, long long col0, uint32_t *smem,
+                                              int32_t *__restrict__ colmax = nullptr)
 {
     __shared__ int seg[2][kBands][kCols];  // per column and band: first surviving entry, number of entries
+    __shared__ int32_t s_max[kBands][kCols];
+    int32_t mx = INT32_MIN;  // largest value this thread writes
     const int c = threadIdx.x % kCols, band = threadIdx.x / kCols;
     const long long cl = col0 + c;
     const bool live = cl < ncols;
@@ -270,10 +274,23 @@ __device__ __forceinline__ void envelope_tile(const TIn *__restrict__ in, int32_
                     }
                     r = set == 0 ? r : -r;
                     o[e * stride] = r;
+                    mx = max(mx, r);
                     if (kSdf)
                         f[e * stride] = sq_to_sdf_fast(r, vox);
                 }
             }
+        }
+        __syncthreads();
+    }
+    if (colmax) {  // every thread reaches here (no early exits above)
+        s_max[band][c] = mx;
+        __syncthreads();
+        if (band == 0 && live) {
+            int32_t m = s_max[0][c];
+#pragma unroll
+            for (int k = 1; k < kBands; ++k)
+                m = max(m, s_max[k][c]);
+            colmax[cl] = m;
         }
         __syncthreads();
     }

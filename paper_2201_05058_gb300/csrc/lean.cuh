@@ -322,13 +322,14 @@ PCDF_HD void merge_seam(uint32_t *tile, Seg<kB> &S, int c, int b, int lo, int hi
 PCDF_HD int tree_seam(int kB, int r, int t) { const int b = (2 * t + 1) << r; return b < kB ? b : 0; }
 
 // 3. Evaluate the band (thread of column c, band b); out(e, value) for every
-// element of the band.  mk: the column-major occupancy words of the tile.
+// element of the band, in increasing e.  mk: the column-major occupancy
+// words of the tile.  Returns the functor (with whatever it accumulated).
 template <int kB, class Out>
-PCDF_HD void eval_band(uint32_t *tile, const uint32_t *mk, Seg<kB> &S, int n, int L, int c, int b, Out out)
+PCDF_HD Out eval_band(uint32_t *tile, const uint32_t *mk, Seg<kB> &S, int n, int L, int c, int b, Out out)
 {
     const int e0 = b * L, e1 = min(e0 + L, n);
     if (e0 >= e1)
-        return;
+        return out;
     Chain<kB> ch{tile + c, &S, c};
     using Pos = typename Chain<kB>::Pos;
     const uint32_t *m = mk + c;
@@ -453,6 +454,7 @@ PCDF_HD void eval_band(uint32_t *tile, const uint32_t *mk, Seg<kB> &S, int n, in
         }
         e = se + 1;
     }
+    return out;
 }
 
 }  // namespace lean

@@ -68,13 +68,17 @@ def test_batched_matches_oracle_and_single_calls(batch_case):
 
 
 def test_an_expired_wait_reports_timeout_and_the_context_stays_usable(batch_case):
-    """The failure path without a GPU fault: environment 0's capsule stage is
-    given a target no run reaches, so its composite items wait until their
-    bound (about a second) expires and are skipped; error() reports
-    PCDF_ETIMEOUT.  A fresh batch on the same context is then exact again."""
+    """The failure path without a GPU fault: environment 0's row stage is
+    given a target no run reaches, so its y items wait until their bound
+    (about a second) expires; every later wait then gives up at once, so
+    nothing reads unfinished inputs, and error() reports PCDF_ETIMEOUT.  The
+    capsule stage, which nothing waits on, is refused.  A fresh batch on the
+    same context is then exact again."""
     envs, dev_envs, want = batch_case
     b = pcdf.Batch(dev_envs)
-    b.block_stage(0, 3)
+    with pytest.raises(RuntimeError):
+        b.block_stage(0, 3)
+    b.block_stage(0, 0)
     b.run()
     assert b.error() == -4  # PCDF_ETIMEOUT
     b.close()
