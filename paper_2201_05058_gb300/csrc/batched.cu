@@ -141,15 +141,17 @@ __global__ void __launch_bounds__(kThreads, 5)
                 full::edt_z_block<kBands, false, true>(E.mid, E.static_sq, nullptr, 0.f, E.nz,
                                                        (long long)E.nx * E.ny, (long long)I.a, smem, E.colmax);
                 break;
-            case kDyn:
-                for (int s = I.b; s < min(I.b + dyn_slices, E.S); ++s) {
+            case kDyn: {  // time I.a, slices from I.b / 16, column block I.b % 16
+                const int s0 = I.b >> 4, x0 = (I.b & 15) * kThreads;
+                for (int s = s0; s < min(s0 + dyn_slices, E.S); ++s) {
                     if (E.rep && E.rep[I.a * E.S + s] != s)
                         continue;  // read from the earlier slice of equal cross-sections
                     comp::dyn_xy_slice(E.caps + (long long)I.a * E.H, E.H, E.nx, E.ny, E.zlo, E.S, I.a, s, E.cap,
-                                       E.dyn, reinterpret_cast<int32_t *>(smem));
+                                       E.dyn, reinterpret_cast<int32_t *>(smem), x0, min(x0 + kThreads, E.nx));
                     __syncthreads();
                 }
                 break;
+            }
             default:
                 break;
             }
@@ -304,10 +306,12 @@ int build_plan(const pcdf_env *envs, int n_env, const pcdf_batch_tiles *tiles, p
         for (int r = 0; r < nrows; r += B.tiles.row_rows)
             rows.push_back({kRow, e, r, 0});
         D.need[kRow] = (nrows + B.tiles.row_rows - 1) / B.tiles.row_rows;
+        const int nxb = (g.nx + kThreads - 1) / kThreads;  // column blocks of a slice (<= 4)
         for (int t = 0; t < U.T; ++t)
             for (int s = 0; s < p.S; s += B.tiles.dyn_slices)
-                dyn.push_back({kDyn, e, t, s});
-        D.need[kDyn] = U.T * ((p.S + B.tiles.dyn_slices - 1) / B.tiles.dyn_slices);
+                for (int xb = 0; xb < nxb; ++xb)
+                    dyn.push_back({kDyn, e, t, s * 16 + xb});
+        D.need[kDyn] = U.T * ((p.S + B.tiles.dyn_slices - 1) / B.tiles.dyn_slices) * nxb;
         const long long zcols = (long long)g.nx * g.ny;
         for (int z = 0; z < g.nz; ++z)
             for (int w = 0; w < D.W; ++w)

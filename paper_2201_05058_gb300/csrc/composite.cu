@@ -7,16 +7,22 @@
 namespace pcdf {
 namespace {
 
+// Columns per CTA of k_dyn_xy: a slice's columns are shared by ceil(nx / 128)
+// CTAs, one column per thread.
+constexpr int kDynCols = 128;
+
 __global__ void __launch_bounds__(128)
     k_dyn_xy(const __grid_constant__ CapBatch caps, const __grid_constant__ SlabMap map, int H, int nx, int ny,
              int zlo, int S, int t0, int cap, int32_t *__restrict__ dyn_mid)
 {
+    const int nxb = (nx + kDynCols - 1) / kDynCols;
+    const int s = (int)blockIdx.x / nxb, xb = (int)blockIdx.x % nxb;
     // a slice whose cross-sections equal an earlier slice's is read from that one
-    if (map.on && map.rep[(t0 + (int)blockIdx.y) * S + (int)blockIdx.x] != (int)blockIdx.x)
+    if (map.on && map.rep[(t0 + (int)blockIdx.y) * S + s] != s)
         return;
     extern __shared__ __align__(16) int32_t sm[];
-    comp::dyn_xy_slice(caps.caps + blockIdx.y * H, H, nx, ny, zlo, S, t0 + (int)blockIdx.y, (int)blockIdx.x, cap,
-                       dyn_mid, sm);
+    comp::dyn_xy_slice(caps.caps + blockIdx.y * H, H, nx, ny, zlo, S, t0 + (int)blockIdx.y, s, cap, dyn_mid, sm,
+                       xb * kDynCols, min((xb + 1) * kDynCols, nx));
 }
 
 // CTAs are ordered t-fastest, so the T CTAs of one column block run together
@@ -75,8 +81,9 @@ cudaError_t launch_dyn_xy(const CapBatch *caps, const SlabMap *map, int H, int n
     cudaError_t e = cudaFuncSetAttribute(k_dyn_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_dyn_xy<<<dim3((unsigned)S, (unsigned)n_t), kDynThreads, smem, stream>>>(*caps, *map, H, nx, ny, zlo, S, t0,
-                                                                               cap, dyn_mid);
+    const unsigned nxb = (unsigned)((nx + kDynCols - 1) / kDynCols);
+    k_dyn_xy<<<dim3((unsigned)S * nxb, (unsigned)n_t), kDynThreads, smem, stream>>>(*caps, *map, H, nx, ny, zlo, S,
+                                                                                     t0, cap, dyn_mid);
     return cudaGetLastError();
 }
 

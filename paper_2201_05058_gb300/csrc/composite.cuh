@@ -87,10 +87,13 @@ __device__ __forceinline__ int row_g_free(const int32_t *r, int x, int nx)
     return 0;
 }
 
-// The CTA computes slab slice s of time t.  caps_t: the H capsules of t;
-// sm: ny * (H + 1) + cap * blockDim.x words.
+// The CTA computes columns [x0, x1) of slab slice s of time t (the capsules'
+// runs of every row of the slice are found first; several CTAs can share a
+// slice by its columns).  caps_t: the H capsules of t; sm: ny * (H + 1) +
+// cap * blockDim.x words.
 __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int nx, int ny, int zlo, int S, int t,
-                                             int s, int cap, int32_t *__restrict__ dyn_mid, int32_t *sm)
+                                             int s, int cap, int32_t *__restrict__ dyn_mid, int32_t *sm, int x0,
+                                             int x1)
 {
     __shared__ int s_ylo, s_yhi;
     __shared__ uint32_t s_rowbits[(PCDF_MAX_DIM + 31) / 32];  // rows holding a run
@@ -157,7 +160,7 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
     const int ylo = s_ylo, yhi = s_yhi;
     const long long V2 = (long long)nx * ny;
 
-    for (int x = tid; x < nx; x += nthr) {
+    for (int x = x0 + tid; x < x1; x += nthr) {
         int32_t *oc = dyn_mid + ((long long)t * S + s) * V2 + x;  // element y at oc[y * nx]
         if (yhi < 0) {
             for (int y = 0; y < ny; ++y)
