@@ -89,6 +89,19 @@ typedef struct pcdf_grid {
 /* Message describing the calling thread's most recent failed call ("" if none). */
 const char *pcdf_last_error(void);
 
+/* pcdf_bounds_check  the debug build's index checks (no counterpart in the
+ * paper; the stand-in for a memory checker).  The library compiled with
+ * PCDF_CHECK_BOUNDS (libpcdf_checked.so) tests every global and shared index
+ * of the static EDT, the capsule field, the composite z pass, the column
+ * maxima and the cost query and its backward before the access; a failed
+ * test skips the access (nothing traps) and records the first failure and a
+ * count on the device.  This call waits for the device, then returns in
+ * *first (nullable) the first failing check as (16-bit hash of its source
+ * file name) << 16 | line, 0 if none, and in *count (nullable) the number of
+ * failed checks; reset != 0 clears both.  In the normal build it returns
+ * PCDF_EINVAL (and zeros). */
+int pcdf_bounds_check(uint32_t *first, uint32_t *count, int32_t reset);
+
 /* ABI version (major * 100 + minor). */
 int pcdf_version(void);
 

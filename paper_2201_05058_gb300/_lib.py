@@ -13,6 +13,8 @@ from . import build as _build
 
 _lock = threading.Lock()
 _lib = None
+_lib_checked = None
+_use_checked = False
 
 
 class PcdfGrid(ctypes.Structure):
@@ -30,7 +32,7 @@ class PcdfBatchTiles(ctypes.Structure):
 
 
 EXPORTS = (
-    "pcdf_last_error", "pcdf_version",
+    "pcdf_last_error", "pcdf_version", "pcdf_bounds_check",
     "pcdf_static_workspace_bytes", "pcdf_build_static_sdf", "pcdf_build_static_sdf_noalloc",
     "pcdf_composite_workspace_bytes", "pcdf_build_predicted_composite",
     "pcdf_composite_prepare", "pcdf_composite_finish", "pcdf_composite_finish_range", "pcdf_composite_slab",
@@ -56,6 +58,7 @@ def _declare(lib):
     lib.pcdf_last_error.argtypes = []
     lib.pcdf_version.restype = ctypes.c_int
     sig = {
+        "pcdf_bounds_check": [P, P, I32],
         "pcdf_static_workspace_bytes": [G, SZP],
         "pcdf_build_static_sdf": [G, P, P, P, P, SZ, P],
         "pcdf_build_static_sdf_noalloc": [G, P, P, P, P],
@@ -124,19 +127,32 @@ def lib_path() -> str:
     return _build.LIB
 
 
-def load(build_if_missing: bool = True):
-    """Load libpcdf.so (building it first if allowed and needed)."""
-    global _lib
+def use_checked(flag: bool):
+    """Route every later load() (so every call of the package) to the
+    bounds-checked debug library, libpcdf_checked.so, or back."""
+    global _use_checked
+    _use_checked = bool(flag)
+
+
+def load(build_if_missing: bool = True, checked: bool = None):
+    """Load libpcdf.so, or the bounds-checked libpcdf_checked.so (checked, or
+    use_checked(True)), building it first if allowed and needed."""
+    global _lib, _lib_checked
+    checked = _use_checked if checked is None else checked
+    path = _build.LIB_CHECKED if checked else _build.LIB
     with _lock:
-        if _lib is None:
-            if build_if_missing and not _build.up_to_date():
-                _build.build_library()
-            if not os.path.exists(_build.LIB):
-                raise RuntimeError(f"libpcdf is not built ({_build.LIB} missing); run build_library()")
-            lib = ctypes.CDLL(_build.LIB)
+        if (_lib_checked if checked else _lib) is None:
+            if build_if_missing and not _build.up_to_date(checked):
+                _build.build_library(checked=checked)
+            if not os.path.exists(path):
+                raise RuntimeError(f"libpcdf is not built ({path} missing); run build_library()")
+            lib = ctypes.CDLL(path)
             _declare(lib)
-            _lib = lib
-    return _lib
+            if checked:
+                _lib_checked = lib
+            else:
+                _lib = lib
+    return _lib_checked if checked else _lib
 
 
 def check(rc: int, what: str):

@@ -2,8 +2,11 @@
 
 ``build_library()`` runs nvcc for sm_103a (one ``-gencode``, ``-lineinfo``,
 IEEE division and square root) on every ``csrc/*.cu`` in parallel and links
-``_build/libpcdf.so`` next to this file.  It rebuilds only when a source or
-the public header is newer than the library.
+``_build/libpcdf.so`` next to this file.  ``build_library(checked=True)``
+builds the debug variant ``_build/checked/libpcdf_checked.so`` with
+``PCDF_CHECK_BOUNDS`` (index checks on the hot path, one error word shared by
+every file through relocatable device code).  Each rebuilds only when a
+source or the public header is newer than its library.
 """
 from __future__ import annotations
 
@@ -19,6 +22,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpcdf.so")
+BUILD_CHECKED = os.path.join(BUILD, "checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libpcdf_checked.so")
+CHECK_FLAGS = ["-DPCDF_CHECK_BOUNDS", "-rdc=true"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -42,23 +48,27 @@ def _deps():
         os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build_library(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    out_dir = BUILD_CHECKED if checked else BUILD
+    extra = CHECK_FLAGS if checked else []
+    if not force and up_to_date(checked):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -68,14 +78,15 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [cc, *ARCH, "-shared", *(["-rdc=true"] if checked else []), "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build_library(force=True, verbose=True))
+    print(build_library(force=True, verbose=True, checked=True))

@@ -13,9 +13,43 @@
 
 using namespace pcdf::host;
 
+#ifdef PCDF_CHECK_BOUNDS
+namespace pcdf {
+__device__ unsigned int g_bounds_error[2];  // see PCDF_IN in pcdf_internal.cuh
+}
+#endif
+
 extern "C" {
 
 const char *pcdf_last_error(void) { return last_error(); }
+
+int pcdf_bounds_check(uint32_t *first, uint32_t *count, int32_t reset)
+{
+#ifdef PCDF_CHECK_BOUNDS
+    unsigned int v[2] = {0u, 0u};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpyFromSymbol(v, pcdf::g_bounds_error, sizeof(v));
+    if (e == cudaSuccess && reset) {
+        const unsigned int zero[2] = {0u, 0u};
+        e = cudaMemcpyToSymbol(pcdf::g_bounds_error, zero, sizeof(zero));
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "bounds-check word");
+    if (first)
+        *first = v[0];
+    if (count)
+        *count = v[1];
+    return PCDF_OK;
+#else
+    (void)reset;
+    if (first)
+        *first = 0;
+    if (count)
+        *count = 0;
+    return fail(PCDF_EINVAL, "not a bounds-checked build (compiled without PCDF_CHECK_BOUNDS)");
+#endif
+}
 
 int pcdf_version(void) { return 100; }
 

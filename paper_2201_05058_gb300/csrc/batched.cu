@@ -97,7 +97,7 @@ __device__ __forceinline__ void run_rows(const BatchEnv &E, int r0, int r1)
 {
     const int lane = threadIdx.x & 31;
     for (int r = r0 + (threadIdx.x >> 5); r < r1; r += kThreads / 32)
-        full::row_bits_row<0>(E.occ, nullptr, 0, E.nx, E.ny, r, E.W, E.bits, E.carry, lane);
+        full::row_bits_row<0>(E.occ, nullptr, 0, E.nx, E.ny, r, (long long)E.ny * E.nz, E.W, E.bits, E.carry, lane);
 }
 
 // 5 CTAs per SM: the envelope stages' shared memory (up to 42 KB at 320-voxel
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 5)
                 run_rows(E, I.a, min(I.a + row_rows, E.ny * E.nz));
                 break;
             case kY:  // slice I.a, row word I.b
-                full::edt_xy_block<kBands, true>(E.bits, E.carry, E.nx, E.ny, E.W, I.b, I.a, E.mid, smem);
+                full::edt_xy_block<kBands, true>(E.bits, E.carry, E.nx, E.ny, E.nz, E.W, I.b, I.a, E.mid, smem);
                 break;
             case kZ:
                 full::edt_z_block<kBands, false, true>(E.mid, E.static_sq, nullptr, 0.f, E.nz,

@@ -162,6 +162,8 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
 
     for (int x = x0 + tid; x < x1; x += nthr) {
         int32_t *oc = dyn_mid + ((long long)t * S + s) * V2 + x;  // element y at oc[y * nx]
+        if (!PCDF_IN(x, nx) || !PCDF_IN(s, S))
+            continue;
         if (yhi < 0) {
             for (int y = 0; y < ny; ++y)
                 oc[(long long)y * nx] = kInf32;
@@ -183,7 +185,7 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
         // occupied voxel is the first free row out of its run.
         if (lo_ >= 0) {
             const int y0 = max(fo - 1, 0), y1 = min(lo_ + 1, ny - 1);
-            EnvBuilder B(stk, nthr);
+            EnvBuilder B(stk, nthr, cap);
             bool prev_occ = false;  // y0 - 1 lies before the first occupied row
             bool cur_occ = y0 >= ylo && y0 <= yhi && row_inside(rows + y0 * rw, x);
             for (int y = y0; y <= y1; ++y) {
@@ -203,13 +205,14 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
                 if (!row_inside(rows + y * rw, x))
                     continue;
                 const int f = F.eval(y);
-                oc[(long long)y * nx] = f < 0 ? -kInf32 : -f;
+                if (PCDF_IN(y, ny))
+                    oc[(long long)y * nx] = f < 0 ? -kInf32 : -f;
             }
         }
 
         // distances to occupied voxels at the free voxels (set O): sites are
         // the rows holding a run (g = 0 where x is inside one)
-        EnvBuilder B(stk, nthr);
+        EnvBuilder B(stk, nthr, cap);
         for (int w = ylo >> 5; w <= yhi >> 5; ++w)
             for (uint32_t b = s_rowbits[w]; b; b &= b - 1) {
                 const int y = (w << 5) + __ffs(b) - 1;
@@ -221,7 +224,7 @@ __device__ __forceinline__ void dyn_xy_slice(const CapInfo *caps_t, int H, int n
         const int ya = min(fo, ny), yb = lo_ >= 0 ? lo_ + 1 : ny;
         O.fill(0, ya, oc, nx);
         for (int y = ya; y < yb; ++y)
-            if (!row_inside(rows + y * rw, x))
+            if (!row_inside(rows + y * rw, x) && PCDF_IN(y, ny))
                 oc[(long long)y * nx] = O.eval(y);
         O.fill(yb, ny, oc, nx);
     }
@@ -281,7 +284,7 @@ __device__ __forceinline__ T ldx(const T *p)
 template <bool kCheck, bool kEval, bool kCoherent, class O_t>
 __device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, bool useO, const uint32_t *mk, bool useMk,
                                            int zlo, int nthr, const int32_t *scol, const float *sfcol, int V2,
-                                           const O_t &out)
+                                           const O_t &out, int nz_chk = 1 << 30)
 {
     constexpr bool kStaticSdf = O_t::kHaveStatic;
     constexpr int kC = PCDF_EMIT_CHUNK;
@@ -291,9 +294,10 @@ __device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, bool us
         float sf[kC];
 #pragma unroll
         for (int i = 0; i < kC; ++i) {
-            sv[i] = ldx<kCoherent>(scol + (z + i) * V2);
+            const bool ok = PCDF_IN(z + i, nz_chk);
+            sv[i] = ok ? ldx<kCoherent>(scol + (z + i) * V2) : kInf32;
             if (kStaticSdf)
-                sf[i] = ldx<kCoherent>(sfcol + (z + i) * V2);
+                sf[i] = ok ? ldx<kCoherent>(sfcol + (z + i) * V2) : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < kC; ++i) {
@@ -304,7 +308,8 @@ __device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, bool us
                     continue;
             }
             const int32_t d = (kEval && useO) ? O.eval(zz) : kInf32;
-            out.put(zz * V2, sv[i], kStaticSdf ? sf[i] : 0.f, d);
+            if (PCDF_IN(zz, nz_chk))
+                out.put(zz * V2, sv[i], kStaticSdf ? sf[i] : 0.f, d);
         }
     }
     for (; z < z1; ++z) {
@@ -314,7 +319,8 @@ __device__ __forceinline__ void emit_range(int z0, int z1, EnvCursor &O, bool us
                 continue;
         }
         const int32_t d = (kEval && useO) ? O.eval(z) : kInf32;
-        out.put(z * V2, ldx<kCoherent>(scol + z * V2), kStaticSdf ? ldx<kCoherent>(sfcol + z * V2) : 0.f, d);
+        if (PCDF_IN(z, nz_chk))
+            out.put(z * V2, ldx<kCoherent>(scol + z * V2), kStaticSdf ? ldx<kCoherent>(sfcol + z * V2) : 0.f, d);
     }
 }
 
@@ -366,11 +372,12 @@ __device__ __forceinline__ void colmax_block(const int32_t *__restrict__ sq, lon
         const int32_t *col = sq + c;
 #pragma unroll 8
         for (int z = z0; z < z1; ++z)
-            m = max(m, __ldg(col + (long long)z * V2));
+            if (PCDF_IN(z, nz))
+                m = max(m, __ldg(col + (long long)z * V2));
     }
     part[w][lane] = m;
     __syncthreads();
-    if (w == 0 && c < V2)
+    if (w == 0 && c < V2 && PCDF_IN(c, V2))
         colmax[c] = max(max(part[0][lane], part[1][lane]), max(part[2][lane], part[3][lane]));
 }
 
@@ -393,6 +400,8 @@ __device__ __forceinline__ void copy_static_block(const int32_t *__restrict__ st
 #pragma unroll 4
     for (int z = zfirst; z < nz; z += zstep) {
         const long long o = (long long)z * V2 + base;
+        if (!PCDF_IN(o + 3, V2 * nz))
+            continue;
         const int4 sv = ldx<kCoherent>(reinterpret_cast<const int4 *>(static_sq + o));
         if (kSq)
             __stcs(reinterpret_cast<int4 *>(osq + o), sv);
@@ -448,7 +457,7 @@ __device__ __forceinline__ int build_sets(uint32_t *tile, uint32_t *mk, bool occ
         // set F over [zo0 - 1, zo1 + 1]; free voxels are sites only next to an
         // occupied one.  Site z sits in slot z - zlo + 1, read before written.
         const int zr0 = max(zo0 - 1, 0), zr1 = min(zo1 + 1, nz - 1);
-        EnvBuilder B(tile + (zr0 - zlo + 1) * nthr, nthr);
+        EnvBuilder B(tile + (zr0 - zlo + 1) * nthr, nthr, S + 2 - (zr0 - zlo + 1));
         for (int z = zr0; z <= zr1; ++z) {
             int g;
             if (occupied(z)) {
@@ -469,17 +478,20 @@ __device__ __forceinline__ int build_sets(uint32_t *tile, uint32_t *mk, bool occ
                 continue;
             const int f = F.eval(z);
             const int o = z * V2i;
-            out.put(o, ldx<kCoherent>(scol + o), kStaticSdf ? ldx<kCoherent>(sfcol + o) : 0.f, f < 0 ? -kInf32 : -f);
+            if (PCDF_IN(z, nz))
+                out.put(o, ldx<kCoherent>(scol + o), kStaticSdf ? ldx<kCoherent>(sfcol + o) : 0.f,
+                        f < 0 ? -kInf32 : -f);
         }
         // restore the staged column for set O
 #pragma unroll 8
         for (int e = 0; e < S; ++e)
-            tile[(e + 1) * nthr] = (uint32_t)ldx<kCoherent>(dcol + (long long)(rep ? rep[e] : e) * V2);
+            if (PCDF_IN(rep ? rep[e] : e, S))
+                tile[(e + 1) * nthr] = (uint32_t)ldx<kCoherent>(dcol + (long long)(rep ? rep[e] : e) * V2);
     }
 
     // set O over the slab: sites are the free slab voxels with a finite
     // partial and the ends of the occupied runs (zero distance)
-    EnvBuilder B(tile + nthr, nthr);
+    EnvBuilder B(tile + nthr, nthr, S + 1);
     for (int e = 0; e < S; ++e) {
         const int32_t v = (int32_t)tile[(e + 1) * nthr];
         int g;
@@ -580,10 +592,11 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
 
     // stage the slab column with every load in flight at once
     int32_t gmin = kInf32;
-    const int32_t cmax = live ? __ldg(colmax + c) : kInf32;
+    const int32_t cmax = live && PCDF_IN(c, V2) ? __ldg(colmax + c) : kInf32;
     if (live) {
         for (int e = 0; e < S; ++e)
-            cp_async4(tile + (e + 1) * nthr, dcol + (long long)(rep ? rep[e] : e) * V2);
+            if (PCDF_IN(rep ? rep[e] : e, S))
+                cp_async4(tile + (e + 1) * nthr, dcol + (long long)(rep ? rep[e] : e) * V2);
         cp_async_wait_all();
 #pragma unroll 8
         for (int e = 0; e < S; ++e)
@@ -605,7 +618,7 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
                 kSq ? comp_sq + (long long)t * V : nullptr, kSdfOut ? comp_sdf + (long long)t * V : nullptr, vox);
         } else if (live) {
             EnvCursor none(tile, nthr, -1);
-            emit_range<false, false, false>(0, nz, none, false, mk, false, zlo, nthr, scol, sfcol, V2i, out);
+            emit_range<false, false, false>(0, nz, none, false, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
         }
         return;
     }
@@ -643,14 +656,14 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
     EnvCursor O(tile + nthr, nthr, top);
     const bool useO = top >= 0;
     const int sa = zlo, sb = zlo + S;
-    emit_range<false, false, false>(0, ww0, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out);
-    emit_range<false, true, false>(ww0, sa, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out);
+    emit_range<false, false, false>(0, ww0, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
+    emit_range<false, true, false>(ww0, sa, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
     if (any_occ)  // skip the occupied slab voxels (set F wrote them)
-        emit_range<true, true, false>(sa, sb, O, useO, mk, occ, zlo, nthr, scol, sfcol, V2i, out);
+        emit_range<true, true, false>(sa, sb, O, useO, mk, occ, zlo, nthr, scol, sfcol, V2i, out, nz);
     else
-        emit_range<false, true, false>(sa, sb, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out);
-    emit_range<false, true, false>(sb, ww1, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out);
-    emit_range<false, false, false>(ww1, nz, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out);
+        emit_range<false, true, false>(sa, sb, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
+    emit_range<false, true, false>(sb, ww1, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
+    emit_range<false, false, false>(ww1, nz, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
 }
 
 }  // namespace comp

@@ -128,8 +128,9 @@ struct EnvBuilder {
     uint32_t *stk;
     int stride, top;
     int s0, g0, s1, g1;
-    __device__ __forceinline__ EnvBuilder(uint32_t *stk_, int stride_)
-        : stk(stk_), stride(stride_), top(-1), s0(0), g0(0), s1(0), g1(0) {}
+    int lim;  // entries the stack may hold (bounds checks)
+    __device__ __forceinline__ EnvBuilder(uint32_t *stk_, int stride_, int lim_ = 1 << 30)
+        : stk(stk_), stride(stride_), top(-1), s0(0), g0(0), s1(0), g1(0), lim(lim_) {}
     __device__ __forceinline__ void push(int e, int g)
     {
         while (top >= 1 && dominated(s0, g0, s1, g1, e, g)) {
@@ -137,13 +138,14 @@ struct EnvBuilder {
             s1 = s0;
             g1 = g0;
             if (top >= 1) {
-                const uint32_t w = stk[(top - 1) * stride];
+                const uint32_t w = PCDF_IN(top - 1, lim) ? stk[(top - 1) * stride] : 0u;
                 s0 = site_of(w);
                 g0 = gval_of(w);
             }
         }
         ++top;
-        stk[top * stride] = pack_site(e, g);
+        if (PCDF_IN(top, lim))
+            stk[top * stride] = pack_site(e, g);
         s0 = s1;
         g0 = g1;
         s1 = e;

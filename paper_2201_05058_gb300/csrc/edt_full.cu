@@ -45,16 +45,16 @@ __global__ void __launch_bounds__(32 * kRowsPerCta)
     const long long row = (long long)blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
     if (row >= nrows)
         return;  // warp-uniform
-    full::row_bits_row<kMode>(occ, caps.caps, H, nx, ny, row, W, bits, carry, threadIdx.x & 31);
+    full::row_bits_row<kMode>(occ, caps.caps, H, nx, ny, row, nrows, W, bits, carry, threadIdx.x & 31);
 }
 
 template <int kB>
 __global__ void __launch_bounds__(kCols * kB)
-    k_edt_xy(const uint32_t *__restrict__ bits, const uint2 *__restrict__ carry, int nx, int ny, int W,
+    k_edt_xy(const uint32_t *__restrict__ bits, const uint2 *__restrict__ carry, int nx, int ny, int nz, int W,
              int32_t *__restrict__ mid)
 {
     extern __shared__ uint32_t smem[];
-    full::edt_xy_block<kB, false>(bits, carry, nx, ny, W, blockIdx.x, blockIdx.y, mid, smem);
+    full::edt_xy_block<kB, false>(bits, carry, nx, ny, nz, W, blockIdx.x, blockIdx.y, mid, smem);
 }
 
 template <int kB, bool kSdf>
@@ -109,7 +109,7 @@ cudaError_t launch_full_edt(int mode, const uint8_t *occ, const CapBatch *caps, 
     const size_t sxy = tile_bytes(ny);
     if ((e = set_smem(k_edt_xy<kXyBands>, sxy)) != cudaSuccess)
         return e;
-    k_edt_xy<kXyBands><<<dim3((unsigned)W, (unsigned)nz), kCols * kXyBands, sxy, st>>>(bits, carry, nx, ny, W, mid);
+    k_edt_xy<kXyBands><<<dim3((unsigned)W, (unsigned)nz), kCols * kXyBands, sxy, st>>>(bits, carry, nx, ny, nz, W, mid);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
 

@@ -44,10 +44,11 @@ __device__ __forceinline__ uint32_t pack16(int lo, int hi)
 
 // One warp: row `row` = z * ny + y.  kMode 0: occupancy, 1: occupancy OR the
 // capsules caps[0 .. H), 2: the capsules alone.  W = ceil(nx / 32) <= 16.
+// nrows: the grid's rows (for the bounds checks).
 template <int kMode>
 __device__ __forceinline__ void row_bits_row(const uint8_t *__restrict__ occ, const CapInfo *caps, int H, int nx,
-                                             int ny, long long row, int W, uint32_t *__restrict__ bits,
-                                             uint2 *__restrict__ carry, int lane)
+                                             int ny, long long row, long long nrows, int W,
+                                             uint32_t *__restrict__ bits, uint2 *__restrict__ carry, int lane)
 {
     const int y = (int)(row % ny), z = (int)(row / ny);
     unsigned long long active = 0;  // capsules whose box crosses this row (H <= 64)
@@ -64,7 +65,7 @@ __device__ __forceinline__ void row_bits_row(const uint8_t *__restrict__ occ, co
         const int x = 32 * w + lane;
         bool o = false;
         if (x < nx) {
-            if (kMode != 2)
+            if (kMode != 2 && PCDF_IN(row * nx + x, nrows * nx))
                 o = __ldg(src + x) != 0;
             if (kMode != 0 && !o) {
                 for (unsigned long long m = active; m; m &= m - 1) {
@@ -105,7 +106,7 @@ __device__ __forceinline__ void row_bits_row(const uint8_t *__restrict__ occ, co
         LO = LF = kLoNone;
     if (lane == 31)
         RO = RF = kHiNone;
-    if (lane < W) {
+    if (lane < W && PCDF_IN(row * W + lane, nrows * W)) {
         bits[row * W + lane] = mine;
         carry[row * W + lane] = make_uint2(pack16(LO, RO), pack16(LF, RF));
     }
@@ -133,13 +134,13 @@ __device__ __forceinline__ int32_t row_value(uint32_t m, uint2 cr, int c, int x,
 // Seam merges of the CTA's columns, as a tree (thread of column c, band b);
 // ends with a barrier.
 template <int kB>
-__device__ __forceinline__ void merge_tree(uint32_t *tile, lean::Seg<kB> &seg, int c, int b)
+__device__ __forceinline__ void merge_tree(uint32_t *tile, lean::Seg<kB> &seg, int n, int c, int b)
 {
 #pragma unroll
     for (int r = 0; (1 << r) < kB; ++r) {
         const int sb = lean::tree_seam(kB, r, b);
         if (sb)
-            lean::merge_seam<kB>(tile, seg, c, sb, sb - (1 << r), min(sb + (1 << r), kB));
+            lean::merge_seam<kB>(tile, seg, n, c, sb, sb - (1 << r), min(sb + (1 << r), kB));
         __syncthreads();
     }
 }
@@ -148,7 +149,7 @@ __device__ __forceinline__ void merge_tree(uint32_t *tile, lean::Seg<kB> &seg, i
 // smem holds kCols * (ny + ceil(ny / 32)) words.
 template <int kB, bool kCoherent>
 __device__ __forceinline__ void edt_xy_block(const uint32_t *__restrict__ bits, const uint2 *__restrict__ carry,
-                                             int nx, int ny, int W, int w, int z, int32_t *__restrict__ mid,
+                                             int nx, int ny, int nz, int W, int w, int z, int32_t *__restrict__ mid,
                                              uint32_t *smem)
 {
     __shared__ lean::Seg<kB> seg;
@@ -167,25 +168,33 @@ __device__ __forceinline__ void edt_xy_block(const uint32_t *__restrict__ bits, 
         const uint2 *pc = carry + rbase + (long long)y0 * W;
 #pragma unroll 8
         for (int i = 0; i < cnt; ++i) {
-            const uint32_t m = ld<kCoherent>(pb);
-            const uint2 cr = ld<kCoherent>(pc);
+            uint32_t m = 0;
+            uint2 cr = make_uint2(0, 0);
+            if (PCDF_IN(rbase + (long long)(y0 + i) * W, (long long)nz * ny * W)) {
+                m = ld<kCoherent>(pb);
+                cr = ld<kCoherent>(pc);
+            }
             pb += W;
             pc += W;
             const int32_t v = live ? row_value(m, cr, c, x, nx, vm) : kInf32;
-            tile[(y0 + i) * kCols + c] = (uint32_t)v;
+            if (PCDF_IN(y0 + i, n))
+                tile[(y0 + i) * kCols + c] = (uint32_t)v;
             ob |= (uint32_t)(v < 0) << i;
         }
-        mk[(y0 >> 5) * kCols + c] = ob;
+        if (PCDF_IN(y0 >> 5, (n + 31) >> 5))
+            mk[(y0 >> 5) * kCols + c] = ob;
     }
     __syncthreads();
     lean::build_band<kB>(tile, seg, n, L, c, b);
     __syncthreads();
-    merge_tree<kB>(tile, seg, c, b);
+    merge_tree<kB>(tile, seg, n, c, b);
     if (live) {
         // elements are emitted in order e0, e0 + 1, ...: running output pointer
         int32_t *dst = mid + ((long long)z * ny + e0) * nx + x;
-        auto out = [=](int, int v) mutable {
-            *dst = v;
+        const long long V = (long long)nz * ny * nx, o0 = (long long)z * ny * nx + x;
+        auto out = [=](int e, int v) mutable {
+            if (PCDF_IN(o0 + (long long)e * nx, V))
+                *dst = v;
             dst += nx;
         };
         lean::eval_band<kB>(tile, mk, seg, n, L, c, b, out);
@@ -201,13 +210,17 @@ struct ZOut {
     long long ncols;
     float vox;
     int32_t mx;
-    __device__ __forceinline__ void operator()(int, int v)
+    long long cl, V;  // the column and the field's size (bounds checks)
+    __device__ __forceinline__ void operator()(int e, int v)
     {
-        __stcs(dq, v);
+        const bool ok = PCDF_IN(cl + (long long)e * ncols, V);
+        if (ok)
+            __stcs(dq, v);
         dq += ncols;
         mx = max(mx, v);
         if (kSdf) {
-            __stcs(df, sq_to_sdf_fast(v, vox));
+            if (ok)
+                __stcs(df, sq_to_sdf_fast(v, vox));
             df += ncols;
         }
     }
@@ -237,36 +250,43 @@ __device__ __forceinline__ void edt_z_block(const int32_t *__restrict__ mid, int
             int32_t v[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-                v[i] = live ? ld<kCoherent>(src + (long long)(z0 + i) * ncols) : kInf32;
+                v[i] = live && PCDF_IN(cl + (long long)(z0 + i) * ncols, (long long)n * ncols)
+                           ? ld<kCoherent>(src + (long long)(z0 + i) * ncols)
+                           : kInf32;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                tile[(z0 + i) * kCols + c] = (uint32_t)v[i];
+                if (PCDF_IN(z0 + i, n))
+                    tile[(z0 + i) * kCols + c] = (uint32_t)v[i];
                 ob |= (uint32_t)(v[i] < 0) << i;
             }
         } else {
             for (int i = 0; i < cnt; ++i) {
-                const int32_t v = live ? ld<kCoherent>(src + (long long)(z0 + i) * ncols) : kInf32;
-                tile[(z0 + i) * kCols + c] = (uint32_t)v;
+                const int32_t v = live && PCDF_IN(cl + (long long)(z0 + i) * ncols, (long long)n * ncols)
+                                      ? ld<kCoherent>(src + (long long)(z0 + i) * ncols)
+                                      : kInf32;
+                if (PCDF_IN(z0 + i, n))
+                    tile[(z0 + i) * kCols + c] = (uint32_t)v;
                 ob |= (uint32_t)(v < 0) << i;
             }
         }
-        mk[(z0 >> 5) * kCols + c] = ob;
+        if (PCDF_IN(z0 >> 5, (n + 31) >> 5))
+            mk[(z0 >> 5) * kCols + c] = ob;
     }
     __syncthreads();
     lean::build_band<kB>(tile, seg, n, L, c, b);
     __syncthreads();
-    merge_tree<kB>(tile, seg, c, b);
+    merge_tree<kB>(tile, seg, n, c, b);
     int32_t mx = INT32_MIN;
     if (live) {
         ZOut<kSdf> out{sq + cl + (long long)e0 * ncols, kSdf ? sdf + cl + (long long)e0 * ncols : nullptr, ncols,
-                       vox, INT32_MIN};
+                       vox, INT32_MIN, cl, (long long)n * ncols};
         mx = lean::eval_band<kB>(tile, mk, seg, n, L, c, b, out).mx;
     }
     if (colmax) {  // uniform over the CTA
         __shared__ int32_t s_max[kB][kCols];
         s_max[b][c] = mx;
         __syncthreads();
-        if (b == 0 && live) {
+        if (b == 0 && live && PCDF_IN(cl, ncols)) {
             int32_t m = s_max[0][c];
 #pragma unroll
             for (int k = 1; k < kB; ++k)

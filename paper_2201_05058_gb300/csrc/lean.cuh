@@ -94,7 +94,7 @@ PCDF_HD int next_change(const uint32_t *m, int e, bool st, int n)
     uint32_t d = (st ? ~m[w * kCols] : m[w * kCols]) & (0xFFFFFFFEu << (e & 31));
     while (!d) {
         ++w;
-        if ((w << 5) >= n)
+        if ((w << 5) >= n || !PCDF_IN(w, (n + 31) >> 5))
             return n;
         d = st ? ~m[w * kCols] : m[w * kCols];
     }
@@ -135,14 +135,14 @@ PCDF_HD void build_band(uint32_t *tile, Seg<kB> &S, int n, int L, int c, int b)
     const bool first_occ = cur;
     bool first_open = true;
     for (int e = e0; e < e1; ++e) {
-        const int32_t v = (int32_t)col[e * kCols];
+        const int32_t v = PCDF_IN(e, n) ? (int32_t)col[e * kCols] : kInf32;
         const bool st = v < 0;
         if (st != cur) {  // the piece [a, e) ends
             if (first_open) {
                 S.fS[b][c] = e0;
                 S.fK[b][c] = top + 1;
                 first_open = false;
-            } else if (top + 1 < e - a) {
+            } else if (top + 1 < e - a && PCDF_IN(e - 1, n)) {
                 col[(e - 1) * kCols] = kMark | (uint32_t)(top + 1);
             }
             a = e;
@@ -159,13 +159,14 @@ PCDF_HD void build_band(uint32_t *tile, Seg<kB> &S, int n, int L, int c, int b)
             s1 = s0;
             f1 = f0;
             if (top >= 1) {
-                const uint32_t w = col[(a + top - 1) * kCols];
+                const uint32_t w = PCDF_IN(a + top - 1, n) ? col[(a + top - 1) * kCols] : 0u;
                 s0 = site_of(w);
                 f0 = s0 * s0 + gval_of(w);
             }
         }
         ++top;
-        col[(a + top) * kCols] = pack_site(e, g);
+        if (PCDF_IN(a + top, n))
+            col[(a + top) * kCols] = pack_site(e, g);
         s0 = s1;
         f0 = f1;
         s1 = e;
@@ -188,6 +189,7 @@ struct Chain {
     const uint32_t *col;
     Seg<kB> *S;
     int c;
+    int n;  // slots of the column (bounds checks)
 
     struct Pos {
         int j, start, slot, end;  // band, first slot of the piece, current slot, one past its last slot
@@ -266,7 +268,7 @@ struct Chain {
         }
         return p.first && cont(p.j) && seek_left(p.j - 1, q, lo);
     }
-    PCDF_HD uint32_t at(const Pos &p) const { return col[p.slot * kCols]; }
+    PCDF_HD uint32_t at(const Pos &p) const { return PCDF_IN(p.slot, n) ? col[p.slot * kCols] : 0u; }
 };
 
 // 2. Join the envelopes across seam b, where a run crosses it: the left chain
@@ -275,9 +277,9 @@ struct Chain {
 // b = step, 3 step, 5 step, ... join groups of `step` bands on either side,
 // so the rounds of one column run on different threads in parallel.
 template <int kB>
-PCDF_HD void merge_seam(uint32_t *tile, Seg<kB> &S, int c, int b, int lo, int hi)
+PCDF_HD void merge_seam(uint32_t *tile, Seg<kB> &S, int n, int c, int b, int lo, int hi)
 {
-    Chain<kB> ch{tile + c, &S, c};
+    Chain<kB> ch{tile + c, &S, c, n};
     if (!ch.cont(b))
         return;
     using Pos = typename Chain<kB>::Pos;
@@ -330,7 +332,7 @@ PCDF_HD Out eval_band(uint32_t *tile, const uint32_t *mk, Seg<kB> &S, int n, int
     const int e0 = b * L, e1 = min(e0 + L, n);
     if (e0 >= e1)
         return out;
-    Chain<kB> ch{tile + c, &S, c};
+    Chain<kB> ch{tile + c, &S, c, n};
     using Pos = typename Chain<kB>::Pos;
     const uint32_t *m = mk + c;
     int e = e0;
@@ -357,7 +359,7 @@ PCDF_HD Out eval_band(uint32_t *tile, const uint32_t *mk, Seg<kB> &S, int n, int
             K = S.lK[b][c];
         } else {
             own.start = e;
-            const uint32_t w = tile[se * kCols + c];
+            const uint32_t w = PCDF_IN(se, n) ? tile[se * kCols + c] : 0u;
             K = (w & kMark) ? (int)(w & ~kMark) : se - e + 1;
         }
         own.slot = own.start;
@@ -411,7 +413,7 @@ PCDF_HD Out eval_band(uint32_t *tile, const uint32_t *mk, Seg<kB> &S, int n, int
                 }
             }
             if (hn) {
-                const uint32_t w2 = tile[nslot * kCols + c];
+                const uint32_t w2 = PCDF_IN(nslot, n) ? tile[nslot * kCols + c] : 0u;
                 sn = site_of(w2);
                 gn = gval_of(w2);
             }
@@ -441,7 +443,7 @@ PCDF_HD Out eval_band(uint32_t *tile, const uint32_t *mk, Seg<kB> &S, int n, int
                         }
                     }
                     if (hn) {
-                        const uint32_t w2 = tile[nslot * kCols + c];
+                        const uint32_t w2 = PCDF_IN(nslot, n) ? tile[nslot * kCols + c] : 0u;
                         sn = site_of(w2);
                         gn = gval_of(w2);
                     }

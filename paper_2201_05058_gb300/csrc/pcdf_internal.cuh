@@ -6,6 +6,53 @@
 
 #include "pcdf.h"
 
+// ---------------------------------------------------------------------------
+// Bounds checks (debug build).  Compiled with PCDF_CHECK_BOUNDS (and
+// relocatable device code, so that every file shares one error word), the
+// kernels of the hot path test each global and shared index before the
+// access: PCDF_IN(i, n) is false when i lies outside [0, n), and then records
+// the first failing check (a 16-bit hash of its file name, its line) and a
+// count in g_bounds_error, and the access is skipped; nothing traps.  In the
+// normal build PCDF_IN is the constant true and costs nothing.
+// ---------------------------------------------------------------------------
+namespace pcdf {
+
+__host__ __device__ constexpr unsigned file_tag(const char *s, const char *base = nullptr, unsigned h = 5381)
+{
+    // djb2 hash of the part after the last '/'
+    return !base ? file_tag(s, s, h)
+                 : (*s == 0 ? (h & 0xffffu)
+                            : (*s == '/' ? file_tag(s + 1, s + 1, 5381) : file_tag(s + 1, base, h * 33u + (unsigned char)*s)));
+}
+
+template <unsigned V>
+struct TagConst {
+    static constexpr unsigned value = V;
+};
+
+#ifdef PCDF_CHECK_BOUNDS
+extern __device__ unsigned int g_bounds_error[2];  // [0] first failing check: tag << 16 | line; [1] count
+__host__ __device__ __forceinline__ bool bounds_ok(long long i, long long n, unsigned code)
+{
+    if (i >= 0 && i < n)
+        return true;
+#ifdef __CUDA_ARCH__
+    atomicCAS(&g_bounds_error[0], 0u, code);
+    atomicAdd(&g_bounds_error[1], 1u);
+#else
+    (void)code;
+#endif
+    return false;
+}
+#define PCDF_IN(i, n)                                                                                               \
+    (::pcdf::bounds_ok((long long)(i), (long long)(n),                                                             \
+                       (::pcdf::TagConst<::pcdf::file_tag(__FILE__)>::value << 16) | (unsigned)__LINE__))
+#else
+#define PCDF_IN(i, n) true
+#endif
+
+}  // namespace pcdf
+
 namespace pcdf {
 
 // 1-D distances along x are stored as int16 with the sign of the voxel's own

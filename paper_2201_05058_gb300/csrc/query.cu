@@ -24,7 +24,7 @@ __global__ void k_query_cost(const QueryGrid g, const float *__restrict__ sdf, i
         const float4 s = __ldg(spheres + q);
         const int t = time_index(__ldg(tidx + q), T);
         const long long V = (long long)g.n[0] * g.n[1] * g.n[2];
-        const Sample r = trilinear(g, sdf + t * V, s, false);
+        const Sample r = trilinear(g, sdf + (PCDF_IN(t, T) ? t : 0) * V, s, false);
         const float hv = (eps + s.w) - r.d;
         h[q] = hv > 0.f ? hv : 0.f;
         oob = r.oob;
@@ -47,7 +47,7 @@ __global__ void k_query_cost_backward(const QueryGrid g, const float *__restrict
     const float4 s = __ldg(spheres + q);
     const int t = time_index(__ldg(tidx + q), T);
     const long long V = (long long)g.n[0] * g.n[1] * g.n[2];
-    const Sample r = trilinear(g, sdf + t * V, s, true);
+    const Sample r = trilinear(g, sdf + (PCDF_IN(t, T) ? t : 0) * V, s, true);
     const float hv = (eps + s.w) - r.d;
     const bool active = hv > 0.f && isfinite(r.d);
     const float gh = active ? __ldg(grad_h + q) : 0.f;

@@ -104,9 +104,11 @@ __device__ __forceinline__ Sample trilinear(const QueryGrid &g, const float *__r
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-            for (int dx = 0; dx < 2; ++dx)
-                c[dz][dy][dx] = __ldg(field + (dz ? cl.i1[2] : cl.i0[2]) * sz + (dy ? cl.i1[1] : cl.i0[1]) * sy +
-                                      (dx ? cl.i1[0] : cl.i0[0]));
+            for (int dx = 0; dx < 2; ++dx) {
+                const long long o = (dz ? cl.i1[2] : cl.i0[2]) * sz + (dy ? cl.i1[1] : cl.i0[1]) * sy +
+                                    (dx ? cl.i1[0] : cl.i0[0]);
+                c[dz][dy][dx] = PCDF_IN(o, sz * g.n[2]) ? __ldg(field + o) : 0.f;
+            }
     return interpolate(cl, c, want_grad);
 }
 

@@ -216,3 +216,13 @@ def test_template_radius_is_the_ceiling_square_root():
         assert R.value == (r if r * r >= m else r + 1), m
     assert lib.pcdf_template_radius(-1, ctypes.byref(R)) == -1
     assert lib.pcdf_template_radius(4, None) == -1
+
+
+def test_bounds_check_entry_point_in_the_normal_build():
+    """pcdf_bounds_check exists in every build; only the debug build
+    (PCDF_CHECK_BOUNDS) has index checks to report, so the normal one refuses."""
+    lib = _lib.load(checked=False)
+    first, count = ctypes.c_uint32(7), ctypes.c_uint32(7)
+    assert lib.pcdf_bounds_check(ctypes.byref(first), ctypes.byref(count), 0) == -1
+    assert "not a bounds-checked build" in err()
+    assert first.value == 0 and count.value == 0
