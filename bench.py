@@ -386,6 +386,21 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
     hist = sg.train(net, grid, fields, caps, tf, T, steps=steps, batch=batch, lr=2e-3, log_every=max(1, steps // 8))
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
+    # one training step at the training batch: the network's products alone
+    # (backward = forward + input and weight gradients), with the Adam update,
+    # and the sample generation that feeds it
+    xb, tb = pcdf.surrogate_samples(grid, fields, caps, tf, T, batch, 12345, 0.6)
+    t_bwd = ev_time(lambda: net.backward(xb, tb), k=20)
+    t_fwd_train = ev_time(lambda: net.forward(xb), k=20)
+
+    def step():
+        net.backward(xb, tb)
+        net.adam(1e-5)
+    t_step = ev_time(step, k=20)
+    t_samples = ev_time(lambda: pcdf.surrogate_samples(grid, fields, caps, tf, T, batch, 777, 0.6), k=20)
+    # tensor-core products per row: forward 2 (16 256 + 2 256^2), input
+    # gradients 2 (2 256^2), weight gradients 2 (2 256^2 + 256 16)
+    train_flops = 802816 * batch
     del fields
 
     def queries(s):
@@ -529,6 +544,10 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
     return {"workload": f"MLP 16-256-256-256-1 bf16/fp32, trained on {n_train_scenes} 64^3 scenes x T=20 "
                         f"({steps * batch} samples); 1,024,000 sphere queries per plan step on held-out scenes",
             "train_s": t_train, "fields_s": t_fields, "loss_first": hist[0][1], "loss_last": hist[-1][1],
+            "train_step": {"batch": batch, "backward_ms": t_bwd, "backward_tflops": train_flops / (t_bwd * 1e-3) / 1e12,
+                           "forward_stored_ms": t_fwd_train, "step_with_adam_ms": t_step,
+                           "step_tflops": train_flops / (t_step * 1e-3) / 1e12, "samples_ms": t_samples,
+                           "flops_per_row": 802816},
             "band_m": BAND, "certified": True,
             "max_err_m": max(x["max_err"] for x in stats), "mean_err_m": float(np.mean([x["mean_err"] for x in stats])),
             "fallback_frac": float(np.mean([x["fallback"] for x in stats])),

@@ -407,17 +407,40 @@ int pcdf_batch_autotune(const pcdf_env *envs, int32_t n_env, void *workspace, si
  * relu(x W_l^T + b_l); activations and input gradients are stored in BF16.
  *
  * x: device BF16 bits [M][16] (16-byte aligned); y, target: device FP32 [M].
- * Workspace: pcdf_mlp_workspace_bytes(M), 256-byte aligned.
- * pcdf_mlp_backward runs the forward pass (y), the loss mean((y - t)^2)
- * (added to *loss if non-NULL, after zeroing it) and overwrites the gradient.
- * On return the workspace holds what the passes stored, in sections of
- * A = M * 512 bytes rounded up to a multiple of 256, in this order: H1, H2,
- * H3 (BF16 [M][256]: the hidden activations relu(Z_l)) and D3, D2, D1 (BF16
- * [M][256]: the loss gradient with respect to Z_3, Z_2, Z_1, zero where the
- * activation is zero).  pcdf_mlp_forward leaves H1, H2, H3
- * the same way.  With dy = 2 (y - t) / M (FP32), D3 = dy * w4 (FP32 product
- * rounded to BF16), D_l = D_{l+1} W_{l+1} (FP32 sum rounded to BF16) and
- * grad W_l = D_l^T H_{l-1} (H_0 = x), grad b_l = the column sums of D_l.
+ * The three padding columns of x (after the PCDF_MLP_IN features) are
+ * ignored: the kernels put 1 there and the first layer's bias in the matching
+ * columns of W1.
+ *
+ * All passes run on the 5th-generation tensor cores (tcgen05.mma, BF16
+ * operands in shared memory, FP32 accumulators in tensor memory) in
+ * persistent warp-specialised kernels over 128-row tiles.  A bounded wait on
+ * the tensor cores or the copies that expires (about a second) gives NaN: in
+ * y for the tiles concerned, in the loss and in the gradient of b4.
+ *
+ * pcdf_mlp_forward  y and the hidden activations, stored in the workspace.
+ * pcdf_mlp_backward  one training step's products: the forward pass (y), the
+ * loss mean((y - t)^2) (written to *loss if non-NULL) and the gradient
+ * (overwritten).  With dy = 2 (y - t) / M (FP32), D3 = dy * w4 where H3 > 0
+ * (FP32 product rounded to BF16), D_l = D_{l+1} W_{l+1} where H_l > 0 (FP32
+ * sum rounded to BF16), grad W_l = D_l^T H_{l-1} (H_0 = x) and grad b_l = the
+ * column sums of D_l (FP32 sums in an unspecified order: atomics).  D3 is
+ * rebuilt on chip from dy and the mask of H3 wherever it is used.
+ *
+ * Workspace: pcdf_mlp_workspace_bytes(M), 256-byte aligned.  For T = ceil(M /
+ * 128) tiles it holds, in this order: H1, H2, H3, D2, D1 (T x 65536 bytes
+ * each: H_l = relu(Z_l), D_l = dL/dZ_l, BF16), the x tiles as multiplied (T x
+ * 4096 bytes), the ReLU masks of H1, H2, H3 (T x 4096 bytes each) and dy (T x
+ * 128 FP32, 0 past M).  A tile is stored in the tensor-core operand layout:
+ * element (m, k) of an [M][256] matrix at byte 65536 (m / 128) + 4096 ((m %
+ * 128) / 8) + 128 (k / 8) + 16 (m % 8) + 2 (k % 8); of x, 4096 (m / 128) +
+ * 256 ((m % 128) / 8) + 128 (k / 8) + 16 (m % 8) + 2 (k % 8).  Mask word (t,
+ * j, r) at 4 (1024 t + 128 j + r) of its section holds the flags H_l(128 t +
+ * r, k) > 0 of the 32 columns k = 32 j + 8 g + c: byte g, bit c / 2 for even
+ * c and bit 4 + (c - 1) / 2 for odd c (a NaN activation counts as > 0).  Rows
+ * past M in the last tile hold the network of zero features (H) and zeros
+ * (D).  pcdf_mlp_forward stores H1, H2, H3, the x tiles and the masks of H1
+ * and H2; pcdf_mlp_backward stores H1, H2, D2, D1, the x tiles, the three
+ * masks and dy (H3 is left as it was).
  * pcdf_mlp_adam applies one Adam step (bias-corrected, step >= 1) to the FP32
  * parameters and refreshes the BF16 copies.
  * ------------------------------------------------------------------------- */
@@ -434,27 +457,21 @@ int pcdf_mlp_init(void *state, uint64_t seed, void *stream);
 int pcdf_mlp_forward(const void *state, const uint16_t *x, int64_t M, float *y, void *workspace,
                      size_t workspace_bytes, void *stream);
 /* pcdf_mlp_infer  y = network(x) for M rows in one fused launch (no
- * workspace): each CTA keeps a 64-row tile's activations in shared memory
- * and streams the hidden weights; the products are accumulated in the same
- * order and rounded at the same points as pcdf_mlp_forward, so y is
- * bit-identical to it.  x device BF16 bits [M][16] (16-byte aligned), y
- * device fp32 [M]. */
+ * workspace) on the legacy mma.sync tensor-core path, kept as the baseline:
+ * each CTA keeps a 64-row tile's activations in shared memory and streams the
+ * hidden weights.  Same arithmetic as the tcgen05 passes up to the order of
+ * the FP32 sums (y within FP32 rounding of theirs, not bit-identical).  x
+ * device BF16 bits [M][16] (16-byte aligned), y device fp32 [M]. */
 int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);
 
-/* pcdf_mlp_infer_tc  the same network on the 5th-generation tensor cores: a
- * persistent kernel (one CTA per SM) walks 128-row tiles; one thread issues
- * tcgen05.mma (BF16 operands in shared memory, FP32 accumulators in tensor
- * memory), a producer warp streams the x tiles and the hidden weights (bulk
- * copies from a packed copy in the state that pcdf_mlp_init and
- * pcdf_mlp_adam keep current; the state is only read here), and eight
- * epilogue warps read each layer back with tcgen05.ld for the bias, ReLU and
- * BF16 rounding, overlapping the next layer's products.  Same arithmetic up
- * to the order of the FP32 sums (outputs within FP32 rounding of
- * pcdf_mlp_infer, not bit-identical).  The three padding columns of x
- * (after the PCDF_MLP_IN features) are ignored: the kernel puts 1 there and
- * the first layer's bias in the matching columns of W1.  A tile whose
- * bounded wait on the tensor cores expires (about a second) gets NaN, as do
- * the CTA's later tiles. */
+/* pcdf_mlp_infer_tc  y alone, with no workspace: a persistent kernel (one
+ * CTA per SM) walks 128-row tiles; one thread issues tcgen05.mma, a producer
+ * warp streams the x tiles and the hidden weights (bulk copies from a packed
+ * copy in the state that pcdf_mlp_init and pcdf_mlp_adam keep current; the
+ * state is only read here), and eight epilogue warps read each layer back
+ * with tcgen05.ld for the bias, ReLU and BF16 rounding, overlapping the next
+ * layer's products.  The same kernel, products and rounding as
+ * pcdf_mlp_forward and pcdf_mlp_backward: y is bit-identical to theirs. */
 int pcdf_mlp_infer_tc(const void *state, const uint16_t *x, int64_t M, float *y, void *stream);
 /* pcdf_mlp_infer_tc_count  pcdf_mlp_infer_tc over the first *count rows of x
  * (count: device int32, read by the kernel, clamped to [0, M_max]), so that

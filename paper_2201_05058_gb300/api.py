@@ -762,14 +762,22 @@ class SurrogateMLP:
         return y, loss
 
     def stored(self, M: int):
-        """Views of what the last forward or backward pass of M rows stored in
-        the workspace (layout in include/pcdf.h): H1, H2, H3, D3, D2, D1
-        (bfloat16 [M, 256])."""
-        a = -(-M * 512 // 256) * 256
+        """What the last forward or backward pass of M rows stored in the
+        workspace (layout in include/pcdf.h), unpacked from the tensor-core
+        tile layout (copies): H1, H2, H3, D2, D1 as bfloat16 [M, 256] and dy
+        as float32 [M].  A forward pass stores H1, H2, H3; a backward pass H1,
+        H2, D2, D1 and dy (D3 = dy w4 where H3 > 0 is not stored)."""
+        T = -(-M // 128)
+        tile = 128 * 256 * 2
         ws = self._ws
         out = {}
-        for i, k in enumerate(("H1", "H2", "H3", "D3", "D2", "D1")):
-            out[k] = ws[i * a:i * a + M * 512].view(torch.bfloat16).view(M, 256)
+        for i, k in enumerate(("H1", "H2", "H3", "D2", "D1")):
+            raw = ws[i * T * tile:(i + 1) * T * tile].view(torch.bfloat16)
+            # element (m, c) at tile m // 128, 8-row group, 8-column group, row in group, column in group
+            t = raw.view(T, 16, 32, 8, 8).permute(0, 1, 3, 2, 4).reshape(T * 128, 256)
+            out[k] = t[:M].clone()
+        o = 5 * T * tile + T * 4096 + 3 * T * 4096
+        out["dy"] = ws[o:o + 4 * M].view(torch.float32).clone()
         return out
 
     def adam(self, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):

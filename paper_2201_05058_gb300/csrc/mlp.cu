@@ -7,19 +7,26 @@
 // stored in BF16, every product is accumulated in FP32.
 //
 // Kernels:
-//   k_gemm     C(m,n) = sum_k A(m,k) B(k,n) with mma.sync m16n8k16 (BF16 in, FP32
-//              accumulate), operands staged in shared memory; the epilogue
-//              adds the bias and applies ReLU (forward), multiplies by the
-//              ReLU mask of the layer below (input gradient) or accumulates
-//              FP32 into a weight gradient (split over the batch).
-//   k_head     the 256 -> 1 output layer, the squared-error loss and its
-//              gradient with respect to the last hidden layer.
-//   k_colsum   bias gradients (column sums of a BF16 gradient matrix).
-//   k_adam     Adam update of the FP32 master copy and refresh of the BF16 copy.
-//   k_init     counter-hash uniform initialisation (fan-in scaled).
+//   k_mlp_ws<0>  inference: persistent, warp-specialised, tcgen05.mma with the
+//                accumulators in tensor memory (all three layers and the head
+//                of a 128-row tile without leaving the SM).
+//   k_mlp_ws<1>  the same pass storing H1, H2, H3 for training or inspection.
+//   k_mlp_ws<2>  the forward of a training step: H1, H2 stored, then the
+//                head's backward (loss, dy, the w4 and b4 gradients).
+//   k_mlp_dgrad  D3 = dy w4 masked by H3 > 0 (built on chip), D2 = (D3 W3)
+//                masked by H2 > 0 and D1 = (D2 W2) masked by H1 > 0, tcgen05
+//                with the packed transposed weights.
+//   k_mlp_wgrad  the weight gradients D_l^T H_{l-1} (tcgen05, MN-major
+//                operands, split over the batch) and the bias gradients.
+//   k_mlp_infer  the legacy mma.sync m16n8k16 inference (baseline).
+//   k_adam       Adam update of the FP32 master copy and refresh of the BF16 copy.
+//   k_init       counter-hash uniform initialisation (fan-in scaled).
+//   k_pack_hidden  the hidden weights (and their transposes) in the chunked
+//                tensor-core operand layout.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "host.h"
@@ -43,31 +50,15 @@ static_assert(kP == PCDF_MLP_PARAMS, "parameter count");
 static_assert(kH == PCDF_MLP_BF16_WEIGHTS, "bf16 weight count");
 
 // state layout (bytes): master, adam m, adam v, grad (FP32 [kPpad] each), bf16 weights
-// then the hidden BF16 weights again, packed for the tensor-core kernel
+// then the hidden BF16 weights again, packed for the tensor-core kernels: W2,
+// W3 (forward) and W3^T, W2^T (input gradients), in that order
 constexpr size_t sMaster = 0, sM = 4 * kPpad, sV = 8 * kPpad, sGrad = 12 * kPpad, sHalf = 16 * kPpad,
-                 sPack = (sHalf + 2 * kH + 255) / 256 * 256, kPackElems = 2LL * kW * kW,
+                 sPack = (sHalf + 2 * kH + 255) / 256 * 256, kPackElems = 4LL * kW * kW,
                  kStateBytes = sPack + 2 * kPackElems;
 
 using bf16 = __nv_bfloat16;
 
-// ---------------------------------------------------------------------------
-// GEMM
-// ---------------------------------------------------------------------------
-constexpr int BM = 64, BN = 64, BK = 32, PADK = 8;
-
-enum Epi { kBiasRelu = 0, kMask = 1, kAtomic = 2 };
-
-struct GemmArgs {
-    const bf16 *A, *B;
-    int lda, ldb, M, N, K, k_split;
-    const float *bias;   // kBiasRelu
-    const bf16 *mask;    // kMask: output zero where mask <= 0
-    int ldm;
-    bf16 *out_h;         // kBiasRelu, kMask
-    float *out_f;        // kAtomic
-    int ldo;
-};
-
+// mma.sync m16n8k16: BF16 in, FP32 accumulate (the legacy tensor-core path)
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
 {
     asm volatile(
@@ -77,127 +68,14 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// Stage a 64 x BK tile whose element (r, k) is at P[r * ld + k] (kT = false)
-// or P[k * ld + r] (kT = true) into S[r][k]; out-of-range elements are zero.
-template <bool kT>
-__device__ __forceinline__ void stage_tile(bf16 (*S)[BK + PADK], const bf16 *__restrict__ P, int ld, int r0, int R,
-                                           int k0, int k1)
-{
-    const bf16 zero = __float2bfloat16_rn(0.f);
-    for (int v = threadIdx.x; v < BM * BK / 8; v += blockDim.x) {
-        if (!kT) {
-            const int r = v / (BK / 8), kq = (v % (BK / 8)) * 8;
-            const int gr = r0 + r, gk = k0 + kq;
-            if (gr < R && gk + 8 <= k1) {
-                const uint4 q = *reinterpret_cast<const uint4 *>(P + (long long)gr * ld + gk);
-                *reinterpret_cast<uint4 *>(&S[r][kq]) = q;
-            } else {
-                for (int j = 0; j < 8; ++j)
-                    S[r][kq + j] = (gr < R && gk + j < k1) ? P[(long long)gr * ld + gk + j] : zero;
-            }
-        } else {
-            const int k = v / (BM / 8), rq = (v % (BM / 8)) * 8;
-            const int gk = k0 + k, gr = r0 + rq;
-            if (gk < k1 && gr + 8 <= R) {
-                const uint4 q = *reinterpret_cast<const uint4 *>(P + (long long)gk * ld + gr);
-                const bf16 *e = reinterpret_cast<const bf16 *>(&q);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    S[rq + j][k] = e[j];
-            } else {
-                for (int j = 0; j < 8; ++j)
-                    S[rq + j][k] = (gk < k1 && gr + j < R) ? P[(long long)gk * ld + gr + j] : zero;
-            }
-        }
-    }
-}
-
-template <bool kTA, bool kTB, int kEpi>
-__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g)
-{
-    __shared__ __align__(16) bf16 As[BM][BK + PADK];
-    __shared__ __align__(16) bf16 Bs[BN][BK + PADK];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kb = blockIdx.z * g.k_split, ke = min(g.K, kb + g.k_split);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wm = warp >> 1, wn = warp & 1, gid = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                acc[i][j][q] = 0.f;
-
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-        stage_tile<kTA>(As, g.A, g.lda, m0, g.M, k0, ke);
-        stage_tile<kTB>(Bs, g.B, g.ldb, n0, g.N, k0, ke);
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = wm * 32 + mt * 16 + gid, c = kk + tig * 2;
-                a[mt][0] = *reinterpret_cast<const uint32_t *>(&As[r][c]);
-                a[mt][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][c]);
-                a[mt][2] = *reinterpret_cast<const uint32_t *>(&As[r][c + 8]);
-                a[mt][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][c + 8]);
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int n = wn * 32 + nt * 8 + gid, k = kk + tig * 2;
-                b[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][k]);
-                b[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][k + 8]);
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-                    mma16816(acc[mt][nt], a[mt], b[nt]);
-        }
-        __syncthreads();
-    }
-
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = m0 + wm * 32 + mt * 16 + gid + (q >= 2 ? 8 : 0);
-                const int c = n0 + wn * 32 + nt * 8 + tig * 2 + (q & 1);
-                if (r >= g.M || c >= g.N)
-                    continue;
-                const float v = acc[mt][nt][q];
-                if (kEpi == kBiasRelu) {
-                    g.out_h[(long long)r * g.ldo + c] = __float2bfloat16_rn(fmaxf(v + g.bias[c], 0.f));
-                } else if (kEpi == kMask) {
-                    const float m = __bfloat162float(g.mask[(long long)r * g.ldm + c]);
-                    g.out_h[(long long)r * g.ldo + c] = __float2bfloat16_rn(m > 0.f ? v : 0.f);
-                } else {
-                    atomicAdd(g.out_f + (long long)r * g.ldo + c, v);
-                }
-            }
-}
-
-template <bool kTA, bool kTB, int kEpi>
-cudaError_t gemm(const GemmArgs &g, int splits, cudaStream_t st)
-{
-    const dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, splits);
-    k_gemm<kTA, kTB, kEpi><<<grid, 128, 0, st>>>(g);
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------------------
 // fused inference: the whole network for a tile of rows in one CTA
 // ---------------------------------------------------------------------------
-// The activations of the tile stay in shared memory between layers; the
+// The legacy path (mma.sync, kept as the baseline of the tcgen05 kernels):
+// the activations of the tile stay in shared memory between layers; the
 // hidden weights stream through a double-buffered shared-memory chunk
-// (cp.async).  Per output element the k16 products are accumulated in the
-// same order as k_gemm and the epilogues and head do the same arithmetic as
-// k_gemm's bias+ReLU and k_head, so y is bit-identical to forward + head.
+// (cp.async).  Same arithmetic as the tcgen05 kernels up to the order of the
+// FP32 sums.
 constexpr int kIR = 64;           // rows per CTA
 constexpr int kIT = 256;          // threads: 8 warps, 2 (rows) x 4 (columns)
 constexpr int kKC = 32;           // K chunk of a hidden weight matrix
@@ -344,7 +222,7 @@ __global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ w
     }
     __syncthreads();
 
-    // head: the 256 -> 1 layer, as k_head (lane j owns columns 8 j .. 8 j + 7)
+    // head: the 256 -> 1 layer (lane j owns columns 8 j .. 8 j + 7)
     float w[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j)
@@ -380,7 +258,7 @@ __global__ void __launch_bounds__(kIT, 2) k_mlp_infer(const bf16 *__restrict__ w
 //
 // W2 and W3 are pre-packed (k_pack_hidden) into 8 chunks of 64 columns, each
 // laid out exactly as the B operand in shared memory, so one bulk copy moves
-// a chunk.
+// a chunk; W3^T and W2^T follow in 8 more chunks for the input gradients.
 //
 // Operand tiles use the canonical K-major layout without swizzling: 8 x 16
 // byte core matrices (8 rows of 8 BF16); element (r, k) of a tile with Kt
@@ -412,6 +290,26 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 // instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16 (bits
 // 7-9 and 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kW >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+
+// the same for an M = 128 product of width n (a multiple of 16, up to 256);
+// with mn_major both operands are MN-major (transposed, bits 15 and 16): then
+// the leading byte offset of a descriptor is still the step between K-adjacent
+// core matrices and the stride byte offset the step between MN-adjacent ones
+__host__ __device__ constexpr uint32_t idesc(int n, bool mn_major)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (mn_major ? (1u << 15) | (1u << 16) : 0u) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+}
+static_assert(idesc(kW, false) == kIdesc, "instruction descriptor");
+
+__device__ __forceinline__ void mma_i(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate)
+        : "memory");
+}
 
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate)
 {
@@ -489,6 +387,20 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// one arrival expecting `bytes` of copy completions, for copies issued next
+__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// a bulk copy that completes its bytes on `bar` (no arrival of its own)
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
@@ -518,19 +430,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 
 }  // namespace tc
 
-// W2 and W3 into the chunked B-operand layout: chunk j (layer j / 4, columns
-// 64 (j % 4) ..) holds element (n, k) at tc::kmaj(n, k, 64) / 2
+// W2, W3, W3^T and W2^T into the chunked B-operand layout: chunk j (matrix
+// j / 4, K columns 64 (j % 4) ..) holds element (n, k) at tc::kmaj(n, k, 64) / 2,
+// where element (n, k) is W[n][k] for W2 and W3 and W[k][n] for the transposes
+// (n an input unit of the layer, k an output unit)
 __global__ void k_pack_hidden(const bf16 *__restrict__ wh, bf16 *__restrict__ packed)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte piece
-    if (v >= 2 * kW * (kW / 8))
+    if (v >= 4 * kW * (kW / 8))
         return;
     const int l = v / (kW * (kW / 8)), rem = v % (kW * (kW / 8));
     const int n = rem / (kW / 8), kq = rem % (kW / 8);
-    const bf16 *W = wh + (l == 0 ? hW2 : hW3);
     const int k = kq * 8, chunk = l * (kW / tc::kKC) + k / tc::kKC;
     bf16 *dst = packed + (long long)chunk * (kW * tc::kKC) + tc::kmaj(n, k % tc::kKC, tc::kKC) / 2;
-    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(W + n * kW + k);
+    if (l < 2) {
+        const bf16 *W = wh + (l == 0 ? hW2 : hW3);
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(W + n * kW + k);
+    } else {
+        const bf16 *W = wh + (l == 2 ? hW3 : hW2);
+        __align__(16) bf16 e[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            e[i] = W[(k + i) * kW + n];
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(e);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -560,7 +483,7 @@ constexpr uint32_t kBytesA = 128 * kW * 2, kBytesChunk = kW * tc::kKC * 2, kByte
                    kBytesW1 = kW * kIn * 2;
 constexpr uint32_t oA = 0, oRing = oA + kBytesA, oX = oRing + kStages * kBytesChunk, oW1 = oX + 2 * kBytesX,
                    oBias = oW1 + kBytesW1, oW4 = oBias + 3 * kW * 4, oPart = oW4 + kW * 4,
-                   kEnd = oPart + 2 * kGroups * 128 * 4;
+                   oDY = oPart + 2 * kGroups * 128 * 4, kEnd = oDY + kBytesX;
 constexpr size_t kSmem = 1024 + (size_t)kEnd;
 static_assert(kSmem <= 227 * 1024, "shared memory");
 static_assert(kEpiWarps % 4 == 0 && 8 % kGroups == 0 && kGroups % 2 == 0,
@@ -581,6 +504,28 @@ __device__ __forceinline__ int warp_uniform(int v, volatile int *slot, int lane)
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *slot, int lane)
 {
     return warp_uniform(lane == 0 ? (int)tc::mbar_wait(bar, parity) : 0, slot, lane) != 0;
+}
+// An epilogue warp's slices of the accumulator at tb (its lane quarter),
+// for kG groups of four warps: the k-th is j = group + k kG; f(v, j, k) gets
+// the 32 columns of slice j while the next slice's load is in flight.
+template <int kG = kGroups, class F>
+__device__ __forceinline__ void each_slice(uint32_t tb, int group, F &&f)
+{
+    constexpr int kS = 8 / kG;
+    uint32_t va[32], vb[32];
+    tc::tmem_ld32_async(tb + (uint32_t)(32 * group), va);
+    tc::tmem_wait_ld(va);
+#pragma unroll
+    for (int k = 0; k < kS; ++k) {
+        const int j = group + k * kG;
+        uint32_t(&cur)[32] = (k & 1) ? vb : va;
+        uint32_t(&nxt)[32] = (k & 1) ? va : vb;
+        if (k + 1 < kS)
+            tc::tmem_ld32_async(tb + (uint32_t)(32 * (j + kG)), nxt);
+        f(cur, j, k);
+        if (k + 1 < kS)
+            tc::tmem_wait_ld(nxt);
+    }
 }
 }  // namespace ws
 
@@ -614,9 +559,66 @@ __device__ __forceinline__ void fma2(float &a0, float &a1, float x0, float x1, f
         : "f"(x0), "f"(x1), "f"(y0), "f"(y1));
 }
 
+// Training outputs of the persistent kernel (modes 1 and 2).  Tiles of an
+// [M][256] matrix are stored packed: element (m, k) at byte 65536 (m / 128) +
+// tc::kmaj(m % 128, k, 256), the A-operand layout of the shared-memory tile,
+// so one 64 KB bulk copy loads a tile as a tensor-core operand.
+struct TrainIO {
+    bf16 *H1, *H2, *H3;      // hidden activations (H3 in mode 1 only)
+    bf16 *X;                 // the x tiles as multiplied (1 in the padding columns), 4 KB each
+    uint32_t *mask1, *mask2; // [tile][slice j][row r]: byte g of the word holds the flags (H_l > 0) of
+                             // columns 32 j + 8 g .. + 7 in the order of nz8
+    uint32_t *mask3;         // mode 2: the same for H3
+    float *dY;               // mode 2: dy per row (0 past M), [tiles * 128]
+    const float *target;     // mode 2
+    float inv_m;             // 1 / M
+    float *gw4, *gb4, *loss; // mode 2: accumulated (atomics)
+};
+constexpr size_t kTileBytes = 128 * kW * 2, kXTileBytes = 128 * kIn * 2, kMaskTileBytes = 8 * 128 * 4;
+
+// Nonzero flags of the eight BF16 values of q (four pairs, low half first)
+// as one byte: bit i for the low half of pair i, bit 4 + i for its high half.
+// Per half, bit 15 of (h & 0x7FFF) + 0x7FFF is set iff |h| != 0; for ReLU
+// outputs (never negative) that is h > 0.
+__device__ __forceinline__ uint32_t nz8(uint4 q)
+{
+    const uint32_t f0 = (q.x & 0x7FFF7FFFu) + 0x7FFF7FFFu, f1 = (q.y & 0x7FFF7FFFu) + 0x7FFF7FFFu,
+                   f2 = (q.z & 0x7FFF7FFFu) + 0x7FFF7FFFu, f3 = (q.w & 0x7FFF7FFFu) + 0x7FFF7FFFu;
+    const uint32_t x = ((f0 >> 15) & 0x10001u) | ((f1 >> 14) & 0x20002u) | ((f2 >> 13) & 0x40004u) |
+                       ((f3 >> 12) & 0x80008u);
+    return (x & 0xFu) | ((x >> 12) & 0xF0u);
+}
+// 0xFFFF in each half of the pair word w whose BF16 value is nonzero
+__device__ __forceinline__ uint32_t nz_halves(uint32_t w)
+{
+    return ((((w & 0x7FFF7FFFu) + 0x7FFF7FFFu) >> 15) & 0x10001u) * 0xFFFFu;
+}
+// (a0, a1) * (b0, b1), each lane an IEEE round-to-nearest product, rounded
+// to a BF16 pair (low half first)
+__device__ __forceinline__ uint32_t bf2_mul_bits(float a0, float a1, float b0, float b1)
+{
+    uint32_t d;
+    asm("{\n\t.reg .b64 a, b, p;\n\t.reg .f32 lo, hi;\n\t"
+        "mov.b64 a, {%1, %2};\n\tmov.b64 b, {%3, %4};\n\tmul.rn.f32x2 p, a, b;\n\t"
+        "mov.b64 {lo, hi}, p;\n\tcvt.rn.bf16x2.f32 %0, hi, lo;\n\t}"
+        : "=r"(d)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+    return d;
+}
+
+// kMode 0: inference (y only).  kMode 1: forward for training, also storing
+// H1, H2, H3, the x tiles and the ReLU masks of H1 and H2.  kMode 2: the
+// forward of a training step: H1, H2, the x tiles and the masks as in mode 1
+// (not H3, but its mask), then the head's backward: y, dy = 2 (y - t) / M
+// (stored), the loss and the gradients of b4 and w4 (H3^T dy on the tensor
+// cores, per tile).  D3 = dy w4 where H3 > 0 is not stored: the kernels that
+// use it rebuild it from dy and the mask.  The products and the head's forward arithmetic are those of mode
+// 0, so y is bit-identical in all three modes.
+template <int kMode>
 __global__ void __launch_bounds__(ws::kThreads, 1)
-    k_mlp_infer_ws(const bf16 *__restrict__ wh, const float *__restrict__ p, const bf16 *__restrict__ packed,
-                   const bf16 *__restrict__ x, long long M, const int32_t *__restrict__ count, float *__restrict__ y)
+    k_mlp_ws(const bf16 *__restrict__ wh, const float *__restrict__ p, const bf16 *__restrict__ packed,
+             const bf16 *__restrict__ x, long long M, const int32_t *__restrict__ count, float *__restrict__ y,
+             const TrainIO io)
 {
     // rows: M, or the first *count of them when a device count is given
     if (count) {
@@ -626,16 +628,19 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     const long long ntiles = (M + 127) / 128;
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full[ws::kStages], empty[ws::kStages], xfull[2], xempty[2], accfull[2], accempty[2],
-        aready[ws::kChunks], partfull[2], drain;
+        aready[ws::kChunks], partfull[2], g4ready, g4full, drain;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_fail;
     __shared__ volatile int s_slot[2 + ws::kEpiWarps];
+    __shared__ float s_gw4[kMode == 2 ? kW : 1], s_red[2];
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     unsigned char *sA = base + ws::oA, *sRing = base + ws::oRing, *sX = base + ws::oX, *sW1 = base + ws::oW1;
     float *sBias = reinterpret_cast<float *>(base + ws::oBias), *sW4 = reinterpret_cast<float *>(base + ws::oW4),
           *sPart = reinterpret_cast<float *>(base + ws::oPart);
-    const uint32_t aA = smem_u32(sA), aRing = smem_u32(sRing), aX = smem_u32(sX), aW1 = smem_u32(sW1);
+    unsigned char *sDY = base + ws::oDY;
+    const uint32_t aA = smem_u32(sA), aRing = smem_u32(sRing), aX = smem_u32(sX), aW1 = smem_u32(sW1),
+                   aDY = smem_u32(sDY);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0)
@@ -654,10 +659,16 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         }
         for (int j = 0; j < ws::kChunks; ++j)
             tc::mbar_init(&aready[j], 2 * 4 * 32);  // two slices, each written by the four warps of its group
+        tc::mbar_init(&g4ready, ws::kEpiWarps * 32);
+        tc::mbar_init(&g4full);
         tc::mbar_init(&drain);
         tc::fence_mbar_init();
         s_fail = 0;
+        s_red[0] = s_red[1] = 0.f;
     }
+    if (kMode == 2)
+        for (int i = tid; i < kW; i += ws::kThreads)
+            s_gw4[i] = 0.f;
     // W1, the biases and the head weights.  The first layer's bias rides in
     // the product: the x tiles carry 1 in their three padding columns (13,
     // 14, 15) and W1 gets b1 there, split into three BF16 parts whose sum is
@@ -699,6 +710,26 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             long long g = 0;  // chunks consumed
             bool ok = true;
             int it = 0;
+            // mode 2: the w4 gradient of the CTA's tile t, H3^T (dy in three
+            // BF16 parts): A = relu(D3 + b3) in the A buffer read MN-major
+            // (units M, rows K), B = the dy tile (MN-major, 16 columns), into
+            // columns 0..31 of that tile's head accumulator once the epilogue
+            // has read it (g4ready)
+            auto gw4_products = [&](int t) -> bool {
+                if (!tc::mbar_wait(&g4ready, (uint32_t)t & 1u))
+                    return false;
+                tc::fence_after();
+                const uint32_t dcol = tmem + (uint32_t)((3LL * t + 2) & 1) * 256u;
+                constexpr uint32_t id = tc::idesc(kIn, true);
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        tc::mma_i(dcol + (uint32_t)(h * kIn), tc::sdesc(aA + 8192u * s + 2048u * h, 4096, 128),
+                                  tc::sdesc(aDY + 512u * s, 256, 128), id, (uint32_t)(s != 0));
+                tc::commit(&g4full);
+                return true;
+            };
             for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
                 const int b = it & 1;
                 const long long q1 = 3LL * it;
@@ -711,6 +742,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                         tc::sdesc(aW1, 128, kIn * 16), 0u);
                 tc::commit(&xempty[b]);
                 tc::commit(&accfull[q1 & 1]);
+                if (kMode == 2 && it > 0 && !gw4_products(it - 1)) {
+                    ok = false;
+                    break;
+                }
                 for (int L = 1; L <= 2 && ok; ++L) {
                     const long long q = q1 + L;
                     const uint32_t dcol = tmem + (uint32_t)(q & 1) * 256u;
@@ -742,6 +777,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                 if (s_fail)
                     ok = false;
             }
+            if (kMode == 2 && ok && it > 0)
+                ok = gw4_products(it - 1);
             if (!ok)
                 s_fail = 1;
             // every product issued has finished before the tensor memory is freed
@@ -776,6 +813,9 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                     val.w = 0x3F803F80u;
                 }
                 *reinterpret_cast<uint4 *>(xb + tc::kmaj(r, h, kIn)) = val;
+                if constexpr (kMode != 0)
+                    *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(io.X) + tile * kXTileBytes +
+                                               tc::kmaj(r, h, kIn)) = val;
             }
             tc::fence_proxy_async();
             tc::mbar_arrive(&xfull[b]);
@@ -801,8 +841,9 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         const int quarter = warp & 3, group = (warp - 2) >> 2;
         const int r = quarter * 32 + lane;
         volatile int *slot = s_slot + warp;
-        long long pend = -1;  // tile whose head sums wait to be added (group 0)
+        long long pend = -1;  // tile whose head sums wait to be added (group 0; modes 0 and 1)
         int pend_it = 0;
+        float gw4acc = 0.f, gb4acc = 0.f, lossacc = 0.f;  // mode 2 (gw4acc: unit 128 group + r)
         auto flush_pending = [&]() -> bool {
             if (!ws::warp_wait(&partfull[pend_it & 1], (uint32_t)(pend_it >> 1) & 1u, slot, lane))
                 return false;
@@ -817,22 +858,26 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             return true;
         };
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        // this warp's slices group, group + kGroups, ... of the accumulator at
-        // tb; the next slice's load is in flight while f converts the current
-        auto each_slice = [&](uint32_t tb, auto &&f) {
-            uint32_t va[32], vb[32];
-            tc::tmem_ld32_async(tb + (uint32_t)(32 * group), va);
-            tc::tmem_wait_ld(va);
+        auto each_slice = [&](uint32_t tb, auto &&f) { ws::each_slice(tb, group, f); };
+        // relu(D + b3) of 8 columns (32 j + 8 g8 ..) as BF16 pairs
+        auto relu8 = [&](const uint32_t *u, int j, int g8, uint32_t(&pp)[4]) {
 #pragma unroll
-            for (int k = 0; k < ws::kSlices; ++k) {
-                const int j = group + k * ws::kGroups;
-                uint32_t(&cur)[32] = (k & 1) ? vb : va;
-                uint32_t(&nxt)[32] = (k & 1) ? va : vb;
-                if (k + 1 < ws::kSlices)
-                    tc::tmem_ld32_async(tb + (uint32_t)(32 * (j + ws::kGroups)), nxt);
-                f(cur, j);
-                if (k + 1 < ws::kSlices)
-                    tc::tmem_wait_ld(nxt);
+            for (int h = 0; h < 2; ++h) {
+                const float4 b = *reinterpret_cast<const float4 *>(sBias + 2 * kW + 32 * j + 8 * g8 + 4 * h);
+                const uint32_t *uu = u + 4 * h;
+                pp[2 * h] = bf2_bias_relu_bits(__uint_as_float(uu[0]), __uint_as_float(uu[1]), b.x, b.y);
+                pp[2 * h + 1] = bf2_bias_relu_bits(__uint_as_float(uu[2]), __uint_as_float(uu[3]), b.z, b.w);
+            }
+        };
+        // their products with w4 added to the head's four partial sums, each
+        // partial sum in column order
+        auto dot8 = [&](int j, int g8, const uint32_t(&pp)[4], float(&acc4)[4]) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float4 w = *reinterpret_cast<const float4 *>(sW4 + 32 * j + 8 * g8 + 4 * h);
+                const uint32_t p0 = pp[2 * h], p1 = pp[2 * h + 1];
+                fma2(acc4[0], acc4[1], __uint_as_float(p0 << 16), __uint_as_float(p0 & 0xffff0000u), w.x, w.y);
+                fma2(acc4[2], acc4[3], __uint_as_float(p1 << 16), __uint_as_float(p1 & 0xffff0000u), w.z, w.w);
             }
         };
         int it = 0;
@@ -851,9 +896,18 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                 if (L < 2) {
                     const float *bias = sBias + L * kW;
                     const bool with_bias = L == 1;  // the first layer's bias came with its product
+                    unsigned char *hg = nullptr;
+                    uint32_t *mk = nullptr;
+                    if constexpr (kMode != 0) {
+                        hg = reinterpret_cast<unsigned char *>(L == 0 ? io.H1 : io.H2) + tile * kTileBytes;
+                        mk = (L == 0 ? io.mask1 : io.mask2) + tile * (kMaskTileBytes / 4);
+                    }
                     // slice j (32 columns): bias, ReLU, BF16 into the A operand, then
-                    // its chunk's barrier; the next slice's load is in flight meanwhile
-                    auto slice = [&](const uint32_t(&v)[32], int j) {
+                    // its chunk's barrier, then (modes 1, 2) the copy to memory, whose
+                    // stores drain while the next products run; the next slice's
+                    // load is in flight meanwhile
+                    auto slice = [&](const uint32_t(&v)[32], int j, int) {
+                        uint4 keep[4];
 #pragma unroll
                         for (int gq = 0; gq < 4; ++gq) {
                             const uint32_t *u = v + 8 * gq;
@@ -872,29 +926,116 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                                 pk.w = bf2_relu_bits(__uint_as_float(u[6]), __uint_as_float(u[7]));
                             }
                             *reinterpret_cast<uint4 *>(sA + tc::kmaj(r, 32 * j + 8 * gq, kW)) = pk;
+                            keep[gq] = pk;
                         }
                         tc::fence_proxy_async();
                         tc::fence_before();
                         tc::mbar_arrive(&aready[j >> 1]);
+                        if constexpr (kMode != 0) {
+                            uint32_t bits = 0;
+#pragma unroll
+                            for (int gq = 0; gq < 4; ++gq) {
+                                *reinterpret_cast<uint4 *>(hg + tc::kmaj(r, 32 * j + 8 * gq, kW)) = keep[gq];
+                                bits |= nz8(keep[gq]) << (8 * gq);
+                            }
+                            mk[j * 128 + r] = bits;
+                        }
                     };
                     each_slice(tb, slice);
                     tc::mbar_arrive(&accempty[a]);
+                } else if constexpr (kMode == 2) {
+                    // head: relu(D + b3) (BF16) into the A buffer, the operand of
+                    // the w4 gradient (the third layer's products have read the
+                    // buffer), and its dot products with w4
+                    float acc4[4] = {0.f, 0.f, 0.f, 0.f};
+                    uint32_t *mk3 = io.mask3 + tile * (kMaskTileBytes / 4);
+                    auto dot = [&](const uint32_t(&v)[32], int j, int) {
+                        uint32_t bits = 0;
+#pragma unroll
+                        for (int g8 = 0; g8 < 4; ++g8) {
+                            uint32_t pp[4];
+                            relu8(v + 8 * g8, j, g8, pp);
+                            dot8(j, g8, pp, acc4);
+                            const uint4 h = make_uint4(pp[0], pp[1], pp[2], pp[3]);
+                            *reinterpret_cast<uint4 *>(sA + tc::kmaj(r, 32 * j + 8 * g8, kW)) = h;
+                            bits |= nz8(h) << (8 * g8);
+                        }
+                        mk3[j * 128 + r] = bits;
+                    };
+                    each_slice(tb, dot);
+                    float *part = sPart + (it & 1) * (ws::kGroups * 128);
+                    part[group * 128 + r] = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
+                    tc::mbar_arrive(&partfull[it & 1]);
+                    if (!ws::warp_wait(&partfull[it & 1], (uint32_t)(it >> 1) & 1u, slot, lane)) {
+                        ok = false;
+                        break;
+                    }
+                    float sum = 0.f;
+#pragma unroll
+                    for (int g2 = 0; g2 < ws::kGroups; ++g2)
+                        sum += part[g2 * 128 + r];
+                    const float yv = sum + b4;
+                    const long long m = tile * 128 + r;
+                    float dy = 0.f;
+                    if (m < M) {
+                        const float e = yv - io.target[m];
+                        dy = (2.f * e) * io.inv_m;
+                        if (group == 0) {
+                            y[m] = yv;
+                            lossacc += e * e * io.inv_m;
+                            gb4acc += dy;
+                        }
+                    }
+                    if (group == 0)
+                        io.dY[m] = dy;
+                    // row r of the dy tile: dy as three BF16 parts (their sum is
+                    // dy to 2^-27 relative: high part, then the high parts of the
+                    // remainders) in columns 0..2, zeros elsewhere
+                    {
+                        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                        if (group == 0) {
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(dy);
+                            const float r1 = dy - __bfloat162float(hi);
+                            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+                            const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+                            q.x = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(mid) << 16);
+                            q.y = (uint32_t)__bfloat16_as_ushort(lo);
+                        }
+                        *reinterpret_cast<uint4 *>(sDY + tc::kmaj(r, 8 * group, kIn)) = q;
+                    }
+                    tc::fence_proxy_async();
+                    tc::fence_before();
+                    tc::mbar_arrive(&g4ready);
+                    // this tile's w4 gradient: unit 128 group + r is lane r of half
+                    // `group` (columns 16 group .. 16 group + 2: the three parts)
+                    if (!ws::warp_wait(&g4full, (uint32_t)it & 1u, slot, lane)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    {
+                        float gv[32];
+                        tc::tmem_ld32(tb, gv);
+                        gw4acc += group ? (gv[16] + gv[17]) + gv[18] : (gv[0] + gv[1]) + gv[2];
+                    }
+                    tc::fence_before();
+                    tc::mbar_arrive(&accempty[a]);
                 } else {
                     // head: relu(D + b3) rounded to BF16 (as stored between layers), . w4,
-                    // in four partial sums
+                    // in four partial sums (mode 1 also stores relu(D + b3) as H3)
                     float acc4[4] = {0.f, 0.f, 0.f, 0.f};
-                    auto slice = [&](const uint32_t(&v)[32], int j) {
+                    unsigned char *h3 = nullptr;
+                    if constexpr (kMode == 1)
+                        h3 = reinterpret_cast<unsigned char *>(io.H3) + tile * kTileBytes;
+                    auto slice = [&](const uint32_t(&v)[32], int j, int) {
 #pragma unroll
-                        for (int gq = 0; gq < 8; ++gq) {
-                            const float4 b = *reinterpret_cast<const float4 *>(sBias + 2 * kW + 32 * j + 4 * gq);
-                            const float4 w = *reinterpret_cast<const float4 *>(sW4 + 32 * j + 4 * gq);
-                            const uint32_t *u = v + 4 * gq;
-                            const uint32_t p0 = bf2_bias_relu_bits(__uint_as_float(u[0]), __uint_as_float(u[1]), b.x, b.y);
-                            const uint32_t p1 = bf2_bias_relu_bits(__uint_as_float(u[2]), __uint_as_float(u[3]), b.z, b.w);
-                            fma2(acc4[0], acc4[1], __uint_as_float(p0 << 16), __uint_as_float(p0 & 0xffff0000u), w.x,
-                                 w.y);
-                            fma2(acc4[2], acc4[3], __uint_as_float(p1 << 16), __uint_as_float(p1 & 0xffff0000u), w.z,
-                                 w.w);
+                        for (int g8 = 0; g8 < 4; ++g8) {
+                            uint32_t pp[4];
+                            relu8(v + 8 * g8, j, g8, pp);
+                            dot8(j, g8, pp, acc4);
+                            if constexpr (kMode == 1)
+                                *reinterpret_cast<uint4 *>(h3 + tc::kmaj(r, 32 * j + 8 * g8, kW)) =
+                                    make_uint4(pp[0], pp[1], pp[2], pp[3]);
                         }
                     };
                     each_slice(tb, slice);
@@ -929,9 +1070,33 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                         y[tile * 128 + r] = __int_as_float(0x7fc00000);
             }
         }
+        if constexpr (kMode == 2) {
+            // the CTA's head gradients: one unit per thread, then the groups' rows
+            s_gw4[128 * group + r] = gw4acc;
+            if (group == 0) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    gb4acc += __shfl_xor_sync(0xffffffffu, gb4acc, o);
+                    lossacc += __shfl_xor_sync(0xffffffffu, lossacc, o);
+                }
+                if (lane == 0) {
+                    atomicAdd(&s_red[0], gb4acc);
+                    atomicAdd(&s_red[1], lossacc);
+                }
+            }
+        }
     }
     tc::fence_before();
     __syncthreads();
+    if constexpr (kMode == 2) {
+        for (int i = tid; i < kW; i += ws::kThreads)
+            atomicAdd(io.gw4 + i, s_gw4[i]);
+        if (tid == 0) {
+            atomicAdd(io.gb4, s_red[0]);
+            if (io.loss)
+                atomicAdd(io.loss, s_fail ? __int_as_float(0x7fc00000) : s_red[1]);
+        }
+    }
     if (warp == 0) {
         tc::fence_after();
         tc::tmem_dealloc(tmem, ws::kCols);
@@ -939,94 +1104,532 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// output layer, loss, bias gradients, Adam, initialisation
+// Input gradients of the hidden layers (after mode 2 of k_mlp_ws): per
+// 128-row tile D3 = dy w4 where H3 > 0 (FP32 product rounded to BF16, built
+// from the stored dy and mask), D2 = (D3 W3) where H2 > 0 and D1 = (D2 W2)
+// where H1 > 0 (FP32 sums rounded to BF16); D2 and D1 are stored packed.
+// Persistent and warp-specialised:
+//   warp 0 (one thread)  issues the products, B = the packed W3^T and W2^T
+//                        chunks (K = the layer's output units);
+//   warp 1 (one thread)  producer: the weight chunks through a 3-stage ring;
+//   warps 2..9           epilogue: D3 of a tile into its A buffer (two
+//                        buffers: tile i uses i % 2; D3 of the next tile is
+//                        built while the products D2 W2 of this one run),
+//                        then mask and round: D2 to the A buffer (each
+//                        chunk's barrier releases its products) and to
+//                        memory, D1 to memory.
 // ---------------------------------------------------------------------------
-constexpr int kHeadRows = 64;  // rows per CTA of k_head (8 warps x 8 rows)
+namespace dg {
+constexpr int kStages = 3, kEpiWarps = 8, kGroups = kEpiWarps / 4, kSlices = 8 / kGroups,
+              kThreads = 32 * (2 + kEpiWarps);
+constexpr uint32_t oA = 0, oRing = 2 * ws::kBytesA, kEnd = oRing + kStages * ws::kBytesChunk;
+constexpr size_t kSmem = 1024 + (size_t)kEnd;
+static_assert(kSmem + 2048 <= 227 * 1024, "shared memory");
+}  // namespace dg
 
-// y[m] = H3[m] . w4 + b4.  With a target: loss += (y - t)^2 / M,
-// dy = 2 (y - t) / M, dZ3[m][k] = dy * w4[k] where H3[m][k] > 0, and the
-// gradients of w4 and b4 accumulate (per CTA in shared memory, then atomics).
-__global__ void __launch_bounds__(256)
-    k_head(const bf16 *__restrict__ H3, const bf16 *__restrict__ w4h, const float *__restrict__ b4, long long M,
-           float *__restrict__ y, const float *__restrict__ target, bf16 *__restrict__ dZ3, float *__restrict__ gw4,
-           float *__restrict__ gb4, float *__restrict__ loss, float inv_m)
+// BF16 pair of (lo, hi) rounded to nearest even, each half kept where its
+// flag is set (flags: bit 0 for lo, bit 16 for hi) and 0 elsewhere
+__device__ __forceinline__ uint32_t bf2_masked(uint32_t lo, uint32_t hi, uint32_t flags)
 {
-    __shared__ float s_gw[kW];
-    __shared__ float s_gb, s_loss;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < kW; k += blockDim.x)
-        s_gw[k] = 0.f;
-    if (threadIdx.x == 0)
-        s_gb = s_loss = 0.f;
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(hi)), "f"(__uint_as_float(lo)));
+    return d & ((flags & 0x10001u) * 0xFFFFu);
+}
+// the flags of byte g of a mask word (nz8 order) for pair i at bits i and 16 + i
+__device__ __forceinline__ uint32_t pair_flags(uint32_t bits, int g)
+{
+    const uint32_t mb = (bits >> (8 * g)) & 0xFFu;
+    return (mb & 0xFu) | ((mb & 0xF0u) << 12);
+}
+// D3 of 8 columns (32 j + 8 g ..) of a row: dy w4 (FP32 products rounded to
+// BF16) where the mask word's flags are set
+__device__ __forceinline__ uint4 d3_8(float dy, uint32_t bits, int g, const float *w)
+{
+    const uint32_t fl = pair_flags(bits, g);
+    const float4 w0 = *reinterpret_cast<const float4 *>(w), w1 = *reinterpret_cast<const float4 *>(w + 4);
+    return make_uint4(bf2_mul_bits(dy, dy, w0.x, w0.y) & ((fl & 0x10001u) * 0xFFFFu),
+                      bf2_mul_bits(dy, dy, w0.z, w0.w) & (((fl >> 1) & 0x10001u) * 0xFFFFu),
+                      bf2_mul_bits(dy, dy, w1.x, w1.y) & (((fl >> 2) & 0x10001u) * 0xFFFFu),
+                      bf2_mul_bits(dy, dy, w1.z, w1.w) & (((fl >> 3) & 0x10001u) * 0xFFFFu));
+}
+
+__global__ void __launch_bounds__(dg::kThreads, 1)
+    k_mlp_dgrad(const bf16 *__restrict__ packedT, const bf16 *__restrict__ w4h, const float *__restrict__ dY,
+                const uint32_t *__restrict__ mask3, const uint32_t *__restrict__ mask2,
+                const uint32_t *__restrict__ mask1, bf16 *__restrict__ D2, bf16 *__restrict__ D1, long long ntiles,
+                float *__restrict__ fail_sink)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t full[dg::kStages], empty[dg::kStages], accfull[2], accempty[2], d3ready[ws::kChunks],
+        aready[ws::kChunks], drain;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_fail;
+    __shared__ volatile int s_slot[2 + dg::kEpiWarps];
+    __shared__ __align__(16) float sW4[kW];
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    unsigned char *sA = base + dg::oA, *sRing = base + dg::oRing;
+    const uint32_t aA = smem_u32(sA), aRing = smem_u32(sRing);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0)
+        tc::tmem_alloc(&s_tmem, ws::kCols);
+    if (tid == 0) {
+        for (int i = 0; i < dg::kStages; ++i) {
+            tc::mbar_init(&full[i]);
+            tc::mbar_init(&empty[i]);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&accfull[i]);
+            tc::mbar_init(&accempty[i], dg::kEpiWarps * 32);
+        }
+        for (int j = 0; j < ws::kChunks; ++j) {
+            tc::mbar_init(&d3ready[j], 2 * 4 * 32);  // two slices, each written by the four warps of its group
+            tc::mbar_init(&aready[j], 2 * 4 * 32);
+        }
+        tc::mbar_init(&drain);
+        tc::fence_mbar_init();
+        s_fail = 0;
+    }
+    for (int i = tid; i < kW; i += dg::kThreads)
+        sW4[i] = __bfloat162float(w4h[i]);
+    tc::fence_before();
     __syncthreads();
-    float w[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        w[j] = __bfloat162float(w4h[lane * 8 + j]);
-    float gw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    float gb = 0.f, ls = 0.f;
-    for (int i = warp; i < kHeadRows; i += blockDim.x / 32) {
-        const long long m = (long long)blockIdx.x * kHeadRows + i;
-        if (m >= M)
-            break;
-        const uint4 q = *reinterpret_cast<const uint4 *>(H3 + m * kW + lane * 8);
-        const bf16 *h = reinterpret_cast<const bf16 *>(&q);
-        float hv[8], s = 0.f;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            hv[j] = __bfloat162float(h[j]);
-            s = fmaf(hv[j], w[j], s);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-        const float yv = s + b4[0];
-        if (lane == 0)
-            y[m] = yv;
-        if (target) {
-            const float e = yv - target[m];
-            const float dy = 2.f * e * inv_m;
-            ls += e * e * inv_m;
-            gb += dy;
-            bf16 dz[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                dz[j] = __float2bfloat16_rn(hv[j] > 0.f ? dy * w[j] : 0.f);
-                gw[j] = fmaf(dy, hv[j], gw[j]);
-            }
-            *reinterpret_cast<uint4 *>(dZ3 + m * kW + lane * 8) = *reinterpret_cast<const uint4 *>(dz);
-        }
-    }
-    if (target) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            atomicAdd(&s_gw[lane * 8 + j], gw[j]);
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0) {
+        // ---- products: tile it uses A buffer it % 2; q = 2 it + layer ------
         if (lane == 0) {
-            atomicAdd(&s_gb, gb);
-            atomicAdd(&s_loss, ls);
+            long long g = 0;
+            bool ok = true;
+            int it = 0;
+            for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+                const int b = it & 1;
+                for (int L = 0; L < 2 && ok; ++L) {
+                    const long long q = 2LL * it + L;
+                    const uint32_t dcol = tmem + (uint32_t)(q & 1) * 256u;
+                    if (q >= 2 && !tc::mbar_wait(&accempty[q & 1], (uint32_t)((q - 2) >> 1) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    for (int c = 0; c < ws::kChunks; ++c, ++g) {
+                        const int st = (int)(g % dg::kStages);
+                        if (!tc::mbar_wait(&full[st], (uint32_t)(g / dg::kStages) & 1u) ||
+                            !tc::mbar_wait(L == 0 ? &d3ready[c] : &aready[c], (uint32_t)it & 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after();
+#pragma unroll
+                        for (int kk = 0; kk < tc::kKC / 16; ++kk) {
+                            const int k0 = tc::kKC * c + 16 * kk;
+                            tc::mma(dcol, tc::sdesc(aA + (uint32_t)b * ws::kBytesA + (uint32_t)(k0 / 8) * 128u, 128, kW * 16),
+                                    tc::sdesc(aRing + (uint32_t)(st * ws::kBytesChunk + kk * 256), 128, tc::kKC * 16),
+                                    (uint32_t)(c | kk));
+                        }
+                        tc::commit(&empty[st]);
+                    }
+                    if (ok)
+                        tc::commit(&accfull[q & 1]);
+                }
+                if (s_fail)
+                    ok = false;
+            }
+            if (!ok)
+                s_fail = 1;
+            tc::commit(&drain);
+            (void)tc::mbar_wait(&drain, 0);
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < kW; k += blockDim.x)
-            atomicAdd(gw4 + k, s_gw[k]);
-        if (threadIdx.x == 0) {
-            atomicAdd(gb4, s_gb);
-            if (loss)
-                atomicAdd(loss, s_loss);
+    } else if (warp == 1) {
+        // ---- producer ------------------------------------------------------
+        if (lane == 0) {
+            long long g = 0;
+            bool ok = true;
+            for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                for (int c = 0; c < 2 * ws::kChunks; ++c, ++g) {
+                    const int st = (int)(g % dg::kStages);
+                    if (s_fail ||
+                        (g >= dg::kStages && !tc::mbar_wait(&empty[st], (uint32_t)(g / dg::kStages - 1) & 1u))) {
+                        s_fail = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::bulk_load(sRing + st * ws::kBytesChunk, packedT + (long long)c * (kW * tc::kKC),
+                                  ws::kBytesChunk, &full[st]);
+                }
+            }
+            // copies still in flight are among the last kStages issued
+            for (long long c = g > dg::kStages ? g - dg::kStages : 0; c < g; ++c)
+                (void)tc::mbar_wait(&full[c % dg::kStages], (uint32_t)(c / dg::kStages) & 1u);
         }
+    } else {
+        // ---- epilogue ------------------------------------------------------
+        const int quarter = warp & 3, group = (warp - 2) >> 2;
+        const int r = quarter * 32 + lane;
+        volatile int *slot = s_slot + warp;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        // dy and the H3 mask words of tile t for this thread's row and slices
+        float ndy = 0.f;
+        uint32_t nm3[dg::kSlices];
+        auto fetch_d3 = [&](long long t) {
+            ndy = dY[t * 128 + r];
+#pragma unroll
+            for (int k = 0; k < dg::kSlices; ++k)
+                nm3[k] = mask3[t * (kMaskTileBytes / 4) + (group + k * dg::kGroups) * 128 + r];
+        };
+        // D3 of the fetched tile into A buffer b, each slice's chunk barrier once written
+        auto build_d3 = [&](int b) {
+            unsigned char *sa = sA + b * ws::kBytesA;
+#pragma unroll
+            for (int k = 0; k < dg::kSlices; ++k) {
+                const int j = group + k * dg::kGroups;
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    *reinterpret_cast<uint4 *>(sa + tc::kmaj(r, 32 * j + 8 * g, kW)) =
+                        d3_8(ndy, nm3[k], g, sW4 + 32 * j + 8 * g);
+                tc::fence_proxy_async();
+                tc::fence_before();
+                tc::mbar_arrive(&d3ready[j >> 1]);
+            }
+        };
+        bool ok = true;
+        int it = 0;
+        long long tile = blockIdx.x;
+        if (tile < ntiles) {
+            fetch_d3(tile);
+            build_d3(0);
+        }
+        for (; tile < ntiles; tile += gridDim.x, ++it) {
+            const int b = it & 1;
+            const bool more = tile + gridDim.x < ntiles;
+            uint32_t m2[dg::kSlices], m1[dg::kSlices];
+#pragma unroll
+            for (int k = 0; k < dg::kSlices; ++k) {
+                const long long o = tile * (kMaskTileBytes / 4) + (group + k * dg::kGroups) * 128 + r;
+                m2[k] = mask2[o];
+                m1[k] = mask1[o];
+            }
+            if (more)
+                fetch_d3(tile + gridDim.x);
+            for (int L = 0; L < 2 && ok; ++L) {
+                const long long q = 2LL * it + L;
+                const int a = (int)(q & 1);
+                if (!ws::warp_wait(&accfull[a], (uint32_t)(q >> 1) & 1u, slot, lane)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t tb = tmem + (uint32_t)a * 256u + lane_off;
+                unsigned char *dst = reinterpret_cast<unsigned char *>(L == 0 ? D2 : D1) + tile * kTileBytes;
+                unsigned char *sa = sA + b * ws::kBytesA;
+                auto slice = [&](const uint32_t(&v)[32], int j, int k) {
+                    const uint32_t bits = L == 0 ? m2[k] : m1[k];
+                    uint4 keep[4];
+#pragma unroll
+                    for (int gq = 0; gq < 4; ++gq) {
+                        const uint32_t *u = v + 8 * gq;
+                        const uint32_t fl = pair_flags(bits, gq);
+                        keep[gq].x = bf2_masked(u[0], u[1], fl);
+                        keep[gq].y = bf2_masked(u[2], u[3], fl >> 1);
+                        keep[gq].z = bf2_masked(u[4], u[5], fl >> 2);
+                        keep[gq].w = bf2_masked(u[6], u[7], fl >> 3);
+                        if (L == 0)
+                            *reinterpret_cast<uint4 *>(sa + tc::kmaj(r, 32 * j + 8 * gq, kW)) = keep[gq];
+                    }
+                    if (L == 0) {
+                        // the A operand first: the next products start while the
+                        // copy to memory drains
+                        tc::fence_proxy_async();
+                        tc::fence_before();
+                        tc::mbar_arrive(&aready[j >> 1]);
+                    }
+#pragma unroll
+                    for (int gq = 0; gq < 4; ++gq)
+                        *reinterpret_cast<uint4 *>(dst + tc::kmaj(r, 32 * j + 8 * gq, kW)) = keep[gq];
+                };
+                ws::each_slice<dg::kGroups>(tb, group, slice);
+                tc::fence_before();
+                tc::mbar_arrive(&accempty[a]);
+                // the next tile's D3 goes into the other buffer while this tile's
+                // second products run (its last reader, the products of the tile
+                // before, finished before that tile's D1 was read)
+                if (L == 0 && more)
+                    build_d3(b ^ 1);
+            }
+            if (!ok || ws::warp_uniform(s_fail, slot, lane))
+                break;
+        }
+        if (!ok)
+            s_fail = 1;
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0 && s_fail)
+        atomicAdd(fail_sink, __int_as_float(0x7fc00000));
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, ws::kCols);
     }
 }
 
-// grad_b[n] += sum_m dZ[m][n] over a block of rows
-__global__ void __launch_bounds__(256) k_colsum(const bf16 *__restrict__ dZ, long long M, float *__restrict__ gb)
+// ---------------------------------------------------------------------------
+// Weight and bias gradients (after k_mlp_dgrad): grad W_l += D_l^T H_{l-1}
+// and grad b_l += the column sums of D_l, H_0 the x tiles as multiplied.  One
+// CTA per job: a layer (3, 2 or 1) and a contiguous range of tiles.  Both
+// operands are the packed tiles read as MN-major (transposed) operands: the
+// rows of the batch are K, D_l's columns (output units) M, H's columns N.
+// Per 32-row piece, two k16 steps of two M = 128 products (output units
+// 0..127 and 128..255) into two FP32 accumulators of 256 columns (16 for the
+// first layer) in tensor memory.  Roles:
+//   warp 0 (one thread)  the products;
+//   warp 1 (one thread)  producer: the D and H (or x) pieces through a
+//                        6-stage ring, two bulk copies on one barrier (the H2
+//                        piece alone for the third layer);
+//   warps 2..9           third layer: build each D3 piece in the ring from
+//                        dy, the mask of H3 and w4 (warp w: columns 32 w ..);
+//                        all layers: while the products run, the column sums
+//                        of each D piece from shared memory (FP32); at the
+//                        end the accumulators (tcgen05.ld) into the gradient
+//                        with vector atomics.
+// The padding columns 13..15 of the first layer's gradient are not written.
+// ---------------------------------------------------------------------------
+namespace wg {
+constexpr int kStages = 6, kSumWarps = 8, kThreads = 32 * (2 + kSumWarps);
+constexpr uint32_t kPiece = 32 * kW * 2;   // 32 rows of a packed tile (16 KB)
+constexpr uint32_t kXPiece = 32 * kIn * 2; // 32 rows of a packed x tile (1 KB)
+constexpr uint32_t kDy = 2 * kPiece, kMask = kDy + 32 * 4;  // third layer: dy and mask words of a piece
+constexpr uint32_t kStage = kMask + 8 * 32 * 4;
+constexpr size_t kSmem = 1024 + (size_t)kStages * kStage;
+static_assert(kSmem + 1024 <= 227 * 1024, "shared memory");
+}  // namespace wg
+
+struct WgradArgs {
+    const float *dY;          // dy per row
+    const uint32_t *mask3;    // ReLU mask of H3
+    const bf16 *w4h;          // BF16 head weights
+    const bf16 *D2, *D1, *H2, *H1, *X;
+    float *g;         // gradient vector (parameter order)
+    long long ntiles;
+    int jobs3, jobs2, jobs1;  // jobs per layer, each at most ntiles
+};
+
+__global__ void __launch_bounds__(wg::kThreads, 1) k_mlp_wgrad(const WgradArgs A)
 {
-    const int n = threadIdx.x;  // blockDim = kW
-    const long long m0 = (long long)blockIdx.x * 256, m1 = min(M, m0 + 256);
-    float s = 0.f;
-    for (long long m = m0; m < m1; ++m)
-        s += __bfloat162float(dZ[m * kW + n]);
-    atomicAdd(gb + n, s);
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t full[wg::kStages], empty[wg::kStages], dfull[wg::kStages], accfull, drain;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_fail;
+    __shared__ volatile int s_slot[2 + wg::kSumWarps];
+    __shared__ __align__(16) float sW4[kW];
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    const uint32_t aS = smem_u32(base);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    int layer, j, J;
+    if ((int)blockIdx.x < A.jobs3) {
+        layer = 3, j = blockIdx.x, J = A.jobs3;
+    } else if ((int)blockIdx.x < A.jobs3 + A.jobs2) {
+        layer = 2, j = blockIdx.x - A.jobs3, J = A.jobs2;
+    } else {
+        layer = 1, j = blockIdx.x - A.jobs3 - A.jobs2, J = A.jobs1;
+    }
+    const long long t0 = A.ntiles * j / J, t1 = A.ntiles * (j + 1) / J;
+    const long long np = 4 * (t1 - t0);  // 32-row pieces
+    const bool wide = layer != 1, build = layer == 3;  // build: D3 made in shared memory
+    const unsigned char *Dp = reinterpret_cast<const unsigned char *>(layer == 2 ? A.D2 : A.D1);
+    const unsigned char *Hp = reinterpret_cast<const unsigned char *>(layer == 3 ? A.H2 : layer == 2 ? A.H1 : A.X);
+    const uint32_t hbytes = wide ? wg::kPiece : wg::kXPiece;
+    const size_t htile = wide ? kTileBytes : kXTileBytes;
+    float *gW = A.g + (layer == 3 ? oW3 : layer == 2 ? oW2 : oW1);
+    float *gb = A.g + (layer == 3 ? oB3 : layer == 2 ? oB2 : oB1);
+
+    if (warp == 0)
+        tc::tmem_alloc(&s_tmem, ws::kCols);
+    if (tid == 0) {
+        for (int i = 0; i < wg::kStages; ++i) {
+            // full: the copies, or for the third layer the eight builders (who
+            // wait for the copies on dfull first)
+            tc::mbar_init(&full[i], build ? wg::kSumWarps : 1);
+            tc::mbar_init(&empty[i], 1 + wg::kSumWarps);  // the products' commit and the summing warps
+            tc::mbar_init(&dfull[i]);
+        }
+        tc::mbar_init(&accfull);
+        tc::mbar_init(&drain);
+        tc::fence_mbar_init();
+        s_fail = 0;
+    }
+    for (int i = tid; i < kW; i += wg::kThreads)
+        sW4[i] = __bfloat162float(A.w4h[i]);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0) {
+        // ---- products ------------------------------------------------------
+        if (lane == 0 && np > 0) {
+            const uint32_t ncol = wide ? kW : kIn, id = tc::idesc((int)ncol, true);
+            for (long long p = 0; p < np; ++p) {
+                const int st = (int)(p % wg::kStages);
+                if (!tc::mbar_wait(&full[st], (uint32_t)(p / wg::kStages) & 1u)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t sa = aS + (uint32_t)st * wg::kStage, sb = sa + wg::kPiece;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    // K = rows: 8-row groups 4096 bytes apart in D and H, 256 in x;
+                    // M (N) = units: 8-unit groups 128 bytes apart
+                    const uint64_t db = wide ? tc::sdesc(sb + 8192u * s, 4096, 128) : tc::sdesc(sb + 512u * s, 256, 128);
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+                        tc::mma_i(tmem + (uint32_t)a * ncol, tc::sdesc(sa + 8192u * s + 2048u * a, 4096, 128), db, id,
+                                  (uint32_t)((p | s) != 0));
+                }
+                tc::commit(&empty[st]);
+            }
+            tc::commit(&accfull);
+            tc::commit(&drain);
+            (void)tc::mbar_wait(&drain, 0);
+        }
+    } else if (warp == 1) {
+        // ---- producer ------------------------------------------------------
+        if (lane == 0) {
+            long long p = 0;
+            for (; p < np; ++p) {
+                const int st = (int)(p % wg::kStages);
+                if (s_fail ||
+                    (p >= wg::kStages && !tc::mbar_wait(&empty[st], (uint32_t)(p / wg::kStages - 1) & 1u))) {
+                    s_fail = 1;
+                    break;
+                }
+                const long long tile = t0 + p / 4;
+                const int pc = (int)(p % 4);
+                unsigned char *dst = base + (size_t)st * wg::kStage;
+                if (build) {
+                    // the H2 piece, the piece's dy and its mask words (eight runs of 32)
+                    uint64_t *bar = &dfull[st];
+                    tc::expect_tx(bar, hbytes + 32 * 4 + 8 * 32 * 4);
+                    tc::bulk_copy(dst + wg::kPiece, Hp + tile * htile + (size_t)pc * hbytes, hbytes, bar);
+                    tc::bulk_copy(dst + wg::kDy, A.dY + tile * 128 + pc * 32, 32 * 4, bar);
+                    for (int j = 0; j < 8; ++j)
+                        tc::bulk_copy(dst + wg::kMask + j * 128,
+                                      A.mask3 + tile * (kMaskTileBytes / 4) + j * 128 + pc * 32, 32 * 4, bar);
+                } else {
+                    tc::expect_tx(&full[st], wg::kPiece + hbytes);
+                    tc::bulk_copy(dst, Dp + tile * kTileBytes + (size_t)pc * wg::kPiece, wg::kPiece, &full[st]);
+                    tc::bulk_copy(dst + wg::kPiece, Hp + tile * htile + (size_t)pc * hbytes, hbytes, &full[st]);
+                }
+            }
+            for (long long c = p > wg::kStages ? p - wg::kStages : 0; c < p; ++c)
+                (void)tc::mbar_wait(build ? &dfull[c % wg::kStages] : &full[c % wg::kStages],
+                                    (uint32_t)(c / wg::kStages) & 1u);
+        }
+    } else {
+        // ---- column sums, then the accumulators ----------------------------
+        const int w = warp - 2, ri = lane & 7, kg = (lane >> 3) + 4 * w;  // row in group, column group
+        volatile int *slot = s_slot + warp;
+        float cs[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            cs[i] = 0.f;
+        bool ok = true;
+        for (long long p = 0; p < np; ++p) {
+            const int st = (int)(p % wg::kStages);
+            unsigned char *sa = base + (size_t)st * wg::kStage;
+            if (build) {
+                // D3 rows 32 pc .. of the tile, columns 32 w .. (this warp's
+                // slice), from the piece's dy and mask words in the stage (the
+                // producer copies them once the slot's products and readers
+                // are done)
+                if (!ws::warp_wait(&dfull[st], (uint32_t)(p / wg::kStages) & 1u, slot, lane)) {
+                    ok = false;
+                    break;
+                }
+                const float dy = reinterpret_cast<const float *>(sa + wg::kDy)[lane];
+                const uint32_t bits = reinterpret_cast<const uint32_t *>(sa + wg::kMask)[w * 32 + lane];
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    *reinterpret_cast<uint4 *>(sa + tc::kmaj(lane, 32 * w + 8 * g, kW)) =
+                        d3_8(dy, bits, g, sW4 + 32 * w + 8 * g);
+                __syncwarp();
+            } else if (!ws::warp_wait(&full[st], (uint32_t)(p / wg::kStages) & 1u, slot, lane)) {
+                ok = false;
+                break;
+            }
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(sa + g * 4096 + kg * 128 + ri * 16);
+                const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    cs[2 * i] += __uint_as_float(u[i] << 16);
+                    cs[2 * i + 1] += __uint_as_float(u[i] & 0xffff0000u);
+                }
+            }
+            if (build) {
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0)
+                    tc::mbar_arrive(&full[st]);
+            }
+            __syncwarp();
+            if (lane == 0)
+                tc::mbar_arrive(&empty[st]);
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                cs[i] += __shfl_xor_sync(0xffffffffu, cs[i], o);
+        if (ok && ri == 0)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                atomicAdd(gb + kg * 8 + i, cs[i]);
+        if (ok && np > 0) {
+            ok = ws::warp_wait(&accfull, 0, slot, lane) && !ws::warp_uniform(s_fail, slot, lane);
+            if (ok) {
+                tc::fence_after();
+                const int quarter = warp & 3, half = w >> 2;
+                const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+                const int n = 128 * half + 32 * quarter + lane;  // output unit of this lane
+                if (wide) {
+                    for (int c = 0; c < kW / 32; ++c) {
+                        float v[32];
+                        tc::tmem_ld32(tl + (uint32_t)(half * kW + 32 * c), v);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            atomicAdd(reinterpret_cast<float4 *>(gW + (long long)n * kW + 32 * c + 4 * i),
+                                      make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
+                    }
+                } else {
+                    float v[32];  // columns 0..15: output units 0..127, 16..31: 128..255
+                    tc::tmem_ld32(tl, v);
+#pragma unroll
+                    for (int k = 0; k < PCDF_MLP_IN; ++k)
+                        atomicAdd(gW + n * kIn + k, half ? v[16 + k] : v[k]);
+                }
+            }
+        }
+        if (!ok)
+            s_fail = 1;
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0 && s_fail)
+        atomicAdd(A.g + oB4, __int_as_float(0x7fc00000));
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, ws::kCols);
+    }
 }
 
+// ---------------------------------------------------------------------------
+// Adam, initialisation
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ long long half_index(long long i)
 {
     if (i < oB1)
@@ -1103,7 +1706,7 @@ __global__ void k_init(float *__restrict__ p, float *__restrict__ mo, float *__r
 // ---------------------------------------------------------------------------
 struct State {
     float *p, *m, *v, *g;
-    bf16 *h, *pk;  // BF16 weights; W2 and W3 packed for the tensor-core kernel
+    bf16 *h, *pk;  // BF16 weights; W2, W3, W3^T, W2^T packed for the tensor-core kernels
     explicit State(void *s)
     {
         char *b = (char *)s;
@@ -1116,104 +1719,110 @@ struct State {
     }
 };
 
-// refreshes the packed copy of W2 and W3 after the BF16 weights change
+// refreshes the packed copies of the hidden weights after the BF16 weights change
 __global__ void k_pack_hidden(const bf16 *__restrict__ wh, bf16 *__restrict__ packed);
 cudaError_t launch_pack(const State &S, cudaStream_t st)
 {
-    k_pack_hidden<<<(2 * kW * (kW / 8) + 255) / 256, 256, 0, st>>>(S.h, S.pk);
+    k_pack_hidden<<<(4 * kW * (kW / 8) + 255) / 256, 256, 0, st>>>(S.h, S.pk);
     return cudaGetLastError();
 }
 
-// Workspace sections (each 256-byte aligned, in this order): the stored
-// activations H1, H2, H3 and the stored pre-activation gradients D3, D2, D1
-// (BF16 [M][256] each); see pcdf_mlp_backward.
+// Workspace sections, in this order, for T = ceil(M / 128) tiles: H1, H2, H3,
+// D2, D1 (T x 64 KB each, tiles packed as in TrainIO), the x tiles as
+// multiplied (T x 4 KB), the ReLU masks of H1, H2 and H3 (T x 4 KB each) and
+// dy (T x 512 bytes); see pcdf_mlp_backward.
 struct Acts {
-    bf16 *H1, *H2, *H3, *D3, *D2, *D1;
+    bf16 *H1, *H2, *H3, *D2, *D1, *X;
+    uint32_t *mask1, *mask2, *mask3;
+    float *dY;
 };
 
-size_t ws_bytes(long long M) { return 6 * align_up((size_t)M * kW * 2); }
+size_t ws_bytes(long long M)
+{
+    const size_t T = (size_t)((M + 127) / 128);
+    return T * (5 * kTileBytes + kXTileBytes + 3 * kMaskTileBytes + 128 * sizeof(float));
+}
 
 Acts carve(void *ws, long long M)
 {
     char *b = (char *)ws;
-    const size_t a = align_up((size_t)M * kW * 2);
+    const size_t T = (size_t)((M + 127) / 128), a = T * kTileBytes, m = T * kMaskTileBytes;
     Acts r;
     r.H1 = (bf16 *)b;
     r.H2 = (bf16 *)(b + a);
     r.H3 = (bf16 *)(b + 2 * a);
-    r.D3 = (bf16 *)(b + 3 * a);
-    r.D2 = (bf16 *)(b + 4 * a);
-    r.D1 = (bf16 *)(b + 5 * a);
+    r.D2 = (bf16 *)(b + 3 * a);
+    r.D1 = (bf16 *)(b + 4 * a);
+    r.X = (bf16 *)(b + 5 * a);
+    char *mk = b + 5 * a + T * kXTileBytes;
+    r.mask1 = (uint32_t *)mk;
+    r.mask2 = (uint32_t *)(mk + m);
+    r.mask3 = (uint32_t *)(mk + 2 * m);
+    r.dY = (float *)(mk + 3 * m);
     return r;
 }
 
-GemmArgs fwd_args(const bf16 *X, int K, const bf16 *W, const float *bias, bf16 *out, long long M)
+cudaError_t sm_count(int *nsm)
 {
-    GemmArgs g;
-    std::memset(&g, 0, sizeof(g));
-    g.A = X;
-    g.lda = K;
-    g.B = W;
-    g.ldb = K;
-    g.M = (int)M;
-    g.N = kW;
-    g.K = K;
-    g.k_split = K;
-    g.bias = bias;
-    g.out_h = out;
-    g.ldo = kW;
-    return g;
-}
-
-int forward(const State &S, const bf16 *x, long long M, const Acts &A, cudaStream_t st)
-{
-    cudaError_t e = gemm<false, false, kBiasRelu>(fwd_args(x, kIn, S.h + hW1, S.p + oB1, A.H1, M), 1, st);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
-        e = gemm<false, false, kBiasRelu>(fwd_args(A.H1, kW, S.h + hW2, S.p + oB2, A.H2, M), 1, st);
+        e = cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, dev);
+    return e;
+}
+
+// the persistent forward kernel: one CTA per SM (or per tile, if fewer)
+template <int kMode>
+cudaError_t launch_ws(const State &S, const bf16 *x, long long M, const int32_t *count, float *y, const TrainIO &io,
+                      cudaStream_t st)
+{
+    int nsm = 0;
+    cudaError_t e = sm_count(&nsm);
     if (e == cudaSuccess)
-        e = gemm<false, false, kBiasRelu>(fwd_args(A.H2, kW, S.h + hW3, S.p + oB3, A.H3, M), 1, st);
-    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp forward");
+        e = cudaFuncSetAttribute(k_mlp_ws<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws::kSmem);
+    if (e != cudaSuccess)
+        return e;
+    const long long ntiles = (M + 127) / 128;
+    k_mlp_ws<kMode><<<(unsigned)(ntiles < nsm ? ntiles : nsm), ws::kThreads, ws::kSmem, st>>>(S.h, S.p, S.pk, x, M,
+                                                                                             count, y, io);
+    return cudaGetLastError();
 }
 
-// dX = dZ W with the ReLU mask of X (layer input); dZ [M][kW], W [kW][Kin]
-cudaError_t back_input(const bf16 *dZ, const bf16 *W, int Kin, const bf16 *X, bf16 *dX, long long M, cudaStream_t st)
+// the input and weight gradients after mode 2 of the forward kernel
+cudaError_t launch_backward(const State &S, const Acts &A, long long M, cudaStream_t st)
 {
-    GemmArgs g;
-    std::memset(&g, 0, sizeof(g));
-    g.A = dZ;
-    g.lda = kW;
-    g.B = W;      // B(k = n_out, n = k_in) at W[k * Kin + n]
-    g.ldb = Kin;
-    g.M = (int)M;
-    g.N = Kin;
-    g.K = kW;
-    g.k_split = kW;
-    g.mask = X;
-    g.ldm = Kin;
-    g.out_h = dX;
-    g.ldo = Kin;
-    return gemm<false, true, kMask>(g, 1, st);
-}
-
-// gW[n][k] += sum_m dZ[m][n] X[m][k]
-cudaError_t back_weight(const bf16 *dZ, const bf16 *X, int Kin, float *gW, long long M, cudaStream_t st)
-{
-    GemmArgs g;
-    std::memset(&g, 0, sizeof(g));
-    g.A = dZ;     // A(m' = n, k' = m) at dZ[k' * kW + m']
-    g.lda = kW;
-    g.B = X;      // B(k' = m, n' = k) at X[k' * Kin + n']
-    g.ldb = Kin;
-    g.M = kW;
-    g.N = Kin;
-    g.K = (int)M;
-    int splits = (int)std::min<long long>(128, (M + 2047) / 2048);
-    splits = std::max(splits, 1);
-    g.k_split = (int)(((M + splits - 1) / splits + BK - 1) / BK * BK);
-    splits = (int)((M + g.k_split - 1) / g.k_split);
-    g.out_f = gW;
-    g.ldo = Kin;
-    return gemm<true, true, kAtomic>(g, splits, st);
+    int nsm = 0;
+    cudaError_t e = sm_count(&nsm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp_dgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dg::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wg::kSmem);
+    if (e != cudaSuccess)
+        return e;
+    const long long T = (M + 127) / 128;
+    k_mlp_dgrad<<<(unsigned)(T < nsm ? T : nsm), dg::kThreads, dg::kSmem, st>>>(
+        S.pk + 2 * kW * kW, S.h + hW4, A.dY, A.mask3, A.mask2, A.mask1, A.D2, A.D1, T, S.g + oB4);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    // jobs in proportion to the bytes a tile moves: 128 KB for the hidden
+    // layers (D and H), 68 KB for the first (D and x)
+    WgradArgs W;
+    W.dY = A.dY;
+    W.mask3 = A.mask3;
+    W.w4h = S.h + hW4;
+    W.D2 = A.D2;
+    W.D1 = A.D1;
+    W.H2 = A.H2;
+    W.H1 = A.H1;
+    W.X = A.X;
+    W.g = S.g;
+    W.ntiles = T;
+    const int big = std::max(1, (int)((long long)nsm * 128 / 324));
+    W.jobs3 = (int)std::min<long long>(big, T);
+    W.jobs2 = W.jobs3;
+    W.jobs1 = (int)std::min<long long>(std::max(1, nsm - 2 * big), T);
+    k_mlp_wgrad<<<(unsigned)(W.jobs3 + W.jobs2 + W.jobs1), wg::kThreads, wg::kSmem, st>>>(W);
+    return cudaGetLastError();
 }
 
 }  // namespace mlp
@@ -1235,20 +1844,9 @@ int infer_tc(const void *state, const uint16_t *x, int64_t M, const int32_t *cou
     if (!aligned(x, 16) || !aligned(state, kAlign))
         return fail(PCDF_EINVAL, "x must be 16-byte aligned, state %zu-byte aligned", kAlign);
     State S(const_cast<void *>(state));
-    cudaStream_t st = (cudaStream_t)stream;
-    int dev = 0, nsm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mlp_infer_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws::kSmem);
-    if (e == cudaSuccess) {
-        // persistent: one CTA per SM (or per tile of the M rows, if fewer)
-        const long long ntiles = (M + 127) / 128;
-        k_mlp_infer_ws<<<(unsigned)(ntiles < nsm ? ntiles : nsm), ws::kThreads, ws::kSmem, st>>>(
-            S.h, S.p, S.pk, (const bf16 *)x, M, count, y);
-        e = cudaGetLastError();
-    }
+    TrainIO io;
+    std::memset(&io, 0, sizeof(io));
+    const cudaError_t e = launch_ws<0>(S, (const bf16 *)x, M, count, y, io, (cudaStream_t)stream);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp inference (tcgen05)");
 }
 }  // namespace
@@ -1303,14 +1901,17 @@ int pcdf_mlp_forward(const void *state, const uint16_t *x, int64_t M, float *y, 
     if (workspace_bytes < ws_bytes(M))
         return fail(PCDF_ENOMEM, "workspace %zu bytes < %zu needed", workspace_bytes, ws_bytes(M));
     State S(const_cast<void *>(state));
-    Acts A = carve(workspace, M);
-    cudaStream_t st = (cudaStream_t)stream;
-    if (int rc = forward(S, (const bf16 *)x, M, A, st))
-        return rc;
-    k_head<<<(unsigned)((M + kHeadRows - 1) / kHeadRows), 256, 0, st>>>(A.H3, S.h + hW4, S.p + oB4, M, y, nullptr,
-                                                                        nullptr, nullptr, nullptr, nullptr, 0.f);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp head");
+    const Acts A = carve(workspace, M);
+    TrainIO io;
+    std::memset(&io, 0, sizeof(io));
+    io.H1 = A.H1;
+    io.H2 = A.H2;
+    io.H3 = A.H3;
+    io.X = A.X;
+    io.mask1 = A.mask1;
+    io.mask2 = A.mask2;
+    const cudaError_t e = launch_ws<1>(S, (const bf16 *)x, M, nullptr, y, io, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp forward");
 }
 
 int pcdf_mlp_infer(const void *state, const uint16_t *x, int64_t M, float *y, void *stream)
@@ -1359,42 +1960,30 @@ int pcdf_mlp_backward(void *state, const uint16_t *x, const float *target, int64
     if (workspace_bytes < ws_bytes(M))
         return fail(PCDF_ENOMEM, "workspace %zu bytes < %zu needed", workspace_bytes, ws_bytes(M));
     State S(state);
-    Acts A = carve(workspace, M);
+    const Acts A = carve(workspace, M);
     cudaStream_t st = (cudaStream_t)stream;
-    const bf16 *X = (const bf16 *)x;
     cudaError_t e = cudaMemsetAsync(S.g, 0, 4 * kPpad, st);
     if (e == cudaSuccess && loss)
         e = cudaMemsetAsync(loss, 0, sizeof(float), st);
     if (e != cudaSuccess)
         return cuda_fail(e, "mlp backward reset");
-    if (int rc = forward(S, X, M, A, st))
-        return rc;
-    k_head<<<(unsigned)((M + kHeadRows - 1) / kHeadRows), 256, 0, st>>>(A.H3, S.h + hW4, S.p + oB4, M, y, target,
-                                                                        A.D3, S.g + oW4, S.g + oB4, loss,
-                                                                        1.f / (float)M);
-    e = cudaGetLastError();
-    const unsigned cs = (unsigned)((M + 255) / 256);
-    // layer 3: Z3 = H2 W3^T + b3
-    if (e == cudaSuccess) {
-        k_colsum<<<cs, kW, 0, st>>>(A.D3, M, S.g + oB3);
-        e = back_weight(A.D3, A.H2, kW, S.g + oW3, M, st);
-    }
+    TrainIO io;
+    std::memset(&io, 0, sizeof(io));
+    io.H1 = A.H1;
+    io.H2 = A.H2;
+    io.X = A.X;
+    io.mask1 = A.mask1;
+    io.mask2 = A.mask2;
+    io.mask3 = A.mask3;
+    io.dY = A.dY;
+    io.target = target;
+    io.inv_m = 1.f / (float)M;
+    io.gw4 = S.g + oW4;
+    io.gb4 = S.g + oB4;
+    io.loss = loss;
+    e = launch_ws<2>(S, (const bf16 *)x, M, nullptr, y, io, st);
     if (e == cudaSuccess)
-        e = back_input(A.D3, S.h + hW3, kW, A.H2, A.D2, M, st);
-    // layer 2
-    if (e == cudaSuccess) {
-        k_colsum<<<cs, kW, 0, st>>>(A.D2, M, S.g + oB2);
-        e = back_weight(A.D2, A.H1, kW, S.g + oW2, M, st);
-    }
-    if (e == cudaSuccess)
-        e = back_input(A.D2, S.h + hW2, kW, A.H1, A.D1, M, st);
-    // layer 1 (the input needs no gradient)
-    if (e == cudaSuccess) {
-        k_colsum<<<cs, kW, 0, st>>>(A.D1, M, S.g + oB1);
-        e = back_weight(A.D1, X, kIn, S.g + oW1, M, st);
-    }
-    if (e == cudaSuccess)
-        e = cudaGetLastError();
+        e = launch_backward(S, A, M, st);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "mlp backward");
 }
 

@@ -62,12 +62,10 @@ def dense(H, W, b=None):
     return E, S
 
 
-def check_passes(P, x, t, st, grads, loss):
-    """Every stored value and every gradient of one backward pass against the
-    network's definition evaluated on the GPU's own stored inputs.
-    P: parameters (float64, as params()); x [M,16], t [M]; st: stored
-    tensors as float64 numpy (H1, H2, H3, D3, D2, D1, y); grads: as grads()."""
-    M = x.shape[0]
+def check_forward(P, x, st):
+    """The stored activations H1, H2, H3 and the outputs y of a forward pass
+    against the network's definition on the GPU's own inputs to each layer.
+    Returns the fractions of entries where two roundings were allowed."""
     amb = {}
     E, S = dense(x, P["W1"], P["b1"])
     amb["H1"] = check_stored("H1", st["H1"], E, S, x.shape[1], True)
@@ -78,15 +76,37 @@ def check_passes(P, x, t, st, grads, loss):
     H3 = st["H3"]
     y_e = H3 @ P["w4"] + P["b4"]
     check_sum("y", st["y"], y_e, np.abs(H3) @ np.abs(P["w4"]) + abs(float(P["b4"])), 256)
-    # the head's FP32 arithmetic on the GPU's y, emulated exactly
+    return amb
+
+
+def head_gradient(P, y, t, H3, dy_gpu=None):
+    """The head's FP32 arithmetic emulated exactly: dy = (2 (y - t)) (1 / M)
+    and D3 = dy w4 (FP32 product) rounded to BF16 where H3 > 0.  If the GPU's
+    stored dy is given it must equal dy bit for bit.  Returns (dy, D3)."""
     f32 = np.float32
-    e = st["y"].astype(f32) - t.astype(f32)
+    M = len(y)
+    e = np.asarray(y).astype(f32) - np.asarray(t).astype(f32)
     dy = (f32(2.0) * e) * f32(1.0 / M)
+    if dy_gpu is not None:
+        bad = np.asarray(dy_gpu, f32) != dy
+        assert not bad.any(), f"dy: {int(bad.sum())} of {M} entries differ from the head's arithmetic"
     d3 = bf16_round((dy[:, None] * P["w4"].astype(f32)[None, :]).astype(np.float64))
-    d3 = np.where(H3 > 0, d3, 0.0)
-    bad = st["D3"] != d3
-    assert not bad.any(), f"D3: {int(bad.sum())} entries differ from the head's arithmetic"
-    E, S = st["D3"] @ P["W3"], np.abs(st["D3"]) @ np.abs(P["W3"])
+    return dy, np.where(H3 > 0, d3, 0.0)
+
+
+def check_passes(P, x, t, st, grads, loss):
+    """Every stored value and every gradient of one backward pass against the
+    network's definition evaluated on the GPU's own stored inputs.
+    P: parameters (float64, as params()); x [M,16], t [M]; st: stored
+    tensors as float64 numpy (H1, H2, H3, D3, D2, D1, y); grads: as grads()."""
+    M = x.shape[0]
+    amb = check_forward(P, x, st)
+    H3 = st["H3"]
+    # the head's FP32 arithmetic on the GPU's y, emulated exactly: the stored
+    # dy bit for bit, and D3 (rebuilt on chip from dy and the mask of H3) as
+    # the input of D2
+    dy, d3 = head_gradient(P, st["y"], t, H3, st.get("dy"))
+    E, S = d3 @ P["W3"], np.abs(d3) @ np.abs(P["W3"])
     amb["D2"] = check_stored("D2", st["D2"], E, S, 256, False, mask=st["H2"] > 0)
     E, S = st["D2"] @ P["W2"], np.abs(st["D2"]) @ np.abs(P["W2"])
     amb["D1"] = check_stored("D1", st["D1"], E, S, 256, False, mask=st["H1"] > 0)
@@ -94,9 +114,9 @@ def check_passes(P, x, t, st, grads, loss):
     dy64 = dy.astype(np.float64)
     check_sum("grad w4", grads["w4"], H3.T @ dy64, np.abs(H3).T @ np.abs(dy64), M)
     check_sum("grad b4", grads["b4"], dy64.sum(), np.abs(dy64).sum(), M)
-    for l, (D, Hp) in {3: (st["D3"], st["H2"]), 2: (st["D2"], st["H1"]), 1: (st["D1"], x)}.items():
+    for l, (D, Hp) in {3: (d3, st["H2"]), 2: (st["D2"], st["H1"]), 1: (st["D1"], x)}.items():
         check_sum(f"grad W{l}", grads[f"W{l}"], D.T @ Hp, np.abs(D).T @ np.abs(Hp), M)
         check_sum(f"grad b{l}", grads[f"b{l}"], D.sum(0), np.abs(D).sum(0), M)
-    ee = e.astype(np.float64)
+    ee = (st["y"].astype(np.float32) - t.astype(np.float32)).astype(np.float64)
     check_sum("loss", loss, float(np.sum(ee * ee) / M), float(np.sum(ee * ee) / M), 2 * M)
     return amb

@@ -29,7 +29,7 @@ def rand_x(M, rng, d):
 
 @pytest.mark.parametrize("M", [300, 4096])
 def test_mlp_forward_and_gradients_match_oracle(M):
-    """Every stored value of a backward pass, element by element, against the
+    """Every stored value of a training step, element by element, against the
     network's definition evaluated on the GPU's own inputs to that step
     (tests/mlp_parity.py): each BF16 activation and pre-activation gradient
     equals the rounding of its exact value unless that value lies within the
@@ -44,8 +44,16 @@ def test_mlp_forward_and_gradients_match_oracle(M):
     t = torch.from_numpy(rng.normal(size=M).astype(np.float32)).to(d)
     y, loss = net.backward(x, t)
     torch.cuda.synchronize()
+    stb = net.stored(M)
+    # the forward pass: the same y and activations, and H3 (which the
+    # training step uses on chip without storing it)
+    y2 = net.forward(x)
+    torch.cuda.synchronize()
+    assert torch.equal(y2, y)
+    stf = net.stored(M)
+    assert torch.equal(stf["H1"], stb["H1"]) and torch.equal(stf["H2"], stb["H2"])
     P = net.params()
-    st = {k: v.float().cpu().double().numpy() for k, v in net.stored(M).items()}
+    st = {k: v.float().cpu().double().numpy() for k, v in stf.items()}
     st["y"] = y.cpu().double().numpy()
     xo = x.float().cpu().double().numpy()
     amb = mlp_parity.check_passes(P, xo, t.cpu().double().numpy(), st, net.grads(), float(loss.item()))
@@ -53,24 +61,75 @@ def test_mlp_forward_and_gradients_match_oracle(M):
     # and the FP64 oracle with its own activations agrees on the loss
     want_loss, _, _ = omlp.loss_and_grad(P, xo, t.cpu().double().numpy(), rounding=True)
     assert abs(float(loss.item()) - want_loss) <= 1e-3 * want_loss
-    # the forward pass alone gives the same outputs, and so does the fused
-    # inference kernel (tail tiles included)
-    y2 = net.forward(x)
-    assert torch.equal(y2, y)
-    assert torch.equal(net.infer(x), y)
-    assert torch.equal(net.infer(x[: M - 7]), y[: M - 7])
-    # the tcgen05 kernel: the same network up to the order of the FP32 sums
+    # inference without a workspace: the same kernel, bit-identical (tail
+    # tiles included); the legacy mma.sync kernel within FP32 rounding
+    assert torch.equal(net.infer_tc(x), y)
+    assert torch.equal(net.infer_tc(x[: M - 7]), y[: M - 7])
+    scale = max(1.0, float(y.abs().max()))
+    assert torch.allclose(net.infer(x), y, rtol=0, atol=1e-5 * scale)
     y_tc = net.infer_tc(x)
-    assert not torch.isnan(y_tc).any()
-    assert torch.allclose(y_tc, y, rtol=0, atol=1e-5 * max(1.0, float(y.abs().max())))
-    y_tc2 = net.infer_tc(x[: M - 7])
-    assert torch.allclose(y_tc2, y[: M - 7], rtol=0, atol=1e-5 * max(1.0, float(y.abs().max())))
     # a row count on the device: the first count rows, the rest untouched
     for c in (M - 7, 0, M + 5, -3):
         cnt = torch.tensor([c], dtype=torch.int32, device=d)
         y_c = net.infer_tc(x, count=cnt)
         k = max(0, min(c, M))
         assert torch.equal(y_c[:k], y_tc[:k])
+
+
+def test_training_step_over_many_tiles_per_cta():
+    """A training step at several 128-row tiles per CTA and a ragged last tile
+    (the A buffers, accumulators and barrier phases of the persistent kernels
+    wrap; every weight-gradient job sums several tiles): stored values on
+    sampled rows (all of the last tile) element by element, and every
+    gradient entry, against the definition on the GPU's own inputs."""
+    d = dev()
+    sms = torch.cuda.get_device_properties(d).multi_processor_count
+    M = sms * 128 * 3 + 77
+    rng = np.random.default_rng(5)
+    net = pcdf.SurrogateMLP(d, seed=11)
+    x = rand_x(M, rng, d)
+    t = torch.from_numpy(rng.normal(size=M).astype(np.float32)).to(d)
+    y, loss = net.backward(x, t)
+    stb = net.stored(M)
+    y2 = net.forward(x)
+    torch.cuda.synchronize()
+    assert torch.equal(y2, y) and not torch.isnan(y).any()
+    stf = net.stored(M)
+    P = net.params()
+    full = {k: v.float().cpu().double().numpy() for k, v in stf.items()}
+    full["y"] = y.cpu().double().numpy()
+    xo = x.float().cpu().double().numpy()
+    to = t.cpu().double().numpy()
+    g = net.grads()
+    rows = np.unique(np.concatenate([rng.choice(M, 600, replace=False), np.arange(M - 77, M)]))
+    # the row-wise values on the sampled rows; the head's dy needs the true M
+    sub = {k: v[rows] for k, v in full.items()}
+    amb = {}
+    E, S = mlp_parity.dense(xo[rows], P["W1"], P["b1"])
+    amb["H1"] = mlp_parity.check_stored("H1", sub["H1"], E, S, 16, True)
+    E, S = mlp_parity.dense(sub["H1"], P["W2"], P["b2"])
+    amb["H2"] = mlp_parity.check_stored("H2", sub["H2"], E, S, 256, True)
+    E, S = mlp_parity.dense(sub["H2"], P["W3"], P["b3"])
+    amb["H3"] = mlp_parity.check_stored("H3", sub["H3"], E, S, 256, True)
+    f32 = np.float32
+    # the head's arithmetic needs the true M: emulate it on all rows, compare the stored dy
+    dyf, d3f = mlp_parity.head_gradient(P, full["y"], to, full["H3"], full["dy"])
+    d3 = d3f[rows]
+    E, S = d3 @ P["W3"], np.abs(d3) @ np.abs(P["W3"])
+    amb["D2"] = mlp_parity.check_stored("D2", sub["D2"], E, S, 256, False, mask=sub["H2"] > 0)
+    E, S = sub["D2"] @ P["W2"], np.abs(sub["D2"]) @ np.abs(P["W2"])
+    amb["D1"] = mlp_parity.check_stored("D1", sub["D1"], E, S, 256, False, mask=sub["H1"] > 0)
+    assert all(v < 0.5 for v in amb.values()), amb
+    # every gradient entry over all M rows
+    dyf = dyf.astype(np.float64)
+    H3 = full["H3"]
+    mlp_parity.check_sum("grad w4", g["w4"], H3.T @ dyf, np.abs(H3).T @ np.abs(dyf), M)
+    mlp_parity.check_sum("grad b4", g["b4"], dyf.sum(), np.abs(dyf).sum(), M)
+    for l, (D, Hp) in {3: (d3f, full["H2"]), 2: (full["D2"], full["H1"]), 1: (full["D1"], xo)}.items():
+        mlp_parity.check_sum(f"grad W{l}", g[f"W{l}"], D.T @ Hp, np.abs(D).T @ np.abs(Hp), M)
+        mlp_parity.check_sum(f"grad b{l}", g[f"b{l}"], D.sum(0), np.abs(D).sum(0), M)
+    e = (full["y"].astype(f32) - to.astype(f32)).astype(np.float64)
+    mlp_parity.check_sum("loss", float(loss.item()), float(np.sum(e * e) / M), float(np.sum(e * e) / M), 2 * M)
 
 
 def test_tensor_core_inference_over_many_tiles_per_cta():
@@ -119,14 +178,19 @@ def test_adam_step():
     # the BF16 copy follows the master copy
     half = net._bf16()
     assert torch.equal(half[4096:4096 + 65536], p1[4352:4352 + 65536].to(torch.bfloat16))
-    # the tensor-core kernel reads the packed copy of W2 and W3, which the
-    # step refreshed: it still agrees with the fused kernel after training
+    # the tensor-core kernels read packed copies of W2 and W3, which the step
+    # refreshed: after more steps a forward pass still follows the network's
+    # definition with the current weights, layer by layer
     for _ in range(3):
         net.backward(x, t)
         net.adam(1e-2)
-    y = net.infer(x)
-    y_tc = net.infer_tc(x)
-    assert torch.allclose(y_tc, y, rtol=0, atol=1e-5 * max(1.0, float(y.abs().max())))
+    y = net.forward(x)
+    torch.cuda.synchronize()
+    st = {k: v.float().cpu().double().numpy() for k, v in net.stored(1024).items()}
+    st["y"] = y.cpu().double().numpy()
+    amb = mlp_parity.check_forward(net.params(), x.float().cpu().double().numpy(), st)
+    assert all(v < 0.5 for v in amb.values()), amb
+    assert torch.equal(net.infer_tc(x), y)
 
 
 def scene_set(seeds, grid_only=False):

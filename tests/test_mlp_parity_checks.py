@@ -2,7 +2,7 @@
 the CPU: passes computed with FP32 sums (numpy) satisfy them, and a single
 planted mistake fails them - a weight-gradient entry off by 10 %, one stored
 activation one BF16 ulp off where the rounding is not ambiguous, one stored
-layer-3 gradient changed."""
+dy one FP32 ulp off."""
 import numpy as np
 import pytest
 
@@ -41,7 +41,7 @@ def simulated_passes(M, seed):
              "b2": D2.astype(f32).sum(0).astype(np.float64), "b1": D1.astype(f32).sum(0).astype(np.float64),
              "w4": (H3.astype(f32).T @ dy).astype(np.float64), "b4": np.array(float(dy.sum()))}
     loss = float(np.sum(e.astype(f32) * e.astype(f32) / f32(M)))
-    st = {"H1": H1, "H2": H2, "H3": H3, "D3": D3, "D2": D2, "D1": D1, "y": y}
+    st = {"H1": H1, "H2": H2, "H3": H3, "D3": D3, "D2": D2, "D1": D1, "y": y, "dy": dy.astype(np.float64)}
     return P, x, t, st, grads, loss
 
 
@@ -82,7 +82,7 @@ def test_a_stored_value_one_ulp_off_fails():
     with pytest.raises(AssertionError):
         mp.check_passes(P, x, t, bad, grads, loss)
     bad = {k: np.array(v, copy=True) for k, v in st.items()}
-    nz = np.argwhere(bad["D3"] != 0)[0]
-    bad["D3"][tuple(nz)] *= 2.0
+    i = int(np.argmax(np.abs(bad["dy"])))
+    bad["dy"][i] = float(np.nextafter(np.float32(bad["dy"][i]), np.float32(np.inf)))
     with pytest.raises(AssertionError):
         mp.check_passes(P, x, t, bad, grads, loss)
