@@ -103,6 +103,15 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def measured_bf16_peak():
+    """Dense BF16 TF/s (cuBLAS burst) of MEASURED_PEAKS.json, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 def sources_sha(names):
     """sha256 (16 hex digits) of the named csrc files, concatenated in order."""
     h = hashlib.sha256()
@@ -351,7 +360,7 @@ def bench_batched(dev, seed, steps):
             "autotune_best_ms": tune_ms, "status": status}
 
 
-def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=65536):
+def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=262144, lr=6e-3):
     """Learned surrogate: trained on the exact fields of n_train_scenes 64^3
     scenes (5 cm voxels, one human walking over T = 20 steps) with n_samples
     samples, then 1M trajectory-sphere queries per plan step on held-out scenes:
@@ -383,7 +392,7 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
     net = pcdf.SurrogateMLP(dev, seed=seed + 17)
     steps = max(1, n_samples // batch)
     t0 = time.perf_counter()
-    hist = sg.train(net, grid, fields, caps, tf, T, steps=steps, batch=batch, lr=2e-3, log_every=max(1, steps // 8))
+    hist = sg.train(net, grid, fields, caps, tf, T, steps=steps, batch=batch, lr=lr, log_every=max(1, steps // 8))
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
     # one training step at the training batch: the network's products alone
@@ -398,9 +407,14 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
         net.adam(1e-5)
     t_step = ev_time(step, k=20)
     t_samples = ev_time(lambda: pcdf.surrogate_samples(grid, fields, caps, tf, T, batch, 777, 0.6), k=20)
+    # the same step at a quarter of the batch (fixed costs per step weigh more)
+    q = batch // 4
+    xq, tq = xb[:q], tb[:q]
+    t_bwd_q = ev_time(lambda: net.backward(xq, tq), k=20)
     # tensor-core products per row: forward 2 (16 256 + 2 256^2), input
     # gradients 2 (2 256^2), weight gradients 2 (2 256^2 + 256 16)
     train_flops = 802816 * batch
+    peak, peak_src = measured_bf16_peak()
     del fields
 
     def queries(s):
@@ -544,10 +558,15 @@ def bench_surrogate(dev, seed, n_train_scenes=500, n_samples=50_000_000, batch=6
     return {"workload": f"MLP 16-256-256-256-1 bf16/fp32, trained on {n_train_scenes} 64^3 scenes x T=20 "
                         f"({steps * batch} samples); 1,024,000 sphere queries per plan step on held-out scenes",
             "train_s": t_train, "fields_s": t_fields, "loss_first": hist[0][1], "loss_last": hist[-1][1],
+            "train_lr": lr, "train_batch": batch, "train_steps": steps,
+            "train_tflops": 802816 * steps * batch / t_train / 1e12,
+            "train_frac_of_bf16_peak": 802816 * steps * batch / t_train / 1e12 / peak,
+            "bf16_peak_tflops": peak, "bf16_peak_source": peak_src,
             "train_step": {"batch": batch, "backward_ms": t_bwd, "backward_tflops": train_flops / (t_bwd * 1e-3) / 1e12,
                            "forward_stored_ms": t_fwd_train, "step_with_adam_ms": t_step,
                            "step_tflops": train_flops / (t_step * 1e-3) / 1e12, "samples_ms": t_samples,
-                           "flops_per_row": 802816},
+                           "flops_per_row": 802816, "quarter_batch": q, "quarter_backward_ms": t_bwd_q,
+                           "quarter_backward_tflops": 802816 * q / (t_bwd_q * 1e-3) / 1e12},
             "band_m": BAND, "certified": True,
             "max_err_m": max(x["max_err"] for x in stats), "mean_err_m": float(np.mean([x["mean_err"] for x in stats])),
             "fallback_frac": float(np.mean([x["fallback"] for x in stats])),

@@ -401,6 +401,18 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// bulk copy of shared memory to global memory in the calling thread's bulk
+// group; wait_read returns once the source may be overwritten, wait_all once
+// the writes are done
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
@@ -761,6 +773,9 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                             ok = false;
                             break;
                         }
+                        if (kMode != 0 && c == ws::kChunks - 1)  // H_L complete in the A buffer: to memory
+                            tc::bulk_store(reinterpret_cast<unsigned char *>(L == 1 ? io.H1 : io.H2) + tile * kTileBytes,
+                                           sA, ws::kBytesA);
                         tc::fence_after();
 #pragma unroll
                         for (int kk = 0; kk < tc::kKC / 16; ++kk) {
@@ -771,6 +786,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                         }
                         tc::commit(&empty[st]);
                     }
+                    // the epilogue overwrites the A buffer once the accumulator is
+                    // full: the copy to memory has read it by then
+                    if (kMode != 0)
+                        tc::bulk_wait_read();
                     if (ok)
                         tc::commit(&accfull[q & 1]);
                 }
@@ -781,6 +800,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                 ok = gw4_products(it - 1);
             if (!ok)
                 s_fail = 1;
+            if (kMode != 0)
+                tc::bulk_wait_all();
             // every product issued has finished before the tensor memory is freed
             tc::commit(&drain);
             (void)tc::mbar_wait(&drain, 0);
@@ -896,16 +917,13 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                 if (L < 2) {
                     const float *bias = sBias + L * kW;
                     const bool with_bias = L == 1;  // the first layer's bias came with its product
-                    unsigned char *hg = nullptr;
                     uint32_t *mk = nullptr;
-                    if constexpr (kMode != 0) {
-                        hg = reinterpret_cast<unsigned char *>(L == 0 ? io.H1 : io.H2) + tile * kTileBytes;
+                    if constexpr (kMode != 0)
                         mk = (L == 0 ? io.mask1 : io.mask2) + tile * (kMaskTileBytes / 4);
-                    }
                     // slice j (32 columns): bias, ReLU, BF16 into the A operand, then
-                    // its chunk's barrier, then (modes 1, 2) the copy to memory, whose
-                    // stores drain while the next products run; the next slice's
-                    // load is in flight meanwhile
+                    // its chunk's barrier (modes 1, 2: the product thread copies the
+                    // complete tile to memory), then the slice's mask word; the next
+                    // slice's load is in flight meanwhile
                     auto slice = [&](const uint32_t(&v)[32], int j, int) {
                         uint4 keep[4];
 #pragma unroll
@@ -934,10 +952,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                         if constexpr (kMode != 0) {
                             uint32_t bits = 0;
 #pragma unroll
-                            for (int gq = 0; gq < 4; ++gq) {
-                                *reinterpret_cast<uint4 *>(hg + tc::kmaj(r, 32 * j + 8 * gq, kW)) = keep[gq];
+                            for (int gq = 0; gq < 4; ++gq)
                                 bits |= nz8(keep[gq]) << (8 * gq);
-                            }
                             mk[j * 128 + r] = bits;
                         }
                     };
@@ -1115,9 +1131,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 //   warps 2..9           epilogue: D3 of a tile into its A buffer (two
 //                        buffers: tile i uses i % 2; D3 of the next tile is
 //                        built while the products D2 W2 of this one run),
-//                        then mask and round: D2 to the A buffer (each
-//                        chunk's barrier releases its products) and to
-//                        memory, D1 to memory.
+//                        then mask and round D2, then D1, into the A buffer;
+//                        both go to memory as 64 KB bulk copies (D2 by the
+//                        product thread, D1 by one epilogue thread), so the
+//                        stores drain while the products run.
 // ---------------------------------------------------------------------------
 namespace dg {
 constexpr int kStages = 3, kEpiWarps = 8, kGroups = kEpiWarps / 4, kSlices = 8 / kGroups,
@@ -1161,7 +1178,7 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
 {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full[dg::kStages], empty[dg::kStages], accfull[2], accempty[2], d3ready[ws::kChunks],
-        aready[ws::kChunks], drain;
+        aready[ws::kChunks], esync, drain;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_fail;
     __shared__ volatile int s_slot[2 + dg::kEpiWarps];
@@ -1187,6 +1204,7 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
             tc::mbar_init(&d3ready[j], 2 * 4 * 32);  // two slices, each written by the four warps of its group
             tc::mbar_init(&aready[j], 2 * 4 * 32);
         }
+        tc::mbar_init(&esync, dg::kEpiWarps * 32);
         tc::mbar_init(&drain);
         tc::fence_mbar_init();
         s_fail = 0;
@@ -1220,6 +1238,9 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
                             ok = false;
                             break;
                         }
+                        if (L == 1 && c == ws::kChunks - 1)  // D2 complete in the A buffer: to memory
+                            tc::bulk_store(reinterpret_cast<unsigned char *>(D2) + tile * kTileBytes,
+                                           sA + b * ws::kBytesA, ws::kBytesA);
                         tc::fence_after();
 #pragma unroll
                         for (int kk = 0; kk < tc::kKC / 16; ++kk) {
@@ -1230,6 +1251,10 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
                         }
                         tc::commit(&empty[st]);
                     }
+                    // the epilogue writes D1 into the A buffer once this
+                    // accumulator is full: the copy of D2 has read it by then
+                    if (L == 1)
+                        tc::bulk_wait_read();
                     if (ok)
                         tc::commit(&accfull[q & 1]);
                 }
@@ -1238,6 +1263,7 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
             }
             if (!ok)
                 s_fail = 1;
+            tc::bulk_wait_all();
             tc::commit(&drain);
             (void)tc::mbar_wait(&drain, 0);
         }
@@ -1269,6 +1295,14 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
         const int r = quarter * 32 + lane;
         volatile int *slot = s_slot + warp;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        // the epilogue warps alone meet (a bounded wait; its phases alternate)
+        bool ok = true;
+        int nsync = 0;
+        auto epi_sync = [&] {
+            tc::mbar_arrive(&esync);
+            if (!ws::warp_wait(&esync, (uint32_t)(nsync++ & 1), slot, lane))
+                ok = false;
+        };
         // dy and the H3 mask words of tile t for this thread's row and slices
         float ndy = 0.f;
         uint32_t nm3[dg::kSlices];
@@ -1278,8 +1312,13 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
             for (int k = 0; k < dg::kSlices; ++k)
                 nm3[k] = mask3[t * (kMaskTileBytes / 4) + (group + k * dg::kGroups) * 128 + r];
         };
-        // D3 of the fetched tile into A buffer b, each slice's chunk barrier once written
+        // D3 of the fetched tile into A buffer b, each slice's chunk barrier once
+        // written; the copy of D1 out of that buffer (two tiles before) has read
+        // it first
         auto build_d3 = [&](int b) {
+            if (warp == 2 && lane == 0)
+                tc::bulk_wait_read();
+            epi_sync();
             unsigned char *sa = sA + b * ws::kBytesA;
 #pragma unroll
             for (int k = 0; k < dg::kSlices; ++k) {
@@ -1293,7 +1332,6 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
                 tc::mbar_arrive(&d3ready[j >> 1]);
             }
         };
-        bool ok = true;
         int it = 0;
         long long tile = blockIdx.x;
         if (tile < ntiles) {
@@ -1321,36 +1359,39 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
                 }
                 tc::fence_after();
                 const uint32_t tb = tmem + (uint32_t)a * 256u + lane_off;
-                unsigned char *dst = reinterpret_cast<unsigned char *>(L == 0 ? D2 : D1) + tile * kTileBytes;
                 unsigned char *sa = sA + b * ws::kBytesA;
+                // D2 (then D1) into the A buffer: D2 is the next products' operand
+                // (each chunk's barrier releases them) and the product thread copies
+                // it to memory; D1 goes to memory from the buffer below
                 auto slice = [&](const uint32_t(&v)[32], int j, int k) {
                     const uint32_t bits = L == 0 ? m2[k] : m1[k];
-                    uint4 keep[4];
 #pragma unroll
                     for (int gq = 0; gq < 4; ++gq) {
                         const uint32_t *u = v + 8 * gq;
                         const uint32_t fl = pair_flags(bits, gq);
-                        keep[gq].x = bf2_masked(u[0], u[1], fl);
-                        keep[gq].y = bf2_masked(u[2], u[3], fl >> 1);
-                        keep[gq].z = bf2_masked(u[4], u[5], fl >> 2);
-                        keep[gq].w = bf2_masked(u[6], u[7], fl >> 3);
-                        if (L == 0)
-                            *reinterpret_cast<uint4 *>(sa + tc::kmaj(r, 32 * j + 8 * gq, kW)) = keep[gq];
+                        uint4 pk;
+                        pk.x = bf2_masked(u[0], u[1], fl);
+                        pk.y = bf2_masked(u[2], u[3], fl >> 1);
+                        pk.z = bf2_masked(u[4], u[5], fl >> 2);
+                        pk.w = bf2_masked(u[6], u[7], fl >> 3);
+                        *reinterpret_cast<uint4 *>(sa + tc::kmaj(r, 32 * j + 8 * gq, kW)) = pk;
                     }
+                    tc::fence_proxy_async();
                     if (L == 0) {
-                        // the A operand first: the next products start while the
-                        // copy to memory drains
-                        tc::fence_proxy_async();
                         tc::fence_before();
                         tc::mbar_arrive(&aready[j >> 1]);
                     }
-#pragma unroll
-                    for (int gq = 0; gq < 4; ++gq)
-                        *reinterpret_cast<uint4 *>(dst + tc::kmaj(r, 32 * j + 8 * gq, kW)) = keep[gq];
                 };
                 ws::each_slice<dg::kGroups>(tb, group, slice);
                 tc::fence_before();
                 tc::mbar_arrive(&accempty[a]);
+                if (L == 1) {
+                    // D1 complete in the buffer (all epilogue warps): one thread
+                    // copies it to memory; the buffer is next written two tiles on
+                    epi_sync();
+                    if (warp == 2 && lane == 0)
+                        tc::bulk_store(reinterpret_cast<unsigned char *>(D1) + tile * kTileBytes, sa, ws::kBytesA);
+                }
                 // the next tile's D3 goes into the other buffer while this tile's
                 // second products run (its last reader, the products of the tile
                 // before, finished before that tile's D1 was read)
@@ -1362,6 +1403,8 @@ __global__ void __launch_bounds__(dg::kThreads, 1)
         }
         if (!ok)
             s_fail = 1;
+        if (warp == 2 && lane == 0)
+            tc::bulk_wait_all();
     }
     tc::fence_before();
     __syncthreads();
@@ -1804,8 +1847,10 @@ cudaError_t launch_backward(const State &S, const Acts &A, long long M, cudaStre
         S.pk + 2 * kW * kW, S.h + hW4, A.dY, A.mask3, A.mask2, A.mask1, A.D2, A.D1, T, S.g + oB4);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    // jobs in proportion to the bytes a tile moves: 128 KB for the hidden
-    // layers (D and H), 68 KB for the first (D and x)
+    // jobs in proportion to the time a tile takes, measured: the second layer
+    // streams D2 and H1 (128 KB), the third H2 with dy and the mask (68 KB)
+    // and builds D3 on chip, which costs about as much; the first streams D1
+    // and x (68 KB)
     WgradArgs W;
     W.dY = A.dY;
     W.mask3 = A.mask3;
@@ -1817,10 +1862,10 @@ cudaError_t launch_backward(const State &S, const Acts &A, long long M, cudaStre
     W.X = A.X;
     W.g = S.g;
     W.ntiles = T;
-    const int big = std::max(1, (int)((long long)nsm * 128 / 324));
-    W.jobs3 = (int)std::min<long long>(big, T);
-    W.jobs2 = W.jobs3;
-    W.jobs1 = (int)std::min<long long>(std::max(1, nsm - 2 * big), T);
+    const int j3 = std::max(1, nsm * 128 / 324), j2 = j3, j1 = std::max(1, nsm - j3 - j2);
+    W.jobs3 = (int)std::min<long long>(j3, T);
+    W.jobs2 = (int)std::min<long long>(j2, T);
+    W.jobs1 = (int)std::min<long long>(j1, T);
     k_mlp_wgrad<<<(unsigned)(W.jobs3 + W.jobs2 + W.jobs1), wg::kThreads, wg::kSmem, st>>>(W);
     return cudaGetLastError();
 }

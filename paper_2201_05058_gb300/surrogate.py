@@ -37,12 +37,19 @@ def exact_dynamic_fields(grid, caps_list, device):
 
 
 def train(model, grid, fields, caps, tf, T, steps, batch, lr=2e-3, lr_min=5e-5, seed=0, near=0.6,
-          log_every=0):
-    """Adam with cosine learning-rate decay on fresh samples every step.
-    Returns the list of (step, loss) at the logged steps (device sync there)."""
+          log_every=0, draw=4):
+    """Adam with cosine learning-rate decay on fresh samples every step, drawn
+    `draw` steps at a time (one sampling launch for several steps: the draw is
+    bound by the latency of its random reads, not by its size).  Returns the
+    list of (step, loss) at the logged steps (device sync there)."""
     hist = []
+    xs = ts = None
     for k in range(steps):
-        x, t = api.surrogate_samples(grid, fields, caps, tf, T, batch, seed * 1_000_003 + k, near)
+        if k % draw == 0:
+            n = min(draw, steps - k)
+            xs, ts = api.surrogate_samples(grid, fields, caps, tf, T, n * batch, seed * 1_000_003 + k, near)
+        i = k % draw
+        x, t = xs[i * batch:(i + 1) * batch], ts[i * batch:(i + 1) * batch]
         rate = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * k / max(steps - 1, 1)))
         loss = model.train_step(x, t, rate)
         if log_every and (k % log_every == 0 or k == steps - 1):
