@@ -58,7 +58,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
-    ap.add_argument("--profile-case", choices=["composite", "static", "scratch", "query", "mlp", "surrogate",
+    ap.add_argument("--profile-case", choices=["composite", "static", "scratch", "query", "mlp", "train", "surrogate",
                                                "translated"],
                     default=None,
                     help="run one small untimed case of the named stage (for ncu captures) and exit")
@@ -939,6 +939,23 @@ def run_profile_case(args):
             net.infer_tc(x)
         torch.cuda.synchronize()
         print("profile case mlp done")
+        return 0
+    if args.profile_case == "train":
+        # two training steps at 65,536 rows inside the NVTX range train_step
+        # (forward with the head's backward, input and weight gradients, Adam)
+        net = pcdf.SurrogateMLP(dev, seed=3)
+        g = torch.Generator(device="cpu").manual_seed(1)
+        x = torch.randn(65536, 16, generator=g).to(torch.bfloat16)
+        x[:, 13:] = 0
+        x, t = x.to(dev), torch.randn(65536, generator=g).to(dev)
+        net.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("train_step")
+        for _ in range(2):
+            net.train_step(x, t, 1e-4)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print("profile case train done")
         return 0
     if args.profile_case == "surrogate":
         return run_profile_surrogate(dev)
