@@ -43,7 +43,9 @@
  *   past the call and allocates nothing.  Calls that need scratch take a
  *   caller-owned device workspace and report its size through the matching
  *   *_workspace_bytes query.  Pointers marked "host" are read during the call
- *   only.
+ *   only.  The one exception is the context (pcdf_create): it owns a scratch
+ *   buffer that it allocates and grows itself, for callers that prefer not to
+ *   size workspaces.
  *
  *   Asynchrony: every device call is enqueued on `stream` (a cudaStream_t; NULL
  *   is the legacy default stream) and returns without waiting for the GPU.
@@ -392,6 +394,57 @@ int pcdf_batch_block_stage(pcdf_batch *batch, int32_t env, int32_t stage);
 int pcdf_batch_autotune_workspace_bytes(const pcdf_env *envs, int32_t n_env, size_t *bytes);
 int pcdf_batch_autotune(const pcdf_env *envs, int32_t n_env, void *workspace, size_t workspace_bytes, void *stream,
                         int32_t reps, pcdf_batch_tiles *best, float *best_ms);
+
+/* ---------------------------------------------------------------------------
+ * Context: the handle of the paper's interface (a device, a stream and scratch
+ * that the library owns), over the workspace calls above.
+ *
+ * pcdf_create         binds a context to `device` (0 <= device < the device
+ *                     count; PCDF_EINVAL otherwise) and `stream` (a
+ *                     cudaStream_t of that device, NULL: the legacy default
+ *                     stream); allocates nothing on the device.
+ * pcdf_destroy        releases the scratch (stream-ordered on the context's
+ *                     stream) and the handle; NULL is ignored.
+ * pcdf_scratch_bytes  an upper bound of the scratch any call of a context
+ *                     needs for `grid` with up to T fields and H humans (the
+ *                     composite bound assumes capsules touching every slice);
+ *                     host only.
+ * pcdf_ctx_reserve    grows the scratch to at least `bytes` now (for example
+ *                     to pcdf_scratch_bytes at start-up), so that later calls
+ *                     allocate nothing.
+ * pcdf_ctx_*          the workspace call of the same name (same arguments,
+ *                     results and checks) on the context's device and stream
+ *                     with the context's scratch.  When the scratch is smaller
+ *                     than the call needs, it is released and reallocated
+ *                     first (cudaFreeAsync / cudaMallocAsync on the context's
+ *                     stream; PCDF_ENOMEM if that fails).  The calls are
+ *                     asynchronous; calls sharing a context must share its
+ *                     stream order (one thread at a time).
+ * pcdf_build_batched  the batched environments (pcdf_batch_* with the default
+ *                     tiles): plans, uploads into the scratch and runs them,
+ *                     the run as a CUDA graph when use_graph is 1 (0: plain
+ *                     launches; other values PCDF_EINVAL); synchronises the
+ *                     context's stream and returns PCDF_ETIMEOUT if a
+ *                     dependency wait inside the run expired.
+ * ------------------------------------------------------------------------- */
+typedef struct pcdf_ctx pcdf_ctx;
+int pcdf_create(pcdf_ctx **out, int32_t device, void *stream);
+void pcdf_destroy(pcdf_ctx *ctx);
+int pcdf_scratch_bytes(const pcdf_grid *grid, int32_t T, int32_t H, size_t *bytes);
+int pcdf_ctx_reserve(pcdf_ctx *ctx, size_t bytes);
+int pcdf_ctx_build_static_sdf(pcdf_ctx *ctx, const pcdf_grid *grid, const uint8_t *occ, int32_t *static_sq,
+                              float *static_sdf);
+int pcdf_ctx_build_predicted_composite(pcdf_ctx *ctx, const pcdf_grid *grid, const int32_t *static_sq,
+                                       const float *static_sdf, int32_t T, int32_t H, const int32_t *caps,
+                                       int32_t *comp_sq, float *comp_sdf);
+int pcdf_ctx_build_from_scratch(pcdf_ctx *ctx, const pcdf_grid *grid, const uint8_t *occ, int32_t T, int32_t H,
+                                const int32_t *caps, int32_t *sq, float *sdf);
+int pcdf_ctx_query_cost(pcdf_ctx *ctx, const pcdf_grid *grid, const float *sdf, int32_t T, const float *spheres,
+                        const int32_t *tidx, int64_t N, float eps, float *h, int32_t *n_oob);
+int pcdf_ctx_query_cost_backward(pcdf_ctx *ctx, const pcdf_grid *grid, const float *sdf, int32_t T,
+                                 const float *spheres, const int32_t *tidx, int64_t N, float eps, const float *grad_h,
+                                 float *grad_c, float *grad_r);
+int pcdf_build_batched(pcdf_ctx *ctx, const pcdf_env *envs, int32_t n_env, int32_t use_graph);
 
 /* ---------------------------------------------------------------------------
  * Learned surrogate of the dynamic field: a BF16 MLP with FP32 accumulation

@@ -16,6 +16,7 @@ from .api import (  # noqa: F401
     surrogate_select,
     surrogate_samples,
     Batch,
+    Context,
     batch_autotune,
     Grid,
     HingeCost,

@@ -43,6 +43,9 @@ EXPORTS = (
     "pcdf_batch_create", "pcdf_batch_destroy", "pcdf_batch_workspace_bytes", "pcdf_batch_tiles_used",
     "pcdf_batch_upload", "pcdf_batch_run", "pcdf_batch_error", "pcdf_batch_block_stage", "pcdf_batch_autotune_workspace_bytes",
     "pcdf_batch_autotune",
+    "pcdf_create", "pcdf_destroy", "pcdf_scratch_bytes", "pcdf_ctx_reserve", "pcdf_ctx_build_static_sdf",
+    "pcdf_ctx_build_predicted_composite", "pcdf_ctx_build_from_scratch", "pcdf_ctx_query_cost",
+    "pcdf_ctx_query_cost_backward", "pcdf_build_batched",
     "pcdf_mlp_state_bytes", "pcdf_mlp_workspace_bytes", "pcdf_mlp_init", "pcdf_mlp_forward", "pcdf_mlp_infer", "pcdf_mlp_infer_tc", "pcdf_mlp_infer_tc_count",
     "pcdf_mlp_backward",
     "pcdf_mlp_adam", "pcdf_surrogate_samples", "pcdf_surrogate_features", "pcdf_surrogate_finish_workspace_bytes",
@@ -115,8 +118,21 @@ def _declare(lib):
                                        P],
         "pcdf_surrogate_select": [G, P, P, P, I64, I32, I32, P, F32, I32, P, P, P, P, P],
     })
+    sig.update({
+        "pcdf_create": [PP, I32, P],
+        "pcdf_scratch_bytes": [G, I32, I32, SZP],
+        "pcdf_ctx_reserve": [P, SZ],
+        "pcdf_ctx_build_static_sdf": [P, G, P, P, P],
+        "pcdf_ctx_build_predicted_composite": [P, G, P, P, I32, I32, P, P, P],
+        "pcdf_ctx_build_from_scratch": [P, G, P, I32, I32, P, P, P],
+        "pcdf_ctx_query_cost": [P, G, P, I32, P, P, I64, F32, P, P],
+        "pcdf_ctx_query_cost_backward": [P, G, P, I32, P, P, I64, F32, P, P, P],
+        "pcdf_build_batched": [P, E, I32, I32],
+    })
     lib.pcdf_batch_destroy.argtypes = [P]
     lib.pcdf_batch_destroy.restype = None
+    lib.pcdf_destroy.argtypes = [P]
+    lib.pcdf_destroy.restype = None
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args

@@ -566,6 +566,131 @@ def hinge_cost(centres, radii, sdf, tidx, eps, grid):
 # batched environments: one persistent launch
 # ---------------------------------------------------------------------------
 
+class Context:
+    """The C interface's context (pcdf_create): a device, a stream and scratch
+    that the library owns and grows, so its calls take no workspace.  Each
+    method marshals its arguments for the pcdf_ctx_* call of the same name;
+    the stream is the device's current PyTorch stream at creation unless one
+    is given.  close() (or garbage collection) releases the scratch."""
+
+    def __init__(self, device, stream=None):
+        self._lib = _lib.load()
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        idx = self.device.index if self.device.index is not None else torch.cuda.current_device()
+        _lib.check(self._lib.pcdf_create(ctypes.byref(h), int(idx), ctypes.c_void_p(self.stream.cuda_stream)),
+                   "pcdf_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pcdf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    @staticmethod
+    def scratch_bytes(grid, T: int, H: int) -> int:
+        """Upper bound of the scratch of any call for grid with up to T fields and H humans."""
+        g = _cgrid(grid)
+        n = ctypes.c_size_t(0)
+        _lib.check(_lib.load().pcdf_scratch_bytes(ctypes.byref(g), int(T), int(H), ctypes.byref(n)),
+                   "pcdf_scratch_bytes")
+        return n.value
+
+    def reserve(self, nbytes: int):
+        _lib.check(self._lib.pcdf_ctx_reserve(self._h, int(nbytes)), "pcdf_ctx_reserve")
+
+    def build_static_sdf(self, occ: torch.Tensor, grid, want_sdf: bool = True):
+        shp = _shape(grid)
+        _need(occ, "occ", torch.uint8, shp)
+        sq = torch.empty(shp, dtype=torch.int32, device=occ.device)
+        sdf = torch.empty(shp, dtype=torch.float32, device=occ.device) if want_sdf else None
+        g = _cgrid(grid)
+        _lib.check(self._lib.pcdf_ctx_build_static_sdf(self._h, ctypes.byref(g), _ptr(occ), _ptr(sq), _ptr(sdf)),
+                   "pcdf_ctx_build_static_sdf")
+        return sq, sdf
+
+    def build_predicted_composite(self, static_sq: torch.Tensor, grid, caps, static_sdf=None, want_sq: bool = True,
+                                  want_sdf: bool = True):
+        shp = _shape(grid)
+        _need(static_sq, "static_sq", torch.int32, shp)
+        caps = _caps_host(caps)
+        T, H = int(caps.shape[0]), int(caps.shape[1])
+        dev = static_sq.device
+        sq = torch.empty((T,) + shp, dtype=torch.int32, device=dev) if want_sq else None
+        sdf = torch.empty((T,) + shp, dtype=torch.float32, device=dev) if want_sdf else None
+        g = _cgrid(grid)
+        cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+        _lib.check(self._lib.pcdf_ctx_build_predicted_composite(self._h, ctypes.byref(g), _ptr(static_sq),
+                                                                _ptr(static_sdf), T, H, cp, _ptr(sq), _ptr(sdf)),
+                   "pcdf_ctx_build_predicted_composite")
+        return sq, sdf
+
+    def build_from_scratch(self, occ: torch.Tensor, grid, caps, want_sdf: bool = True):
+        shp = _shape(grid)
+        _need(occ, "occ", torch.uint8, shp)
+        caps = _caps_host(caps)
+        T, H = int(caps.shape[0]), int(caps.shape[1])
+        sq = torch.empty((T,) + shp, dtype=torch.int32, device=occ.device)
+        sdf = torch.empty((T,) + shp, dtype=torch.float32, device=occ.device) if want_sdf else None
+        g = _cgrid(grid)
+        cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+        _lib.check(self._lib.pcdf_ctx_build_from_scratch(self._h, ctypes.byref(g), _ptr(occ), T, H, cp, _ptr(sq),
+                                                         _ptr(sdf)), "pcdf_ctx_build_from_scratch")
+        return sq, sdf
+
+    def query_cost(self, sdf: torch.Tensor, grid, spheres: torch.Tensor, tidx: torch.Tensor, eps: float):
+        sdf, T, N = _query_args(sdf, grid, spheres, tidx)
+        h = torch.empty(tidx.shape, dtype=torch.float32, device=sdf.device)
+        g = _cgrid(grid)
+        _lib.check(self._lib.pcdf_ctx_query_cost(self._h, ctypes.byref(g), _ptr(sdf), T, _ptr(spheres), _ptr(tidx),
+                                                 N, float(eps), _ptr(h), None), "pcdf_ctx_query_cost")
+        return h
+
+    def query_cost_backward(self, sdf: torch.Tensor, grid, spheres: torch.Tensor, tidx: torch.Tensor, eps: float,
+                            grad_h: torch.Tensor):
+        sdf, T, N = _query_args(sdf, grid, spheres, tidx)
+        _need(grad_h, "grad_h", torch.float32)
+        if grad_h.numel() != N:
+            raise ValueError("grad_h must have one entry per sphere")
+        gc = torch.empty(tuple(spheres.shape[:-1]) + (3,), dtype=torch.float32, device=sdf.device)
+        gr = torch.empty(tidx.shape, dtype=torch.float32, device=sdf.device)
+        g = _cgrid(grid)
+        _lib.check(self._lib.pcdf_ctx_query_cost_backward(self._h, ctypes.byref(g), _ptr(sdf), T, _ptr(spheres),
+                                                          _ptr(tidx), N, float(eps), _ptr(grad_h), _ptr(gc),
+                                                          _ptr(gr)), "pcdf_ctx_query_cost_backward")
+        return gc, gr
+
+    def build_batched(self, envs, use_graph: bool = True):
+        """envs: sequence of (grid, occ CUDA uint8, caps host int32 [T][H][7]);
+        returns the int32 composite fields of every environment.  Synchronises
+        the context's stream."""
+        arr = (_lib.PcdfEnv * len(envs))()
+        keep, outs = [], []
+        for i, (grid, occ, caps) in enumerate(envs):
+            _need(occ, f"occ[{i}]", torch.uint8, _shape(grid))
+            c = _caps_host(caps)
+            keep.append(c)
+            T, H = int(c.shape[0]), int(c.shape[1])
+            out = torch.empty((T,) + _shape(grid), dtype=torch.int32, device=occ.device)
+            outs.append(out)
+            arr[i].grid = _cgrid(grid)
+            arr[i].T = T
+            arr[i].H = H
+            arr[i].caps = c.ctypes.data if H > 0 else None
+            arr[i].occ = occ.data_ptr()
+            arr[i].comp_sq = out.data_ptr()
+        _lib.check(self._lib.pcdf_build_batched(self._h, arr, len(envs), 1 if use_graph else 0),
+                   "pcdf_build_batched")
+        return outs
+
+
 class Batch:
     """Many environments updated by one persistent kernel launch.
 

@@ -226,3 +226,35 @@ def test_bounds_check_entry_point_in_the_normal_build():
     assert lib.pcdf_bounds_check(ctypes.byref(first), ctypes.byref(count), 0) == -1
     assert "not a bounds-checked build" in err()
     assert first.value == 0 and count.value == 0
+
+
+def test_context_calls_check_their_arguments_before_the_device():
+    """The context calls refuse a NULL context (and pcdf_create a NULL out,
+    pcdf_build_batched a bad use_graph) before touching a device;
+    pcdf_destroy(NULL) is a no-op; pcdf_scratch_bytes bounds the scratch of
+    every context call (host only)."""
+    lib = _lib.load()
+    g = grid(64, 48, 32)
+    fake = ctypes.c_void_p(256)  # never dereferenced: the checks fail first
+    assert lib.pcdf_create(None, 0, None) == -1
+    lib.pcdf_destroy(None)
+    assert lib.pcdf_ctx_reserve(None, 1024) == -1
+    assert lib.pcdf_ctx_build_static_sdf(None, ctypes.byref(g), fake, fake, None) == -1
+    assert "ctx is NULL" in err()
+    assert lib.pcdf_ctx_build_predicted_composite(None, ctypes.byref(g), fake, None, 1, 0, None, fake, None) == -1
+    assert lib.pcdf_ctx_build_from_scratch(None, ctypes.byref(g), fake, 1, 0, None, fake, None) == -1
+    assert lib.pcdf_ctx_query_cost(None, ctypes.byref(g), fake, 1, fake, fake, 1, 0.2, fake, None) == -1
+    assert lib.pcdf_ctx_query_cost_backward(None, ctypes.byref(g), fake, 1, fake, fake, 1, 0.2, fake, fake,
+                                            None) == -1
+    assert lib.pcdf_build_batched(None, None, 1, 0) == -1
+    n = ctypes.c_size_t(0)
+    assert lib.pcdf_scratch_bytes(ctypes.byref(g), 5, 2, ctypes.byref(n)) == 0
+    V = 64 * 48 * 32
+    # a composite touching every slice: int16 and int32 slab intermediates and the column maxima
+    assert n.value >= 5 * V * 6 + 64 * 48 * 4
+    static = ctypes.c_size_t(0)
+    assert lib.pcdf_static_workspace_bytes(ctypes.byref(g), ctypes.byref(static)) == 0
+    assert n.value >= static.value
+    assert lib.pcdf_scratch_bytes(ctypes.byref(g), 0, 2, ctypes.byref(n)) == -1
+    assert lib.pcdf_scratch_bytes(ctypes.byref(g), 5, -1, ctypes.byref(n)) == -1
+    assert lib.pcdf_scratch_bytes(ctypes.byref(g), 5, 2, None) == -1
