@@ -217,6 +217,22 @@ int pcdf_composite_finish_range(const pcdf_grid *grid, const int32_t *static_sq,
                                 int32_t H, const int32_t *caps, int32_t t0, int32_t nt, int32_t *comp_sq,
                                 float *comp_sdf, void *workspace, size_t workspace_bytes, void *stream);
 
+/* One map update (Sec. 6, Sec. 8): the static field of occ and the T composite
+ * fields, with the same results as pcdf_build_static_sdf (static_sq, and
+ * static_sdf if non-NULL) followed by pcdf_build_predicted_composite, on two
+ * streams of the same device: the capsules' x+y pass runs on side_stream
+ * beside the static build on `stream`, and the composite's z stage on
+ * `stream` once both are done.  side_stream first waits for the work already
+ * on `stream`, and `stream` waits for side_stream's pass, so the call is
+ * ordered on `stream` like a one-stream call (events between the streams;
+ * nothing synchronises the host; capturable in a CUDA graph from `stream`).
+ * workspace: pcdf_update_workspace_bytes(grid, T, H, caps) bytes, 256-byte
+ * aligned (the static build's scratch, then the composite's). */
+int pcdf_update_workspace_bytes(const pcdf_grid *grid, int32_t T, int32_t H, const int32_t *caps, size_t *bytes);
+int pcdf_update_fields(const pcdf_grid *grid, const uint8_t *occ, int32_t T, int32_t H, const int32_t *caps,
+                       int32_t *static_sq, float *static_sdf, int32_t *comp_sq, float *comp_sdf, void *workspace,
+                       size_t workspace_bytes, void *stream, void *side_stream);
+
 /* ---------------------------------------------------------------------------
  * From-scratch comparator (Sec. 6 benchmark: a full exact EDT per subsequent
  * field instead of the composition).

@@ -32,6 +32,7 @@ from .api import (  # noqa: F401
     capsule_fixed,
     composite_finish,
     predicted_fields,
+    update_workspace,
     filter_voxels,
     collapse_2d,
     edt_2d,

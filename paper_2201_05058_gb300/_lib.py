@@ -36,7 +36,7 @@ EXPORTS = (
     "pcdf_static_workspace_bytes", "pcdf_build_static_sdf", "pcdf_build_static_sdf_noalloc",
     "pcdf_composite_workspace_bytes", "pcdf_build_predicted_composite",
     "pcdf_composite_prepare", "pcdf_composite_finish", "pcdf_composite_finish_range", "pcdf_composite_slab",
-    "pcdf_filter_voxels", "pcdf_collapse_2d",
+    "pcdf_filter_voxels", "pcdf_collapse_2d", "pcdf_update_workspace_bytes", "pcdf_update_fields",
     "pcdf_scratch_workspace_bytes", "pcdf_build_from_scratch",
     "pcdf_field_max", "pcdf_template_radius", "pcdf_lattice_placements", "pcdf_template_box", "pcdf_template_workspace_bytes", "pcdf_build_template", "pcdf_composite_translated",
     "pcdf_query_cost", "pcdf_query_cost_backward",
@@ -72,6 +72,8 @@ def _declare(lib):
         "pcdf_composite_finish": [G, P, P, I32, I32, P, P, P, P, SZ, P],
         "pcdf_composite_finish_range": [G, P, P, I32, I32, P, I32, I32, P, P, P, SZ, P],
         "pcdf_filter_voxels": [G, P, I32, P, P],
+        "pcdf_update_workspace_bytes": [G, I32, I32, P, SZP],
+        "pcdf_update_fields": [G, P, I32, I32, P, P, P, P, P, P, SZ, P, P],
         "pcdf_collapse_2d": [G, P, I32, I32, P, P],
         "pcdf_scratch_workspace_bytes": [G, I32, I32, SZP],
         "pcdf_build_from_scratch": [G, P, I32, I32, P, P, P, P, SZ, P],

@@ -271,32 +271,51 @@ def _side_stream(dev):
     return st
 
 
+def update_workspace(grid, caps, device) -> torch.Tensor:
+    """Workspace of predicted_fields (pcdf_update_workspace_bytes)."""
+    caps = _caps_host(caps)
+    T, H = int(caps.shape[0]), int(caps.shape[1])
+    g = _cgrid(grid)
+    cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+    n = ctypes.c_size_t(0)
+    _lib.check(_lib.load().pcdf_update_workspace_bytes(ctypes.byref(g), T, H, cp, ctypes.byref(n)),
+               "pcdf_update_workspace_bytes")
+    return _workspace(n.value, torch.device(device))
+
+
 def predicted_fields(occ: torch.Tensor, grid, caps, workspace=None, out_static_sq=None, out_static_sdf=None,
                      out_sq=None, out_sdf=None):
     """One map update (Sec. 6, Sec. 8): the static field of `occ` and the T
-    composite fields with the capsules `caps` (host int32 [T][H][7]).
-
-    The capsules' x+y pass does not depend on the static field, so it runs
-    on a side stream while the static field is built on the current stream;
-    the current stream then waits for it and runs the fused z pass.  Returns
-    (static_sq, static_sdf, comp_sq, comp_sdf); `workspace` (from
-    composite_workspace) and the outputs may be passed in to reuse them."""
+    composite fields with the capsules `caps` (host int32 [T][H][7]), through
+    pcdf_update_fields on the current stream and a side stream (the capsule
+    pass beside the static build).  Returns (static_sq, static_sdf, comp_sq,
+    comp_sdf); `workspace` (from update_workspace) and the outputs may be
+    passed in to reuse them."""
     dev = occ.device
     caps = _caps_host(caps)
-    T = int(caps.shape[0])
+    T, H = int(caps.shape[0]), int(caps.shape[1])
     shp = _shape(grid)
-    ws = workspace if workspace is not None else composite_workspace(grid, caps, dev)
+    _need(occ, "occ", torch.uint8, shp)
+    ws = workspace if workspace is not None else update_workspace(grid, caps, dev)
+    st_sq = out_static_sq if out_static_sq is not None else torch.empty(shp, dtype=torch.int32, device=dev)
+    st_sdf = out_static_sdf if out_static_sdf is not None else torch.empty(shp, dtype=torch.float32, device=dev)
     sq = out_sq if out_sq is not None else torch.empty((T,) + shp, dtype=torch.int32, device=dev)
     sdf = out_sdf if out_sdf is not None else torch.empty((T,) + shp, dtype=torch.float32, device=dev)
+    _need(st_sq, "static_sq", torch.int32, shp)
+    _need(st_sdf, "static_sdf", torch.float32, shp)
+    _need(sq, "comp_sq", torch.int32, (T,) + shp)
+    _need(sdf, "comp_sdf", torch.float32, (T,) + shp)
     main = torch.cuda.current_stream(dev)
     side = _side_stream(dev)
-    side.wait_stream(main)
-    with torch.cuda.stream(side):
-        composite_prepare(grid, caps, ws)
+    g = _cgrid(grid)
+    cp = caps.ctypes.data_as(ctypes.c_void_p) if H > 0 else None
+    _lib.check(_lib.load().pcdf_update_fields(ctypes.byref(g), _ptr(occ), T, H, cp, _ptr(st_sq), _ptr(st_sdf),
+                                              _ptr(sq), _ptr(sdf), _ptr(ws), ws.numel(),
+                                              ctypes.c_void_p(main.cuda_stream), ctypes.c_void_p(side.cuda_stream)),
+               "pcdf_update_fields")
     ws.record_stream(side)
-    st_sq, st_sdf = build_static_sdf(occ, grid, out_sq=out_static_sq, out_sdf=out_static_sdf)
-    main.wait_stream(side)
-    composite_finish(st_sq, grid, caps, ws, sq, sdf, static_sdf=st_sdf)
+    for t_ in (st_sq, st_sdf, sq, sdf, occ):
+        t_.record_stream(side)
     return st_sq, st_sdf, sq, sdf
 
 

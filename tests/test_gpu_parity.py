@@ -434,9 +434,9 @@ def test_query_edge_cases():
 
 
 def test_predicted_fields_overlapped_and_graph_captured():
-    """The one-call update (capsule x+y pass on a side stream, overlapping the
-    static build) equals the oracle, also when captured in a CUDA graph and
-    replayed on a new occupancy in the same buffers."""
+    """The one-call update (pcdf_update_fields: capsule x+y pass on a side
+    stream beside the static build) equals the oracle, also when captured in a
+    CUDA graph and replayed on a new occupancy in the same buffers."""
     sc = scenes.scene_small_walking(seed=31, T=6, H=2)
     grid, caps = sc["grid"], sc["caps"]
     d = torch.device("cuda", 0)
@@ -447,7 +447,7 @@ def test_predicted_fields_overlapped_and_graph_captured():
         assert_equal_fields(sq[t].cpu().numpy(), want[t], f"comp_sq[{t}]")
         assert_bits_equal(sdf[t].cpu().numpy(), oracle.sdf_from_sq(want[t], grid.vox), f"comp_sdf[{t}]")
     assert_equal_fields(st_sq.cpu().numpy(), oracle.edt(sc["occ"]), "static")
-    ws = pcdf.composite_workspace(grid, caps, d)
+    ws = pcdf.update_workspace(grid, caps, d)
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream(device=d)
     s.wait_stream(torch.cuda.current_stream(d))
