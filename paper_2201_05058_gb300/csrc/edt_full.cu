@@ -57,13 +57,14 @@ __global__ void __launch_bounds__(kCols * kB)
     full::edt_xy_block<kB, false>(bits, carry, nx, ny, nz, W, blockIdx.x, blockIdx.y, mid, smem);
 }
 
+// colmax (nullable): each column's largest value of sq
 template <int kB, bool kSdf>
 __global__ void __launch_bounds__(kCols * kB)
     k_edt_z(const int32_t *__restrict__ mid, int32_t *__restrict__ sq, float *__restrict__ sdf, float vox, int n,
-            long long ncols)
+            long long ncols, int32_t *__restrict__ colmax)
 {
     extern __shared__ uint32_t smem[];
-    full::edt_z_block<kB, kSdf, false>(mid, sq, sdf, vox, n, ncols, (long long)blockIdx.x * kCols, smem, nullptr);
+    full::edt_z_block<kB, kSdf, false>(mid, sq, sdf, vox, n, ncols, (long long)blockIdx.x * kCols, smem, colmax);
 }
 
 template <class K>
@@ -87,7 +88,7 @@ size_t full_edt_scratch(int nx, int ny, int nz, size_t *bits_off, size_t *carry_
 }
 
 cudaError_t launch_full_edt(int mode, const uint8_t *occ, const CapBatch *caps, int H, int nx, int ny, int nz,
-                            int32_t *sq, float *sdf, float vox, void *ws, cudaStream_t st)
+                            int32_t *sq, float *sdf, float vox, void *ws, cudaStream_t st, int32_t *colmax)
 {
     size_t bo, co, mo;
     full_edt_scratch(nx, ny, nz, &bo, &co, &mo);
@@ -119,11 +120,11 @@ cudaError_t launch_full_edt(int mode, const uint8_t *occ, const CapBatch *caps, 
     if (sdf) {
         if ((e = set_smem(k_edt_z<kZBands, true>, sz)) != cudaSuccess)
             return e;
-        k_edt_z<kZBands, true><<<nbz, kCols * kZBands, sz, st>>>(mid, sq, sdf, vox, nz, ncols);
+        k_edt_z<kZBands, true><<<nbz, kCols * kZBands, sz, st>>>(mid, sq, sdf, vox, nz, ncols, colmax);
     } else {
         if ((e = set_smem(k_edt_z<kZBands, false>, sz)) != cudaSuccess)
             return e;
-        k_edt_z<kZBands, false><<<nbz, kCols * kZBands, sz, st>>>(mid, sq, nullptr, vox, nz, ncols);
+        k_edt_z<kZBands, false><<<nbz, kCols * kZBands, sz, st>>>(mid, sq, nullptr, vox, nz, ncols, colmax);
     }
     return cudaGetLastError();
 }

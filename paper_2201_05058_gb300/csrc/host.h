@@ -26,7 +26,7 @@ int make_capinfo(const pcdf_grid *g, int T, int H, const int32_t *caps, std::vec
 int check_caps_args(int T, int H, const int32_t *caps);
 bool aligned(const void *p, size_t a);
 int run_full_edt(const pcdf_grid *g, int mode, const uint8_t *occ, const CapBatch *caps, int H, int32_t *sq,
-                 float *sdf, void *ws, cudaStream_t st);
+                 float *sdf, void *ws, cudaStream_t st, int32_t *colmax = nullptr);
 size_t full_edt_ws(const pcdf_grid *g);
 
 // Slab geometry and capsule table of one composite request.
@@ -49,9 +49,12 @@ int32_t *plan_mid(const CompositePlan &p, void *workspace);
 int check_ws(const CompositePlan &p, void *workspace, size_t workspace_bytes);
 int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &p, void *workspace,
                       cudaStream_t st);
-// fields t = t0 .. t0 + nt - 1 (outputs indexed by the absolute t)
+// fields t = t0 .. t0 + nt - 1 (outputs indexed by the absolute t);
+// have_colmax: the static column maxima are already at p.colmax_off in the
+// workspace (written by the static build), so they are not recomputed
 int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int t0, int nt,
-                     const CompositePlan &p, int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st);
+                     const CompositePlan &p, int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st,
+                     bool have_colmax = false);
 
 }  // namespace host
 }  // namespace pcdf

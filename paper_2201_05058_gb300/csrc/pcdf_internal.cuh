@@ -119,9 +119,12 @@ cudaError_t launch_pass_x(int mode, const uint8_t *occ, const CapBatch *caps, in
 // the capsules alone (mode 2), then the fused x+y pass and the z pass; sq and
 // (nullable) sdf are [nz][ny][nx].  ws holds full_edt_scratch() bytes
 // (256-byte aligned): row words, their carries and the 2-D partial field.
+// colmax (nullable): receives the largest value of every column of sq, as
+// launch_colmax would write it.
 size_t full_edt_scratch(int nx, int ny, int nz, size_t *bits_off, size_t *carry_off, size_t *mid_off);
 cudaError_t launch_full_edt(int mode, const uint8_t *occ, const CapBatch *caps, int H, int nx, int ny, int nz,
-                            int32_t *sq, float *sdf, float vox, void *ws, cudaStream_t stream);
+                            int32_t *sq, float *sdf, float vox, void *ws, cudaStream_t stream,
+                            int32_t *colmax = nullptr);
 
 // Lower-envelope pass over ncols columns: element e of column c lives at
 // (c / nx) * outer_stride + (c % nx) + e * stride, e in [0, n).

@@ -126,9 +126,9 @@ bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 // occupancy OR the capsules of one t, 2 the capsules alone), fused x+y pass,
 // z pass with optional float epilogue.
 int run_full_edt(const pcdf_grid *g, int mode, const uint8_t *occ, const pcdf::CapBatch *caps, int H, int32_t *sq,
-                 float *sdf, void *ws, cudaStream_t st)
+                 float *sdf, void *ws, cudaStream_t st, int32_t *colmax)
 {
-    cudaError_t e = pcdf::launch_full_edt(mode, occ, caps, H, g->nx, g->ny, g->nz, sq, sdf, g->vox, ws, st);
+    cudaError_t e = pcdf::launch_full_edt(mode, occ, caps, H, g->nx, g->ny, g->nz, sq, sdf, g->vox, ws, st, colmax);
     return e == cudaSuccess ? PCDF_OK : cuda_fail(e, "full EDT");
 }
 
@@ -292,7 +292,8 @@ int composite_prepare(const pcdf_grid *grid, int T, int H, const CompositePlan &
 }
 
 int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const float *static_sdf, int t0, int nt,
-                     const CompositePlan &p, int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st)
+                     const CompositePlan &p, int32_t *comp_sq, float *comp_sdf, void *workspace, cudaStream_t st,
+                     bool have_colmax)
 {
     cudaError_t e;
     if (p.S == 0) {
@@ -301,9 +302,11 @@ int composite_finish(const pcdf_grid *grid, const int32_t *static_sq, const floa
     }
     const int32_t *mid = plan_mid(p, workspace);
     int32_t *colmax = (int32_t *)((char *)workspace + p.colmax_off);
-    e = pcdf::launch_colmax(static_sq, grid->nx, grid->ny, grid->nz, colmax, st);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "static column maxima");
+    if (!have_colmax) {
+        e = pcdf::launch_colmax(static_sq, grid->nx, grid->ny, grid->nz, colmax, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "static column maxima");
+    }
     static thread_local pcdf::SlabMap map;
     slab_map(p, map);
     e = pcdf::launch_composite_z(static_sq, static_sdf, colmax, mid, &map, grid->nx, grid->ny, grid->nz, p.zlo, p.S,

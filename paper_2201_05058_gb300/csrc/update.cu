@@ -86,11 +86,13 @@ int pcdf_update_fields(const pcdf_grid *grid, const uint8_t *occ, int32_t T, int
             return rc;
     if ((e = cudaEventRecord(ev.done, sd)) != cudaSuccess)
         return cuda_fail(e, "update stream order");
-    if (int rc = run_full_edt(grid, 0, occ, &none, 0, static_sq, static_sdf, workspace, st))
+    // the static z pass also writes the column maxima that the z stage reads
+    int32_t *colmax = p.S > 0 ? (int32_t *)((char *)wsC + p.colmax_off) : nullptr;
+    if (int rc = run_full_edt(grid, 0, occ, &none, 0, static_sq, static_sdf, workspace, st, colmax))
         return rc;
     if ((e = cudaStreamWaitEvent(st, ev.done, 0)) != cudaSuccess)
         return cuda_fail(e, "update stream order");
-    return composite_finish(grid, static_sq, static_sdf, 0, T, p, comp_sq, comp_sdf, wsC, st);
+    return composite_finish(grid, static_sq, static_sdf, 0, T, p, comp_sq, comp_sdf, wsC, st, colmax != nullptr);
 }
 
 }  // extern "C"

@@ -271,15 +271,19 @@ def big_scene():
     grid = sc["grid"]
     static_sq, static_sdf = pcdf.build_static_sdf(cuda(sc["occ"]), grid)
     comp_sq, comp_sdf = pcdf.build_predicted_composite(static_sq, grid, sc["caps"], static_sdf=static_sdf)
+    # the benchmark's one-call update (its static z pass also writes the column maxima of the z stage)
+    up = pcdf.predicted_fields(cuda(sc["occ"]), grid, sc["caps"])
     torch.cuda.synchronize()
-    return sc, static_sq.cpu().numpy(), static_sdf.cpu().numpy(), comp_sq, comp_sdf
+    return sc, static_sq.cpu().numpy(), static_sdf.cpu().numpy(), comp_sq, comp_sdf, up
 
 
 def test_full_size_static_matches_oracle(big_scene):
-    sc, static_sq, static_sdf, _, _ = big_scene
+    sc, static_sq, static_sdf, _, _, up = big_scene
     want = oracle.edt(sc["occ"])
     assert_equal_fields(static_sq, want, "static_sq 256^3")
     assert_bits_equal(static_sdf, oracle.sdf_from_sq(want, sc["grid"].vox), "static_sdf 256^3")
+    assert_equal_fields(up[0].cpu().numpy(), want, "update static_sq 256^3")
+    assert_bits_equal(up[1].cpu().numpy(), oracle.sdf_from_sq(want, sc["grid"].vox), "update static_sdf 256^3")
     # and against the definition at sampled voxels
     rng = np.random.default_rng(0)
     for _ in range(60):
@@ -289,14 +293,17 @@ def test_full_size_static_matches_oracle(big_scene):
 
 @pytest.mark.parametrize("t", [0, 9, 19])
 def test_full_size_composite_matches_oracle(big_scene, t):
-    sc, _, _, comp_sq, comp_sdf = big_scene
+    sc, _, _, comp_sq, comp_sdf, up = big_scene
     grid = sc["grid"]
     S_static = oracle.edt(sc["occ"])
     dyn_occ = oracle.capsule_occupancy(grid.shape, sc["caps"][t])
     want = oracle.composite(S_static, oracle.edt(dyn_occ))
     got = comp_sq[t].cpu().numpy()
+    want_sdf = oracle.sdf_from_sq(want, grid.vox)
     assert_equal_fields(got, want, f"comp_sq[{t}] 256^3")
-    assert_bits_equal(comp_sdf[t].cpu().numpy(), oracle.sdf_from_sq(want, grid.vox), f"comp_sdf[{t}] 256^3")
+    assert_bits_equal(comp_sdf[t].cpu().numpy(), want_sdf, f"comp_sdf[{t}] 256^3")
+    assert_equal_fields(up[2][t].cpu().numpy(), want, f"update comp_sq[{t}] 256^3")
+    assert_bits_equal(up[3][t].cpu().numpy(), want_sdf, f"update comp_sdf[{t}] 256^3")
     # sampled against the definition, biased towards the humans
     rng = np.random.default_rng(t)
     occ_pts = np.argwhere(dyn_occ)
