@@ -26,7 +26,8 @@ __global__ void __launch_bounds__(128)
 }
 
 // CTAs are ordered t-fastest, so the T CTAs of one column block run together
-// and read the static column block from DRAM once.
+// and read the static column block from DRAM once; each of them prefetches
+// every nt-th plane of that block into L2 before its own work.
 template <bool kSq, bool kSdfOut, bool kStaticSdf>
 __global__ void __launch_bounds__(128, 8)
     k_composite_z(const int32_t *__restrict__ static_sq, const float *__restrict__ static_sdf,
@@ -39,7 +40,8 @@ __global__ void __launch_bounds__(128, 8)
     comp::composite_block_short<kSq, kSdfOut, kStaticSdf>(static_sq, static_sdf, colmax, dyn_mid,
                                                           map.on ? map.rep + t * S : nullptr, nx, ny, nz, zlo, S, t,
                                                           (long long)(blockIdx.x / nt) * blockDim.x, comp_sq, comp_sdf,
-                                                          vox, vec != 0, smem);
+                                                          vox, vec != 0, smem, (int)(blockIdx.x % nt),
+                                                          vec ? nt : 0);
 }
 
 __global__ void __launch_bounds__(128) k_colmax(const int32_t *__restrict__ sq, long long V2, int nz,

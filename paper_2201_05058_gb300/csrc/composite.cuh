@@ -358,6 +358,13 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16); nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Largest value of each column c of a field [nz][V2]: warp w of the CTA reads
 // the z quarter w of 32 consecutive columns (lane = column).
 __device__ __forceinline__ void colmax_block(const int32_t *__restrict__ sq, long long V2, int nz,
@@ -556,8 +563,12 @@ __device__ __forceinline__ void composite_block(const int32_t *__restrict__ stat
 // the static shortcuts.  colmax: the largest static value of every column;
 // rep (nullable: the identity): slab element e of time t is stored in slice
 // rep[e] (slices of equal capsule cross-sections computed once); vec: the
-// CTA may copy with 16-byte accesses.  Block-wide barriers: every thread of
-// the CTA calls.
+// CTA may copy with 16-byte accesses.  pf_parts > 0 (needs vec): the CTA
+// first asks L2 to prefetch planes pf_part, pf_part + pf_parts, ... of its
+// static column block (bulk prefetches, no registers held), so that the
+// CTAs that share the block (one per t) split the block between them and
+// their loads of it hit L2.  Block-wide barriers: every thread of the CTA
+// calls.
 //  * every column static (colmax <= gmin): the CTA copies the static block;
 //  * else each column with dynamic influence has a window [w0, w1) (the slab
 //    and every z less than R slices from it, R the least integer with
@@ -573,13 +584,27 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
                                                       const uint8_t *__restrict__ rep, int nx, int ny, int nz,
                                                       int zlo, int S, int t, long long col0,
                                                       int32_t *__restrict__ comp_sq, float *__restrict__ comp_sdf,
-                                                      float vox, bool vec, uint32_t *smem)
+                                                      float vox, bool vec, uint32_t *smem, int pf_part = 0,
+                                                      int pf_parts = 0)
 {
     __shared__ int s_w0, s_w1, s_occ;
     const int nthr = blockDim.x, tid = threadIdx.x;
     const long long V2 = (long long)nx * ny;
     const long long c = col0 + tid;
     const bool live = c < V2;
+    if (pf_parts > 0) {
+        // the block's columns of one plane: a multiple of 16 bytes from a
+        // 16-byte boundary (V2 % 4 == 0, col0 % 4 == 0, aligned fields)
+        const uint32_t nb = (uint32_t)min((long long)nthr, V2 - col0) * 4u;
+        for (int z = pf_part + pf_parts * tid; z < nz; z += pf_parts * nthr) {
+            const long long o = (long long)z * V2 + col0;
+            if (!PCDF_IN(o + nb / 4 - 1, V2 * nz))
+                continue;
+            prefetch_l2(static_sq + o, nb);
+            if (kStaticSdf)
+                prefetch_l2(static_sdf + o, nb);
+        }
+    }
     uint32_t *tile = smem + tid;                              // slot k at tile[k * nthr]
     uint32_t *mk = smem + (size_t)(S + 2) * nthr + tid;       // word w at mk[w * nthr]
     const int32_t *dcol = dyn_mid + (long long)t * S * V2 + c;
