@@ -185,11 +185,15 @@ __global__ void __launch_bounds__(kThreads)
             break;
         const BatchItem I = items[it];
         const BatchEnv &E = envs[I.env];
+        // the items of a column block (one per group of comp_t steps) split
+        // the L2 prefetch of its static columns, before their first step
+        const int ngroups = (E.T + comp_t - 1) / comp_t;
         for (int t = I.a; t < min(I.a + comp_t, E.T); ++t) {
             comp::composite_block_short<true, false, false>(E.static_sq, nullptr, E.colmax, E.dyn,
                                                             E.rep ? E.rep + t * E.S : nullptr, E.nx, E.ny, E.nz,
                                                             E.zlo, E.S, t, (long long)I.b, E.comp_sq, nullptr,
-                                                            E.vox, E.vec != 0, smem);
+                                                            E.vox, E.vec != 0, smem, I.a / comp_t,
+                                                            t == I.a && E.vec ? ngroups : 0);
             __syncthreads();
         }
     }
