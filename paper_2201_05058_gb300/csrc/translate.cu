@@ -13,11 +13,11 @@
 //
 // k_composite_translated: each warp owns kTrRowIters output rows (y, z) of
 // one t, lanes over x in 16-byte groups of 4 voxels (two groups per lane in
-// flight); each CTA owns a block of
-// rows and the T CTAs of a row block are adjacent, so the static rows come
-// from DRAM once.  The boxes that cross a row are found from the placements
-// alone (kernel parameters), so rows outside every box are plain copies of
-// the static row.
+// flight); each CTA owns a block of rows and the T CTAs of a row block are
+// adjacent, so the static rows come from DRAM once (prefetched into L2 by
+// those CTAs together).  The boxes that cross a row are found from the
+// placements alone (kernel parameters), so rows outside every box are plain
+// copies of the static row.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -163,6 +163,22 @@ __global__ void __launch_bounds__(32 * kTrWarps)
     const int4 *place = pl.place + lt * H;
     int32_t *oq = kSq ? comp_sq + (long long)(t0 + lt) * V : nullptr;
     float *of = kSdfOut ? comp_sdf + (long long)(t0 + lt) * V : nullptr;
+    if (vec) {
+        // the CTA's static rows are one contiguous range; the nt CTAs of the
+        // row block split its L2 prefetch in 4 KB pieces (16-byte aligned,
+        // whole multiples of 16 bytes: nx % 4 == 0, aligned fields)
+        const long long r0 = blk * kTrRowIters * kTrWarps;
+        const long long r1 = min(r0 + kTrRowIters * kTrWarps, nrows);
+        const long long e0 = r0 * nx, e1 = r1 * nx;
+        for (long long a = e0 + (long long)(lt + nt * (int)threadIdx.x) * 1024; a < e1;
+             a += (long long)nt * blockDim.x * 1024) {
+            const uint32_t bytes = (uint32_t)(min(a + 1024, e1) - a) * 4u;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_sq + a), "r"(bytes) : "memory");
+            if (kStaticSdf)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_sdf + a), "r"(bytes)
+                             : "memory");
+        }
+    }
     for (int it = 0; it < kTrRowIters; ++it) {
         const long long row = (blk * kTrRowIters + it) * kTrWarps + warp;
         if (row >= nrows)
