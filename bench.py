@@ -58,8 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
-    ap.add_argument("--profile-case", choices=["composite", "static", "scratch", "query", "mlp", "train", "surrogate",
-                                               "translated"],
+    ap.add_argument("--profile-case", choices=["composite", "update", "static", "scratch", "query", "mlp", "train",
+                                               "surrogate", "translated"],
                     default=None,
                     help="run one small untimed case of the named stage (for ncu captures) and exit")
     ap.add_argument("--profile-T", type=int, default=4, help="horizon of the --profile-case composite")
@@ -981,6 +981,14 @@ def run_profile_case(args):
             pcdf.composite_translated(static_sq, grid, tmpl, lo, R, static_sdf=static_sdf)
         torch.cuda.synchronize()
         print("profile case translated done")
+        return 0
+    if args.profile_case == "update":
+        # the headline step: one-call update (capsule pass on a side stream)
+        ws = pcdf.update_workspace(grid, caps, dev)
+        for _ in range(2):
+            pcdf.predicted_fields(occ, grid, caps, workspace=ws)
+        torch.cuda.synchronize()
+        print("profile case update done")
         return 0
     for _ in range(2):
         if args.profile_case in ("static", "composite"):

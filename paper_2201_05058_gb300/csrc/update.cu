@@ -3,8 +3,10 @@
 // then pcdf_build_predicted_composite, with the capsules' x+y pass (it needs
 // no static field) on a side stream beside the static build.  The side stream
 // first waits for the work already on the stream; the stream waits for the
-// capsule pass before the composite's z stage.  Events are created per call
-// (no timing) and released before returning; nothing synchronises the host.
+// capsule pass before the composite's z stage.  The static z pass also writes
+// the static column maxima that the z stage reads (no separate pass over the
+// static field).  Events are created per call (no timing) and released before
+// returning; nothing synchronises the host.
 //
 // Splitting the z stage into column chunks that start behind the static z
 // pass, chunk by chunk, was measured slower (0.967 ms per headline step
