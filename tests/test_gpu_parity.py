@@ -169,6 +169,19 @@ def test_composite_slab_map_dedup_and_its_limits():
     check_composite(occ_m, caps_m, mid)
 
 
+def test_composite_tall_slab_narrow_ctas():
+    """A slab of more than 400 slices leaves shared memory for 64 columns per
+    CTA of the z stage: with 96 columns per slice the second CTA of each t has
+    32 live columns, and each CTA prefetches its own part of the static planes
+    into L2 (16-byte aligned outputs)."""
+    grid = scenes.Grid(12, 8, 512, 0.05)
+    occ = np.zeros(grid.shape, np.uint8)
+    occ[100:140, 2:5, 1:4] = 1
+    occ[300:310, :, 9] = 1
+    caps = np.array([[[96, 64, 168, 96, 64, 7048, 24]], [[112, 64, 168, 112, 64, 7048, 24]]], np.int32)
+    check_composite(occ, caps, grid)
+
+
 def test_composite_odd_slice_size():
     # nx * ny not a multiple of 4: all-static column blocks are copied one
     # column per thread instead of with 16-byte accesses
