@@ -28,12 +28,38 @@ def noisy(shape, seed, density=0.01):
     return grid, occ
 
 
-@pytest.mark.parametrize("shape", [(64, 64, 64), (30, 17, 33), (40, 1, 1), (5, 9, 70), (1, 1, 1), (20, 260, 37)])
+# nx a multiple of 4 takes the kernel that filters four voxels per thread
+# (one warp per row of up to 128 voxels: 132 spans two warps, 4 is one word);
+# the other widths take the byte kernel
+@pytest.mark.parametrize("shape", [(64, 64, 64), (30, 17, 33), (40, 1, 1), (5, 9, 70), (1, 1, 1), (20, 260, 37),
+                                   (33, 7, 132), (3, 70, 36), (17, 5, 4), (70, 9, 8)])
 @pytest.mark.parametrize("k", [5, 0, 3, 27])
 def test_voxel_filter_matches_oracle(shape, k):
     grid, occ = noisy(shape, seed=sum(shape) + k)
     got = pcdf.filter_voxels(cuda(occ), grid, k).cpu().numpy()
     assert np.array_equal(got, oracle.voxel_filter(occ, k))
+
+
+def test_voxel_filter_any_nonzero_byte_is_occupied():
+    """Occupancy bytes other than 0 and 1 (2, 7, 128, 255) count as occupied in
+    both kernels; the output is 0/1."""
+    for shape in ((21, 13, 48), (21, 13, 47)):
+        grid, occ = noisy(shape, seed=77, density=0.05)
+        rng = np.random.default_rng(5)
+        vals = rng.choice(np.array([1, 2, 7, 128, 255], np.uint8), size=occ.shape)
+        occ_v = (occ * vals).astype(np.uint8)
+        got = pcdf.filter_voxels(cuda(occ_v), grid, 4).cpu().numpy()
+        assert np.array_equal(got, oracle.voxel_filter(occ_v, 4)), shape
+
+
+def test_voxel_filter_unaligned_map_takes_the_byte_kernel():
+    grid, occ = noisy((12, 10, 64), seed=9, density=0.05)
+    d = cuda(occ)
+    flat = torch.zeros(occ.size + 1, dtype=torch.uint8, device=d.device)
+    flat[1:].copy_(d.reshape(-1))
+    view = flat[1:].view(occ.shape)  # starts one byte past an aligned address
+    got = pcdf.filter_voxels(view, grid, 5).cpu().numpy()
+    assert np.array_equal(got, oracle.voxel_filter(occ, 5))
 
 
 def test_voxel_filter_full_size_scene():
