@@ -40,12 +40,12 @@ constexpr int kZBands = PCDF_Z_BANDS;    // envelope threads per column, z pass
 template <int kMode>
 __global__ void __launch_bounds__(32 * kRowsPerCta)
     k_row_bits(const uint8_t *__restrict__ occ, const __grid_constant__ CapBatch caps, int H, int nx, int ny,
-               long long nrows, int W, uint32_t *__restrict__ bits, uint2 *__restrict__ carry)
+               long long nrows, int W, uint32_t *__restrict__ bits, uint2 *__restrict__ carry, int vec4)
 {
     const long long row = (long long)blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
     if (row >= nrows)
         return;  // warp-uniform
-    full::row_bits_row<kMode>(occ, caps.caps, H, nx, ny, row, nrows, W, bits, carry, threadIdx.x & 31);
+    full::row_bits_row<kMode>(occ, caps.caps, H, nx, ny, row, nrows, W, bits, carry, threadIdx.x & 31, vec4 != 0);
 }
 
 template <int kB>
@@ -98,10 +98,18 @@ cudaError_t launch_full_edt(int mode, const uint8_t *occ, const CapBatch *caps, 
     const int W = (nx + 31) / 32;
     const long long nrows = (long long)ny * nz;
     const unsigned nb = (unsigned)((nrows + kRowsPerCta - 1) / kRowsPerCta);
+    // occupancy rows of whole 32-bit words: read four bytes per lane
+    const int vec4 = nx % 4 == 0 && ((uintptr_t)occ & 3u) == 0;
     switch (mode) {
-    case 0: k_row_bits<0><<<nb, 32 * kRowsPerCta, 0, st>>>(occ, *caps, H, nx, ny, nrows, W, bits, carry); break;
-    case 1: k_row_bits<1><<<nb, 32 * kRowsPerCta, 0, st>>>(occ, *caps, H, nx, ny, nrows, W, bits, carry); break;
-    default: k_row_bits<2><<<nb, 32 * kRowsPerCta, 0, st>>>(occ, *caps, H, nx, ny, nrows, W, bits, carry); break;
+    case 0:
+        k_row_bits<0><<<nb, 32 * kRowsPerCta, 0, st>>>(occ, *caps, H, nx, ny, nrows, W, bits, carry, vec4);
+        break;
+    case 1:
+        k_row_bits<1><<<nb, 32 * kRowsPerCta, 0, st>>>(occ, *caps, H, nx, ny, nrows, W, bits, carry, 0);
+        break;
+    default:
+        k_row_bits<2><<<nb, 32 * kRowsPerCta, 0, st>>>(occ, *caps, H, nx, ny, nrows, W, bits, carry, 0);
+        break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

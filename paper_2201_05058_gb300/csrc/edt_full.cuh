@@ -42,13 +42,25 @@ __device__ __forceinline__ uint32_t pack16(int lo, int hi)
     return (uint32_t)(uint16_t)(int16_t)lo | ((uint32_t)(uint16_t)(int16_t)hi << 16);
 }
 
+// 0x01 in every byte of w that is non-zero, 0x00 elsewhere
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t w)
+{
+    uint32_t t = w | (w >> 4);
+    t |= t >> 2;
+    t |= t >> 1;
+    return t & 0x01010101u;
+}
+
 // One warp: row `row` = z * ny + y.  kMode 0: occupancy, 1: occupancy OR the
 // capsules caps[0 .. H), 2: the capsules alone.  W = ceil(nx / 32) <= 16.
-// nrows: the grid's rows (for the bounds checks).
+// nrows: the grid's rows (for the bounds checks).  vec4 (mode 0 only; needs
+// nx % 4 == 0 and a 4-byte aligned occ): the occupancy is read four bytes per
+// lane, and the eight lanes of a row word assemble its bits by shuffles.
 template <int kMode>
 __device__ __forceinline__ void row_bits_row(const uint8_t *__restrict__ occ, const CapInfo *caps, int H, int nx,
                                              int ny, long long row, long long nrows, int W,
-                                             uint32_t *__restrict__ bits, uint2 *__restrict__ carry, int lane)
+                                             uint32_t *__restrict__ bits, uint2 *__restrict__ carry, int lane,
+                                             bool vec4 = false)
 {
     const int y = (int)(row % ny), z = (int)(row / ny);
     unsigned long long active = 0;  // capsules whose box crosses this row (H <= 64)
@@ -61,7 +73,25 @@ __device__ __forceinline__ void row_bits_row(const uint8_t *__restrict__ occ, co
     }
     const uint8_t *src = occ + row * nx;
     uint32_t mine = 0;  // word `lane` of the row
-    for (int w = 0; w < W; ++w) {
+    if (kMode == 0 && vec4) {
+        // pass p: lane l reads voxels 128 p + 4 l .. + 3; lanes 8 g .. 8 g + 7
+        // hold word 4 p + g, four bits each
+        const uint32_t *src4 = reinterpret_cast<const uint32_t *>(src);
+        for (int p = 0; 4 * p < W; ++p) {
+            const int x = 128 * p + 4 * lane;
+            uint32_t v = 0;
+            if (x < nx && PCDF_IN(row * nx + x + 3, nrows * nx))
+                v = __ldg(src4 + (x >> 2));
+            uint32_t m = ((nonzero_bytes(v) * 0x01020408u) >> 24) << (4 * (lane & 7));
+            m |= __shfl_xor_sync(0xffffffffu, m, 1);
+            m |= __shfl_xor_sync(0xffffffffu, m, 2);
+            m |= __shfl_xor_sync(0xffffffffu, m, 4);
+            const uint32_t word = __shfl_sync(0xffffffffu, m, 8 * ((lane - 4 * p) & 3));
+            if (lane >= 4 * p && lane < 4 * p + 4)
+                mine = word;
+        }
+    }
+    for (int w = 0; w < W && !(kMode == 0 && vec4); ++w) {
         const int x = 32 * w + lane;
         bool o = false;
         if (x < nx) {
