@@ -48,8 +48,10 @@ __global__ void __launch_bounds__(32 * kRowsPerCta)
     full::row_bits_row<kMode>(occ, caps.caps, H, nx, ny, row, nrows, W, bits, carry, threadIdx.x & 31, vec4 != 0);
 }
 
+// six CTAs of 256 threads per SM: 42 registers, and the tile (33 KB at 256
+// rows) with the 16-bit band table fits six times
 template <int kB>
-__global__ void __launch_bounds__(kCols * kB)
+__global__ void __launch_bounds__(kCols * kB, 6)
     k_edt_xy(const uint32_t *__restrict__ bits, const uint2 *__restrict__ carry, int nx, int ny, int nz, int W,
              int32_t *__restrict__ mid)
 {
@@ -57,9 +59,10 @@ __global__ void __launch_bounds__(kCols * kB)
     full::edt_xy_block<kB, false>(bits, carry, nx, ny, nz, W, blockIdx.x, blockIdx.y, mid, smem);
 }
 
-// colmax (nullable): each column's largest value of sq
+// colmax (nullable): each column's largest value of sq; five CTAs of 256
+// threads per SM (51 registers)
 template <int kB, bool kSdf>
-__global__ void __launch_bounds__(kCols * kB)
+__global__ void __launch_bounds__(kCols * kB, 5)
     k_edt_z(const int32_t *__restrict__ mid, int32_t *__restrict__ sq, float *__restrict__ sdf, float vox, int n,
             long long ncols, int32_t *__restrict__ colmax)
 {

@@ -56,12 +56,14 @@ constexpr int kMaxSide = 512;           // longest axis (PCDF_MAX_DIM)
 enum : int { kSingle = 1, kFirstOcc = 2, kLastOcc = 4, kEmpty = 8 };
 
 // Per band and column: the first piece (start slot, entries), the last piece
-// (unused when kSingle: the band is one piece) and flags.
+// (unused when kSingle: the band is one piece) and flags.  16-bit entries
+// (slots and counts are at most kMaxSide), so that the table takes half the
+// shared memory of 32-bit ones.
 template <int kB>
 struct Seg {
-    int fS[kB][kCols], fK[kB][kCols];
-    int lS[kB][kCols], lK[kB][kCols];
-    int fl[kB][kCols];
+    int16_t fS[kB][kCols], fK[kB][kCols];
+    int16_t lS[kB][kCols], lK[kB][kCols];
+    int16_t fl[kB][kCols];
 };
 
 PCDF_HD int clz32(uint32_t x)
