@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kCols * kB, 6)
 }
 
 // colmax (nullable): each column's largest value of sq; five CTAs of 256
-// threads per SM (51 registers)
+// threads per SM (51 registers: held to 42 for six, it spills and is slower)
 template <int kB, bool kSdf>
 __global__ void __launch_bounds__(kCols * kB, 5)
     k_edt_z(const int32_t *__restrict__ mid, int32_t *__restrict__ sq, float *__restrict__ sdf, float vox, int n,

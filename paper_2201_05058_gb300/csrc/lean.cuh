@@ -60,7 +60,7 @@ enum : int { kSingle = 1, kFirstOcc = 2, kLastOcc = 4, kEmpty = 8 };
 // (slots and counts are at most kMaxSide), so that the table takes half the
 // shared memory of 32-bit ones.
 template <int kB>
-struct Seg {
+struct alignas(16) Seg {
     int16_t fS[kB][kCols], fK[kB][kCols];
     int16_t lS[kB][kCols], lK[kB][kCols];
     int16_t fl[kB][kCols];
