@@ -313,7 +313,11 @@ __device__ __forceinline__ void edt_z_block(const int32_t *__restrict__ mid, int
         mx = lean::eval_band<kB>(tile, mk, seg, n, L, c, b, out).mx;
     }
     if (colmax) {  // uniform over the CTA
-        __shared__ int32_t s_max[kB][kCols];
+        // the band table is done with once every band has been evaluated:
+        // its storage holds the bands' maxima
+        static_assert(sizeof(lean::Seg<kB>) >= sizeof(int32_t) * kB * kCols, "band table too small");
+        __syncthreads();
+        int32_t(*s_max)[kCols] = reinterpret_cast<int32_t(*)[kCols]>(&seg);
         s_max[b][c] = mx;
         __syncthreads();
         if (b == 0 && live && PCDF_IN(cl, ncols)) {
