@@ -773,9 +773,6 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                             ok = false;
                             break;
                         }
-                        if (kMode != 0 && c == ws::kChunks - 1)  // H_L complete in the A buffer: to memory
-                            tc::bulk_store(reinterpret_cast<unsigned char *>(L == 1 ? io.H1 : io.H2) + tile * kTileBytes,
-                                           sA, ws::kBytesA);
                         tc::fence_after();
 #pragma unroll
                         for (int kk = 0; kk < tc::kKC / 16; ++kk) {
@@ -786,10 +783,6 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                         }
                         tc::commit(&empty[st]);
                     }
-                    // the epilogue overwrites the A buffer once the accumulator is
-                    // full: the copy to memory has read it by then
-                    if (kMode != 0)
-                        tc::bulk_wait_read();
                     if (ok)
                         tc::commit(&accfull[q & 1]);
                 }
@@ -800,8 +793,6 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                 ok = gw4_products(it - 1);
             if (!ok)
                 s_fail = 1;
-            if (kMode != 0)
-                tc::bulk_wait_all();
             // every product issued has finished before the tensor memory is freed
             tc::commit(&drain);
             (void)tc::mbar_wait(&drain, 0);
@@ -918,12 +909,15 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                     const float *bias = sBias + L * kW;
                     const bool with_bias = L == 1;  // the first layer's bias came with its product
                     uint32_t *mk = nullptr;
-                    if constexpr (kMode != 0)
+                    unsigned char *hst = nullptr;
+                    if constexpr (kMode != 0) {
                         mk = (L == 0 ? io.mask1 : io.mask2) + tile * (kMaskTileBytes / 4);
-                    // slice j (32 columns): bias, ReLU, BF16 into the A operand, then
-                    // its chunk's barrier (modes 1, 2: the product thread copies the
-                    // complete tile to memory), then the slice's mask word; the next
-                    // slice's load is in flight meanwhile
+                        hst = reinterpret_cast<unsigned char *>(L == 0 ? io.H1 : io.H2) + tile * kTileBytes;
+                    }
+                    // slice j (32 columns): bias, ReLU, BF16 into the A operand (modes
+                    // 1, 2: and the same 16 bytes into the stored tile, which has the
+                    // operand's layout), then its chunk's barrier, then the slice's
+                    // mask word; the next slice's load is in flight meanwhile
                     auto slice = [&](const uint32_t(&v)[32], int j, int) {
                         uint4 keep[4];
 #pragma unroll
@@ -943,7 +937,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                                 pk.z = bf2_relu_bits(__uint_as_float(u[4]), __uint_as_float(u[5]));
                                 pk.w = bf2_relu_bits(__uint_as_float(u[6]), __uint_as_float(u[7]));
                             }
-                            *reinterpret_cast<uint4 *>(sA + tc::kmaj(r, 32 * j + 8 * gq, kW)) = pk;
+                            const uint32_t off = tc::kmaj(r, 32 * j + 8 * gq, kW);
+                            *reinterpret_cast<uint4 *>(sA + off) = pk;
+                            if constexpr (kMode != 0)
+                                *reinterpret_cast<uint4 *>(hst + off) = pk;
                             keep[gq] = pk;
                         }
                         tc::fence_proxy_async();
