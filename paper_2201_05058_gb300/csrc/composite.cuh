@@ -388,15 +388,16 @@ __device__ __forceinline__ void colmax_block(const int32_t *__restrict__ sq, lon
         colmax[c] = max(max(part[0][lane], part[1][lane]), max(part[2][lane], part[3][lane]));
 }
 
-// The static field as the composite of time t on columns [col0, col0 + ncols)
-// (ncols a multiple of 4): 16-byte loads and stores, thread tid on the column
-// quad tid % nq of the planes tid / nq, tid / nq + nthr / nq, ...  Needs
-// V2 % 4 == 0, col0 % 4 == 0 and 16-byte aligned fields.
+// The static field as the composite of time t on planes [z0, z1) of columns
+// [col0, col0 + ncols) (ncols a multiple of 4): 16-byte loads and stores,
+// thread tid on the column quad tid % nq of the planes z0 + tid / nq,
+// z0 + tid / nq + nthr / nq, ...  Needs V2 % 4 == 0, col0 % 4 == 0 and 16-byte
+// aligned fields.
 template <bool kSq, bool kSdfOut, bool kStaticSdf, bool kCoherent>
-__device__ __forceinline__ void copy_static_block(const int32_t *__restrict__ static_sq,
-                                                  const float *__restrict__ static_sdf, long long V2, int nz,
-                                                  long long col0, int ncols, int32_t *__restrict__ osq,
-                                                  float *__restrict__ osdf, float vox)
+__device__ __forceinline__ void copy_static_planes(const int32_t *__restrict__ static_sq,
+                                                   const float *__restrict__ static_sdf, long long V2, int nz, int z0,
+                                                   int z1, long long col0, int ncols, int32_t *__restrict__ osq,
+                                                   float *__restrict__ osdf, float vox)
 {
     const int nq = ncols >> 2;
     const int zstep = blockDim.x / nq;
@@ -405,7 +406,7 @@ __device__ __forceinline__ void copy_static_block(const int32_t *__restrict__ st
         return;
     const long long base = col0 + 4 * qd;
 #pragma unroll 4
-    for (int z = zfirst; z < nz; z += zstep) {
+    for (int z = z0 + zfirst; z < z1; z += zstep) {
         const long long o = (long long)z * V2 + base;
         if (!PCDF_IN(o + 3, V2 * nz))
             continue;
@@ -572,10 +573,11 @@ __device__ __forceinline__ void composite_block(const int32_t *__restrict__ stat
 //  * every column static (colmax <= gmin): the CTA copies the static block;
 //  * else each column with dynamic influence has a window [w0, w1) (the slab
 //    and every z less than R slices from it, R the least integer with
-//    gmin + R^2 >= colmax; beyond it the static field wins).  All threads
-//    work over the union of the windows, so every lane of a warp runs the
-//    same z loops and the accesses of a z stay coalesced: copies outside it,
-//    the envelope inside it (+INF for the static columns).
+//    gmin + R^2 >= colmax; beyond it the static field wins).  Outside the
+//    union of the windows the block is copied (16-byte accesses when vec,
+//    else per column); inside it every lane of a warp runs the same z loops,
+//    so the accesses of a z stay coalesced, with the envelope (+INF for the
+//    static columns).
 template <bool kSq, bool kSdfOut, bool kStaticSdf>
 __device__ __forceinline__ void composite_block_short(const int32_t *__restrict__ static_sq,
                                                       const float *__restrict__ static_sdf,
@@ -638,8 +640,8 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
     const int V2i = (int)V2;
     if (__syncthreads_and(!live || col_static)) {
         if (vec) {
-            copy_static_block<kSq, kSdfOut, kStaticSdf, false>(
-                static_sq, static_sdf, V2, nz, col0, (int)min((long long)nthr, V2 - col0),
+            copy_static_planes<kSq, kSdfOut, kStaticSdf, false>(
+                static_sq, static_sdf, V2, nz, 0, nz, col0, (int)min((long long)nthr, V2 - col0),
                 kSq ? comp_sq + (long long)t * V : nullptr, kSdfOut ? comp_sdf + (long long)t * V : nullptr, vox);
         } else if (live) {
             EnvCursor none(tile, nthr, -1);
@@ -670,6 +672,18 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
     __syncthreads();
     const int ww0 = s_w0, ww1 = s_w1;  // some column is dynamic: ww0 <= zlo, ww1 >= zlo + S
     const bool any_occ = s_occ != 0;
+    // the planes outside the window union are copies of the static block:
+    // 16-byte accesses by all threads first (the CTA's per-column loops below
+    // are what its time depends on)
+    if (vec) {
+        const int nc = (int)min((long long)nthr, V2 - col0);
+        int32_t *osq = kSq ? comp_sq + (long long)t * V : nullptr;
+        float *osdf = kSdfOut ? comp_sdf + (long long)t * V : nullptr;
+        copy_static_planes<kSq, kSdfOut, kStaticSdf, false>(static_sq, static_sdf, V2, nz, 0, ww0, col0, nc, osq,
+                                                            osdf, vox);
+        copy_static_planes<kSq, kSdfOut, kStaticSdf, false>(static_sq, static_sdf, V2, nz, ww1, nz, col0, nc, osq,
+                                                            osdf, vox);
+    }
     if (!live)
         return;  // no block-level synchronisation below
 
@@ -681,14 +695,16 @@ __device__ __forceinline__ void composite_block_short(const int32_t *__restrict_
     EnvCursor O(tile + nthr, nthr, top);
     const bool useO = top >= 0;
     const int sa = zlo, sb = zlo + S;
-    emit_range<false, false, false>(0, ww0, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
+    if (!vec)
+        emit_range<false, false, false>(0, ww0, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
     emit_range<false, true, false>(ww0, sa, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
     if (any_occ)  // skip the occupied slab voxels (set F wrote them)
         emit_range<true, true, false>(sa, sb, O, useO, mk, occ, zlo, nthr, scol, sfcol, V2i, out, nz);
     else
         emit_range<false, true, false>(sa, sb, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
     emit_range<false, true, false>(sb, ww1, O, useO, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
-    emit_range<false, false, false>(ww1, nz, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
+    if (!vec)
+        emit_range<false, false, false>(ww1, nz, O, false, mk, false, zlo, nthr, scol, sfcol, V2i, out, nz);
 }
 
 }  // namespace comp
