@@ -29,7 +29,7 @@
 #include "edt_common.cuh"
 
 #ifndef PCDF_EMIT_CHUNK
-#define PCDF_EMIT_CHUNK 4  // static values loaded ahead per lane in the z loops
+#define PCDF_EMIT_CHUNK 6  // static values loaded ahead per lane in the z loops
 #endif
 
 namespace pcdf {
