@@ -191,21 +191,23 @@ __device__ __forceinline__ void edt_xy_block(const uint32_t *__restrict__ bits, 
     const int e0 = b * L, e1 = min(e0 + L, n);
     const uint32_t vm = nx - 32 * w >= 32 ? 0xffffffffu : (1u << (nx - 32 * w)) - 1u;
     const long long rbase = (long long)z * ny * W + w;  // word of row y: rbase + y * W
+    // warp b is band b and its lanes are the 32 columns, which share each
+    // row's word and carries: lane i loads those of row y0 + i (all loads in
+    // flight at once) and the warp reads them by shuffles
     for (int y0 = e0; y0 < e1; y0 += 32) {
-        const int cnt = min(32, e1 - y0);
+        const int cnt = min(32, e1 - y0);  // warp-uniform
         uint32_t ob = 0;
-        const uint32_t *pb = bits + rbase + (long long)y0 * W;
-        const uint2 *pc = carry + rbase + (long long)y0 * W;
+        uint32_t mi = 0;
+        uint2 ci = make_uint2(0, 0);
+        const long long wi = rbase + (long long)(y0 + c) * W;
+        if (c < cnt && PCDF_IN(wi, (long long)nz * ny * W)) {
+            mi = ld<kCoherent>(bits + wi);
+            ci = ld<kCoherent>(carry + wi);
+        }
 #pragma unroll 8
         for (int i = 0; i < cnt; ++i) {
-            uint32_t m = 0;
-            uint2 cr = make_uint2(0, 0);
-            if (PCDF_IN(rbase + (long long)(y0 + i) * W, (long long)nz * ny * W)) {
-                m = ld<kCoherent>(pb);
-                cr = ld<kCoherent>(pc);
-            }
-            pb += W;
-            pc += W;
+            const uint32_t m = __shfl_sync(0xffffffffu, mi, i);
+            const uint2 cr = make_uint2(__shfl_sync(0xffffffffu, ci.x, i), __shfl_sync(0xffffffffu, ci.y, i));
             const int32_t v = live ? row_value(m, cr, c, x, nx, vm) : kInf32;
             if (PCDF_IN(y0 + i, n))
                 tile[(y0 + i) * kCols + c] = (uint32_t)v;
